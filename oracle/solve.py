@@ -1,0 +1,258 @@
+"""One divide step (RSEP / RNEP / RGNEP) and the recursive drivers (oracle).
+
+One step (Algorithms 4-6): map the region to the unit circle, run IRS
+(Algorithm 3), take the splitter U = GRURV(2, A_p + B_p, A_p, -1, +1), form
+A^ = U^T A U (symmetrised for RSEP), choose k minimising ||E21||_1 / ||A||_1.
+The leading k columns of U span the (right) deflating subspace of the
+eigenvalues outside the unit circle, so A11 = A^(1:k, 1:k) holds the
+eigenvalues outside the circle / right of the line (Sec. 3.1, Sec. 3.2).
+
+Recursive strategy, symmetric (Sec. 3.4): keep an interval [lo, hi] that
+contains the node's eigenvalues (root: Gershgorin), split at a point x and,
+if no split happens but one side is empty, shrink the interval and redraw.
+Readings (paper silent or other sources):
+  * first attempt: x = median(diag A_node) + 0.01 R (2 xi - 1), later attempts
+    x uniform in [c - R/2, c + R/2] (the paper's rule), with c, R the centre
+    and half-width of [lo, hi] and xi a Philox uniform of the node;
+  * line scale s = R (the paper assumes ||A|| = O(1), Sec. 3.3);
+  * the side of an unsplit node is read from the numerical rank of R2 in
+    RURV(A_p): rank 0 means no eigenvalue right of x, rank n none left of it;
+  * a split is accepted when 0 < k < n and e(k) <= split_tol; after max_fail
+    unproductive attempts the solve stops with status NO_SPLIT;
+  * Theorem 2.1 holds with high probability only: when IRS converged and the
+    rank is strictly between 0 and n but e(k) > split_tol, the step redraws V
+    (up to v_draws times) and reuses A_p, B_p before giving up on the shift;
+  * nonsymmetric nodes use real lines only (angle 0 in Sec. 3.3's strategy)
+    on the Gershgorin interval of the real parts, optionally the unit circle
+    at the root; complex pairs end in 2x2 blocks of the leaf solver.
+
+Parity: one step is pinned through its parts (IRS, GRURV, split test); the
+drivers are pinned by prescribed spectra, closed forms and backward error in
+tests/test_oracle_method.py.
+"""
+import numpy as np
+
+from .irs import irs, region_map, norm1, default_tau, REGION_LINE, REGION_UNIT_CIRCLE
+from .rurv import haar, splitter_right, splitter_left, numerical_rank
+from .split import split_test, symmetrise
+from .leaves import jacobi_eig, real_schur
+from .philox import (uniform_scalar, attempt_code, PURPOSE_SHIFT, PURPOSE_HAAR,
+                     PURPOSE_HAAR_LEFT, ROOT_NODE, child_node)
+
+STATUS_OK = 0
+STATUS_NO_CONVERGENCE = 1
+STATUS_NO_SPLIT = 2
+
+
+class StepResult:
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def split_from_irs(A, B, res, res_t, seed, stream, attempt, draw, symmetric):
+    """Splitter, similarity and split test for one Haar draw (Algorithms 4-6)."""
+    n = A.shape[0]
+    V = haar(n, seed, stream, attempt_code(attempt, draw), PURPOSE_HAAR)
+    QR_, R1, R2 = splitter_right(res.Ap, res.Bp, V)
+    rank = numerical_rank(R2)
+    out = dict(QR=QR_, rank=rank, R1=R1, R2=R2, draw=draw)
+    if B is None:
+        Ahat = QR_.T @ A @ QR_
+        if symmetric:
+            Ahat = symmetrise(Ahat)
+        k, e, es = split_test(Ahat, normA=norm1(A))
+        out.update(Ahat=Ahat, Bhat=None, QL=QR_, k=k, e=e, scores=es)
+    else:
+        VL = haar(n, seed, stream, attempt_code(attempt, draw), PURPOSE_HAAR_LEFT)
+        QL, _, _ = splitter_left(res_t.Ap, res_t.Bp, VL)
+        Ahat = QL.T @ A @ QR_
+        Bhat = QL.T @ B @ QR_
+        k, e, es = split_test(Ahat, Bhat, normA=norm1(A), normB=norm1(B))
+        out.update(Ahat=Ahat, Bhat=Bhat, QL=QL, k=k, e=e, scores=es)
+    return out
+
+
+def divide_step(A, B=None, region=(REGION_UNIT_CIRCLE, 0.0, 1.0), seed=0,
+                stream=ROOT_NODE, attempt=0, tau=None, maxit=60,
+                symmetric=False, split_tol=1e-12, record_R=False, v_draws=4):
+    """One step of RSEP (symmetric) / RNEP (B None) / RGNEP (B given)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    kind, c, r = region
+    Am, Bm = region_map(A, B, kind, c, r)
+    res = irs(Am, Bm, tau=tau, maxit=maxit, record_R=record_R)
+    res_t = None
+    if B is not None:
+        B = np.asarray(B, dtype=np.float64)
+        AmT, BmT = region_map(A.T, B.T, kind, c, r)
+        res_t = irs(AmT, BmT, tau=tau, maxit=maxit)
+    out = None
+    for draw in range(v_draws):
+        out = split_from_irs(A, B, res, res_t, seed, stream, attempt, draw, symmetric)
+        k, e = out["k"], out["e"]
+        out["accepted"] = bool(res.converged and (res_t is None or res_t.converged)
+                               and 0 < k < n and e <= split_tol)
+        if out["accepted"] or not res.converged or out["rank"] in (0, n):
+            break
+    out["irs"] = res
+    out["irs_left"] = res_t
+    return StepResult(**out)
+
+
+def gershgorin_interval(A):
+    """[lo, hi] containing the real parts of all eigenvalues (row discs)."""
+    A = np.asarray(A)
+    d = np.diag(A)
+    rad = np.sum(np.abs(A), axis=1) - np.abs(d)
+    return float(np.min(d - rad)), float(np.max(d + rad))
+
+
+def choose_shift(A_node, lo, hi, seed, node, attempt):
+    """(sigma, s) for the node's attempt (reading in the module docstring)."""
+    c = 0.5 * (lo + hi)
+    R = 0.5 * (hi - lo)
+    if R <= 0.0:
+        R = max(abs(c), 1.0) * 1e-3
+    xi = uniform_scalar(seed, PURPOSE_SHIFT, node, attempt)
+    if attempt == 0:
+        sigma = float(np.median(np.diag(A_node))) + 0.01 * R * (2.0 * xi - 1.0)
+    else:
+        sigma = c + R * (xi - 0.5)
+    sigma = min(max(sigma, lo + 1e-3 * R), hi - 1e-3 * R)
+    return sigma, R
+
+
+class SolveInfo:
+    def __init__(self):
+        self.status = STATUS_OK
+        self.nodes = 0
+        self.splits = 0
+        self.iters = []
+        self.depth = 0
+        self.failed_attempts = 0
+
+
+def _recurse(A, seed, leaf_size, tau, maxit, split_tol, max_fail, symmetric,
+             root_unit_circle, info):
+    """Shared recursion; returns (Q, blocks) with A = Q T Q^T block structure."""
+    n = A.shape[0]
+    Q = np.eye(n)
+    leaves = []       # (offset, size, node matrix)
+    lo0, hi0 = gershgorin_interval(A)
+    work = [(0, n, np.array(A, dtype=np.float64), lo0, hi0, ROOT_NODE, 0)]
+    while work:
+        off, m, An, lo, hi, node, depth = work.pop()
+        info.nodes += 1
+        info.depth = max(info.depth, depth)
+        if m <= leaf_size:
+            leaves.append((off, m, An))
+            continue
+        attempt = 0
+        fails = 0
+        done = False
+        while not done:
+            if root_unit_circle and node == ROOT_NODE and attempt == 0:
+                region = (REGION_UNIT_CIRCLE, 0.0, 1.0)
+            else:
+                sigma, s = choose_shift(An, lo, hi, seed, node, attempt)
+                region = (REGION_LINE, sigma, s)
+            st = divide_step(An, None, region, seed, node, attempt, tau, maxit,
+                             symmetric=symmetric, split_tol=split_tol)
+            info.iters.append(st.irs.iters)
+            if st.accepted:
+                k = st.k
+                Q[:, off:off + m] = Q[:, off:off + m] @ st.QR
+                A11 = st.Ahat[:k, :k].copy()
+                A22 = st.Ahat[k:, k:].copy()
+                if region[0] == REGION_LINE:
+                    sig = region[1]
+                    lo1, hi1 = sig, hi
+                    lo2, hi2 = lo, sig
+                else:
+                    lo1, hi1 = gershgorin_interval(A11)
+                    lo2, hi2 = gershgorin_interval(A22)
+                if not symmetric:
+                    g1 = gershgorin_interval(A11)
+                    g2 = gershgorin_interval(A22)
+                    lo1, hi1 = max(lo1, g1[0]), min(hi1, g1[1])
+                    lo2, hi2 = max(lo2, g2[0]), min(hi2, g2[1])
+                    if lo1 >= hi1:
+                        lo1, hi1 = g1
+                    if lo2 >= hi2:
+                        lo2, hi2 = g2
+                info.splits += 1
+                work.append((off + k, m - k, A22, lo2, hi2, child_node(node, 1), depth + 1))
+                work.append((off, k, A11, lo1, hi1, child_node(node, 0), depth + 1))
+                done = True
+                continue
+            info.failed_attempts += 1
+            if region[0] == REGION_LINE and st.irs.converged:
+                if st.rank == 0:
+                    hi = region[1]       # nothing right of the line
+                elif st.rank == m:
+                    lo = region[1]       # nothing left of the line
+                else:
+                    fails += 1
+            else:
+                fails += 1
+            attempt += 1
+            if fails > max_fail or attempt > 250:
+                info.status = STATUS_NO_SPLIT
+                return Q, leaves, False
+    return Q, leaves, True
+
+
+def eig_sym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=1e-12, max_fail=8):
+    """(w ascending, U, info) for symmetric A by RSEP recursion + Jacobi leaves."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    info = SolveInfo()
+    Q, leaves, ok = _recurse(A, seed, leaf_size, tau, maxit, split_tol, max_fail,
+                             True, False, info)
+    w = np.zeros(n)
+    if not ok:
+        return w, Q, info
+    for off, m, An in leaves:
+        wl, Vl = jacobi_eig(An)
+        Q[:, off:off + m] = Q[:, off:off + m] @ Vl
+        w[off:off + m] = wl
+    order = np.argsort(w, kind="stable")
+    return w[order], Q[:, order], info
+
+
+def schur_nonsym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=1e-12,
+                 max_fail=8, root_unit_circle=True):
+    """(T, Q, wr, wi, info): A = Q T Q^T, T quasi-triangular (RNEP + Francis)."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    info = SolveInfo()
+    Q, leaves, ok = _recurse(A, seed, leaf_size, tau, maxit, split_tol, max_fail,
+                             False, root_unit_circle, info)
+    wr = np.zeros(n)
+    wi = np.zeros(n)
+    if not ok:
+        return None, Q, wr, wi, info
+    for off, m, An in leaves:
+        _, Zl, wrl, wil, good = real_schur(An)
+        if not good:
+            info.status = STATUS_NO_CONVERGENCE
+        Q[:, off:off + m] = Q[:, off:off + m] @ Zl
+        wr[off:off + m] = wrl
+        wi[off:off + m] = wil
+    T = Q.T @ A @ Q
+    T = quasi_triangular_part(T, wi)
+    return T, Q, wr, wi, info
+
+
+def quasi_triangular_part(T, wi):
+    """Zero everything below the diagonal except the 2x2 blocks of complex pairs."""
+    n = T.shape[0]
+    out = np.triu(T)
+    i = 0
+    while i < n - 1:
+        if wi[i] != 0.0 and wi[i + 1] == -wi[i]:
+            out[i + 1, i] = T[i + 1, i]
+            i += 2
+        else:
+            i += 1
+    return out

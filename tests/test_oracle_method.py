@@ -1,0 +1,350 @@
+"""Pins for the oracle's IRS, GRURV, leaves and drivers against the mathematics.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a transposed factor, a swapped block) fails at least one test:
+closed forms, identities checked with independent long-double Gaussian
+elimination, prescribed spectra and the experiment facts stated in the paper.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import irs as irs_mod
+from oracle.irs import irs, irs_step, region_map, REGION_LINE, REGION_CIRCLE, REGION_UNIT_CIRCLE
+from oracle.rurv import haar, grurv2, splitter_right, rurv, numerical_rank
+from oracle.leaves import jacobi_eig, real_schur, hessenberg
+from oracle.solve import divide_step, eig_sym, schur_nonsym, STATUS_OK
+from paper_1011_3077_gb300 import workloads
+from tests.pinlib import cholesky_upper, ld_solve, ld_inv, eig2_sym, eig3_sym, subspace_residual
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _paper_facts():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_experiments.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+# ------------------------------------------------------------------- IRS
+
+def test_irs_one_step_diagonal_closed_form():
+    # [B; -A] with diagonal A, B: each column has two entries (b_j, -a_j); the
+    # reflector of column j acts in the plane (j, n+j) only, R = diag(r_j),
+    # r_j = sqrt(a_j^2 + b_j^2), and the complement columns are -(a_j, b_j)/r_j,
+    # so A_1 = -diag(a^2 / r), B_1 = -diag(b^2 / r).
+    a = np.array([0.3, -2.0, 1.5, 0.01, 4.0])
+    b = np.array([1.0, 0.5, -1.5, 2.0, -0.25])
+    r = np.sqrt(a * a + b * b)
+    A1, B1, R0 = irs_step(np.diag(a), np.diag(b))
+    assert np.allclose(R0, np.diag(r), atol=1e-15)
+    assert np.allclose(A1, -np.diag(a * a / r), atol=1e-15)
+    assert np.allclose(B1, -np.diag(b * b / r), atol=1e-15)
+
+
+def test_irs_R_is_cholesky_of_gram():
+    rng = np.random.default_rng(1)
+    n = 12
+    A = rng.standard_normal((n, n))
+    B = rng.standard_normal((n, n))
+    res = irs(A, B, maxit=4, record_R=True)
+    Aj, Bj = A, B
+    for j in range(3):
+        R = cholesky_upper(Aj.T @ Aj + Bj.T @ Bj)
+        assert np.allclose(res.Rs[j], R, atol=1e-12 * np.linalg.norm(R))
+        Aj, Bj, _ = irs_step(Aj, Bj)
+
+
+@pytest.mark.parametrize("n,p", [(3, 1), (6, 2), (8, 3)])
+def test_irs_repeated_squaring_identity(n, p):
+    # A_p^{-1} B_p = (A^{-1} B)^(2^p)  (Sec. 3.2), checked in long double
+    rng = np.random.default_rng(10 * n + p)
+    A = 0.3 * rng.standard_normal((n, n)) + 2 * np.eye(n)
+    B = 0.6 * rng.standard_normal((n, n))
+    M = ld_solve(A, B)
+    for _ in range(p):
+        M = M @ M
+    Aj, Bj = A, B
+    for _ in range(p):
+        Aj, Bj, _ = irs_step(Aj, Bj)
+    got = ld_solve(Aj, Bj)
+    scale = max(1.0, float(np.max(np.abs(M))))
+    assert np.max(np.abs(np.asarray(got - M, dtype=np.float64))) < 1e-12 * scale
+
+
+def test_irs_projector_limit_diagonal():
+    # (A_p + B_p)^{-1} A_p = (I + (A^{-1} B)^(2^p))^{-1}; for A = Q diag(l) Q^T,
+    # B = I this is Q diag(l^(2^p) / (l^(2^p) + 1)) Q^T (Sec. 3.2).
+    rng = np.random.default_rng(4)
+    n = 10
+    lam = np.array([0.5, -0.7, 0.9, -0.3, 1.2, -1.6, 2.0, 0.2, -3.0, 1.1])
+    Q = workloads.random_orthogonal(n, rng)
+    A = (Q * lam) @ Q.T
+    p = 3
+    Aj, Bj = A, np.eye(n)
+    for _ in range(p):
+        Aj, Bj, _ = irs_step(Aj, Bj)
+    P = np.asarray(ld_solve(Aj + Bj, Aj), dtype=np.float64)
+    lp = lam ** (2 ** p)
+    want = (Q * (lp / (lp + 1.0))) @ Q.T
+    assert np.allclose(P, want, atol=1e-12)
+
+
+def test_region_maps_eigenvalues():
+    rng = np.random.default_rng(8)
+    n = 6
+    lam = np.array([-2.0, -0.5, 0.25, 0.75, 1.5, 3.0])
+    Q = workloads.random_orthogonal(n, rng)
+    A = (Q * lam) @ Q.T
+    sigma, s = 0.5, 2.0
+    Am, Bm = region_map(A, None, REGION_LINE, sigma, s)
+    z = np.sort(np.linalg.eigvals(np.asarray(ld_solve(Bm, Am), dtype=np.float64)).real)
+    f = np.sort((lam - sigma + s) / (lam - sigma - s))
+    assert np.allclose(z, f, atol=1e-12)
+    # outside the unit circle <=> right of the line
+    assert np.all((np.abs(f) > 1) == (np.sort(lam)[np.argsort(np.argsort(f))] > sigma)) or True
+    for l in lam:
+        assert (abs((l - sigma + s) / (l - sigma - s)) > 1.0) == (l > sigma)
+    c, r = 0.5, 1.0
+    Am, Bm = region_map(A, None, REGION_CIRCLE, c, r)
+    z = np.sort(np.linalg.eigvals(np.asarray(ld_solve(Bm, Am), dtype=np.float64)).real)
+    assert np.allclose(z, np.sort((lam - c) / r), atol=1e-12)
+
+
+def test_irs_converges_config1_and_stops_by_R_test():
+    A, lam = workloads.symmetric_split(128, seed=3)
+    Am, Bm = region_map(A, None, REGION_LINE, 0.0, 1.0)
+    res = irs(Am, Bm)
+    # |f(lam)| is at least (1.05/0.95) -> log2 of the Moebius distance ~ 8-10 squarings
+    assert res.converged and 6 <= res.iters <= 14
+    assert res.ratios[-1] <= irs_mod.default_tau(128)
+    assert all(r > irs_mod.default_tau(128) for r in res.ratios[:-1])
+
+
+def test_iteration_count_depends_on_distance_not_size():
+    # Sec. 3.3.1, Fig. 1: random normal matrices, split line = imaginary axis;
+    # the number of squarings follows the distance of the nearest eigenvalue to
+    # the line, not n.  Same distance forced for two sizes.
+    counts = []
+    for n, seed in ((60, 1), (200, 2)):
+        rng = np.random.default_rng(seed)
+        npair = n // 2
+        re = rng.uniform(-1.5, 1.5, npair)
+        re[np.argmin(np.abs(re))] = 4e-3
+        re = np.where(np.abs(re) < 4e-3, np.sign(re) * 4e-3 + (re == 0) * 4e-3, re)
+        im = rng.uniform(-1.5, 1.5, npair)
+        D = np.zeros((n, n))
+        for i in range(npair):
+            D[2 * i:2 * i + 2, 2 * i:2 * i + 2] = [[re[i], im[i]], [-im[i], re[i]]]
+        Q = workloads.random_orthogonal(n, rng)
+        A = Q @ D @ Q.T
+        Am, Bm = region_map(A, None, REGION_LINE, 0.0, 1.0)
+        res = irs(Am, Bm)
+        assert res.converged
+        counts.append(res.iters)
+    assert abs(counts[0] - counts[1]) <= 1
+
+
+def test_near_axis_converges_within_paper_bound():
+    facts = _paper_facts()
+    n = int(facts["near_axis_n"])
+    A = workloads.near_axis(n)
+    Am, Bm = region_map(A, None, REGION_LINE, 0.0, 1.0)
+    res = irs(Am, Bm, maxit=int(facts["plot_iterations"]))
+    assert res.converged
+    assert res.iters <= facts["near_axis_max_iterations"] + 1
+
+
+def test_jordan_case_does_not_split():
+    facts = _paper_facts()
+    A = workloads.jordan_hard(int(facts["jordan_n"]))
+    st = divide_step(A, None, (REGION_LINE, 0.0, 1.0), seed=1,
+                     maxit=int(facts["plot_iterations"]))
+    assert not st.accepted
+
+
+# ------------------------------------------------------------------- GRURV
+
+def test_haar_moments():
+    n, draws = 6, 600
+    tr = np.zeros(draws)
+    sq = np.zeros((n, n))
+    for t in range(draws):
+        V = haar(n, seed=77, stream=1000 + t)
+        assert np.allclose(V.T @ V, np.eye(n), atol=1e-14)
+        tr[t] = np.trace(V)
+        sq += V * V
+    sq /= draws
+    # E[V_ij^2] = 1/n; trace of a Haar orthogonal matrix: mean 0, variance 1
+    assert np.max(np.abs(sq - 1.0 / n)) < 0.04
+    assert abs(tr.mean()) < 0.15
+    assert abs(tr.var() - 1.0) < 0.2
+
+
+@pytest.mark.parametrize("m1,m2", [(1, 1), (1, -1), (-1, 1), (-1, -1)])
+def test_grurv_lemma_identity(m1, m2):
+    # M = A1^{m1} A2^{m2} = U_cur R1^{m1} R2^{m2} V (Lemma after Algorithm 2)
+    rng = np.random.default_rng(100 + 10 * m1 + m2)
+    n = 7
+    A1 = rng.standard_normal((n, n)) + 3 * np.eye(n)
+    A2 = rng.standard_normal((n, n)) + 3 * np.eye(n)
+    V = haar(n, seed=5, stream=3)
+    U, R1, R2 = grurv2(A1, A2, m1, m2, V)
+    f1 = A1 if m1 == 1 else ld_inv(A1)
+    f2 = A2 if m2 == 1 else ld_inv(A2)
+    M = np.asarray(np.asarray(f1, dtype=np.longdouble) @ np.asarray(f2, dtype=np.longdouble))
+    g1 = R1 if m1 == 1 else ld_inv(R1)
+    g2 = R2 if m2 == 1 else ld_inv(R2)
+    rhs = U @ np.asarray(np.asarray(g1, np.longdouble) @ np.asarray(g2, np.longdouble)) @ V
+    assert np.allclose(np.asarray(M, np.float64), np.asarray(rhs, np.float64), atol=1e-11)
+    assert np.allclose(U.T @ U, np.eye(n), atol=1e-13)
+    assert np.all(np.tril(R1, -1) == 0) and np.all(np.tril(R2, -1) == 0)
+
+
+def test_splitter_spans_outside_subspace():
+    # nonsymmetric diagonalisable A = S diag(l) S^{-1}: the leading r columns of
+    # U_cur span the right eigenvectors of the |l| > 1 eigenvalues.
+    rng = np.random.default_rng(21)
+    n = 9
+    lam = np.array([2.5, -1.8, 1.3, 0.4, -0.6, 0.1, -0.3, 3.0, 0.7])
+    S = rng.standard_normal((n, n)) + 2 * np.eye(n)
+    A = np.asarray(S @ np.diag(lam) @ ld_inv(S), dtype=np.float64)
+    res = irs(A, None)
+    assert res.converged
+    V = haar(n, seed=9, stream=1)
+    U, R1, R2 = splitter_right(res.Ap, res.Bp, V)
+    out = np.abs(lam) > 1.0
+    r = int(out.sum())
+    assert numerical_rank(R2) == r
+    assert subspace_residual(U[:, :r], S[:, out]) < 1e-10
+    Ahat = U.T @ A @ U
+    assert np.linalg.norm(Ahat[r:, :r]) < 1e-10 * np.linalg.norm(A)
+    assert np.allclose(np.sort(np.abs(np.linalg.eigvals(Ahat[:r, :r]))),
+                       np.sort(np.abs(lam[out])), atol=1e-9)
+
+
+# ------------------------------------------------------------------- leaves
+
+def test_jacobi_closed_forms():
+    w, V = jacobi_eig(np.array([[2.0, 1.0], [1.0, -1.0]]))
+    assert np.allclose(w, eig2_sym(2.0, 1.0, -1.0), atol=1e-15)
+    rng = np.random.default_rng(2)
+    M = rng.standard_normal((3, 3))
+    M = M + M.T
+    w, V = jacobi_eig(M)
+    assert np.allclose(w, eig3_sym(M), atol=1e-13)
+    assert np.allclose(M @ V, V * w, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 5, 33, 64])
+def test_jacobi_prescribed_spectrum(n):
+    A, lam = workloads.symmetric_uniform(n, seed=n)
+    w, V = jacobi_eig(A)
+    assert np.max(np.abs(w - lam)) <= 1e-13
+    assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-13
+    assert np.linalg.norm(A @ V - V * w) <= 1e-13 * max(1.0, np.linalg.norm(A))
+
+
+def test_hessenberg_structure():
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((12, 12))
+    H, Z = hessenberg(A)
+    assert np.all(np.tril(H, -2) == 0.0)
+    assert np.allclose(Z @ H @ Z.T, A, atol=1e-13)
+
+
+def test_real_schur_2x2_closed_forms():
+    # complex pair: eigenvalues 1 +- 2i
+    A = np.array([[1.0, 4.0], [-1.0, 1.0]])
+    T, Z, wr, wi, ok = real_schur(A)
+    assert ok and np.allclose(sorted(wr), [1.0, 1.0]) and np.allclose(sorted(wi), [-2.0, 2.0])
+    assert T[0, 0] == T[1, 1] and T[0, 1] * T[1, 0] < 0
+    assert np.allclose(Z @ T @ Z.T, A, atol=1e-14)
+    # real pair of [[4, 1], [2, 3]]: eigenvalues 5 and 2
+    A = np.array([[4.0, 1.0], [2.0, 3.0]])
+    T, Z, wr, wi, ok = real_schur(A)
+    assert ok and np.allclose(sorted(wr), [2.0, 5.0]) and T[1, 0] == 0.0
+    assert np.allclose(Z @ T @ Z.T, A, atol=1e-14)
+
+
+def test_real_schur_companion_roots():
+    # companion matrix of (x-1)(x-2)(x+3)(x^2+1) -> roots 1, 2, -3, +-i
+    coeffs = np.poly([1.0, 2.0, -3.0, 1j, -1j]).real
+    n = len(coeffs) - 1
+    C = np.zeros((n, n))
+    C[0, :] = -coeffs[1:] / coeffs[0]
+    C[1:, :-1] = np.eye(n - 1)
+    T, Z, wr, wi, ok = real_schur(C)
+    assert ok
+    got = np.sort_complex(wr + 1j * wi)
+    want = np.sort_complex(np.array([1, 2, -3, 1j, -1j]))
+    assert np.allclose(got, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [10, 64])
+def test_real_schur_prescribed_and_backward(n):
+    rng = np.random.default_rng(n)
+    T0, d = workloads.nonsymmetric_triangular(n, rng, offdiag_scale=0.1 / np.sqrt(n))
+    Q = workloads.random_orthogonal(n, rng)
+    A = Q @ T0 @ Q.T
+    T, Z, wr, wi, ok = real_schur(A)
+    assert ok
+    assert np.linalg.norm(Z @ T @ Z.T - A) <= 1e-13 * np.linalg.norm(A)
+    assert np.max(np.abs(Z.T @ Z - np.eye(n))) <= 1e-13
+    assert np.all(np.tril(T, -2) == 0.0)
+    assert np.allclose(np.sort(wr), np.sort(d), atol=1e-10)
+    assert np.all(wi == 0.0)
+
+
+# ------------------------------------------------------------------- drivers
+
+def test_config1_divide_step_splits_at_zero():
+    A, lam = workloads.symmetric_split(256, seed=1)
+    st = divide_step(A, None, (REGION_LINE, 0.0, 1.0), seed=0xE16D0001,
+                     symmetric=True, split_tol=1e-12)
+    assert st.accepted and st.k == 128 and st.e < 1e-12
+    w11 = np.linalg.eigvalsh(st.Ahat[:128, :128])
+    w22 = np.linalg.eigvalsh(st.Ahat[128:, 128:])
+    assert np.allclose(w11, lam[lam > 0], atol=1e-12)
+    assert np.allclose(w22, lam[lam < 0], atol=1e-12)
+    # cluster lemma (Sec. 3.4): ||A21||_2 <= (lmax - lmin) / 2 for any partition
+    for k in (3, 100, 200):
+        assert np.linalg.norm(st.Ahat[k:, :k], 2) <= (lam[-1] - lam[0]) / 2 + 1e-14
+
+
+def test_eig_sym_prescribed_spectrum():
+    n = 150
+    A, lam = workloads.symmetric_uniform(n, seed=9)
+    w, U, info = eig_sym(A, seed=5, leaf_size=40)
+    assert info.status == STATUS_OK and info.splits >= 2
+    nA = np.linalg.norm(A, 2)
+    assert np.max(np.abs(w - lam)) <= 1e-10 * nA
+    assert np.linalg.norm(U.T @ U - np.eye(n), 2) <= 1e-12
+    assert np.linalg.norm(A - (U * w) @ U.T) / np.linalg.norm(A) <= 1e-12
+
+
+def test_schur_nonsym_config2_small():
+    n = 128
+    A, d, T0 = workloads.nonsymmetric_schur(n, seed=4)
+    T, Q, wr, wi, info = schur_nonsym(A, seed=2, leaf_size=32)
+    assert info.status == STATUS_OK and info.splits >= 2
+    assert np.linalg.norm(A - Q @ T @ Q.T) / np.linalg.norm(A) <= 1e-12
+    assert np.linalg.norm(Q.T @ Q - np.eye(n), 2) <= 1e-12
+    assert np.all(np.tril(T, -2) == 0.0)
+    # eigenvalue error within the condition-number bound of T0's eigenvalues
+    wl, VL = np.linalg.eig(T0.T)
+    wr0, VR = np.linalg.eig(T0)
+    kappa = np.zeros(n)
+    for i in range(n):
+        j = int(np.argmin(np.abs(wl - wr0[i])))
+        kappa[i] = np.linalg.norm(VL[:, j]) * np.linalg.norm(VR[:, i]) / abs(VL[:, j] @ VR[:, i])
+    got = np.sort(wr)
+    order = np.argsort(wr0.real)
+    err = np.abs(got - wr0.real[order])
+    assert np.all(err <= 1e-13 * kappa[order] * np.linalg.norm(A, 2) * n + 1e-12)
