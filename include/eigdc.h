@@ -1,0 +1,193 @@
+/*
+ * eigdc.h -- C-ABI of the GB300 inverse-free spectral divide-and-conquer
+ * eigensolver (Ballard, Demmel, Dumitriu, "Minimizing Communication for
+ * Eigenproblems and the Singular Value Decomposition", arXiv 1011.3077).
+ *
+ * Conventions for every entry point
+ *   - Matrices are FP64, column-major, with a leading dimension >= rows.
+ *     Pointers whose name starts with "d" are DEVICE pointers owned by the
+ *     caller (for example from PyTorch); the library never frees them.  A
+ *     row-major PyTorch tensor is passed as its transpose.
+ *   - All work is stream-ordered on the stream given to eig_create.  Calls
+ *     return after the work has completed (they synchronize that stream);
+ *     the info structs are filled on return.
+ *   - Return value: EIG_OK (0); a negative value is a caller or system error
+ *     (arguments are checked before any launch; eig_last_error() gives the
+ *     message); a positive value is a numerical outcome (no convergence, no
+ *     split, ...), in which case the outputs hold the last iterate.
+ *   - Workspace is owned by the handle and grown on demand (cudaMalloc);
+ *     eig_workspace_size reports the requirement in advance.
+ *   - Orientation: after a split, the leading k columns of the splitter span
+ *     the (right) deflating subspace of the eigenvalues of det(A - z B) = 0
+ *     outside the unit circle of the mapped pencil, i.e. outside the circle
+ *     or right of the line of the region (Sec. 3.1 and 3.2).
+ */
+#ifndef EIGDC_H
+#define EIGDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eig_handle_s* eig_handle_t;
+
+/* status codes */
+#define EIG_OK 0
+#define EIG_ERR_ARG (-1)      /* invalid argument (message in eig_last_error) */
+#define EIG_ERR_CUDA (-2)     /* CUDA runtime error */
+#define EIG_ERR_NOMEM (-3)    /* workspace allocation failed */
+#define EIG_NO_CONVERGENCE 1  /* IRS hit maxit (Algorithm 3), or a leaf solver gave up */
+#define EIG_NO_SPLIT 2        /* repeated failure to split a node (Sec. 3.3-3.5) */
+#define EIG_NEAR_SINGULAR_PENCIL 3 /* pencil strategy found no dividing circle (Sec. 3.5) */
+#define EIG_NONFINITE 4       /* NaN/Inf met in an input or an iterate */
+
+/* arithmetic of the contractions */
+#define EIG_FP64 0
+
+/* regions (Sec. 3.1 unit circle; Sec. 3.3 line via the Moebius map
+ * f(z) = (z - sigma + s)/(z - sigma - s); Sec. 3.5 circles |z - c| = r) */
+#define EIG_REGION_UNIT_CIRCLE 0
+#define EIG_REGION_CIRCLE 1   /* c_or_sigma = centre c (real), r_or_s = radius r */
+#define EIG_REGION_LINE 2     /* c_or_sigma = sigma, r_or_s = scale s > 0 */
+
+/* problem kinds for eig_solve */
+#define EIG_KIND_SYM 0        /* RSEP recursion (Algorithm 6, Sec. 3.4) */
+#define EIG_KIND_NONSYM 1     /* RNEP recursion (Algorithm 5, Sec. 3.3) */
+
+typedef struct {
+  int kind;
+  double c_or_sigma;
+  double r_or_s;
+} eig_region_t;
+
+typedef struct {
+  double tau;        /* IRS stopping ratio ||R_j - R_{j-1}||_1 <= tau ||R_{j-1}||_1; <= 0: default */
+  int maxit;         /* IRS runs j = 0..maxit (Algorithm 3, "until j > maxit") */
+  double split_tol;  /* accept a split when ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) <= split_tol */
+  int leaf_size;     /* nodes of at most this size go to the leaf solver (<= 64) */
+  int prec;          /* EIG_FP64 */
+  uint64_t seed;     /* Philox key of every draw of the method */
+  int max_fail;      /* unproductive attempts per node before EIG_NO_SPLIT */
+  int nb;            /* panel width of the blocked QR (0: automatic) */
+  int v_draws;       /* Haar redraws per converged IRS (Theorem 2.1 holds w.h.p.) */
+  int root_unit_circle; /* eig_solve nonsymmetric: split the root on |z| = 1 */
+} eig_params_t;
+
+typedef struct {
+  int iters;            /* p: squarings performed by IRS */
+  double last_ratio;    /* last ||R_j - R_{j-1}||_1 / ||R_{j-1}||_1 */
+  int converged;        /* 1 if the R-test fired */
+  int k;                /* chosen block size (eig_split) */
+  double split_residual;/* ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) at k */
+  int rank;             /* numerical rank of R2 in RURV(A_p) */
+  int draw;             /* Haar draw that was used (0-based) */
+} eig_step_info_t;
+
+typedef struct {
+  int status;
+  int nodes;
+  int splits;
+  int max_depth;
+  int total_iters;      /* squarings summed over all IRS runs */
+  int failed_attempts;
+  int leaves;
+  double flops;         /* algorithmic flops executed (formula counts, see bench) */
+} eig_solve_info_t;
+
+/* Defaults: tau = max(1e-14, 4 sqrt(n) 2^-53) at call time, maxit = 60,
+ * split_tol = 1e-12, leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
+ * v_draws = 4, root_unit_circle = 1. */
+void eig_default_params(eig_params_t* p);
+
+/* Create a handle bound to CUDA device `device` and stream `stream`
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream). */
+int eig_create(eig_handle_t* h, int device, void* stream);
+int eig_destroy(eig_handle_t h);
+/* Message of the last error on this handle (valid until the next call). */
+const char* eig_last_error(eig_handle_t h);
+/* Number of CUDA kernels this library has launched in the process so far
+ * (instrumentation for benchmarks; no device work). */
+unsigned long long eig_kernel_launches(void);
+/* Device workspace (bytes) the handle needs for calls on size n. */
+int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes);
+
+/* --------------------------------------------------------------- the path */
+
+/* Implicit repeated squaring (Algorithm 3) on the region-mapped pencil.
+ * dA (n x n) and dB (n x n, or NULL for B = I) are overwritten with A_p, B_p
+ * of the MAPPED pencil.  With params->tau < 0 the R-test never fires and
+ * exactly maxit+1 squarings run (used to compare iterates).  Returns
+ * EIG_NO_CONVERGENCE if j > maxit without the R-test firing. */
+int eig_divide_step(eig_handle_t h, int n, double* dA, int lda, double* dB, int ldb,
+                    const eig_region_t* region, const eig_params_t* params,
+                    eig_step_info_t* info);
+
+/* R_j of the last squaring of the previous eig_divide_step (upper triangle,
+ * diag >= 0) copied to dR (n x n). */
+int eig_last_R(eig_handle_t h, int n, double* dR, int ldr);
+
+/* Splitter and split test of one divide step (Algorithms 5 and 6, lines 2-3):
+ * Q = GRURV(2, A_p + B_p, A_p, -1, +1) with the Haar draw of (seed, stream,
+ * attempt), A^ = Q^T A Q (symmetrised when symmetric != 0), k minimising
+ * ||E21||_1 / ||A||_1 (Sec. 4.2.1).  dAp, dBp: converged IRS output; dA: the
+ * ORIGINAL matrix, overwritten with A^; dQ (n x n) receives Q.  Redraws V up
+ * to params->v_draws times while the split is rejected and 0 < rank < n.
+ * Returns EIG_NO_SPLIT when no accepted split exists (outputs hold the last
+ * draw). */
+int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int ldp,
+              double* dA, int lda, double* dQ, int ldq, int symmetric,
+              uint64_t stream, int attempt, const eig_params_t* params,
+              eig_step_info_t* info);
+
+/* Full recursive solve (Sec. 3.3 / 3.4 strategies, leaves by cyclic Jacobi or
+ * Hessenberg + Francis double-shift QR).
+ *   EIG_KIND_SYM:    dA symmetric; dwr <- eigenvalues ascending (n); dU <-
+ *                    orthonormal eigenvectors (n x n); dwi unused (may be NULL).
+ *   EIG_KIND_NONSYM: dA <- real Schur form T (quasi-upper-triangular, 2x2
+ *                    blocks standardised), dU <- Schur vectors with
+ *                    A = U T U^T, dwr/dwi <- eigenvalues (block order).
+ * dA is overwritten in both cases. */
+int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
+              double* dwi, double* dU, int ldu, const eig_params_t* params,
+              eig_solve_info_t* info);
+
+/* ------------------------------------------------------ building blocks
+ * The steps of the path, exposed so each can be checked on its own. */
+
+/* Householder QR of dX (m x n, m >= n), R with non-negative diagonal:
+ * dQ (m x n, orthonormal columns) and dR (n x n upper; strictly lower part
+ * zeroed).  dX is not modified.  (Sec. 3 intro; Sec. 4.2.1 explicit Q.) */
+int eig_qr(eig_handle_t h, int m, int n, const double* dX, int ldx, double* dQ,
+           int ldq, double* dR, int ldr);
+
+/* rows x cols N(0,1) matrix from Philox4x32-10 + Box-Muller, counter layout
+ * (pair index, attempt, purpose, stream), key = seed (Algorithm 1, line 1). */
+int eig_gaussian(eig_handle_t h, int rows, int cols, uint64_t seed, int purpose,
+                 uint64_t stream, int attempt, double* dG, int ldg);
+
+/* Haar orthogonal V = Q factor (diag R >= 0) of the Gaussian draw
+ * (Sec. 2, Algorithm 1, lines 1-2). */
+int eig_haar(eig_handle_t h, int n, uint64_t seed, int purpose, uint64_t stream,
+             int attempt, double* dV, int ldv);
+
+/* Split test (Sec. 4.2.1): e(k) = max_{j<k} sum_{i>=k} |A_ij| / normA
+ * (+ the same for dB / normB when dB != NULL) for k = 1..n-1; *k gets the
+ * minimiser (ties: closest to n/2, then smaller k), *e its value.  If
+ * hscores != NULL it receives the n-1 values (host memory). */
+int eig_split_test(eig_handle_t h, int n, const double* dA, int lda, double normA,
+                   const double* dB, int ldb, double normB, int* k, double* e,
+                   double* hscores);
+
+/* C = alpha op(A) op(B) + beta C with op = transpose when ta / tb != 0
+ * (the FP64 contraction every step uses). */
+int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+             const double* dA, int lda, const double* dB, int ldb, double beta,
+             double* dC, int ldc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIGDC_H */

@@ -1,0 +1,1066 @@
+// C-ABI of libeigdc and the host-side drivers of the divide-and-conquer path
+// (Ballard, Demmel, Dumitriu, arXiv 1011.3077):
+//   blocked Householder QR (Sec. 3 intro) -> IRS (Algorithm 3) -> GRURV
+//   splitter (Algorithm 2 with k = 2, exponents (-1, +1)) -> similarity and
+//   split test (Algorithms 5 / 6, Sec. 4.2.1) -> recursion (Sec. 3.3 / 3.4).
+// Every arithmetic step runs in the sm_103a kernels of linalg.cu, misc.cu and
+// leaves.cu; the host only orders launches, reads the convergence ratio once
+// per squaring, the chosen k / rank once per split, and takes the strategy
+// decisions (shift, interval) of the recursion.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/eigdc.h"
+#include "internal.h"
+
+using namespace eigdc;
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void eigdc::note_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int PURPOSE_HAAR = 4;
+constexpr int PURPOSE_SHIFT = 5;
+constexpr uint64_t ROOT_NODE = 1;
+
+}  // namespace
+
+struct eig_handle_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  double* lastR = nullptr;
+  int lastR_n = 0;
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+struct Fail {
+  int code;
+};
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e__ = (call);                                                 \
+    if (e__ != cudaSuccess) {                                                 \
+      h->err = std::string("CUDA error: ") + cudaGetErrorString(e__) + " at " \
+               + __FILE__ + ":" + std::to_string(__LINE__);                   \
+      throw Fail{EIG_ERR_CUDA};                                               \
+    }                                                                         \
+  } while (0)
+
+static size_t round_up(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bump allocator over the handle workspace.  With base == nullptr it only
+// measures, so the same carving code gives the size and the pointers.
+struct Arena {
+  char* base;
+  size_t used = 0;
+  explicit Arena(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += round_up(count * sizeof(T));
+    return p;
+  }
+};
+
+static void ensure_ws(eig_handle_t h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return;
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    h->err = "workspace allocation of " + std::to_string(bytes) + " bytes failed";
+    throw Fail{EIG_ERR_NOMEM};
+  }
+  h->ws_bytes = bytes;
+}
+
+static void* pinned(eig_handle_t h, size_t bytes) {
+  if (bytes > h->pinned_bytes) {
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+    h->pinned_bytes = 0;
+    if (cudaMallocHost(&h->pinned, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->err = "pinned host allocation failed";
+      throw Fail{EIG_ERR_NOMEM};
+    }
+    h->pinned_bytes = bytes;
+  }
+  return h->pinned;
+}
+
+static size_t gemm_partial_doubles(int m, int n, int k) {
+  const int s = gemm_choose_splits(m, n, k);
+  return s > 1 ? (size_t)(s + 1) * m * n : 0;
+}
+
+// Split-K scratch for the square m x m x m products of every node size m <= n
+// (smaller nodes use more K chunks, so the maximum is not at m = n).
+static size_t square_partial_doubles(int n) {
+  size_t best = 1;
+  for (int m = 1; m <= n; ++m) best = std::max(best, gemm_partial_doubles(m, m, m));
+  return best;
+}
+
+// ---------------------------------------------------------------- QR
+struct QRBufs {
+  double* W;   int ldw;    // matrix being factorised (in place)
+  double* V;   int ldv;    // explicit unit-lower-trapezoidal reflectors
+  double* T;   int ldt;    // block T factors, jb x n
+  double* tau;
+  double* Wk;              // jb x cols product of a block reflector
+  double* part;            // split-K partials
+};
+
+constexpr int JB_LD = 32;
+
+static size_t qr_part_doubles(int m, int cols) { return (size_t)17 * JB_LD * std::max(cols, 1) + 0 * m; }
+
+// Blocked right-looking Householder QR of the m x n matrix in q.W.
+static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
+  cudaStream_t s = h->stream;
+  const int jbmax = panel_max_width(m);
+  if (jbmax <= 0) {
+    h->err = "matrix too tall for the on-chip panel factorisation";
+    throw Fail{EIG_ERR_ARG};
+  }
+  for (int j0 = 0; j0 < n; j0 += jbmax) {
+    const int jb = std::min(jbmax, n - j0);
+    double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
+    CK(panel_qr(s, m - j0, jb, q.W + j0 + (size_t)j0 * q.ldw, q.ldw, Vb, q.ldv, q.tau + j0,
+                q.T + (size_t)j0 * q.ldt, q.ldt));
+    const int nc = n - j0 - jb;
+    if (nc > 0) {
+      const int mb = m - j0;
+      double* C = q.W + j0 + (size_t)(j0 + jb) * q.ldw;
+      int sp = gemm_choose_splits(jb, nc, mb);
+      sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
+      if (sp < 0) CK(cudaGetLastError());
+      CK(reduce_trmm(s, jb, nc, q.part, sp, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk));
+      CK(gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw));
+    }
+  }
+  return jbmax;
+}
+
+// Y <- Q Y for the reflectors of an m x nref factorisation (applied last
+// block first).  skip_identity: Y started as [I; 0], so columns left of a
+// block's first row are still unit vectors it does not touch.
+static void apply_q(eig_handle_t h, int m, int nref, int jbmax, QRBufs& q, double* Y, int ldy,
+                    int ncols, bool skip_identity) {
+  cudaStream_t s = h->stream;
+  const int nblocks = (nref + jbmax - 1) / jbmax;
+  for (int b = nblocks - 1; b >= 0; --b) {
+    const int j0 = b * jbmax;
+    const int jb = std::min(jbmax, nref - j0);
+    const int mb = m - j0;
+    const int c0 = skip_identity ? j0 : 0;
+    const int nc = ncols - c0;
+    if (nc <= 0) continue;
+    double* Yb = Y + j0 + (size_t)c0 * ldy;
+    const double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
+    int sp = gemm_choose_splits(jb, nc, mb);
+    sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, Yb, ldy, sp, q.part);
+    if (sp < 0) CK(cudaGetLastError());
+    CK(reduce_trmm(s, jb, nc, q.part, sp, q.T + (size_t)j0 * q.ldt, q.ldt, false, q.Wk));
+    CK(gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy));
+  }
+}
+
+struct QRWork {
+  QRBufs q;
+};
+
+static size_t carve_qr(Arena& a, int m, int n, QRWork& w) {
+  const size_t start = a.used;
+  w.q.W = a.take<double>((size_t)m * n);
+  w.q.ldw = m;
+  w.q.V = a.take<double>((size_t)m * n);
+  w.q.ldv = m;
+  w.q.T = a.take<double>((size_t)JB_LD * n);
+  w.q.ldt = JB_LD;
+  w.q.tau = a.take<double>(n);
+  w.q.Wk = a.take<double>((size_t)JB_LD * n);
+  w.q.part = a.take<double>(qr_part_doubles(m, n));
+  return a.used - start;
+}
+
+// Explicit Q (m x n) and optionally R (n x n) of X (m x n).
+static void qr_explicit(eig_handle_t h, QRWork& w, int m, int n, const double* X, int ldx,
+                        double* Q, int ldq, double* R, int ldr) {
+  cudaStream_t s = h->stream;
+  CK(copy_matrix(s, m, n, X, ldx, w.q.W, w.q.ldw));
+  const int jbmax = geqrf(h, m, n, w.q);
+  if (R) CK(upper_triangle(s, n, w.q.W, w.q.ldw, R, ldr));
+  if (Q) {
+    CK(fill_identity_block(s, m, n, Q, ldq, 0));
+    apply_q(h, m, n, jbmax, w.q, Q, ldq, n, true);
+  }
+}
+
+// ---------------------------------------------------------------- IRS
+struct IRSWork {
+  double *Aj, *Bj, *An, *Bn, *Y, *Rc, *Rp, *gpart;
+  unsigned long long* sums;
+  int* flag;
+  QRWork qr;   // W is the stacked 2n x n matrix
+};
+
+static size_t carve_irs(Arena& a, int n, IRSWork& w) {
+  const size_t start = a.used;
+  const size_t nn = (size_t)n * n;
+  w.Aj = a.take<double>(nn);
+  w.Bj = a.take<double>(nn);
+  w.An = a.take<double>(nn);
+  w.Bn = a.take<double>(nn);
+  w.Y = a.take<double>(2 * nn);
+  w.Rc = a.take<double>(nn);
+  w.Rp = a.take<double>(nn);
+  w.gpart = a.take<double>(square_partial_doubles(n));
+  w.sums = a.take<unsigned long long>(4);
+  w.flag = a.take<int>(4);
+  carve_qr(a, 2 * n, n, w.qr);
+  return a.used - start;
+}
+
+struct IRSOut {
+  int iters;
+  bool converged;
+  double last_ratio;
+  double* Ap;
+  double* Bp;
+  double* Rlast;
+};
+
+static double default_tau(int n) { return std::max(1e-14, 4.0 * std::sqrt((double)n) * 0x1p-53); }
+
+static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int lda, const double* B,
+                      int ldb, const eig_region_t& rg, double tau, int maxit) {
+  cudaStream_t s = h->stream;
+  const size_t nn = (size_t)n * n;
+  QRBufs& q = w.qr.q;
+  q.ldw = 2 * n;   // the stacked matrix of this (node) size, packed
+  q.ldv = 2 * n;
+  CK(region_stack(s, n, A, lda, B, ldb, rg.kind, rg.c_or_sigma, rg.r_or_s, w.Aj, w.Bj, q.W));
+  double* Aj = w.Aj;
+  double* Bj = w.Bj;
+  double* An = w.An;
+  double* Bn = w.Bn;
+  double* Rc = w.Rc;
+  double* Rp = w.Rp;
+  unsigned long long* hsum = static_cast<unsigned long long*>(pinned(h, 64));
+  const int gsplit = gemm_choose_splits(n, n, n);
+  IRSOut out{0, false, 0.0, nullptr, nullptr, nullptr};
+  bool have_prev = false;
+  for (int j = 0;; ++j) {
+    const int jbmax = geqrf(h, 2 * n, n, q);
+    if (have_prev) {
+      CK(cudaMemsetAsync(w.sums, 0, 2 * sizeof(unsigned long long), s));
+      CK(r_extract_diff(s, n, q.W, q.ldw, Rc, Rp, w.sums));
+    } else {
+      CK(r_extract_diff(s, n, q.W, q.ldw, Rc, nullptr, nullptr));
+    }
+    // [Q12; Q22]: the last n columns of the 2n x 2n orthogonal factor
+    CK(fill_identity_block(s, 2 * n, n, w.Y, 2 * n, n));
+    apply_q(h, 2 * n, n, jbmax, q, w.Y, 2 * n, n, false);
+    CK(gemm(s, true, false, n, n, n, 1.0, w.Y, 2 * n, Aj, n, 0.0, An, n, gsplit, w.gpart));
+    CK(gemm(s, true, false, n, n, n, 1.0, w.Y + n, 2 * n, Bj, n, 0.0, Bn, n, gsplit, w.gpart));
+    std::swap(Aj, An);
+    std::swap(Bj, Bn);
+    CK(stack_pencil(s, n, Aj, Bj, q.W));
+    if (have_prev) {
+      CK(cudaMemcpyAsync(hsum, w.sums, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      double num, den;
+      std::memcpy(&num, &hsum[0], 8);
+      std::memcpy(&den, &hsum[1], 8);
+      const double ratio = den > 0.0 ? num / den : (num == 0.0 ? 0.0 : INFINITY);
+      out.last_ratio = ratio;
+      if (ratio <= tau) {
+        out.iters = j + 1;
+        out.converged = true;
+        out.Rlast = Rc;
+        break;
+      }
+    }
+    std::swap(Rc, Rp);
+    have_prev = true;
+    if (j + 1 > maxit) {
+      out.iters = j + 1;
+      out.converged = false;
+      out.Rlast = Rp;
+      break;
+    }
+  }
+  (void)nn;
+  out.Ap = Aj;
+  out.Bp = Bj;
+  return out;
+}
+
+// ---------------------------------------------------------------- split
+struct SplitWork {
+  double *G, *Vh, *X, *U, *R2, *S, *Y, *Z, *Qt, *Ucur, *tmp, *Ahat, *scores, *colpart, *gpart;
+  unsigned long long* nbits;
+  int* rank;
+  QRWork qr;
+};
+
+static size_t carve_split(Arena& a, int n, SplitWork& w) {
+  const size_t start = a.used;
+  const size_t nn = (size_t)n * n;
+  w.G = a.take<double>(nn);
+  w.Vh = a.take<double>(nn);
+  w.X = a.take<double>(nn);
+  w.U = a.take<double>(nn);
+  w.R2 = a.take<double>(nn);
+  w.S = a.take<double>(nn);
+  w.Y = a.take<double>(nn);
+  w.Z = a.take<double>(nn);
+  w.Qt = a.take<double>(nn);
+  w.Ucur = a.take<double>(nn);
+  w.tmp = a.take<double>(nn);
+  w.Ahat = a.take<double>(nn);
+  w.scores = a.take<double>(std::max(n, 1));
+  const size_t nrb = (size_t)(n + 31) / 32;
+  w.colpart = a.take<double>(nrb * n + n + 8);
+  w.gpart = a.take<double>(square_partial_doubles(n));
+  w.nbits = a.take<unsigned long long>(4);
+  w.rank = a.take<int>(4);
+  carve_qr(a, n, n, w.qr);
+  return a.used - start;
+}
+
+// Tie rule (paper silent): smallest e(k); exact ties -> k closest to n/2,
+// then the smaller k.
+static int choose_k(const double* e, int n) {
+  int best = -1;
+  for (int k = 1; k < n; ++k) {
+    if (best < 0) {
+      best = k;
+      continue;
+    }
+    const double v = e[k - 1], bv = e[best - 1];
+    const int d = std::abs(2 * k - n), bd = std::abs(2 * best - n);
+    if (v < bv || (v == bv && (d < bd || (d == bd && k < best)))) best = k;
+  }
+  return best;
+}
+
+struct SplitOut {
+  int k;
+  double e;
+  int rank;
+  int draw;
+  bool accepted;
+};
+
+static double device_norm1(eig_handle_t h, int rows, int cols, const double* A, int lda,
+                           unsigned long long* dbits) {
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(dbits, 0, sizeof(unsigned long long), s));
+  CK(norm1_bits(s, rows, cols, A, lda, dbits));
+  unsigned long long* hb = static_cast<unsigned long long*>(pinned(h, 64));
+  CK(cudaMemcpyAsync(hb, dbits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double v;
+  std::memcpy(&v, hb, 8);
+  return v;
+}
+
+// Splitter Q = GRURV(2, A_p + B_p, A_p, -1, +1), A^ = Q^T A Q, split test.
+// Results stay in w.Ahat / w.Ucur.
+static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
+                          const double* Bp, int ldp, const double* A, int lda, bool symmetric,
+                          uint64_t stream_id, int attempt, const eig_params_t& p,
+                          bool irs_converged, std::vector<double>& hscores) {
+  cudaStream_t s = h->stream;
+  const double normA = device_norm1(h, n, n, A, lda, w.nbits);
+  const int gsplit = gemm_choose_splits(n, n, n);
+  SplitOut out{0, INFINITY, 0, 0, false};
+  const int draws = std::max(1, p.v_draws);
+  hscores.assign(std::max(n - 1, 0), 0.0);
+  for (int draw = 0; draw < draws; ++draw) {
+    const int code = ((attempt & 0x3F) << 2) | (draw & 3);
+    // Haar V (Algorithm 1, lines 1-2)
+    CK(gaussian(s, n, n, p.seed, PURPOSE_HAAR, stream_id, code, w.G, n));
+    qr_explicit(h, w.qr, n, n, w.G, n, w.Vh, n, nullptr, 0);
+    // RURV(A_p): [U, R2] = QR(A_p V^T)
+    CK(gemm(s, false, true, n, n, n, 1.0, Ap, ldp, w.Vh, n, 0.0, w.X, n, gsplit, w.gpart));
+    qr_explicit(h, w.qr, n, n, w.X, n, w.U, n, w.R2, n);
+    CK(count_rank(s, n, w.R2, n, 1e-8, w.rank));
+    // RQ(U^T (A_p + B_p)) by reversal: Z = (J Y)^T = Q~ R~, U_cur = Q~ J
+    CK(add_matrices(s, n, n, Ap, ldp, Bp, ldp, w.S, n));
+    CK(gemm(s, true, false, n, n, n, 1.0, w.U, n, w.S, n, 0.0, w.Y, n, gsplit, w.gpart));
+    CK(reverse_transpose(s, n, w.Y, n, w.Z, n));
+    qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, nullptr, 0);
+    CK(reverse_columns(s, n, n, w.Qt, n, w.Ucur, n));
+    // similarity and split test
+    CK(gemm(s, false, false, n, n, n, 1.0, A, lda, w.Ucur, n, 0.0, w.tmp, n, gsplit, w.gpart));
+    CK(gemm(s, true, false, n, n, n, 1.0, w.Ucur, n, w.tmp, n, 0.0, w.Ahat, n, gsplit, w.gpart));
+    if (symmetric) CK(symmetrize(s, n, w.Ahat, n));
+    if (n >= 2) CK(split_scores(s, n, w.Ahat, n, normA > 0 ? 1.0 / normA : 1.0, w.colpart, w.scores, false));
+    const size_t sbytes = sizeof(double) * std::max(n - 1, 1);
+    char* hb = static_cast<char*>(pinned(h, sbytes + 64));
+    if (n >= 2) CK(cudaMemcpyAsync(hb, w.scores, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hb + sbytes, w.rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (n >= 2) std::memcpy(hscores.data(), hb, sizeof(double) * (n - 1));
+    int rank;
+    std::memcpy(&rank, hb + sbytes, sizeof(int));
+    out.rank = rank;
+    out.draw = draw;
+    if (n >= 2) {
+      out.k = choose_k(hscores.data(), n);
+      out.e = hscores[out.k - 1];
+    } else {
+      out.k = 0;
+      out.e = 0.0;
+    }
+    out.accepted = irs_converged && out.k > 0 && out.k < n && out.e <= p.split_tol;
+    if (out.accepted || !irs_converged || rank == 0 || rank == n) break;
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------- strategy
+static void philox_host(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// u2 of pair 0 of (purpose, stream, attempt): a uniform in [0, 1).
+static double philox_uniform(uint64_t seed, int purpose, uint64_t stream, int attempt) {
+  uint32_t c[4] = {0u, ((uint32_t)(attempt & 0xFF) << 8) | ((uint32_t)(purpose & 0xFFFF) << 16),
+                   (uint32_t)(stream & 0xFFFFFFFFull), (uint32_t)(stream >> 32)};
+  philox_host(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  const uint64_t m2 = ((uint64_t)c[2] << 20) | (c[3] >> 12);
+  return (double)m2 * 0x1p-52;
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood 2014): child ids of the tree.
+static uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static uint64_t child_node(uint64_t parent, int side) {
+  return splitmix64(2 * parent + (uint64_t)side + 1);
+}
+
+struct Node {
+  int off, m;
+  double lo, hi;
+  uint64_t id;
+  int depth;
+};
+
+static void node_diag(eig_handle_t h, const double* Acur, int ld, int off, int m,
+                      std::vector<double>& diag) {
+  diag.resize(m);
+  double* hb = static_cast<double*>(pinned(h, sizeof(double) * (m + 8)));
+  CK(cudaMemcpy2DAsync(hb, sizeof(double), Acur + off + (size_t)off * ld, sizeof(double) * (ld + 1),
+                       sizeof(double), m, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(diag.data(), hb, sizeof(double) * m);
+}
+
+static void gershgorin_interval(eig_handle_t h, const double* A, int ld, int m, double* dtmp,
+                                double& lo, double& hi) {
+  CK(diag_gershgorin(h->stream, m, A, ld, dtmp, dtmp + m));
+  double* hb = static_cast<double*>(pinned(h, sizeof(double) * (2 * m + 8)));
+  CK(cudaMemcpyAsync(hb, dtmp, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  lo = INFINITY;
+  hi = -INFINITY;
+  for (int i = 0; i < m; ++i) {
+    lo = std::min(lo, hb[i] - hb[m + i]);
+    hi = std::max(hi, hb[i] + hb[m + i]);
+  }
+}
+
+static double median_of(std::vector<double> v) {
+  std::sort(v.begin(), v.end());
+  const size_t n = v.size();
+  if (n == 0) return 0.0;
+  if (n & 1) return v[n / 2];
+  return (v[n / 2 - 1] + v[n / 2]) / 2.0;
+}
+
+// Shift of an attempt (first: median of the diagonal plus 1% jitter, later:
+// uniform in the middle half of [lo, hi], Sec. 3.4), scale s = half-width.
+static void choose_shift(const std::vector<double>& diag, double lo, double hi, uint64_t seed,
+                         uint64_t node, int attempt, double& sigma, double& scale) {
+  const double c = 0.5 * (lo + hi);
+  double R = 0.5 * (hi - lo);
+  if (R <= 0.0) R = std::max(std::fabs(c), 1.0) * 1e-3;
+  const double xi = philox_uniform(seed, PURPOSE_SHIFT, node, attempt);
+  if (attempt == 0) sigma = median_of(diag) + 0.01 * R * (2.0 * xi - 1.0);
+  else sigma = c + R * (xi - 0.5);
+  sigma = std::min(std::max(sigma, lo + 1e-3 * R), hi - 1e-3 * R);
+  scale = R;
+}
+
+struct SolveWork {
+  double *Acur, *Unode, *wtmp, *Zleaf, *dtmp, *sortbuf;
+  int* status;
+  LeafDesc* ddesc;
+  IRSWork irs;
+  SplitWork split;
+};
+
+static size_t carve_solve(Arena& a, int n, SolveWork& w) {
+  const size_t start = a.used;
+  const size_t nn = (size_t)n * n;
+  const int maxleaves = n;   // upper bound: every leaf has >= 1 row
+  w.Acur = a.take<double>(nn);
+  w.Unode = a.take<double>(nn);
+  w.wtmp = a.take<double>(2 * (size_t)n + 8);
+  w.Zleaf = a.take<double>((size_t)64 * 64 * std::max(1, std::min(maxleaves, (n + 0) )));
+  w.dtmp = a.take<double>(2 * (size_t)n + 8);
+  w.sortbuf = a.take<double>(nn);
+  w.status = a.take<int>(8);
+  w.ddesc = a.take<LeafDesc>(std::max(1, maxleaves));
+  carve_irs(a, n, w.irs);
+  carve_split(a, n, w.split);
+  return a.used - start;
+}
+
+static double flops_irs_iter(double m) { return 22.0 / 3.0 * m * m * m; }
+static double flops_grurv(double m) { return 12.0 * m * m * m; }
+static double flops_similarity(double m) { return 4.0 * m * m * m; }
+
+__global__ void permute_columns_kernel(int n, const double* __restrict__ U, int ldu,
+                                       const int* __restrict__ perm, double* __restrict__ out,
+                                       int ldo) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * n) return;
+  const int i = (int)(idx % n), j = (int)(idx / n);
+  out[i + (size_t)j * ldo] = U[i + (size_t)perm[j] * ldu];
+}
+
+static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
+                      double* dwi, double* dU, int ldu, const eig_params_t& p,
+                      eig_solve_info_t* info) {
+  cudaStream_t s = h->stream;
+  const bool sym = (kind == EIG_KIND_SYM);
+  const int leaf = std::max(1, std::min(64, p.leaf_size));
+  const char* venv = std::getenv("EIGDC_VERBOSE");
+  const bool verbose = venv && venv[0] == '1';
+  Arena meas(nullptr);
+  SolveWork w;
+  const size_t need = carve_solve(meas, n, w);
+  ensure_ws(h, need);
+  Arena arena(h->ws);
+  carve_solve(arena, n, w);
+  eig_solve_info_t inf;
+  std::memset(&inf, 0, sizeof(inf));
+  // working copy of A; global U = I
+  CK(copy_matrix(s, n, n, dA, lda, w.Acur, n));
+  CK(fill_identity_block(s, n, n, dU, ldu, 0));
+  CK(cudaMemsetAsync(w.status, 0, 8 * sizeof(int), s));
+  CK(nonfinite_check(s, n, n, dA, lda, w.status + 2));
+  {
+    int* hf = static_cast<int*>(pinned(h, 64));
+    CK(cudaMemcpyAsync(hf, w.status + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*hf) {
+      h->err = "input contains NaN or Inf";
+      inf.status = EIG_NONFINITE;
+      if (info) *info = inf;
+      return EIG_NONFINITE;
+    }
+  }
+  double lo0, hi0;
+  gershgorin_interval(h, w.Acur, n, n, w.dtmp, lo0, hi0);
+  std::vector<Node> stack{Node{0, n, lo0, hi0, ROOT_NODE, 0}};
+  std::vector<LeafDesc> leaves;
+  std::vector<double> diag, hscores;
+  const double tau = p.tau > 0 ? p.tau : -1.0;
+  const int gsplit_max = 1;
+  (void)gsplit_max;
+  int status = EIG_OK;
+  while (!stack.empty() && status == EIG_OK) {
+    Node nd = stack.back();
+    stack.pop_back();
+    inf.nodes++;
+    inf.max_depth = std::max(inf.max_depth, nd.depth);
+    const int m = nd.m;
+    double* An = w.Acur + nd.off + (size_t)nd.off * n;
+    if (m <= leaf) {
+      leaves.push_back(LeafDesc{nd.off, m, (int)leaves.size() * 64 * 64});
+      continue;
+    }
+    int attempt = 0, fails = 0;
+    bool done = false;
+    while (!done) {
+      eig_region_t rg;
+      if (!sym && p.root_unit_circle && nd.id == ROOT_NODE && attempt == 0) {
+        rg.kind = EIG_REGION_UNIT_CIRCLE;
+        rg.c_or_sigma = 0.0;
+        rg.r_or_s = 1.0;
+      } else {
+        node_diag(h, w.Acur, n, nd.off, m, diag);
+        double sigma, sc;
+        choose_shift(diag, nd.lo, nd.hi, p.seed, nd.id, attempt, sigma, sc);
+        rg.kind = EIG_REGION_LINE;
+        rg.c_or_sigma = sigma;
+        rg.r_or_s = sc;
+      }
+      const double tau_m = tau > 0 ? tau : default_tau(m);
+      IRSOut ir = run_irs(h, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit);
+      inf.total_iters += ir.iters;
+      inf.flops += ir.iters * flops_irs_iter(m);
+      SplitOut so = run_split(h, w.split, m, ir.Ap, ir.Bp, m, An, n, sym, nd.id, attempt, p,
+                              ir.converged, hscores);
+      inf.flops += (so.draw + 1) * (flops_grurv(m) + flops_similarity(m));
+      if (verbose)
+        std::fprintf(stderr,
+                     "[eigdc] node off=%d m=%d depth=%d attempt=%d region=%d (%.6g, %.6g) "
+                     "iters=%d conv=%d ratio=%.3g k=%d e=%.3g rank=%d draw=%d accepted=%d\n",
+                     nd.off, m, nd.depth, attempt, rg.kind, rg.c_or_sigma, rg.r_or_s, ir.iters,
+                     (int)ir.converged, ir.last_ratio, so.k, so.e, so.rank, so.draw,
+                     (int)so.accepted);
+      if (so.accepted) {
+        const int k = so.k;
+        // U[:, off:off+m] <- U[:, off:off+m] Q ; node block <- A^
+        CK(gemm(s, false, false, n, m, m, 1.0, dU + (size_t)nd.off * ldu, ldu, w.split.Ucur, m,
+                0.0, w.Unode, n));
+        CK(copy_matrix(s, n, m, w.Unode, n, dU + (size_t)nd.off * ldu, ldu));
+        inf.flops += 2.0 * n * (double)m * m;
+        CK(copy_matrix(s, m, m, w.split.Ahat, m, An, n));
+        double lo1, hi1, lo2, hi2;
+        double* A11 = An;
+        double* A22 = An + k + (size_t)k * n;
+        if (rg.kind == EIG_REGION_LINE) {
+          lo1 = rg.c_or_sigma;
+          hi1 = nd.hi;
+          lo2 = nd.lo;
+          hi2 = rg.c_or_sigma;
+        } else {
+          gershgorin_interval(h, A11, n, k, w.dtmp, lo1, hi1);
+          gershgorin_interval(h, A22, n, m - k, w.dtmp, lo2, hi2);
+        }
+        if (!sym) {
+          double g1l, g1h, g2l, g2h;
+          gershgorin_interval(h, A11, n, k, w.dtmp, g1l, g1h);
+          gershgorin_interval(h, A22, n, m - k, w.dtmp, g2l, g2h);
+          lo1 = std::max(lo1, g1l);
+          hi1 = std::min(hi1, g1h);
+          lo2 = std::max(lo2, g2l);
+          hi2 = std::min(hi2, g2h);
+          if (lo1 >= hi1) { lo1 = g1l; hi1 = g1h; }
+          if (lo2 >= hi2) { lo2 = g2l; hi2 = g2h; }
+        }
+        inf.splits++;
+        stack.push_back(Node{nd.off + k, m - k, lo2, hi2, child_node(nd.id, 1), nd.depth + 1});
+        stack.push_back(Node{nd.off, k, lo1, hi1, child_node(nd.id, 0), nd.depth + 1});
+        done = true;
+        continue;
+      }
+      inf.failed_attempts++;
+      if (rg.kind == EIG_REGION_LINE && ir.converged) {
+        if (so.rank == 0) nd.hi = rg.c_or_sigma;
+        else if (so.rank == m) nd.lo = rg.c_or_sigma;
+        else fails++;
+      } else {
+        fails++;
+      }
+      attempt++;
+      if (fails > p.max_fail || attempt > 250) {
+        status = EIG_NO_SPLIT;
+        h->err = "no split found for a node of size " + std::to_string(m);
+        break;
+      }
+    }
+  }
+  if (status == EIG_OK) {
+    inf.leaves = (int)leaves.size();
+    CK(cudaMemcpyAsync(w.ddesc, leaves.data(), sizeof(LeafDesc) * leaves.size(),
+                       cudaMemcpyHostToDevice, s));
+    if (sym) {
+      CK(jacobi_leaves(s, (int)leaves.size(), w.ddesc, w.Acur, n, w.wtmp, w.Zleaf, w.status));
+    } else {
+      CK(francis_leaves(s, (int)leaves.size(), w.ddesc, w.Acur, n, dwr, dwi, w.Zleaf, w.status));
+    }
+    CK(apply_leaf_vectors(s, (int)leaves.size(), w.ddesc, n, dU, ldu, dU, ldu, w.Zleaf));
+    int* hs = static_cast<int*>(pinned(h, 64));
+    CK(cudaMemcpyAsync(hs, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs[0]) {
+      status = EIG_NO_CONVERGENCE;
+      h->err = "a leaf solver did not converge";
+    }
+    if (sym) {
+      // eigenvalues ascending with their vectors
+      std::vector<double> wv(n);
+      double* hb = static_cast<double*>(pinned(h, sizeof(double) * (n + 8)));
+      CK(cudaMemcpyAsync(hb, w.wtmp, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::memcpy(wv.data(), hb, sizeof(double) * n);
+      std::vector<int> perm(n);
+      for (int i = 0; i < n; ++i) perm[i] = i;
+      std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return wv[a] < wv[b]; });
+      std::vector<double> ws(n);
+      for (int i = 0; i < n; ++i) ws[i] = wv[perm[i]];
+      int* dperm = reinterpret_cast<int*>(w.dtmp);
+      CK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(dwr, ws.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      const size_t t = (size_t)n * n;
+      if (t) {
+        note_launches(1);
+        permute_columns_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(n, dU, ldu, dperm, w.sortbuf, n);
+        CK(cudaGetLastError());
+      }
+      CK(copy_matrix(s, n, n, w.sortbuf, n, dU, ldu));
+      CK(copy_matrix(s, n, n, w.Acur, n, dA, lda));
+      CK(cudaStreamSynchronize(s));
+    } else {
+      // T = U^T A U with the quasi-triangular pattern of the leaves
+      const int gs = gemm_choose_splits(n, n, n);
+      CK(gemm(s, false, false, n, n, n, 1.0, dA, lda, dU, ldu, 0.0, w.Unode, n, gs, w.irs.gpart));
+      CK(gemm(s, true, false, n, n, n, 1.0, dU, ldu, w.Unode, n, 0.0, w.sortbuf, n, gs, w.irs.gpart));
+      inf.flops += 4.0 * (double)n * n * n;
+      CK(zero_lower_quasi(s, n, w.sortbuf, n, dwi));
+      CK(copy_matrix(s, n, n, w.sortbuf, n, dA, lda));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  inf.status = status;
+  if (info) *info = inf;
+  return status;
+}
+
+static void check_params(eig_handle_t h, const eig_params_t& p) {
+  if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0) {
+    h->err = "invalid eig_params_t";
+    throw Fail{EIG_ERR_ARG};
+  }
+}
+
+static eig_params_t params_or_default(const eig_params_t* p) {
+  eig_params_t q;
+  eig_default_params(&q);
+  return p ? *p : q;
+}
+
+}  // namespace
+
+// =================================================================== C-ABI
+extern "C" {
+
+void eig_default_params(eig_params_t* p) {
+  if (!p) return;
+  p->tau = 0.0;
+  p->maxit = 60;
+  p->split_tol = 1e-12;
+  p->leaf_size = 64;
+  p->prec = EIG_FP64;
+  p->seed = 0;
+  p->max_fail = 8;
+  p->nb = 0;
+  p->v_draws = 4;
+  p->root_unit_circle = 1;
+}
+
+int eig_create(eig_handle_t* out, int device, void* stream) {
+  if (!out) return EIG_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return EIG_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return EIG_ERR_CUDA;
+  eig_handle_t h = new eig_handle_s();
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(stream);
+  panel_init();
+  *out = h;
+  return EIG_OK;
+}
+
+int eig_destroy(eig_handle_t h) {
+  if (!h) return EIG_ERR_ARG;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->lastR) cudaFree(h->lastR);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  delete h;
+  return EIG_OK;
+}
+
+const char* eig_last_error(eig_handle_t h) { return h ? h->err.c_str() : "null handle"; }
+
+unsigned long long eig_kernel_launches(void) { return g_launches.load(); }
+
+int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
+  if (!h || !bytes || n < 0) return EIG_ERR_ARG;
+  (void)kind;
+  Arena a(nullptr);
+  SolveWork w;
+  *bytes = carve_solve(a, n, w);
+  return EIG_OK;
+}
+
+#define API_BEGIN                   \
+  if (!h) return EIG_ERR_ARG;       \
+  h->err.clear();                   \
+  try {                             \
+    if (cudaSetDevice(h->device) != cudaSuccess) { h->err = "cudaSetDevice failed"; return EIG_ERR_CUDA; }
+#define API_END                     \
+  }                                 \
+  catch (Fail f) {                  \
+    return f.code;                  \
+  }
+
+#define REQUIRE(cond, msg)          \
+  do {                              \
+    if (!(cond)) {                  \
+      h->err = msg;                 \
+      return EIG_ERR_ARG;           \
+    }                               \
+  } while (0)
+
+int eig_divide_step(eig_handle_t h, int n, double* dA, int lda, double* dB, int ldb,
+                    const eig_region_t* region, const eig_params_t* params,
+                    eig_step_info_t* info) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dA && lda >= n, "dA / lda invalid");
+  REQUIRE(!dB || ldb >= n, "ldb invalid");
+  REQUIRE(region, "region is NULL");
+  REQUIRE(region->kind >= 0 && region->kind <= 2, "unknown region kind");
+  REQUIRE(region->kind != EIG_REGION_LINE || region->r_or_s > 0, "line scale must be > 0");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  Arena meas(nullptr);
+  IRSWork w;
+  ensure_ws(h, carve_irs(meas, n, w));
+  Arena a(h->ws);
+  carve_irs(a, n, w);
+  const double tau = p.tau > 0 ? p.tau : (p.tau < 0 ? -1.0 : default_tau(n));
+  IRSOut o = run_irs(h, w, n, dA, lda, dB, ldb, *region, tau, p.maxit);
+  cudaStream_t s = h->stream;
+  CK(copy_matrix(s, n, n, o.Ap, n, dA, lda));
+  if (dB) CK(copy_matrix(s, n, n, o.Bp, n, dB, ldb));
+  if (h->lastR_n < n) {
+    if (h->lastR) cudaFree(h->lastR);
+    h->lastR = nullptr;
+    if (cudaMalloc(&h->lastR, sizeof(double) * (size_t)n * n) != cudaSuccess) {
+      cudaGetLastError();
+      h->lastR_n = 0;
+      h->err = "allocation for R failed";
+      return EIG_ERR_NOMEM;
+    }
+    h->lastR_n = n;
+  }
+  CK(copy_matrix(s, n, n, o.Rlast, n, h->lastR, n));
+  CK(cudaMemsetAsync(w.flag, 0, sizeof(int), s));
+  CK(nonfinite_check(s, n, n, o.Ap, n, w.flag));
+  CK(nonfinite_check(s, n, n, o.Bp, n, w.flag));
+  int* hf = static_cast<int*>(pinned(h, 64));
+  CK(cudaMemcpyAsync(hf, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = o.iters;
+    info->last_ratio = o.last_ratio;
+    info->converged = o.converged ? 1 : 0;
+  }
+  if (*hf) {
+    h->err = "non-finite iterate";
+    return EIG_NONFINITE;
+  }
+  if (!o.converged) {
+    h->err = "IRS did not converge within maxit";
+    return EIG_NO_CONVERGENCE;
+  }
+  return EIG_OK;
+  API_END
+}
+
+int eig_last_R(eig_handle_t h, int n, double* dR, int ldr) {
+  API_BEGIN
+  REQUIRE(dR && ldr >= n && n >= 1, "dR / ldr invalid");
+  REQUIRE(h->lastR && h->lastR_n >= n, "no R of this size recorded");
+  CK(copy_matrix(h->stream, n, n, h->lastR, n, dR, ldr));
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int ldp, double* dA,
+              int lda, double* dQ, int ldq, int symmetric, uint64_t stream, int attempt,
+              const eig_params_t* params, eig_step_info_t* info) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dAp && dBp && ldp >= n, "dAp / dBp / ldp invalid");
+  REQUIRE(dA && lda >= n, "dA / lda invalid");
+  REQUIRE(dQ && ldq >= n, "dQ / ldq invalid");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  Arena meas(nullptr);
+  SplitWork w;
+  ensure_ws(h, carve_split(meas, n, w));
+  Arena a(h->ws);
+  carve_split(a, n, w);
+  std::vector<double> hs;
+  SplitOut so = run_split(h, w, n, dAp, dBp, ldp, dA, lda, symmetric != 0, stream, attempt, p,
+                          true, hs);
+  cudaStream_t s = h->stream;
+  CK(copy_matrix(s, n, n, w.Ahat, n, dA, lda));
+  CK(copy_matrix(s, n, n, w.Ucur, n, dQ, ldq));
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->k = so.k;
+    info->split_residual = so.e;
+    info->rank = so.rank;
+    info->draw = so.draw;
+    info->converged = 1;
+  }
+  if (!so.accepted) {
+    h->err = "no acceptable split";
+    return EIG_NO_SPLIT;
+  }
+  return EIG_OK;
+  API_END
+}
+
+int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr, double* dwi,
+              double* dU, int ldu, const eig_params_t* params, eig_solve_info_t* info) {
+  API_BEGIN
+  REQUIRE(kind == EIG_KIND_SYM || kind == EIG_KIND_NONSYM, "unknown kind");
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dA && lda >= n, "dA / lda invalid");
+  REQUIRE(dwr, "dwr is NULL");
+  REQUIRE(kind == EIG_KIND_SYM || dwi, "dwi is NULL");
+  REQUIRE(dU && ldu >= n, "dU / ldu invalid");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  return solve_impl(h, kind, n, dA, lda, dwr, dwi, dU, ldu, p, info);
+  API_END
+}
+
+int eig_qr(eig_handle_t h, int m, int n, const double* dX, int ldx, double* dQ, int ldq,
+           double* dR, int ldr) {
+  API_BEGIN
+  REQUIRE(m >= n && n >= 1, "need m >= n >= 1");
+  REQUIRE(dX && ldx >= m, "dX / ldx invalid");
+  REQUIRE(!dQ || ldq >= m, "ldq invalid");
+  REQUIRE(!dR || ldr >= n, "ldr invalid");
+  Arena meas(nullptr);
+  QRWork w;
+  ensure_ws(h, carve_qr(meas, m, n, w));
+  Arena a(h->ws);
+  carve_qr(a, m, n, w);
+  qr_explicit(h, w, m, n, dX, ldx, dQ, ldq, dR, ldr);
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_gaussian(eig_handle_t h, int rows, int cols, uint64_t seed, int purpose, uint64_t stream,
+                 int attempt, double* dG, int ldg) {
+  API_BEGIN
+  REQUIRE(rows >= 0 && cols >= 0 && dG && ldg >= std::max(rows, 1), "invalid arguments");
+  CK(gaussian(h->stream, rows, cols, seed, purpose, stream, attempt, dG, ldg));
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_haar(eig_handle_t h, int n, uint64_t seed, int purpose, uint64_t stream, int attempt,
+             double* dV, int ldv) {
+  API_BEGIN
+  REQUIRE(n >= 1 && dV && ldv >= n, "invalid arguments");
+  Arena meas(nullptr);
+  QRWork w;
+  size_t need = carve_qr(meas, n, n, w) + round_up(sizeof(double) * (size_t)n * n);
+  ensure_ws(h, need);
+  Arena a(h->ws);
+  double* G = a.take<double>((size_t)n * n);
+  carve_qr(a, n, n, w);
+  CK(gaussian(h->stream, n, n, seed, purpose, stream, attempt, G, n));
+  qr_explicit(h, w, n, n, G, n, dV, ldv, nullptr, 0);
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_split_test(eig_handle_t h, int n, const double* dA, int lda, double normA, const double* dB,
+                   int ldb, double normB, int* k, double* e, double* hscores) {
+  API_BEGIN
+  REQUIRE(n >= 2 && dA && lda >= n && k && e, "invalid arguments");
+  REQUIRE(!dB || ldb >= n, "ldb invalid");
+  REQUIRE(normA > 0 && (!dB || normB > 0), "norms must be > 0");
+  Arena meas(nullptr);
+  const size_t nrb = (size_t)(n + 31) / 32;
+  meas.take<double>(n);
+  meas.take<double>(nrb * n + n + 8);
+  ensure_ws(h, meas.used);
+  Arena a(h->ws);
+  double* sc = a.take<double>(n);
+  double* colpart = a.take<double>(nrb * n + n + 8);
+  cudaStream_t s = h->stream;
+  CK(split_scores(s, n, dA, lda, 1.0 / normA, colpart, sc, false));
+  if (dB) CK(split_scores(s, n, dB, ldb, 1.0 / normB, colpart, sc, true));
+  std::vector<double> hv(n - 1);
+  CK(cudaMemcpyAsync(hv.data(), sc, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *k = choose_k(hv.data(), n);
+  *e = hv[*k - 1];
+  if (hscores) std::memcpy(hscores, hv.data(), sizeof(double) * (n - 1));
+  return EIG_OK;
+  API_END
+}
+
+int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha, const double* dA,
+             int lda, const double* dB, int ldb, double beta, double* dC, int ldc) {
+  API_BEGIN
+  REQUIRE(m >= 0 && n >= 0 && k >= 0 && dC && ldc >= std::max(m, 1), "invalid arguments");
+  const int sp = gemm_choose_splits(m, n, k);
+  size_t need = sp > 1 ? sizeof(double) * (size_t)sp * m * n : 256;
+  ensure_ws(h, need);
+  CK(gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, sp,
+          reinterpret_cast<double*>(h->ws)));
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal declarations shared by the translation units of libeigdc.
+// Host-side launchers for the sm_103a kernels; every launcher enqueues on the
+// given stream and returns a cudaError_t from the launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eigdc {
+
+// Running count of kernel launches made by this library (all launchers add
+// to it); read through eig_kernel_launches().
+void note_launches(unsigned long long k);
+
+// ------------------------------------------------------------- linalg.cu
+// C = alpha op(A) op(B) + beta C, column-major FP64.  When splits > 1 the K
+// range is cut into `splits` chunks written to `partial` (splits*m*n doubles)
+// and reduced in a fixed order (deterministic).
+cudaError_t gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                 const double* A, int lda, const double* B, int ldb, double beta,
+                 double* C, int ldc, int splits = 1, double* partial = nullptr);
+int gemm_choose_splits(int m, int n, int k);
+// op(A) B (ta selects op) written as `splits` K-chunk partials in the layout
+// partial[z][i + j*m] (ld = m, even for one split); returns the number of
+// chunks actually used, or -1 on a launch error.
+int gemm_partials(cudaStream_t s, bool ta, int m, int n, int k, const double* A, int lda,
+                  const double* B, int ldb, int splits, double* partial);
+
+// Householder panel factorisation of the m x jb panel P (ldp) on a thread-block
+// cluster.  In place: R on and above the diagonal, Householder vectors below.
+// Writes the explicit unit-lower-trapezoidal V (ldv), tau[jb] and the jb x jb
+// upper-triangular T (ldt) of the compact WY form H_0..H_{jb-1} = I - V T V^T.
+cudaError_t panel_qr(cudaStream_t s, int m, int jb, double* P, int ldp, double* V,
+                     int ldv, double* tau, double* T, int ldt);
+int panel_max_width(int m);
+void panel_init();   // once per device: picks the largest usable cluster size
+
+// Out = op(T) * (sum_z partial[z]) for a jb x n block (op = T^T if trans).
+// With splits == 1 `partial` is read directly.
+cudaError_t reduce_trmm(cudaStream_t s, int jb, int n, const double* partial, int splits,
+                        const double* T, int ldt, bool trans, double* out);
+
+// ------------------------------------------------------------- misc.cu
+cudaError_t fill_identity_block(cudaStream_t s, int rows, int cols, double* Y, int ldy,
+                                int diag_row_offset);
+cudaError_t region_stack(cudaStream_t s, int n, const double* A, int lda, const double* B,
+                         int ldb, int kind, double c_or_sigma, double r_or_s, double* Aj,
+                         double* Bj, double* W);
+cudaError_t stack_pencil(cudaStream_t s, int n, const double* Aj, const double* Bj, double* W);
+// R (upper part of W's top n x n) -> Rcur; accumulates max column sums of
+// |Rcur - Rprev| and |Rprev| into sums[0], sums[1] (as ordered bit patterns).
+cudaError_t r_extract_diff(cudaStream_t s, int n, const double* W, int ldw, double* Rcur,
+                           const double* Rprev, unsigned long long* sums);
+cudaError_t copy_matrix(cudaStream_t s, int rows, int cols, const double* A, int lda, double* B,
+                        int ldb);
+cudaError_t add_matrices(cudaStream_t s, int rows, int cols, const double* A, int lda,
+                         const double* B, int ldb, double* C, int ldc);
+// Z[i][k] = Y[n-1-k][i]   (Z = (J Y)^T)
+cudaError_t reverse_transpose(cudaStream_t s, int n, const double* Y, int ldy, double* Z, int ldz);
+// B[:, j] = A[:, n-1-j]
+cudaError_t reverse_columns(cudaStream_t s, int rows, int n, const double* A, int lda, double* B,
+                            int ldb);
+cudaError_t symmetrize(cudaStream_t s, int n, double* A, int lda);
+cudaError_t upper_triangle(cudaStream_t s, int n, const double* W, int ldw, double* R, int ldr);
+cudaError_t gaussian(cudaStream_t s, int rows, int cols, uint64_t seed, int purpose,
+                     uint64_t stream, int attempt, double* G, int ldg);
+// column sums of |A| max -> bits in out (atomic max), for ||A||_1
+cudaError_t norm1_bits(cudaStream_t s, int rows, int cols, const double* A, int lda,
+                       unsigned long long* out);
+// nonfinite flag (1 if any NaN/Inf) ORed into *flag
+cudaError_t nonfinite_check(cudaStream_t s, int rows, int cols, const double* A, int lda,
+                            int* flag);
+// split test scores e(k) (k = 1..n-1) -> scores[k-1] (accumulates += f(k)/norm)
+cudaError_t split_scores(cudaStream_t s, int n, const double* A, int lda, double inv_norm,
+                         double* colpart, double* scores, bool accumulate);
+cudaError_t diag_gershgorin(cudaStream_t s, int n, const double* A, int lda, double* diag,
+                            double* lo_hi);
+cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, double rel_tol,
+                       int* rank);
+cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const double* wi);
+
+// ------------------------------------------------------------- leaves.cu
+// Batched leaves: leaf i is the m_i x m_i block at A + off_i*(lda+1) of the
+// global matrix; eigenvectors / Schur vectors go to Z + zoff_i (ldz = 64).
+struct LeafDesc {
+  int off;      // row/col offset of the leaf in the global matrix
+  int m;        // size (<= 64)
+  int zoff;     // offset of its 64x64 Z slot in the Z buffer (doubles)
+};
+cudaError_t jacobi_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                          int lda, double* w, double* Z, int* status);
+cudaError_t francis_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                           int lda, double* wr, double* wi, double* Z, int* status);
+// U[:, off:off+m] = U[:, off:off+m] * Z_i for each leaf (batched, U is n x n)
+cudaError_t apply_leaf_vectors(cudaStream_t s, int count, const LeafDesc* d_desc, int n,
+                               const double* Uin, int ldu_in, double* Uout, int ldu_out,
+                               const double* Z);
+
+}  // namespace eigdc

@@ -1,0 +1,480 @@
+// Leaf solvers of the recursion ("the standard algorithm" for small
+// subproblems, Sec. 3.6): one CTA per leaf of size <= 64, the whole leaf and
+// its vectors resident in shared memory.
+//   * symmetric leaves: Jacobi with the parallel (round-robin) ordering, the
+//     m/2 rotations of a round act on disjoint index pairs and are applied
+//     together; sweeps until off(A) <= m u ||A||_F (u = 2^-53);
+//   * nonsymmetric leaves: Householder Hessenberg reduction, then Francis
+//     implicit double-shift QR steps with deflation on
+//     |h_{i+1,i}| <= u (|h_ii| + |h_{i+1,i+1}|) and standardised 2x2 blocks
+//     (Golub and Van Loan, Matrix Computations, Ch. 7-8).
+// The control decisions (deflation, shifts) are taken by thread 0 and
+// broadcast through shared memory; the row / column updates are spread over
+// the threads.  Every loop has a fixed iteration budget.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+
+namespace eigdc {
+
+constexpr int LMAX = 64;
+constexpr double U_ROUND = 1.1102230246251565e-16;   // 2^-53
+
+// ---------------------------------------------------------------- Jacobi
+__device__ __forceinline__ void sym_schur2(double app, double aqq, double apq, double& c,
+                                           double& s) {
+  if (apq == 0.0) {
+    c = 1.0;
+    s = 0.0;
+    return;
+  }
+  const double tau = (aqq - app) / (2.0 * apq);
+  double t;
+  if (tau >= 0.0) t = 1.0 / (tau + sqrt(1.0 + tau * tau));
+  else t = -1.0 / (-tau + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
+__global__ void __launch_bounds__(256)
+jacobi_kernel(const LeafDesc* __restrict__ desc, const double* __restrict__ A, int lda,
+              double* __restrict__ w, double* __restrict__ Z, int* status) {
+  __shared__ double S[LMAX][LMAX + 1];
+  __shared__ double Vs[LMAX][LMAX + 1];
+  __shared__ int pr[LMAX / 2][2];
+  __shared__ double rot[LMAX / 2][2];
+  __shared__ double red[8];
+  __shared__ double sh_tol, sh_off;
+  const LeafDesc d = desc[blockIdx.x];
+  const int m = d.m, off = d.off;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < m * m; idx += 256) {
+    const int i = idx % m, j = idx / m;
+    S[i][j] = A[(size_t)(off + i) + (size_t)(off + j) * lda];
+    Vs[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // ||A||_F
+  double f = 0.0;
+  for (int idx = tid; idx < m * m; idx += 256) {
+    const double x = S[idx % m][idx / m];
+    f = fma(x, x, f);
+  }
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if ((tid & 31) == 0) red[tid >> 5] = f;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += red[q];
+    sh_tol = m * U_ROUND * sqrt(t);
+  }
+  __syncthreads();
+  const int mm = m + (m & 1);
+  const int npairs = mm / 2;
+  bool converged = (m <= 1);
+  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
+    double o2 = 0.0;
+    for (int idx = tid; idx < m * m; idx += 256) {
+      const int i = idx % m, j = idx / m;
+      if (i != j) o2 = fma(S[i][j], S[i][j], o2);
+    }
+    for (int o = 16; o > 0; o >>= 1) o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+    if ((tid & 31) == 0) red[tid >> 5] = o2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += red[q];
+      sh_off = sqrt(t);
+    }
+    __syncthreads();
+    if (sh_off <= sh_tol) {
+      converged = true;
+      break;
+    }
+    for (int r = 0; r < mm - 1; ++r) {
+      if (tid < npairs) {
+        auto pos = [&](int q) { return q == 0 ? 0 : ((q - 1 + r) % (mm - 1)) + 1; };
+        int a = pos(tid), b = pos(mm - 1 - tid);
+        const int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < m) sym_schur2(S[p][p], S[q][q], S[p][q], c, s);
+        pr[tid][0] = p;
+        pr[tid][1] = q;
+        rot[tid][0] = c;
+        rot[tid][1] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * m; idx += 256) {
+        const int t = idx / m, j = idx % m;
+        const double s = rot[t][1];
+        if (s == 0.0) continue;
+        const double c = rot[t][0];
+        const int p = pr[t][0], q = pr[t][1];
+        const double a = S[p][j], b = S[q][j];
+        S[p][j] = c * a - s * b;
+        S[q][j] = s * a + c * b;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npairs * m; idx += 256) {
+        const int t = idx / m, i = idx % m;
+        const double s = rot[t][1];
+        if (s == 0.0) continue;
+        const double c = rot[t][0];
+        const int p = pr[t][0], q = pr[t][1];
+        const double a = S[i][p], b = S[i][q];
+        S[i][p] = c * a - s * b;
+        S[i][q] = s * a + c * b;
+        const double va = Vs[i][p], vb = Vs[i][q];
+        Vs[i][p] = c * va - s * vb;
+        Vs[i][q] = s * va + c * vb;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < m; i += 256) w[off + i] = S[i][i];
+  for (int idx = tid; idx < m * m; idx += 256) {
+    const int i = idx % m, j = idx / m;
+    Z[(size_t)d.zoff + i + (size_t)j * LMAX] = Vs[i][j];
+  }
+  if (tid == 0 && !converged) atomicOr(status, 1);
+}
+
+cudaError_t jacobi_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                          int lda, double* w, double* Z, int* status) {
+  if (count == 0) return cudaSuccess;
+  note_launches(1);
+  jacobi_kernel<<<count, 256, 0, s>>>(d_desc, A, lda, w, Z, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Francis
+// Reflector of a short vector (one thread): (I - beta v v^T) x = ||x|| e1, v[0] = 1.
+__device__ void house_small(const double* x, int len, double* v, double& beta) {
+  double sigma = 0.0;
+  for (int i = 1; i < len; ++i) sigma += x[i] * x[i];
+  const double x0 = x[0];
+  v[0] = 1.0;
+  if (sigma == 0.0) {
+    for (int i = 1; i < len; ++i) v[i] = 0.0;
+    beta = (x0 >= 0.0) ? 0.0 : 2.0;
+    return;
+  }
+  const double mu = sqrt(x0 * x0 + sigma);
+  const double v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+  beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+  for (int i = 1; i < len; ++i) v[i] = x[i] / v0;
+}
+
+struct FrancisShared {
+  double H[LMAX][LMAX + 1];
+  double Z[LMAX][LMAX + 1];
+  double v[LMAX];
+  double xv[LMAX];
+  double beta;
+  double rc, rs;       // rotation for 2x2 standardisation
+  int action, kind, lo, hi, k, q, r, len;
+};
+
+// left: H[k0 + i][j] -= beta v_i (v . H[k0:k0+len, j]) for j in [c0, c1)
+__device__ __forceinline__ void apply_left(FrancisShared& F, int k0, int len, int c0, int c1) {
+  for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
+    double dsum = 0.0;
+    for (int i = 0; i < len; ++i) dsum += F.v[i] * F.H[k0 + i][j];
+    for (int i = 0; i < len; ++i) F.H[k0 + i][j] -= F.beta * (F.v[i] * dsum);
+  }
+}
+
+// right: M[i][k0 + l] -= beta (M[i, k0:k0+len] . v) v_l for i in [0, r1)
+__device__ __forceinline__ void apply_right(double (*M)[LMAX + 1], const double* v, double beta,
+                                            int k0, int len, int r1) {
+  for (int i = threadIdx.x; i < r1; i += blockDim.x) {
+    double e = 0.0;
+    for (int l = 0; l < len; ++l) e += M[i][k0 + l] * v[l];
+    for (int l = 0; l < len; ++l) M[i][k0 + l] -= beta * (e * v[l]);
+  }
+}
+
+// rotation G = [[c, -s], [s, c]] on (k, k+1): H <- G^T H G, Z <- Z G
+__device__ void apply_rot(FrancisShared& F, int m, int k, double c, double s) {
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const double r0 = F.H[k][j], r1 = F.H[k + 1][j];
+    F.H[k][j] = c * r0 + s * r1;
+    F.H[k + 1][j] = -s * r0 + c * r1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double c0 = F.H[i][k], c1 = F.H[i][k + 1];
+    F.H[i][k] = c * c0 + s * c1;
+    F.H[i][k + 1] = -s * c0 + c * c1;
+    const double z0 = F.Z[i][k], z1 = F.Z[i][k + 1];
+    F.Z[i][k] = c * z0 + s * z1;
+    F.Z[i][k + 1] = -s * z0 + c * z1;
+  }
+  __syncthreads();
+}
+
+enum { ACT_DONE = 0, ACT_ONE = 1, ACT_TWO = 2, ACT_STEP = 3, ACT_FAIL = 4 };
+
+__global__ void __launch_bounds__(128)
+francis_kernel(const LeafDesc* __restrict__ desc, const double* __restrict__ A, int lda,
+               double* __restrict__ wr, double* __restrict__ wi, double* __restrict__ Zout,
+               int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FrancisShared& F = *reinterpret_cast<FrancisShared*>(smem_raw);
+  const LeafDesc d = desc[blockIdx.x];
+  const int m = d.m, off = d.off;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    F.H[i][j] = A[(size_t)(off + i) + (size_t)(off + j) * lda];
+    F.Z[i][j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // ---- Hessenberg reduction
+  for (int k = 0; k < m - 2; ++k) {
+    if (tid == 0) {
+      const int len = m - k - 1;
+      for (int i = 0; i < len; ++i) F.xv[i] = F.H[k + 1 + i][k];
+      house_small(F.xv, len, F.v, F.beta);
+      F.len = len;
+    }
+    __syncthreads();
+    if (F.beta != 0.0) {
+      apply_left(F, k + 1, F.len, k, m);
+      __syncthreads();
+      apply_right(F.H, F.v, F.beta, k + 1, F.len, m);
+      apply_right(F.Z, F.v, F.beta, k + 1, F.len, m);
+      __syncthreads();
+      for (int i = k + 2 + tid; i < m; i += blockDim.x) F.H[i][k] = 0.0;
+      __syncthreads();
+    }
+  }
+  // ---- Francis double-shift QR with deflation
+  int hi = m - 1, its = 0, budget = 40 * (m > 0 ? m : 1);
+  bool ok = true;
+  while (true) {
+    if (tid == 0) {
+      int act;
+      if (hi < 0) {
+        act = ACT_DONE;
+      } else if (hi == 0) {
+        wr[off] = F.H[0][0];
+        wi[off] = 0.0;
+        act = ACT_ONE;
+      } else {
+        int lo = hi;
+        while (lo > 0) {
+          double scale = fabs(F.H[lo - 1][lo - 1]) + fabs(F.H[lo][lo]);
+          if (scale == 0.0) {
+            scale = 0.0;
+            const int a0 = lo - 1 > 0 ? lo - 1 : 0;
+            for (int i = a0; i <= hi; ++i)
+              for (int j = a0; j <= hi; ++j) scale += fabs(F.H[i][j]);
+          }
+          if (fabs(F.H[lo][lo - 1]) <= U_ROUND * scale) {
+            F.H[lo][lo - 1] = 0.0;
+            break;
+          }
+          --lo;
+        }
+        F.lo = lo;
+        if (lo == hi) {
+          wr[off + hi] = F.H[hi][hi];
+          wi[off + hi] = 0.0;
+          act = ACT_ONE;
+        } else if (lo == hi - 1) {
+          act = ACT_TWO;
+        } else {
+          ++its;
+          --budget;
+          act = (budget < 0) ? ACT_FAIL : ACT_STEP;
+        }
+      }
+      F.action = act;
+      F.hi = hi;
+    }
+    __syncthreads();
+    const int act = F.action;
+    if (act == ACT_DONE) break;
+    if (act == ACT_FAIL) {
+      ok = false;
+      break;
+    }
+    if (act == ACT_ONE) {
+      hi -= 1;
+      its = 0;
+      __syncthreads();
+      continue;
+    }
+    if (act == ACT_TWO) {
+      const int k = hi - 1;
+      // standardise the 2x2 block at (k, k+1)
+      int kind = 0;   // 0: already triangular, 1: real pair, 2: complex pair
+      if (tid == 0) {
+        const double a = F.H[k][k], b = F.H[k][k + 1], c = F.H[k + 1][k], dd = F.H[k + 1][k + 1];
+        if (c == 0.0) {
+          F.kind = 0;
+        } else {
+          const double p = 0.5 * (a - dd);
+          const double disc = p * p + b * c;
+          if (disc >= 0.0) {
+            const double z = p + copysign(sqrt(disc), p);
+            const double nrm = hypot(z, c);
+            F.rc = z / nrm;
+            F.rs = c / nrm;
+            F.kind = 1;
+          } else {
+            const double th = 0.5 * atan2(-(a - dd), b + c);
+            F.rc = cos(th);
+            F.rs = sin(th);
+            F.kind = 2;
+          }
+        }
+      }
+      __syncthreads();
+      kind = F.kind;
+      if (kind != 0) apply_rot(F, m, k, F.rc, F.rs);
+      if (tid == 0) {
+        if (kind == 0) {
+          wr[off + k] = F.H[k][k];
+          wi[off + k] = 0.0;
+          wr[off + k + 1] = F.H[k + 1][k + 1];
+          wi[off + k + 1] = 0.0;
+        } else if (kind == 1) {
+          F.H[k + 1][k] = 0.0;
+          wr[off + k] = F.H[k][k];
+          wi[off + k] = 0.0;
+          wr[off + k + 1] = F.H[k + 1][k + 1];
+          wi[off + k + 1] = 0.0;
+        } else {
+          const double mid = 0.5 * (F.H[k][k] + F.H[k + 1][k + 1]);
+          F.H[k][k] = mid;
+          F.H[k + 1][k + 1] = mid;
+          const double im = sqrt(fabs(F.H[k][k + 1] * F.H[k + 1][k]));
+          wr[off + k] = mid;
+          wi[off + k] = im;
+          wr[off + k + 1] = mid;
+          wi[off + k + 1] = -im;
+        }
+      }
+      hi -= 2;
+      its = 0;
+      __syncthreads();
+      continue;
+    }
+    // ---- one implicit double-shift step on lo..hi (size >= 3)
+    const int lo = F.lo;
+    if (tid == 0) {
+      const int mh = hi;
+      double s, t;
+      if (its % 11 == 10) {
+        const double wv = fabs(F.H[mh][mh - 1]) + fabs(F.H[mh - 1][mh - 2]);
+        s = 1.5 * wv + F.H[mh][mh];
+        t = wv * wv;
+      } else {
+        s = F.H[mh - 1][mh - 1] + F.H[mh][mh];
+        t = F.H[mh - 1][mh - 1] * F.H[mh][mh] - F.H[mh - 1][mh] * F.H[mh][mh - 1];
+      }
+      F.xv[0] = F.H[lo][lo] * F.H[lo][lo] + F.H[lo][lo + 1] * F.H[lo + 1][lo] - s * F.H[lo][lo] + t;
+      F.xv[1] = F.H[lo + 1][lo] * (F.H[lo][lo] + F.H[lo + 1][lo + 1] - s);
+      F.xv[2] = F.H[lo + 1][lo] * F.H[lo + 2][lo + 1];
+    }
+    __syncthreads();
+    for (int k = lo; k < hi - 1; ++k) {
+      if (tid == 0) {
+        house_small(F.xv, 3, F.v, F.beta);
+        F.q = max(lo, k - 1);
+        F.r = min(k + 3, hi);
+      }
+      __syncthreads();
+      apply_left(F, k, 3, F.q, m);
+      __syncthreads();
+      apply_right(F.H, F.v, F.beta, k, 3, F.r + 1);
+      apply_right(F.Z, F.v, F.beta, k, 3, m);
+      __syncthreads();
+      if (tid == 0) {
+        if (k > lo) {
+          F.H[k + 1][k - 1] = 0.0;
+          F.H[k + 2][k - 1] = 0.0;
+        }
+        F.xv[0] = F.H[k + 1][k];
+        F.xv[1] = F.H[k + 2][k];
+        if (k < hi - 2) F.xv[2] = F.H[k + 3][k];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) house_small(F.xv, 2, F.v, F.beta);
+    __syncthreads();
+    apply_left(F, hi - 1, 2, hi - 2, m);
+    __syncthreads();
+    apply_right(F.H, F.v, F.beta, hi - 1, 2, hi + 1);
+    apply_right(F.Z, F.v, F.beta, hi - 1, 2, m);
+    __syncthreads();
+    if (tid == 0) F.H[hi][hi - 2] = 0.0;
+    __syncthreads();
+  }
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    Zout[(size_t)d.zoff + i + (size_t)j * LMAX] = F.Z[i][j];
+  }
+  if (tid == 0 && !ok) atomicOr(status, 1);
+}
+
+cudaError_t francis_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                           int lda, double* wr, double* wi, double* Z, int* status) {
+  if (count == 0) return cudaSuccess;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(francis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(FrancisShared));
+    attr = true;
+  }
+  note_launches(1);
+  francis_kernel<<<count, 128, sizeof(FrancisShared), s>>>(d_desc, A, lda, wr, wi, Z, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- U * Z
+// For leaf t and a 64-row slab of U: U[rows, off:off+m] <- U[rows, off:off+m] Z_t.
+// Each CTA reads its rows of the leaf's columns into shared memory before
+// writing them, so in-place use (Uin == Uout) is safe.
+__global__ void __launch_bounds__(256)
+apply_leaf_vectors_kernel(const LeafDesc* __restrict__ desc, int n, const double* Uin,
+                          int ldu_in, double* Uout, int ldu_out, const double* __restrict__ Z) {
+  __shared__ double Us[64][LMAX + 1];
+  __shared__ double Zs[LMAX][LMAX + 1];
+  const LeafDesc d = desc[blockIdx.x];
+  const int m = d.m, off = d.off;
+  const int r0 = blockIdx.y * 64;
+  const int rows = min(64, n - r0);
+  if (rows <= 0) return;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < rows * m; idx += 256) {
+    const int i = idx % rows, j = idx / rows;
+    Us[i][j] = Uin[(size_t)(r0 + i) + (size_t)(off + j) * ldu_in];
+  }
+  for (int idx = tid; idx < m * m; idx += 256) {
+    const int i = idx % m, j = idx / m;
+    Zs[i][j] = Z[(size_t)d.zoff + i + (size_t)j * LMAX];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < rows * m; idx += 256) {
+    const int i = idx % rows, j = idx / rows;
+    double t = 0.0;
+    for (int l = 0; l < m; ++l) t = fma(Us[i][l], Zs[l][j], t);
+    Uout[(size_t)(r0 + i) + (size_t)(off + j) * ldu_out] = t;
+  }
+}
+
+cudaError_t apply_leaf_vectors(cudaStream_t s, int count, const LeafDesc* d_desc, int n,
+                               const double* Uin, int ldu_in, double* Uout, int ldu_out,
+                               const double* Z) {
+  if (count == 0 || n == 0) return cudaSuccess;
+  dim3 grid(count, (n + 63) / 64);
+  note_launches(1);
+  apply_leaf_vectors_kernel<<<grid, 256, 0, s>>>(d_desc, n, Uin, ldu_in, Uout, ldu_out, Z);
+  return cudaGetLastError();
+}
+
+}  // namespace eigdc

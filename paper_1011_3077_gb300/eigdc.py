@@ -1,0 +1,270 @@
+"""ctypes binding of libeigdc (include/eigdc.h): same entry-point names,
+argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module only converts
+Python values and torch tensors (device memory, stream) to the C-ABI's plain
+pointers and sizes.  If the shared library is missing or cannot be loaded the
+import of :func:`lib` raises: there is no CPU fallback.
+
+Matrices cross the boundary column-major.  :func:`to_device` stores a numpy
+matrix A as the row-major torch tensor A^T (whose memory is A column-major)
+and :func:`to_host` undoes it.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeigdc.so")
+
+EIG_OK = 0
+EIG_ERR_ARG = -1
+EIG_ERR_CUDA = -2
+EIG_ERR_NOMEM = -3
+EIG_NO_CONVERGENCE = 1
+EIG_NO_SPLIT = 2
+EIG_NEAR_SINGULAR_PENCIL = 3
+EIG_NONFINITE = 4
+
+EIG_REGION_UNIT_CIRCLE = 0
+EIG_REGION_CIRCLE = 1
+EIG_REGION_LINE = 2
+EIG_KIND_SYM = 0
+EIG_KIND_NONSYM = 1
+PURPOSE_HAAR = 4
+PURPOSE_SHIFT = 5
+ROOT_NODE = 1
+
+
+class Region(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("c_or_sigma", ctypes.c_double),
+                ("r_or_s", ctypes.c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("split_tol", ctypes.c_double), ("leaf_size", ctypes.c_int),
+                ("prec", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("max_fail", ctypes.c_int), ("nb", ctypes.c_int),
+                ("v_draws", ctypes.c_int), ("root_unit_circle", ctypes.c_int)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("last_ratio", ctypes.c_double),
+                ("converged", ctypes.c_int), ("k", ctypes.c_int),
+                ("split_residual", ctypes.c_double), ("rank", ctypes.c_int),
+                ("draw", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nodes", ctypes.c_int), ("splits", ctypes.c_int),
+                ("max_depth", ctypes.c_int), ("total_iters", ctypes.c_int),
+                ("failed_attempts", ctypes.c_int), ("leaves", ctypes.c_int),
+                ("flops", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_U64 = ctypes.c_uint64
+
+_SIGNATURES = {
+    "eig_default_params": (None, [ctypes.POINTER(Params)]),
+    "eig_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "eig_destroy": (_I, [_P]),
+    "eig_last_error": (ctypes.c_char_p, [_P]),
+    "eig_kernel_launches": (ctypes.c_ulonglong, []),
+    "eig_workspace_size": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "eig_divide_step": (_I, [_P, _I, _P, _I, _P, _I, ctypes.POINTER(Region),
+                             ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
+    "eig_last_R": (_I, [_P, _I, _P, _I]),
+    "eig_split": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _I, _I, _U64, _I,
+                       ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
+    "eig_solve": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
+                       ctypes.POINTER(SolveInfo)]),
+    "eig_qr": (_I, [_P, _I, _I, _P, _I, _P, _I, _P, _I]),
+    "eig_gaussian": (_I, [_P, _I, _I, _U64, _I, _U64, _I, _P, _I]),
+    "eig_haar": (_I, [_P, _I, _U64, _I, _U64, _I, _P, _I]),
+    "eig_split_test": (_I, [_P, _I, _P, _I, _D, _P, _I, _D, ctypes.POINTER(_I),
+                            ctypes.POINTER(_D), _P]),
+    "eig_gemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+}
+
+EXPORTED = tuple(_SIGNATURES)
+
+
+def lib():
+    """The loaded libeigdc (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libeigdc.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class EigError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("eigdc error %d: %s" % (code, msg))
+        self.code = code
+
+
+def default_params(**kw):
+    p = Params()
+    lib().eig_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Handle:
+    """eig_create / eig_destroy around a torch CUDA stream."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self._h = ctypes.c_void_p()
+        rc = lib().eig_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(stream.cuda_stream))
+        if rc != EIG_OK:
+            raise EigError(rc, "eig_create failed")
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def last_error(self):
+        return lib().eig_last_error(self._h).decode()
+
+    def check(self, rc, allow=()):
+        if rc != EIG_OK and rc not in allow:
+            raise EigError(rc, self.last_error())
+        return rc
+
+    def close(self):
+        if self._h:
+            lib().eig_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------- layout
+
+def to_device(A, device="cuda"):
+    """numpy (rows x cols) -> torch float64 tensor holding A column-major."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.float64).T)).to(device)
+
+
+def to_host(t):
+    """Inverse of to_device."""
+    return t.detach().cpu().numpy().T.copy()
+
+
+def ld(t):
+    """Leading dimension of a to_device() tensor (its row stride)."""
+    return int(t.stride(0)) if t.dim() == 2 else int(t.shape[0])
+
+
+# ----------------------------------------------------------------- entry points
+
+def eig_kernel_launches():
+    return int(lib().eig_kernel_launches())
+
+
+def eig_divide_step(h, n, dA, lda, dB, ldb, region, params):
+    info = StepInfo()
+    rc = lib().eig_divide_step(h.ptr, n, _ptr(dA), lda, _ptr(dB), ldb, ctypes.byref(region),
+                               ctypes.byref(params), ctypes.byref(info))
+    return rc, info
+
+
+def eig_last_R(h, n, dR, ldr):
+    return h.check(lib().eig_last_R(h.ptr, n, _ptr(dR), ldr))
+
+
+def eig_split(h, n, dAp, dBp, ldp, dA, lda, dQ, ldq, symmetric, stream, attempt, params):
+    info = StepInfo()
+    rc = lib().eig_split(h.ptr, n, _ptr(dAp), _ptr(dBp), ldp, _ptr(dA), lda, _ptr(dQ), ldq,
+                         int(symmetric), int(stream), int(attempt), ctypes.byref(params),
+                         ctypes.byref(info))
+    return rc, info
+
+
+def eig_solve(h, kind, n, dA, lda, dwr, dwi, dU, ldu, params):
+    info = SolveInfo()
+    rc = lib().eig_solve(h.ptr, kind, n, _ptr(dA), lda, _ptr(dwr), _ptr(dwi), _ptr(dU), ldu,
+                         ctypes.byref(params), ctypes.byref(info))
+    return rc, info
+
+
+def eig_qr(h, m, n, dX, ldx, dQ, ldq, dR, ldr):
+    return h.check(lib().eig_qr(h.ptr, m, n, _ptr(dX), ldx, _ptr(dQ), ldq, _ptr(dR), ldr))
+
+
+def eig_gaussian(h, rows, cols, seed, purpose, stream, attempt, dG, ldg):
+    return h.check(lib().eig_gaussian(h.ptr, rows, cols, seed, purpose, stream, attempt,
+                                      _ptr(dG), ldg))
+
+
+def eig_haar(h, n, seed, purpose, stream, attempt, dV, ldv):
+    return h.check(lib().eig_haar(h.ptr, n, seed, purpose, stream, attempt, _ptr(dV), ldv))
+
+
+def eig_split_test(h, n, dA, lda, normA, dB=None, ldb=0, normB=0.0, want_scores=False):
+    k = ctypes.c_int()
+    e = ctypes.c_double()
+    scores = np.zeros(max(n - 1, 1)) if want_scores else None
+    sp = scores.ctypes.data_as(ctypes.c_void_p) if want_scores else ctypes.c_void_p(0)
+    h.check(lib().eig_split_test(h.ptr, n, _ptr(dA), lda, normA, _ptr(dB), ldb, normB,
+                                 ctypes.byref(k), ctypes.byref(e), sp))
+    return k.value, e.value, (scores[:n - 1] if want_scores else None)
+
+
+def eig_gemm(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
+    return h.check(lib().eig_gemm(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
+                                  _ptr(dB), ldb, beta, _ptr(dC), ldc))
+
+
+# ----------------------------------------------------------------- convenience
+
+def solve_symmetric(h, A, params=None):
+    """(w ascending, U, info) for a symmetric numpy matrix, through eig_solve."""
+    import torch
+    n = A.shape[0]
+    params = params or default_params()
+    dA = to_device(A)
+    dw = torch.zeros(n, dtype=torch.float64, device=dA.device)
+    dU = torch.zeros((n, n), dtype=torch.float64, device=dA.device)
+    rc, info = eig_solve(h, EIG_KIND_SYM, n, dA, n, dw, None, dU, n, params)
+    return rc, dw.cpu().numpy(), to_host(dU), info
+
+
+def schur_nonsymmetric(h, A, params=None):
+    """(T, U, wr, wi, info) for a real numpy matrix, through eig_solve."""
+    import torch
+    n = A.shape[0]
+    params = params or default_params()
+    dA = to_device(A)
+    dwr = torch.zeros(n, dtype=torch.float64, device=dA.device)
+    dwi = torch.zeros(n, dtype=torch.float64, device=dA.device)
+    dU = torch.zeros((n, n), dtype=torch.float64, device=dA.device)
+    rc, info = eig_solve(h, EIG_KIND_NONSYM, n, dA, n, dwr, dwi, dU, n, params)
+    return rc, to_host(dA), to_host(dU), dwr.cpu().numpy(), dwi.cpu().numpy(), info
