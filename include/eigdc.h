@@ -39,6 +39,7 @@ typedef struct eig_handle_s* eig_handle_t;
 #define EIG_ERR_ARG (-1)      /* invalid argument (message in eig_last_error) */
 #define EIG_ERR_CUDA (-2)     /* CUDA runtime error */
 #define EIG_ERR_NOMEM (-3)    /* workspace allocation failed */
+#define EIG_ERR_SCRATCH (-4)  /* eig_gemm_noalloc: the split-K partials exceed its static scratch */
 #define EIG_NO_CONVERGENCE 1  /* IRS hit maxit (Algorithm 3), or a leaf solver gave up */
 #define EIG_NO_SPLIT 2        /* repeated failure to split a node (Sec. 3.3-3.5) */
 #define EIG_NEAR_SINGULAR_PENCIL 3 /* pencil strategy found no dividing circle (Sec. 3.5) */
@@ -186,6 +187,30 @@ int eig_split_test(eig_handle_t h, int n, const double* dA, int lda, double norm
 int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
              const double* dA, int lda, const double* dB, int ldb, double beta,
              double* dC, int ldc);
+
+/* ------------------------------------------------------ no-allocation GEMM
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc -- for example a process whose device memory is reserved by
+ * another allocator's pool, or a latency-critical loop that cannot take the
+ * device synchronisation an allocation brings.  It computes what eig_gemm
+ * computes, with the same split-K decomposition, but needs no handle and
+ * allocates nothing: its K-chunk partials live in a static device array of
+ * 2^20 doubles (8 MiB) that every GPU loading the library holds until the
+ * process exits.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream);
+ *     the call only enqueues work on it and returns.
+ *   - All matrix pointers are caller-owned device memory, column-major.
+ *   - Returns EIG_ERR_SCRATCH when the split-K partials of this shape
+ *     (splits * m * n doubles) exceed 2^20 doubles; shapes that need no
+ *     split (large m * n, or small k) never use the array.
+ *   - The array's device address is looked up on the first call on each
+ *     device (with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the array; calls that overlap on the GPU race on it.
+ */
+int eig_gemm_noalloc(void* stream, int ta, int tb, int m, int n, int k, double alpha,
+                     const double* dA, int lda, const double* dB, int ldb, double beta,
+                     double* dC, int ldc);
 
 #ifdef __cplusplus
 }

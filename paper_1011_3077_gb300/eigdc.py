@@ -22,6 +22,7 @@ EIG_OK = 0
 EIG_ERR_ARG = -1
 EIG_ERR_CUDA = -2
 EIG_ERR_NOMEM = -3
+EIG_ERR_SCRATCH = -4
 EIG_NO_CONVERGENCE = 1
 EIG_NO_SPLIT = 2
 EIG_NEAR_SINGULAR_PENCIL = 3
@@ -90,6 +91,7 @@ _SIGNATURES = {
     "eig_split_test": (_I, [_P, _I, _P, _I, _D, _P, _I, _D, ctypes.POINTER(_I),
                             ctypes.POINTER(_D), _P]),
     "eig_gemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+    "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
 }
 
 EXPORTED = tuple(_SIGNATURES)
@@ -241,6 +243,13 @@ def eig_split_test(h, n, dA, lda, normA, dB=None, ldb=0, normB=0.0, want_scores=
 def eig_gemm(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
     return h.check(lib().eig_gemm(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
                                   _ptr(dB), ldb, beta, _ptr(dC), ldc))
+
+
+def eig_gemm_noalloc(stream, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
+    """Returns the status code (no handle: EIG_ERR_SCRATCH for shapes whose
+    split-K partials exceed the static scratch)."""
+    return lib().eig_gemm_noalloc(ctypes.c_void_p(stream.cuda_stream), int(ta), int(tb), m, n, k,
+                                  alpha, _ptr(dA), lda, _ptr(dB), ldb, beta, _ptr(dC), ldc)
 
 
 # ----------------------------------------------------------------- convenience
