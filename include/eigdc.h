@@ -47,6 +47,13 @@ typedef struct eig_handle_s* eig_handle_t;
 
 /* arithmetic of the contractions */
 #define EIG_FP64 0
+/* split precision: the GEMMs of the iteration, the splitter and the similarity
+ * run as three-term BF16 products with FP32 accumulation on the tcgen05
+ * tensor cores (eig_gemm_split); panels, norms, the R-test, the split test
+ * and the rank decision stay FP64.  Defaults then read tau = 1e-5 and
+ * split_tol >= 1e-4, and eig_solve(EIG_KIND_SYM) ends with an FP64
+ * refinement of the eigenvectors and eigenvalues. */
+#define EIG_SPLIT_BF16X3 1
 
 /* regions (Sec. 3.1 unit circle; Sec. 3.3 line via the Moebius map
  * f(z) = (z - sigma + s)/(z - sigma - s); Sec. 3.5 circles |z - c| = r) */
@@ -69,7 +76,7 @@ typedef struct {
   int maxit;         /* IRS runs j = 0..maxit (Algorithm 3, "until j > maxit") */
   double split_tol;  /* accept a split when ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) <= split_tol */
   int leaf_size;     /* nodes of at most this size go to the leaf solver (<= 64) */
-  int prec;          /* EIG_FP64 */
+  int prec;          /* EIG_FP64 or EIG_SPLIT_BF16X3 */
   uint64_t seed;     /* Philox key of every draw of the method */
   int max_fail;      /* unproductive attempts per node before EIG_NO_SPLIT */
   int nb;            /* panel width of the blocked QR (0: automatic) */
@@ -187,6 +194,16 @@ int eig_split_test(eig_handle_t h, int n, const double* dA, int lda, double norm
 int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
              const double* dA, int lda, const double* dB, int ldb, double beta,
              double* dC, int ldc);
+
+/* C = alpha op(A) op(B) + beta C in the split-precision form of the
+ * contractions: FP64 operands split into three BF16 planes (hi + mid + lo),
+ * the six plane products of weight >= 2^-16 accumulated in FP32 on the
+ * tcgen05 tensor cores, FP64 result (FP32-level accuracy, about 2^-22 |A||B|
+ * per entry).  The split-precision reading of the trailing-update and
+ * complement GEMMs of the inverse-free iteration. */
+int eig_gemm_split(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+                   const double* dA, int lda, const double* dB, int ldb, double beta,
+                   double* dC, int ldc);
 
 /* ------------------------------------------------------ no-allocation GEMM
  * The paper has no counterpart: this entry point serves callers that cannot

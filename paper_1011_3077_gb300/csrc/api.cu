@@ -29,6 +29,7 @@ void eigdc::note_launches(unsigned long long k) { g_launches.fetch_add(k, std::m
 
 namespace {
 
+constexpr int JB_LD_C = 32;   // largest panel width (leading dimension of T)
 constexpr int PURPOSE_HAAR = 4;
 constexpr int PURPOSE_SHIFT = 5;
 constexpr uint64_t ROOT_NODE = 1;
@@ -131,11 +132,32 @@ struct QRBufs {
   double* tau;
   double* Wk;              // jb x cols product of a block reflector
   double* part;            // split-K partials
+  int prec = EIG_FP64;     // arithmetic of the reflector products
+  void* tcw = nullptr;     // BF16 planes (split precision)
+  int* tcerr = nullptr;    // device flag of the tensor-core kernel
 };
+
+static bool split_mode(int prec) { return prec == EIG_SPLIT_BF16X3; }
+
+// C = alpha op(A) op(B) + beta C in the arithmetic of `prec`.
+static void mm(eig_handle_t h, int prec, void* tcw, int* tcerr, bool ta, bool tb, int m, int n,
+               int k, double alpha, const double* A, int lda, const double* B, int ldb,
+               double beta, double* C, int ldc, int splits, double* part) {
+  if (split_mode(prec))
+    CK(tc_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
+  else
+    CK(gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, splits, part));
+}
+
+// BF16 plane scratch of the reflector products of an m x n QR.
+static size_t tcw_qr_bytes(int m, int n) {
+  return std::max(tc_gemm_workspace_bytes(n, JB_LD_C, m), tc_gemm_workspace_bytes(m, n, JB_LD_C));
+}
 
 constexpr int JB_LD = 32;
 
-static size_t qr_part_doubles(int m, int cols) { return (size_t)17 * JB_LD * std::max(cols, 1) + 0 * m; }
+// split-K partials of the jb x cols reflector products (at most 32 K-chunks)
+static size_t qr_part_doubles(int m, int cols) { return (size_t)33 * JB_LD * std::max(cols, 1) + 0 * m; }
 
 // Blocked right-looking Householder QR of the m x n matrix in q.W.
 static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
@@ -154,11 +176,20 @@ static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
     if (nc > 0) {
       const int mb = m - j0;
       double* C = q.W + j0 + (size_t)(j0 + jb) * q.ldw;
-      int sp = gemm_choose_splits(jb, nc, mb);
-      sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
-      if (sp < 0) CK(cudaGetLastError());
-      CK(reduce_trmm(s, jb, nc, q.part, sp, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk));
-      CK(gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw));
+      if (split_mode(q.prec)) {
+        // (V^T C)^T = C^T V on the tensor cores (M = nc rows, N = jb)
+        CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
+                   q.tcerr));
+        CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk, true));
+        CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw, q.tcw,
+                   q.tcerr));
+      } else {
+        int sp = gemm_choose_splits(jb, nc, mb);
+        sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
+        if (sp < 0) CK(cudaGetLastError());
+        CK(reduce_trmm(s, jb, nc, q.part, sp, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk));
+        CK(gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw));
+      }
     }
   }
   return jbmax;
@@ -180,6 +211,14 @@ static void apply_q(eig_handle_t h, int m, int nref, int jbmax, QRBufs& q, doubl
     if (nc <= 0) continue;
     double* Yb = Y + j0 + (size_t)c0 * ldy;
     const double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
+    if (split_mode(q.prec)) {
+      CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
+                 q.tcerr));
+      CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, false, q.Wk, true));
+      CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy, q.tcw,
+                 q.tcerr));
+      continue;
+    }
     int sp = gemm_choose_splits(jb, nc, mb);
     sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, Yb, ldy, sp, q.part);
     if (sp < 0) CK(cudaGetLastError());
@@ -192,7 +231,7 @@ struct QRWork {
   QRBufs q;
 };
 
-static size_t carve_qr(Arena& a, int m, int n, QRWork& w) {
+static size_t carve_qr(Arena& a, int m, int n, QRWork& w, int prec = EIG_FP64) {
   const size_t start = a.used;
   w.q.W = a.take<double>((size_t)m * n);
   w.q.ldw = m;
@@ -203,6 +242,9 @@ static size_t carve_qr(Arena& a, int m, int n, QRWork& w) {
   w.q.tau = a.take<double>(n);
   w.q.Wk = a.take<double>((size_t)JB_LD * n);
   w.q.part = a.take<double>(qr_part_doubles(m, n));
+  w.q.prec = prec;
+  w.q.tcw = split_mode(prec) ? (void*)a.take<char>(tcw_qr_bytes(m, n)) : nullptr;
+  w.q.tcerr = a.take<int>(4);
   return a.used - start;
 }
 
@@ -225,9 +267,11 @@ struct IRSWork {
   unsigned long long* sums;
   int* flag;
   QRWork qr;   // W is the stacked 2n x n matrix
+  int prec = EIG_FP64;
+  void* tcw = nullptr;
 };
 
-static size_t carve_irs(Arena& a, int n, IRSWork& w) {
+static size_t carve_irs(Arena& a, int n, IRSWork& w, int prec = EIG_FP64) {
   const size_t start = a.used;
   const size_t nn = (size_t)n * n;
   w.Aj = a.take<double>(nn);
@@ -240,7 +284,15 @@ static size_t carve_irs(Arena& a, int n, IRSWork& w) {
   w.gpart = a.take<double>(square_partial_doubles(n));
   w.sums = a.take<unsigned long long>(4);
   w.flag = a.take<int>(4);
-  carve_qr(a, 2 * n, n, w.qr);
+  w.prec = prec;
+  // one plane buffer serves the QR's reflector products and the complement
+  // products (they run one after the other on the stream)
+  w.tcw = split_mode(prec) ? (void*)a.take<char>(std::max(tc_gemm_workspace_bytes(n, n, n),
+                                                          tcw_qr_bytes(2 * n, n)))
+                           : nullptr;
+  carve_qr(a, 2 * n, n, w.qr, EIG_FP64);
+  w.qr.q.prec = prec;
+  w.qr.q.tcw = w.tcw;
   return a.used - start;
 }
 
@@ -255,8 +307,11 @@ struct IRSOut {
 
 static double default_tau(int n) { return std::max(1e-14, 4.0 * std::sqrt((double)n) * 0x1p-53); }
 
+// stagnate: also stop once the ratio is below 1e-3 and has stopped falling
+// quadratically (the FP32-level floor of the split-precision iterates).
 static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int lda, const double* B,
-                      int ldb, const eig_region_t& rg, double tau, int maxit) {
+                      int ldb, const eig_region_t& rg, double tau, int maxit,
+                      bool stagnate = false) {
   cudaStream_t s = h->stream;
   const size_t nn = (size_t)n * n;
   QRBufs& q = w.qr.q;
@@ -271,6 +326,7 @@ static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int ld
   double* Rp = w.Rp;
   unsigned long long* hsum = static_cast<unsigned long long*>(pinned(h, 64));
   const int gsplit = gemm_choose_splits(n, n, n);
+  CK(cudaMemsetAsync(q.tcerr, 0, sizeof(int), s));
   IRSOut out{0, false, 0.0, nullptr, nullptr, nullptr};
   bool have_prev = false;
   for (int j = 0;; ++j) {
@@ -284,20 +340,29 @@ static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int ld
     // [Q12; Q22]: the last n columns of the 2n x 2n orthogonal factor
     CK(fill_identity_block(s, 2 * n, n, w.Y, 2 * n, n));
     apply_q(h, 2 * n, n, jbmax, q, w.Y, 2 * n, n, false);
-    CK(gemm(s, true, false, n, n, n, 1.0, w.Y, 2 * n, Aj, n, 0.0, An, n, gsplit, w.gpart));
-    CK(gemm(s, true, false, n, n, n, 1.0, w.Y + n, 2 * n, Bj, n, 0.0, Bn, n, gsplit, w.gpart));
+    mm(h, w.prec, w.tcw, q.tcerr, true, false, n, n, n, 1.0, w.Y, 2 * n, Aj, n, 0.0, An, n, gsplit,
+       w.gpart);
+    mm(h, w.prec, w.tcw, q.tcerr, true, false, n, n, n, 1.0, w.Y + n, 2 * n, Bj, n, 0.0, Bn, n,
+       gsplit, w.gpart);
     std::swap(Aj, An);
     std::swap(Bj, Bn);
     CK(stack_pencil(s, n, Aj, Bj, q.W));
     if (have_prev) {
       CK(cudaMemcpyAsync(hsum, w.sums, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&hsum[2], q.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (static_cast<int>(hsum[2] & 0xFFFFFFFFull) != 0) {
+        h->err = "tensor-core GEMM: a bounded wait timed out";
+        throw Fail{EIG_ERR_CUDA};
+      }
       double num, den;
       std::memcpy(&num, &hsum[0], 8);
       std::memcpy(&den, &hsum[1], 8);
       const double ratio = den > 0.0 ? num / den : (num == 0.0 ? 0.0 : INFINITY);
+      const double prev = out.last_ratio;
       out.last_ratio = ratio;
-      if (ratio <= tau) {
+      const bool stalled = stagnate && j >= 2 && ratio <= 1e-3 && ratio > 0.25 * prev;
+      if (ratio <= tau || stalled) {
         out.iters = j + 1;
         out.converged = true;
         out.Rlast = Rc;
@@ -325,9 +390,11 @@ struct SplitWork {
   unsigned long long* nbits;
   int* rank;
   QRWork qr;
+  int prec = EIG_FP64;
+  void* tcw = nullptr;
 };
 
-static size_t carve_split(Arena& a, int n, SplitWork& w) {
+static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64) {
   const size_t start = a.used;
   const size_t nn = (size_t)n * n;
   w.G = a.take<double>(nn);
@@ -348,7 +415,13 @@ static size_t carve_split(Arena& a, int n, SplitWork& w) {
   w.gpart = a.take<double>(square_partial_doubles(n));
   w.nbits = a.take<unsigned long long>(4);
   w.rank = a.take<int>(4);
-  carve_qr(a, n, n, w.qr);
+  w.prec = prec;
+  w.tcw = split_mode(prec) ? (void*)a.take<char>(std::max(tc_gemm_workspace_bytes(n, n, n),
+                                                          tcw_qr_bytes(n, n)))
+                           : nullptr;
+  carve_qr(a, n, n, w.qr, EIG_FP64);
+  w.qr.q.prec = prec;
+  w.qr.q.tcw = w.tcw;
   return a.used - start;
 }
 
@@ -401,31 +474,45 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
   SplitOut out{0, INFINITY, 0, 0, false};
   const int draws = std::max(1, p.v_draws);
   hscores.assign(std::max(n - 1, 0), 0.0);
+  CK(cudaMemsetAsync(w.qr.q.tcerr, 0, sizeof(int), s));
   for (int draw = 0; draw < draws; ++draw) {
     const int code = ((attempt & 0x3F) << 2) | (draw & 3);
     // Haar V (Algorithm 1, lines 1-2)
     CK(gaussian(s, n, n, p.seed, PURPOSE_HAAR, stream_id, code, w.G, n));
     qr_explicit(h, w.qr, n, n, w.G, n, w.Vh, n, nullptr, 0);
     // RURV(A_p): [U, R2] = QR(A_p V^T)
-    CK(gemm(s, false, true, n, n, n, 1.0, Ap, ldp, w.Vh, n, 0.0, w.X, n, gsplit, w.gpart));
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, true, n, n, n, 1.0, Ap, ldp, w.Vh, n, 0.0, w.X, n,
+       gsplit, w.gpart);
     qr_explicit(h, w.qr, n, n, w.X, n, w.U, n, w.R2, n);
     CK(count_rank(s, n, w.R2, n, 1e-8, w.rank));
     // RQ(U^T (A_p + B_p)) by reversal: Z = (J Y)^T = Q~ R~, U_cur = Q~ J
     CK(add_matrices(s, n, n, Ap, ldp, Bp, ldp, w.S, n));
-    CK(gemm(s, true, false, n, n, n, 1.0, w.U, n, w.S, n, 0.0, w.Y, n, gsplit, w.gpart));
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.U, n, w.S, n, 0.0, w.Y, n,
+       gsplit, w.gpart);
     CK(reverse_transpose(s, n, w.Y, n, w.Z, n));
     qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, nullptr, 0);
     CK(reverse_columns(s, n, n, w.Qt, n, w.Ucur, n));
     // similarity and split test
-    CK(gemm(s, false, false, n, n, n, 1.0, A, lda, w.Ucur, n, 0.0, w.tmp, n, gsplit, w.gpart));
-    CK(gemm(s, true, false, n, n, n, 1.0, w.Ucur, n, w.tmp, n, 0.0, w.Ahat, n, gsplit, w.gpart));
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, false, n, n, n, 1.0, A, lda, w.Ucur, n, 0.0, w.tmp,
+       n, gsplit, w.gpart);
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.Ucur, n, w.tmp, n, 0.0,
+       w.Ahat, n, gsplit, w.gpart);
     if (symmetric) CK(symmetrize(s, n, w.Ahat, n));
     if (n >= 2) CK(split_scores(s, n, w.Ahat, n, normA > 0 ? 1.0 / normA : 1.0, w.colpart, w.scores, false));
     const size_t sbytes = sizeof(double) * std::max(n - 1, 1);
     char* hb = static_cast<char*>(pinned(h, sbytes + 64));
     if (n >= 2) CK(cudaMemcpyAsync(hb, w.scores, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hb + sbytes, w.rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hb + sbytes + 8, w.qr.q.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    {
+      int terr;
+      std::memcpy(&terr, hb + sbytes + 8, sizeof(int));
+      if (terr != 0) {
+        h->err = "tensor-core GEMM: a bounded wait timed out";
+        throw Fail{EIG_ERR_CUDA};
+      }
+    }
     if (n >= 2) std::memcpy(hscores.data(), hb, sizeof(double) * (n - 1));
     int rank;
     std::memcpy(&rank, hb + sbytes, sizeof(int));
@@ -540,7 +627,7 @@ struct SolveWork {
   SplitWork split;
 };
 
-static size_t carve_solve(Arena& a, int n, SolveWork& w) {
+static size_t carve_solve(Arena& a, int n, SolveWork& w, int prec = EIG_FP64) {
   const size_t start = a.used;
   const size_t nn = (size_t)n * n;
   const int maxleaves = n;   // upper bound: every leaf has >= 1 row
@@ -552,8 +639,8 @@ static size_t carve_solve(Arena& a, int n, SolveWork& w) {
   w.sortbuf = a.take<double>(nn);
   w.status = a.take<int>(8);
   w.ddesc = a.take<LeafDesc>(std::max(1, maxleaves));
-  carve_irs(a, n, w.irs);
-  carve_split(a, n, w.split);
+  carve_irs(a, n, w.irs, prec);
+  carve_split(a, n, w.split, prec);
   return a.used - start;
 }
 
@@ -570,6 +657,53 @@ __global__ void permute_columns_kernel(int n, const double* __restrict__ U, int 
   out[i + (size_t)j * ldo] = U[i + (size_t)perm[j] * ldu];
 }
 
+// FP64 refinement of a symmetric eigendecomposition (a12): steps of
+// Ogita-Aishima with FP64 GEMMs until the Gram and off-diagonal residuals
+// reach the FP64 level (at most 4 steps), then Rayleigh quotients.  G, AU, S,
+// E are n x n scratch; lam receives the eigenvalues.  Returns flops executed.
+static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, double* U, int ldu,
+                               double* lam, double* G, double* AU, double* S, double* E,
+                               unsigned long long* dbits) {
+  cudaStream_t s = h->stream;
+  double flops = 0.0;
+  const double u = 0x1p-53;
+  unsigned long long* hb = static_cast<unsigned long long*>(pinned(h, 64));
+  for (int step = 0; step < 6; ++step) {
+    CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
+    CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
+    CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, AU, n, 0.0, S, n));
+    flops += 6.0 * (double)n * n * n;
+    CK(cudaMemsetAsync(dbits, 0, 3 * sizeof(unsigned long long), s));
+    CK(oa_diag(s, n, G, S, lam, &dbits[0]));
+    CK(oa_offmax(s, n, G, S, &dbits[1]));
+    CK(cudaMemcpyAsync(hb, dbits, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double normA, offS, maxR;
+    std::memcpy(&normA, &hb[0], 8);
+    std::memcpy(&offS, &hb[1], 8);
+    std::memcpy(&maxR, &hb[2], 8);
+    const double floor_ = 8.0 * std::sqrt((double)n) * u;
+    if (offS <= floor_ * normA && maxR <= floor_) break;
+    CK(oa_correction(s, n, G, S, lam, 64.0 * u * normA, E));
+    CK(gemm(s, false, false, n, n, n, 1.0, U, ldu, E, n, 0.0, AU, n));
+    flops += 2.0 * (double)n * n * n;
+    if (ldu == n) {
+      CK(add_inplace(s, (size_t)n * n, U, AU));
+    } else {
+      CK(add_matrices(s, n, n, U, ldu, AU, n, U, ldu));
+    }
+  }
+  CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
+  flops += 2.0 * (double)n * n * n;
+  if (ldu == n) {
+    CK(rayleigh(s, n, U, AU, lam));
+  } else {
+    CK(copy_matrix(s, n, n, U, ldu, G, n));
+    CK(rayleigh(s, n, G, AU, lam));
+  }
+  return flops;
+}
+
 static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
                       double* dwi, double* dU, int ldu, const eig_params_t& p,
                       eig_solve_info_t* info) {
@@ -580,10 +714,14 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
   const bool verbose = venv && venv[0] == '1';
   Arena meas(nullptr);
   SolveWork w;
-  const size_t need = carve_solve(meas, n, w);
+  const size_t need = carve_solve(meas, n, w, p.prec);
   ensure_ws(h, need);
   Arena arena(h->ws);
-  carve_solve(arena, n, w);
+  carve_solve(arena, n, w, p.prec);
+  // split precision: FP32-level iterates, so the R-test and the split test
+  // are read at that level; the FP64 refinement at the end restores accuracy
+  eig_params_t pp = p;
+  if (split_mode(p.prec)) pp.split_tol = std::max(p.split_tol, 1e-3);
   eig_solve_info_t inf;
   std::memset(&inf, 0, sizeof(inf));
   // working copy of A; global U = I
@@ -638,11 +776,11 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
         rg.c_or_sigma = sigma;
         rg.r_or_s = sc;
       }
-      const double tau_m = tau > 0 ? tau : default_tau(m);
-      IRSOut ir = run_irs(h, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit);
+      const double tau_m = tau > 0 ? tau : (split_mode(p.prec) ? 1e-5 : default_tau(m));
+      IRSOut ir = run_irs(h, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(p.prec));
       inf.total_iters += ir.iters;
       inf.flops += ir.iters * flops_irs_iter(m);
-      SplitOut so = run_split(h, w.split, m, ir.Ap, ir.Bp, m, An, n, sym, nd.id, attempt, p,
+      SplitOut so = run_split(h, w.split, m, ir.Ap, ir.Bp, m, An, n, sym, nd.id, attempt, pp,
                               ir.converged, hscores);
       inf.flops += (so.draw + 1) * (flops_grurv(m) + flops_similarity(m));
       if (verbose)
@@ -722,6 +860,10 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
       status = EIG_NO_CONVERGENCE;
       h->err = "a leaf solver did not converge";
     }
+    if (sym && split_mode(p.prec)) {
+      inf.flops += refine_symmetric(h, n, dA, lda, dU, ldu, w.wtmp, w.irs.Aj, w.irs.An, w.irs.Bj,
+                                    w.irs.Bn, w.split.nbits);
+    }
     if (sym) {
       // eigenvalues ascending with their vectors
       std::vector<double> wv(n);
@@ -763,7 +905,8 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
 }
 
 static void check_params(eig_handle_t h, const eig_params_t& p) {
-  if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0) {
+  if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0 ||
+      (p.prec != EIG_FP64 && p.prec != EIG_SPLIT_BF16X3)) {
     h->err = "invalid eig_params_t";
     throw Fail{EIG_ERR_ARG};
   }
@@ -869,11 +1012,13 @@ int eig_divide_step(eig_handle_t h, int n, double* dA, int lda, double* dB, int 
   check_params(h, p);
   Arena meas(nullptr);
   IRSWork w;
-  ensure_ws(h, carve_irs(meas, n, w));
+  ensure_ws(h, carve_irs(meas, n, w, p.prec));
   Arena a(h->ws);
-  carve_irs(a, n, w);
-  const double tau = p.tau > 0 ? p.tau : (p.tau < 0 ? -1.0 : default_tau(n));
-  IRSOut o = run_irs(h, w, n, dA, lda, dB, ldb, *region, tau, p.maxit);
+  carve_irs(a, n, w, p.prec);
+  const double tau = p.tau > 0 ? p.tau
+                               : (p.tau < 0 ? -1.0 : (split_mode(p.prec) ? 1e-5 : default_tau(n)));
+  IRSOut o = run_irs(h, w, n, dA, lda, dB, ldb, *region, tau, p.maxit,
+                     split_mode(p.prec) && p.tau >= 0);
   cudaStream_t s = h->stream;
   CK(copy_matrix(s, n, n, o.Ap, n, dA, lda));
   if (dB) CK(copy_matrix(s, n, n, o.Bp, n, dB, ldb));
@@ -935,9 +1080,9 @@ int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int l
   check_params(h, p);
   Arena meas(nullptr);
   SplitWork w;
-  ensure_ws(h, carve_split(meas, n, w));
+  ensure_ws(h, carve_split(meas, n, w, p.prec));
   Arena a(h->ws);
-  carve_split(a, n, w);
+  carve_split(a, n, w, p.prec);
   std::vector<double> hs;
   SplitOut so = run_split(h, w, n, dAp, dBp, ldp, dA, lda, symmetric != 0, stream, attempt, p,
                           true, hs);
@@ -1059,6 +1204,29 @@ int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha, 
   CK(gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, sp,
           reinterpret_cast<double*>(h->ws)));
   CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_gemm_split(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+                   const double* dA, int lda, const double* dB, int ldb, double beta, double* dC,
+                   int ldc) {
+  API_BEGIN
+  REQUIRE(m >= 0 && n >= 0 && k >= 0 && dC && ldc >= std::max(m, 1), "invalid arguments");
+  REQUIRE(lda >= std::max(1, ta ? k : m) && ldb >= std::max(1, tb ? n : k), "invalid ld");
+  const size_t need = tc_gemm_workspace_bytes(m, n, k) + 256;
+  ensure_ws(h, need);
+  int* derr = reinterpret_cast<int*>(h->ws + need - 256);
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
+  CK(tc_gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, h->ws,
+             derr));
+  int* hf = static_cast<int*>(pinned(h, 64));
+  CK(cudaMemcpyAsync(hf, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (*hf) {
+    h->err = "tensor-core GEMM: a bounded wait timed out (flag " + std::to_string(*hf) + ")";
+    return EIG_ERR_CUDA;
+  }
   return EIG_OK;
   API_END
 }

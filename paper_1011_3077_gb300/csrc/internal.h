@@ -35,9 +35,20 @@ int panel_max_width(int m);
 void panel_init();   // once per device: picks the largest usable cluster size
 
 // Out = op(T) * (sum_z partial[z]) for a jb x n block (op = T^T if trans).
-// With splits == 1 `partial` is read directly.
+// With splits == 1 `partial` is read directly; with in_trans the (single)
+// input is stored as its n x jb transpose.
 cudaError_t reduce_trmm(cudaStream_t s, int jb, int n, const double* partial, int splits,
-                        const double* T, int ldt, bool trans, double* out);
+                        const double* T, int ldt, bool trans, double* out, bool in_trans = false);
+
+// ------------------------------------------------------------- tc_gemm.cu
+// Split-BF16 (three-term) GEMM on tcgen05 tensor cores, FP64 in and out,
+// FP32-level accuracy.  `ws` must hold tc_gemm_workspace_bytes(m, n, k)
+// (the BF16 planes of both operands); *err gets a nonzero bit if a bounded
+// wait in the kernel timed out.
+size_t tc_gemm_workspace_bytes(int m, int n, int k);
+cudaError_t tc_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                    int ldc, void* ws, int* err);
 
 // ------------------------------------------------------------- misc.cu
 cudaError_t fill_identity_block(cudaStream_t s, int rows, int cols, double* Y, int ldy,
@@ -77,6 +88,15 @@ cudaError_t diag_gershgorin(cudaStream_t s, int n, const double* A, int lda, dou
 cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, double rel_tol,
                        int* rank);
 cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const double* wi);
+// FP64 refinement of a symmetric eigendecomposition (n x n packed operands)
+cudaError_t oa_diag(cudaStream_t s, int n, const double* G, const double* S, double* lam,
+                    unsigned long long* maxabs);
+cudaError_t oa_offmax(cudaStream_t s, int n, const double* G, const double* S,
+                      unsigned long long* bits);
+cudaError_t oa_correction(cudaStream_t s, int n, const double* G, const double* S,
+                          const double* lam, double delta, double* E);
+cudaError_t rayleigh(cudaStream_t s, int n, const double* X, const double* AX, double* lam);
+cudaError_t add_inplace(cudaStream_t s, size_t count, double* X, const double* D);
 
 // ------------------------------------------------------------- leaves.cu
 // Batched leaves: leaf i is the m_i x m_i block at A + off_i*(lda+1) of the

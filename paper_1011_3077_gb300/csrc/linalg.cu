@@ -9,6 +9,7 @@
 // The reflector convention maps x to +||x|| e1 (R with non-negative diagonal,
 // Golub-Van Loan Sec. 5.1), so R_j of the stacked matrix is unique (it is the
 // Cholesky factor of A_j^T A_j + B_j^T B_j) and can be compared elementwise.
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,22 +21,29 @@ namespace cg = cooperative_groups;
 namespace eigdc {
 
 // ------------------------------------------------------------------ GEMM
-// 64x64 output tile, K step 16, 256 threads, 4x4 outputs per thread.  FP64
-// on GB300 is issue-bound on the DFMA pipe (the data moved per tile is a few
-// GB/s per SM), so the tile only has to keep that pipe fed; double-buffered
-// shared memory with a register prefetch of the next K step does that.
-constexpr int GBM = 64, GBN = 64, GBK = 16, GTHREADS = 256;
+// BM x BN output tile (64 x 64, or 32 x 128 for the M <= 32 products V^T C of
+// the compact-WY updates), K step 16, 256 threads, 4x4 outputs per thread.
+// FP64 on GB300 is issue-bound on the DFMA pipe (the data moved per tile is a
+// few GB/s per SM), so the tile only has to keep that pipe fed and waste no
+// FMAs on padding; double-buffered shared memory with a register prefetch of
+// the next K step does that.
+constexpr int GBK = 16, GTHREADS = 256;
 
-template <bool TA, bool TB>
+template <bool TA, bool TB, int BM, int BN>
 __global__ void __launch_bounds__(GTHREADS)
 dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, int lda,
              const double* __restrict__ B, int ldb, double beta, double* __restrict__ C,
              int ldc, int kchunk, double* __restrict__ partial) {
-  __shared__ double As[2][GBK][GBM + 1];
-  __shared__ double Bs[2][GBK][GBN + 1];
+  constexpr int TXD = BM / 4;              // threads along M
+  constexpr int TYD = GTHREADS / TXD;      // threads along N
+  static_assert(TYD * 4 == BN, "tile shape");
+  constexpr int NA = BM * GBK / GTHREADS;  // A elements per thread per K step
+  constexpr int NB = BN * GBK / GTHREADS;
+  __shared__ double As[2][GBK][BM + 1];
+  __shared__ double Bs[2][GBK][BN + 1];
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+  const int tx = tid % TXD, ty = tid / TXD;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   double acc[4][4];
@@ -43,14 +51,23 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, in
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  double ra[4], rb[4];
+  double ra[NA], rb[NB];
 
+  auto a_index = [&](int r, int& m, int& k) {
+    const int idx = tid + GTHREADS * r;
+    if (!TA) { m = idx % BM; k = idx / BM; }
+    else { k = idx % GBK; m = idx / GBK; }
+  };
+  auto b_index = [&](int r, int& n, int& k) {
+    const int idx = tid + GTHREADS * r;
+    if (!TB) { k = idx % GBK; n = idx / GBK; }
+    else { n = idx % BN; k = idx / BN; }
+  };
   auto loadA = [&](int k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < NA; ++r) {
       int m, k;
-      if (!TA) { m = tid & 63; k = (tid >> 6) + 4 * r; }
-      else { k = tid & 15; m = (tid >> 4) + 16 * r; }
+      a_index(r, m, k);
       const int gm = m0 + m, gk = k0 + k;
       double v = 0.0;
       if (gm < M && gk < kend) v = TA ? A[gk + (size_t)gm * lda] : A[gm + (size_t)gk * lda];
@@ -59,19 +76,17 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, in
   };
   auto storeA = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < NA; ++r) {
       int m, k;
-      if (!TA) { m = tid & 63; k = (tid >> 6) + 4 * r; }
-      else { k = tid & 15; m = (tid >> 4) + 16 * r; }
+      a_index(r, m, k);
       As[buf][k][m] = ra[r];
     }
   };
   auto loadB = [&](int k0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < NB; ++r) {
       int n, k;
-      if (!TB) { k = tid & 15; n = (tid >> 4) + 16 * r; }
-      else { n = tid & 63; k = (tid >> 6) + 4 * r; }
+      b_index(r, n, k);
       const int gn = n0 + n, gk = k0 + k;
       double v = 0.0;
       if (gn < N && gk < kend) v = TB ? B[gn + (size_t)gk * ldb] : B[gk + (size_t)gn * ldb];
@@ -80,10 +95,9 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, in
   };
   auto storeB = [&](int buf) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < NB; ++r) {
       int n, k;
-      if (!TB) { k = tid & 15; n = (tid >> 4) + 16 * r; }
-      else { n = tid & 63; k = (tid >> 6) + 4 * r; }
+      b_index(r, n, k);
       Bs[buf][k][n] = rb[r];
     }
   };
@@ -106,9 +120,9 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, in
     for (int kk = 0; kk < GBK; ++kk) {
       double a[4], b[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tx + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tx + TXD * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][ty + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][ty + TYD * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -123,11 +137,11 @@ dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A, in
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + tx + 16 * i;
+    const int gm = m0 + tx + TXD * i;
     if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + ty + 16 * j;
+      const int gn = n0 + ty + TYD * j;
       if (gn >= N) continue;
       if (partial) {
         partial[(size_t)blockIdx.z * M * N + gm + (size_t)gn * M] = alpha * acc[i][j];
@@ -152,16 +166,53 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const double* __r
   C[i + (size_t)j * ldc] = s;
 }
 
+static inline bool narrow_tile(int m) { return m <= 32; }
+
+// K-chunk count: aim at whole waves of 2 CTAs per SM on the 152 SMs (the 4x4
+// register tile allows two resident CTAs), each chunk at least 128 of K.
 int gemm_choose_splits(int m, int n, int k) {
-  const int tiles = ((m + GBM - 1) / GBM) * ((n + GBN - 1) / GBN);
-  const int target = 2 * 152;
-  if (tiles >= target) return 1;
-  int s = (target + tiles - 1) / tiles;
-  const int maxk = k / 256;   // at least 256 of K per chunk
-  if (s > maxk) s = maxk;
-  if (s > 16) s = 16;
-  if (s < 1) s = 1;
-  return s;
+  const int bm = narrow_tile(m) ? 32 : 64, bn = narrow_tile(m) ? 128 : 64;
+  const int tiles = ((m + bm - 1) / bm) * ((n + bn - 1) / bn);
+  const int wave = 2 * 152;
+  if (tiles >= wave) return 1;
+  const int maxk = std::max(1, std::min(32, k / 128));
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= maxk; ++s) {
+    const long ctas = (long)tiles * s;
+    const long waves = (ctas + wave - 1) / wave;
+    // useful fraction of the issued waves, lightly favouring fewer chunks
+    const double eff = (double)ctas / (double)(waves * wave) - 0.002 * s;
+    if (eff > best_eff) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+template <bool TA, bool TB>
+static void launch_dgemm(cudaStream_t s, int m, int n, int k, int splits, int kchunk, double alpha,
+                         const double* A, int lda, const double* B, int ldb, double beta,
+                         double* C, int ldc, double* part) {
+  note_launches(1);
+  if (narrow_tile(m)) {
+    dim3 grid((m + 31) / 32, (n + 127) / 128, splits);
+    dgemm_kernel<TA, TB, 32, 128><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta,
+                                                             C, ldc, kchunk, part);
+  } else {
+    dim3 grid((m + 63) / 64, (n + 63) / 64, splits);
+    dgemm_kernel<TA, TB, 64, 64><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta,
+                                                           C, ldc, kchunk, part);
+  }
+}
+
+static int effective_splits(int k, int splits, int& kchunk) {
+  if (splits < 1) splits = 1;
+  kchunk = (k + splits - 1) / splits;
+  kchunk = ((kchunk + GBK - 1) / GBK) * GBK;
+  if (kchunk < GBK) kchunk = GBK;
+  return k > 0 ? (k + kchunk - 1) / kchunk : 1;
 }
 
 cudaError_t gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
@@ -169,21 +220,13 @@ cudaError_t gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double a
                  int ldc, int splits, double* partial) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (splits < 1 || partial == nullptr) splits = 1;
-  int kchunk = (k + splits - 1) / splits;
-  kchunk = ((kchunk + GBK - 1) / GBK) * GBK;
-  if (kchunk < GBK) kchunk = GBK;
-  splits = k > 0 ? (k + kchunk - 1) / kchunk : 1;
-  dim3 grid((m + GBM - 1) / GBM, (n + GBN - 1) / GBN, splits);
+  int kchunk;
+  splits = effective_splits(k, splits, kchunk);
   double* part = splits > 1 ? partial : nullptr;
-  note_launches(1);
-  if (!ta && !tb)
-    dgemm_kernel<false, false><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, part);
-  else if (ta && !tb)
-    dgemm_kernel<true, false><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, part);
-  else if (!ta && tb)
-    dgemm_kernel<false, true><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, part);
-  else
-    dgemm_kernel<true, true><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, part);
+  if (!ta && !tb) launch_dgemm<false, false>(s, m, n, k, splits, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, part);
+  else if (ta && !tb) launch_dgemm<true, false>(s, m, n, k, splits, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, part);
+  else if (!ta && tb) launch_dgemm<false, true>(s, m, n, k, splits, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, part);
+  else launch_dgemm<true, true>(s, m, n, k, splits, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const size_t total = (size_t)m * n;
@@ -195,17 +238,10 @@ cudaError_t gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double a
 int gemm_partials(cudaStream_t s, bool ta, int m, int n, int k, const double* A, int lda,
                   const double* B, int ldb, int splits, double* partial) {
   if (m <= 0 || n <= 0) return 0;
-  if (splits < 1) splits = 1;
-  int kchunk = (k + splits - 1) / splits;
-  kchunk = ((kchunk + GBK - 1) / GBK) * GBK;
-  if (kchunk < GBK) kchunk = GBK;
-  splits = k > 0 ? (k + kchunk - 1) / kchunk : 1;
-  dim3 grid((m + GBM - 1) / GBM, (n + GBN - 1) / GBN, splits);
-  note_launches(1);
-  if (ta)
-    dgemm_kernel<true, false><<<grid, GTHREADS, 0, s>>>(m, n, k, 1.0, A, lda, B, ldb, 0.0, nullptr, m, kchunk, partial);
-  else
-    dgemm_kernel<false, false><<<grid, GTHREADS, 0, s>>>(m, n, k, 1.0, A, lda, B, ldb, 0.0, nullptr, m, kchunk, partial);
+  int kchunk;
+  splits = effective_splits(k, splits, kchunk);
+  if (ta) launch_dgemm<true, false>(s, m, n, k, splits, kchunk, 1.0, A, lda, B, ldb, 0.0, nullptr, m, partial);
+  else launch_dgemm<false, false>(s, m, n, k, splits, kchunk, 1.0, A, lda, B, ldb, 0.0, nullptr, m, partial);
   if (cudaGetLastError() != cudaSuccess) return -1;
   return splits;
 }
@@ -294,28 +330,33 @@ panel_qr_kernel(int m, int jb, double* __restrict__ P, int ldp, double* __restri
       sc->red_sig[par][1] = (c >= r0 && c < r0 + rcount) ? colc[c - r0] : 0.0;
     }
     cluster.sync();
-    // ---- B: combine in rank order, form the reflector
-    if (tid == 0) {
-      double sigma = 0.0, x0 = 0.0;
-      for (int q = 0; q < CS; ++q) {
-        const double* rq = cluster.map_shared_rank(&sc->red_sig[0][0], q);
-        sigma += rq[par * 2 + 0];
-        x0 += rq[par * 2 + 1];
+    // ---- B: combine the CS partials (lane q reads rank q; fixed shuffle tree,
+    //      so every CTA gets bit-identical scalars), form the reflector
+    if (warp == 0) {
+      double sg = 0.0, xv = 0.0;
+      if (lane < CS) {
+        const double* rq = cluster.map_shared_rank(&sc->red_sig[0][0], lane);
+        sg = rq[par * 2 + 0];
+        xv = rq[par * 2 + 1];
       }
-      double beta, mu, v0;
-      if (sigma == 0.0) {
-        v0 = 0.0;                          // v = e1 (nothing below the pivot)
-        if (x0 >= 0.0) { beta = 0.0; mu = x0; }
-        else { beta = 2.0; mu = -x0; }
-      } else {
-        mu = sqrt(x0 * x0 + sigma);
-        v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
-        beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+      const double sigma = warp_sum(sg);
+      const double x0 = warp_sum(xv);
+      if (lane == 0) {
+        double beta, mu, v0;
+        if (sigma == 0.0) {
+          v0 = 0.0;                          // v = e1 (nothing below the pivot)
+          if (x0 >= 0.0) { beta = 0.0; mu = x0; }
+          else { beta = 2.0; mu = -x0; }
+        } else {
+          mu = sqrt(x0 * x0 + sigma);
+          v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+          beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        }
+        sc->bc[0] = beta;
+        sc->bc[1] = mu;
+        sc->bc[2] = v0;
+        sc->taus[c] = beta;
       }
-      sc->bc[0] = beta;
-      sc->bc[1] = mu;
-      sc->bc[2] = v0;
-      sc->taus[c] = beta;
     }
     __syncthreads();
     const double beta = sc->bc[0];
@@ -348,13 +389,23 @@ panel_qr_kernel(int m, int jb, double* __restrict__ P, int ldp, double* __restri
       sc->red_dot[par][tid] = t;
     }
     cluster.sync();
-    // ---- C: combine dots in rank order, update, extend T
+    // ---- C: combine dots (thread (k, g) reads ranks g and g + 8 in parallel,
+    //      then a fixed-order sum over g), update, extend T
+    {
+      const int k = lane, g = warp;
+      double t = 0.0;
+      if (k < jb) {
+        for (int q = g; q < CS; q += PQ_GROUPS) {
+          const double* rq = cluster.map_shared_rank(&sc->red_dot[0][0], q);
+          t += rq[par * PQ_MAXJB + k];
+        }
+      }
+      sc->grp[g][k] = t;
+    }
+    __syncthreads();
     if (tid < jb) {
       double t = 0.0;
-      for (int q = 0; q < CS; ++q) {
-        const double* rq = cluster.map_shared_rank(&sc->red_dot[0][0], q);
-        t += rq[par * PQ_MAXJB + tid];
-      }
+      for (int g = 0; g < PQ_GROUPS; ++g) t += sc->grp[g][tid];
       sc->dk[tid] = t;
     }
     __syncthreads();
@@ -470,7 +521,8 @@ cudaError_t panel_qr(cudaStream_t s, int m, int jb, double* P, int ldp, double* 
 // (lower) for Q^T C, T (upper) for Q C.  Eight columns per CTA.
 __global__ void __launch_bounds__(256)
 reduce_trmm_kernel(int jb, int n, const double* __restrict__ partial, int splits,
-                   const double* __restrict__ T, int ldt, int trans, double* __restrict__ out) {
+                   const double* __restrict__ T, int ldt, int trans, int in_trans,
+                   double* __restrict__ out) {
   __shared__ double Ts[PQ_MAXJB][PQ_MAXJB + 1];
   __shared__ double Ws[PQ_MAXJB][9];
   const int tid = threadIdx.x;
@@ -482,8 +534,12 @@ reduce_trmm_kernel(int jb, int n, const double* __restrict__ partial, int splits
   const int col = blockIdx.x * 8 + cc;
   if (i < jb && col < n) {
     double s = 0.0;
-    const size_t stride = (size_t)jb * n;
-    for (int z = 0; z < splits; ++z) s += partial[(size_t)z * stride + i + (size_t)col * jb];
+    if (in_trans) {
+      s = partial[col + (size_t)i * n];       // input stored n x jb (the transpose)
+    } else {
+      const size_t stride = (size_t)jb * n;
+      for (int z = 0; z < splits; ++z) s += partial[(size_t)z * stride + i + (size_t)col * jb];
+    }
     Ws[i][cc] = s;
   }
   __syncthreads();
@@ -499,10 +555,11 @@ reduce_trmm_kernel(int jb, int n, const double* __restrict__ partial, int splits
 }
 
 cudaError_t reduce_trmm(cudaStream_t s, int jb, int n, const double* partial, int splits,
-                        const double* T, int ldt, bool trans, double* out) {
+                        const double* T, int ldt, bool trans, double* out, bool in_trans) {
   if (n <= 0) return cudaSuccess;
   note_launches(1);
-  reduce_trmm_kernel<<<(n + 7) / 8, 256, 0, s>>>(jb, n, partial, splits, T, ldt, trans ? 1 : 0, out);
+  reduce_trmm_kernel<<<(n + 7) / 8, 256, 0, s>>>(jb, n, partial, splits, T, ldt, trans ? 1 : 0,
+                                                 in_trans ? 1 : 0, out);
   return cudaGetLastError();
 }
 

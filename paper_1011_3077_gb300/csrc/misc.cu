@@ -492,4 +492,121 @@ cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const do
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- refinement
+// One FP64 refinement step for a symmetric eigendecomposition from approximate
+// eigenvectors X (Ogita and Aishima, "Iterative refinement for symmetric
+// eigenvalue decomposition", 2018): with G = X^T X and S = X^T A X,
+//   lam_i = s_ii / g_ii,  R = I - G,
+//   E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) if |lam_i - lam_j| > delta,
+//   E_ij = r_ij / 2 otherwise (and on the diagonal),
+// and X <- X + X E.
+__global__ void oa_diag_kernel(int n, const double* __restrict__ G, const double* __restrict__ S,
+                               double* __restrict__ lam, unsigned long long* maxabs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l = S[i + (size_t)i * n] / G[i + (size_t)i * n];
+  lam[i] = l;
+  atomic_max_nonneg(maxabs, fabs(l));
+}
+
+// max_{i != j} |s_ij| -> bits[0], max_{i,j} |r_ij| -> bits[1]
+__global__ void oa_offmax_kernel(int n, const double* __restrict__ G, const double* __restrict__ S,
+                                 unsigned long long* bits) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double so = 0.0, ro = 0.0;
+  if (idx < (size_t)n * n) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    const double r = ((i == j) ? 1.0 : 0.0) - G[idx];
+    ro = fabs(r);
+    if (i != j) so = fabs(S[idx]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    so = fmax(so, __shfl_xor_sync(0xffffffffu, so, o));
+    ro = fmax(ro, __shfl_xor_sync(0xffffffffu, ro, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&bits[0], so);
+    atomic_max_nonneg(&bits[1], ro);
+  }
+}
+
+// Pair (i, j) counts as separated when |lam_i - lam_j| > delta and the
+// first-order correction stays below 1/64 (reading: a per-pair form of the
+// paper's global delta, so one close pair does not stop the others).
+__global__ void oa_correction_kernel(int n, const double* __restrict__ G,
+                                     const double* __restrict__ S, const double* __restrict__ lam,
+                                     double delta, double* __restrict__ E) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * n) return;
+  const int i = (int)(idx % n), j = (int)(idx / n);
+  const double r = ((i == j) ? 1.0 : 0.0) - G[idx];
+  double e = 0.5 * r;
+  if (i != j) {
+    const double num = S[idx] + lam[j] * r;
+    const double gap = lam[j] - lam[i];
+    if (fabs(gap) > delta && fabs(gap) > 64.0 * fabs(num)) e = num / gap;
+  }
+  E[idx] = e;
+}
+
+// lam_i = (x_i . (A x_i)) / (x_i . x_i), one warp per column
+__global__ void add_inplace_kernel(size_t count, double* __restrict__ X, const double* __restrict__ D) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < count) X[idx] += D[idx];
+}
+
+cudaError_t add_inplace(cudaStream_t s, size_t count, double* X, const double* D) {
+  if (count == 0) return cudaSuccess;
+  note_launches(1);
+  add_inplace_kernel<<<blocks_for(count, 256), 256, 0, s>>>(count, X, D);
+  return cudaGetLastError();
+}
+
+__global__ void rayleigh_kernel(int n, const double* __restrict__ X, const double* __restrict__ AX,
+                                double* __restrict__ lam) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  double num = 0.0, den = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double x = X[i + (size_t)warp * n];
+    num = fma(x, AX[i + (size_t)warp * n], num);
+    den = fma(x, x, den);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if (lane == 0) lam[warp] = num / den;
+}
+
+cudaError_t oa_diag(cudaStream_t s, int n, const double* G, const double* S, double* lam,
+                    unsigned long long* maxabs) {
+  note_launches(1);
+  oa_diag_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, G, S, lam, maxabs);
+  return cudaGetLastError();
+}
+
+cudaError_t oa_offmax(cudaStream_t s, int n, const double* G, const double* S,
+                      unsigned long long* bits) {
+  note_launches(1);
+  oa_offmax_kernel<<<blocks_for((size_t)n * n, 256), 256, 0, s>>>(n, G, S, bits);
+  return cudaGetLastError();
+}
+
+cudaError_t oa_correction(cudaStream_t s, int n, const double* G, const double* S,
+                          const double* lam, double delta, double* E) {
+  note_launches(1);
+  oa_correction_kernel<<<blocks_for((size_t)n * n, 256), 256, 0, s>>>(n, G, S, lam, delta, E);
+  return cudaGetLastError();
+}
+
+cudaError_t rayleigh(cudaStream_t s, int n, const double* X, const double* AX, double* lam) {
+  note_launches(1);
+  rayleigh_kernel<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(n, X, AX, lam);
+  return cudaGetLastError();
+}
+
 }  // namespace eigdc

@@ -31,6 +31,8 @@ EIG_NONFINITE = 4
 EIG_REGION_UNIT_CIRCLE = 0
 EIG_REGION_CIRCLE = 1
 EIG_REGION_LINE = 2
+EIG_FP64 = 0
+EIG_SPLIT_BF16X3 = 1
 EIG_KIND_SYM = 0
 EIG_KIND_NONSYM = 1
 PURPOSE_HAAR = 4
@@ -91,6 +93,7 @@ _SIGNATURES = {
     "eig_split_test": (_I, [_P, _I, _P, _I, _D, _P, _I, _D, ctypes.POINTER(_I),
                             ctypes.POINTER(_D), _P]),
     "eig_gemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+    "eig_gemm_split": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
 }
 
@@ -243,6 +246,11 @@ def eig_split_test(h, n, dA, lda, normA, dB=None, ldb=0, normB=0.0, want_scores=
 def eig_gemm(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
     return h.check(lib().eig_gemm(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
                                   _ptr(dB), ldb, beta, _ptr(dC), ldc))
+
+
+def eig_gemm_split(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
+    return h.check(lib().eig_gemm_split(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
+                                        _ptr(dB), ldb, beta, _ptr(dC), ldc))
 
 
 def eig_gemm_noalloc(stream, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
