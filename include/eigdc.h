@@ -82,6 +82,8 @@ typedef struct {
   int nb;            /* panel width of the blocked QR (0: automatic) */
   int v_draws;       /* Haar redraws per converged IRS (Theorem 2.1 holds w.h.p.) */
   int root_unit_circle; /* eig_solve nonsymmetric: split the root on |z| = 1 */
+  int workers;       /* eig_solve: host workers (each with its own CUDA stream) that process
+                        independent nodes of the recursion concurrently; 1 = sequential */
 } eig_params_t;
 
 typedef struct {
@@ -107,7 +109,7 @@ typedef struct {
 
 /* Defaults: tau = max(1e-14, 4 sqrt(n) 2^-53) at call time, maxit = 60,
  * split_tol = 1e-12, leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
- * v_draws = 4, root_unit_circle = 1. */
+ * v_draws = 4, root_unit_circle = 1, workers = 8. */
 void eig_default_params(eig_params_t* p);
 
 /* Create a handle bound to CUDA device `device` and stream `stream`
@@ -161,6 +163,20 @@ int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int l
 int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
               double* dwi, double* dU, int ldu, const eig_params_t* params,
               eig_solve_info_t* info);
+
+/* Batched solves of independent problems (the units of parallelism of
+ * Sec. 4.3, here spread over the handle's host workers, each with its own
+ * CUDA stream; problems run largest first, each sequentially inside one
+ * worker).  Arrays are HOST arrays of length count; dA[i], dwr[i], dwi[i]
+ * (NONSYM) and dU[i] are device pointers with the meaning of eig_solve.
+ * status[i] receives each problem's return code and infos[i] (if infos !=
+ * NULL) its info.  Returns a negative code only for argument or system
+ * errors; numerical outcomes are reported per problem.  Results are
+ * identical to separate eig_solve calls with workers = 1. */
+int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double* const* dA,
+                      const int* lda, double* const* dwr, double* const* dwi, double* const* dU,
+                      const int* ldu, const eig_params_t* params, int* status,
+                      eig_solve_info_t* infos);
 
 /* ------------------------------------------------------ building blocks
  * The steps of the path, exposed so each can be checked on its own. */

@@ -14,7 +14,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -46,6 +51,7 @@ struct eig_handle_s {
   int lastR_n = 0;
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
+  std::vector<eig_handle_s*> workers;   // sub-handles of the node / batch executor
 };
 
 namespace {
@@ -63,6 +69,16 @@ struct Fail {
                + __FILE__ + ":" + std::to_string(__LINE__);                   \
       throw Fail{EIG_ERR_CUDA};                                               \
     }                                                                         \
+  } while (0)
+
+#define CK2(hh, call)                                                          \
+  do {                                                                         \
+    cudaError_t e__ = (call);                                                  \
+    if (e__ != cudaSuccess) {                                                  \
+      (hh)->err = std::string("CUDA error: ") + cudaGetErrorString(e__) + " at " \
+                  + __FILE__ + ":" + std::to_string(__LINE__);                 \
+      throw Fail{EIG_ERR_CUDA};                                                \
+    }                                                                          \
   } while (0)
 
 static size_t round_up(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -619,31 +635,6 @@ static void choose_shift(const std::vector<double>& diag, double lo, double hi, 
   scale = R;
 }
 
-struct SolveWork {
-  double *Acur, *Unode, *wtmp, *Zleaf, *dtmp, *sortbuf;
-  int* status;
-  LeafDesc* ddesc;
-  IRSWork irs;
-  SplitWork split;
-};
-
-static size_t carve_solve(Arena& a, int n, SolveWork& w, int prec = EIG_FP64) {
-  const size_t start = a.used;
-  const size_t nn = (size_t)n * n;
-  const int maxleaves = n;   // upper bound: every leaf has >= 1 row
-  w.Acur = a.take<double>(nn);
-  w.Unode = a.take<double>(nn);
-  w.wtmp = a.take<double>(2 * (size_t)n + 8);
-  w.Zleaf = a.take<double>((size_t)64 * 64 * std::max(1, std::min(maxleaves, (n + 0) )));
-  w.dtmp = a.take<double>(2 * (size_t)n + 8);
-  w.sortbuf = a.take<double>(nn);
-  w.status = a.take<int>(8);
-  w.ddesc = a.take<LeafDesc>(std::max(1, maxleaves));
-  carve_irs(a, n, w.irs, prec);
-  carve_split(a, n, w.split, prec);
-  return a.used - start;
-}
-
 static double flops_irs_iter(double m) { return 22.0 / 3.0 * m * m * m; }
 static double flops_grurv(double m) { return 12.0 * m * m * m; }
 static double flops_similarity(double m) { return 4.0 * m * m * m; }
@@ -667,7 +658,10 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
   cudaStream_t s = h->stream;
   double flops = 0.0;
   const double u = 0x1p-53;
-  unsigned long long* hb = static_cast<unsigned long long*>(pinned(h, 64));
+  // one pinned staging area: n eigenvalues, then the residual words
+  char* pin = static_cast<char*>(pinned(h, sizeof(double) * ((size_t)n + 16) + 64));
+  double* hl = reinterpret_cast<double*>(pin);
+  unsigned long long* hb = reinterpret_cast<unsigned long long*>(pin + sizeof(double) * ((size_t)n + 8));
   for (int step = 0; step < 6; ++step) {
     CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
     CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
@@ -682,6 +676,10 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
     std::memcpy(&normA, &hb[0], 8);
     std::memcpy(&offS, &hb[1], 8);
     std::memcpy(&maxR, &hb[2], 8);
+    const char* venv = std::getenv("EIGDC_VERBOSE");
+    if (venv && venv[0] == '1')
+      std::fprintf(stderr, "[eigdc] refine step %d: |A| %.3e max|S_offdiag| %.3e max|I - U^T U| %.3e\n",
+                   step, normA, offS, maxR);
     const double floor_ = 8.0 * std::sqrt((double)n) * u;
     if (offS <= floor_ * normA && maxR <= floor_) break;
     CK(oa_correction(s, n, G, S, lam, 64.0 * u * normA, E));
@@ -693,15 +691,317 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
       CK(add_matrices(s, n, n, U, ldu, AU, n, U, ldu));
     }
   }
-  CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
-  flops += 2.0 * (double)n * n * n;
-  if (ldu == n) {
-    CK(rayleigh(s, n, U, AU, lam));
-  } else {
-    CK(copy_matrix(s, n, n, U, ldu, G, n));
-    CK(rayleigh(s, n, G, AU, lam));
+  // Clusters: pairs the first-order correction leaves coupled are resolved
+  // by diagonalising S = U^T A U on each cluster block (cyclic Jacobi).
+  // Order U by the current eigenvalue estimates so clusters are contiguous.
+  {
+    std::vector<double> lv(n);
+    CK(cudaMemcpyAsync(hl, lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::memcpy(lv.data(), hl, sizeof(double) * n);
+    std::vector<int> perm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return lv[a] < lv[b]; });
+    int* dperm = reinterpret_cast<int*>(E);
+    CK(cudaMemcpyAsync(dperm, perm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    const size_t t = (size_t)n * n;
+    note_launches(1);
+    permute_columns_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(n, U, ldu, dperm, G, n);
+    CK(cudaGetLastError());
+    CK(copy_matrix(s, n, n, G, n, U, ldu));
+    CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
+    CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, AU, n, 0.0, S, n));
+    flops += 4.0 * (double)n * n * n;
+    // lam = diag(S) (the radii output is not used)
+    CK(diag_gershgorin(s, n, S, n, lam, E));
+    CK(cudaMemsetAsync(dbits, 0, 3 * sizeof(unsigned long long), s));
+    CK(oa_offmax(s, n, G, S, &dbits[1]));   // max off-diagonal |S| (the G part is unused)
+    CK(cudaMemcpyAsync(hb, dbits, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hl, lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double offS;
+    std::memcpy(&offS, &hb[1], 8);
+    std::memcpy(lv.data(), hl, sizeof(double) * n);
+    double normA = 0.0;
+    for (double x : lv) normA = std::max(normA, std::fabs(x));
+    const double dclu = 64.0 * std::max(offS, (double)n * u * normA);
+    std::vector<LeafDesc> clusters;
+    for (int i = 0; i < n;) {
+      int j = i + 1;
+      while (j < n && lv[j] - lv[j - 1] <= dclu && j - i < 64) ++j;
+      if (j - i >= 2) clusters.push_back(LeafDesc{i, j - i, (int)clusters.size() * 64 * 64});
+      i = j;
+    }
+    // descriptors in AU, the 64 x 64 vector slots in G (both free here),
+    // processed in chunks that fit G
+    const size_t cap = std::max<size_t>(1, ((size_t)n * n) / 4096);
+    for (size_t c0 = 0; c0 < clusters.size(); c0 += cap) {
+      const size_t cnt = std::min(cap, clusters.size() - c0);
+      std::vector<LeafDesc> chunk(clusters.begin() + c0, clusters.begin() + c0 + cnt);
+      for (size_t q = 0; q < cnt; ++q) chunk[q].zoff = (int)(q * 4096);
+      LeafDesc* dd = reinterpret_cast<LeafDesc*>(AU);
+      CK(cudaMemcpyAsync(dd, chunk.data(), sizeof(LeafDesc) * cnt, cudaMemcpyHostToDevice, s));
+      int* dstat = reinterpret_cast<int*>(&dbits[4]);
+      CK(cudaMemsetAsync(dstat, 0, sizeof(int), s));
+      CK(jacobi_leaves(s, (int)cnt, dd, S, n, lam, G, dstat));
+      CK(apply_leaf_vectors(s, (int)cnt, dd, n, U, ldu, U, ldu, G));
+      CK(cudaStreamSynchronize(s));
+    }
+    const char* venv = std::getenv("EIGDC_VERBOSE");
+    if (venv && venv[0] == '1')
+      std::fprintf(stderr, "[eigdc] refine clusters: %zu (threshold %.3e, max|S_offdiag| %.3e)\n",
+                   clusters.size(), dclu, offS);
   }
+  // final orthogonalisation without eigen-corrections (no division by gaps,
+  // so no amplification of rounding): X <- X + X (I - X^T X) / 2
+  CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
+  CK(oa_correction(s, n, G, S, lam, INFINITY, E));   // every pair takes r_ij / 2
+  CK(gemm(s, false, false, n, n, n, 1.0, U, ldu, E, n, 0.0, AU, n));
+  if (ldu == n) CK(add_inplace(s, (size_t)n * n, U, AU));
+  else CK(add_matrices(s, n, n, U, ldu, AU, n, U, ldu));
+  flops += 4.0 * (double)n * n * n;
   return flops;
+}
+
+// ---------------------------------------------------------------- solve
+// Per-node scratch: IRS and splitter work for a node of size m, and the
+// n x m panel of U that the node's splitter updates.
+struct NodeWork {
+  IRSWork irs;
+  SplitWork split;
+  double* Unode;
+  double* dtmp;
+};
+
+static size_t carve_node(Arena& a, int n_total, int m, int prec, NodeWork& w) {
+  const size_t start = a.used;
+  carve_irs(a, m, w.irs, prec);
+  carve_split(a, m, w.split, prec);
+  w.Unode = a.take<double>((size_t)n_total * m);
+  w.dtmp = a.take<double>(2 * (size_t)m + 8);
+  return a.used - start;
+}
+
+// Solve-level buffers (leaves, sorting, Schur assembly, refinement).
+struct SolveMain {
+  double *Acur, *wtmp, *Zleaf, *dtmp, *sortbuf, *Tbuf, *gpart;
+  double *G, *AU, *S, *E;   // refinement scratch (split precision, symmetric)
+  unsigned long long* bits;
+  int* status;
+  LeafDesc* ddesc;
+};
+
+static size_t carve_main(Arena& a, int n, bool refine, SolveMain& w) {
+  const size_t start = a.used;
+  const size_t nn = (size_t)n * n;
+  w.Acur = a.take<double>(nn);
+  w.wtmp = a.take<double>(2 * (size_t)n + 8);
+  w.Zleaf = a.take<double>((size_t)64 * 64 * std::max(1, n));
+  w.dtmp = a.take<double>(2 * (size_t)n + 8);
+  w.sortbuf = a.take<double>(nn);
+  w.Tbuf = a.take<double>(nn);
+  w.gpart = a.take<double>(square_partial_doubles(n));
+  w.G = refine ? a.take<double>(nn) : nullptr;
+  w.AU = refine ? a.take<double>(nn) : nullptr;
+  w.S = refine ? a.take<double>(nn) : nullptr;
+  w.E = refine ? a.take<double>(nn) : nullptr;
+  w.bits = a.take<unsigned long long>(8);
+  w.status = a.take<int>(8);
+  w.ddesc = a.take<LeafDesc>(std::max(1, n));
+  return a.used - start;
+}
+
+// State shared by the workers of one solve.
+struct SolveShared {
+  int n = 0, ldu = 0, leaf = 64;
+  bool sym = true, verbose = false;
+  double* Acur = nullptr;
+  double* dU = nullptr;
+  eig_params_t p, pp;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Node> queue;
+  int outstanding = 0;
+  std::vector<LeafDesc> leaves;
+  eig_solve_info_t inf;
+  int status = EIG_OK;
+  std::string err;
+};
+
+// One node of the recursion: attempts (shift, IRS, splitter, split test)
+// until a split is accepted; then U and the node's diagonal block are
+// updated and the two children are queued.  Runs on the worker handle hw;
+// `base` points at scratch of carve_node(n, m) bytes.
+static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
+  cudaStream_t s = hw->stream;
+  const int n = S.n, m = nd.m;
+  const eig_params_t& p = S.p;
+  double* An = S.Acur + nd.off + (size_t)nd.off * n;
+  if (m <= S.leaf) {
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.inf.nodes++;
+    S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
+    S.leaves.push_back(LeafDesc{nd.off, m, (int)S.leaves.size() * 64 * 64});
+    return;
+  }
+  Arena arena(base);
+  NodeWork w;
+  carve_node(arena, n, m, p.prec, w);
+  std::vector<double> diag, hscores;
+  const double tau = p.tau > 0 ? p.tau : -1.0;
+  int attempt = 0, fails = 0;
+  double flops = 0.0;
+  int iters = 0, failed = 0;
+  while (true) {
+    eig_region_t rg;
+    if (!S.sym && p.root_unit_circle && nd.id == ROOT_NODE && attempt == 0) {
+      rg.kind = EIG_REGION_UNIT_CIRCLE;
+      rg.c_or_sigma = 0.0;
+      rg.r_or_s = 1.0;
+    } else {
+      node_diag(hw, S.Acur, n, nd.off, m, diag);
+      double sigma, sc;
+      choose_shift(diag, nd.lo, nd.hi, p.seed, nd.id, attempt, sigma, sc);
+      rg.kind = EIG_REGION_LINE;
+      rg.c_or_sigma = sigma;
+      rg.r_or_s = sc;
+    }
+    const double tau_m = tau > 0 ? tau : (split_mode(p.prec) ? 1e-5 : default_tau(m));
+    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(p.prec));
+    iters += ir.iters;
+    flops += ir.iters * flops_irs_iter(m);
+    SplitOut so = run_split(hw, w.split, m, ir.Ap, ir.Bp, m, An, n, S.sym, nd.id, attempt, S.pp,
+                            ir.converged, hscores);
+    flops += (so.draw + 1) * (flops_grurv(m) + flops_similarity(m));
+    if (S.verbose)
+      std::fprintf(stderr,
+                   "[eigdc] node off=%d m=%d depth=%d attempt=%d region=%d (%.6g, %.6g) "
+                   "iters=%d conv=%d ratio=%.3g k=%d e=%.3g rank=%d draw=%d accepted=%d\n",
+                   nd.off, m, nd.depth, attempt, rg.kind, rg.c_or_sigma, rg.r_or_s, ir.iters,
+                   (int)ir.converged, ir.last_ratio, so.k, so.e, so.rank, so.draw,
+                   (int)so.accepted);
+    if (so.accepted) {
+      const int k = so.k;
+      // U[:, off:off+m] <- U[:, off:off+m] Q ; node block <- A^
+      CK2(hw, gemm(s, false, false, n, m, m, 1.0, S.dU + (size_t)nd.off * S.ldu, S.ldu,
+                   w.split.Ucur, m, 0.0, w.Unode, n));
+      CK2(hw, copy_matrix(s, n, m, w.Unode, n, S.dU + (size_t)nd.off * S.ldu, S.ldu));
+      flops += 2.0 * n * (double)m * m;
+      CK2(hw, copy_matrix(s, m, m, w.split.Ahat, m, An, n));
+      double lo1, hi1, lo2, hi2;
+      double* A11 = An;
+      double* A22 = An + k + (size_t)k * n;
+      if (rg.kind == EIG_REGION_LINE) {
+        lo1 = rg.c_or_sigma;
+        hi1 = nd.hi;
+        lo2 = nd.lo;
+        hi2 = rg.c_or_sigma;
+      } else {
+        gershgorin_interval(hw, A11, n, k, w.dtmp, lo1, hi1);
+        gershgorin_interval(hw, A22, n, m - k, w.dtmp, lo2, hi2);
+      }
+      if (!S.sym) {
+        double g1l, g1h, g2l, g2h;
+        gershgorin_interval(hw, A11, n, k, w.dtmp, g1l, g1h);
+        gershgorin_interval(hw, A22, n, m - k, w.dtmp, g2l, g2h);
+        lo1 = std::max(lo1, g1l);
+        hi1 = std::min(hi1, g1h);
+        lo2 = std::max(lo2, g2l);
+        hi2 = std::min(hi2, g2h);
+        if (lo1 >= hi1) { lo1 = g1l; hi1 = g1h; }
+        if (lo2 >= hi2) { lo2 = g2l; hi2 = g2h; }
+      }
+      CK2(hw, cudaStreamSynchronize(s));   // children may run on other streams
+      std::lock_guard<std::mutex> lock(S.mu);
+      S.inf.nodes++;
+      S.inf.splits++;
+      S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
+      S.inf.total_iters += iters;
+      S.inf.failed_attempts += failed;
+      S.inf.flops += flops;
+      S.queue.push_back(Node{nd.off, k, lo1, hi1, child_node(nd.id, 0), nd.depth + 1});
+      S.queue.push_back(Node{nd.off + k, m - k, lo2, hi2, child_node(nd.id, 1), nd.depth + 1});
+      S.outstanding += 2;
+      S.cv.notify_all();
+      return;
+    }
+    failed++;
+    if (rg.kind == EIG_REGION_LINE && ir.converged) {
+      if (so.rank == 0) nd.hi = rg.c_or_sigma;
+      else if (so.rank == m) nd.lo = rg.c_or_sigma;
+      else fails++;
+    } else {
+      fails++;
+    }
+    attempt++;
+    if (fails > p.max_fail || attempt > 250) {
+      std::lock_guard<std::mutex> lock(S.mu);
+      S.inf.nodes++;
+      S.inf.total_iters += iters;
+      S.inf.failed_attempts += failed;
+      S.inf.flops += flops;
+      if (S.status == EIG_OK) {
+        S.status = EIG_NO_SPLIT;
+        S.err = "no split found for a node of size " + std::to_string(m);
+      }
+      return;
+    }
+  }
+}
+
+// Worker loop: take nodes until the tree is finished or a node failed.
+// With own_ws the node scratch is grown in hw's workspace per node; else
+// `fixed_base` (carved for the root size) is used.
+static void worker_loop(eig_handle_t hw, SolveShared& S, bool own_ws, char* fixed_base) {
+  if (cudaSetDevice(hw->device) != cudaSuccess) {
+    std::lock_guard<std::mutex> lock(S.mu);
+    if (S.status == EIG_OK) { S.status = EIG_ERR_CUDA; S.err = "cudaSetDevice failed"; }
+    S.cv.notify_all();
+    return;
+  }
+  while (true) {
+    Node nd;
+    {
+      std::unique_lock<std::mutex> lock(S.mu);
+      S.cv.wait(lock, [&] { return !S.queue.empty() || S.outstanding == 0 || S.status != EIG_OK; });
+      if (S.status != EIG_OK || S.queue.empty()) return;
+      nd = S.queue.front();
+      S.queue.pop_front();
+    }
+    try {
+      char* base = fixed_base;
+      if (own_ws && nd.m > S.leaf) {
+        Arena meas(nullptr);
+        NodeWork tmp;
+        ensure_ws(hw, carve_node(meas, S.n, nd.m, S.p.prec, tmp));
+        base = hw->ws;
+      }
+      process_node(hw, S, nd, base);
+    } catch (Fail f) {
+      std::lock_guard<std::mutex> lock(S.mu);
+      if (S.status == EIG_OK) {
+        S.status = f.code;
+        S.err = hw->err;
+      }
+    }
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.outstanding--;
+    S.cv.notify_all();
+  }
+}
+
+static void ensure_workers(eig_handle_t h, int count) {
+  while ((int)h->workers.size() < count) {
+    eig_handle_t w = new eig_handle_s();
+    w->device = h->device;
+    if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete w;
+      h->err = "cudaStreamCreate failed";
+      throw Fail{EIG_ERR_CUDA};
+    }
+    h->workers.push_back(w);
+  }
 }
 
 static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
@@ -709,21 +1009,35 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
                       eig_solve_info_t* info) {
   cudaStream_t s = h->stream;
   const bool sym = (kind == EIG_KIND_SYM);
-  const int leaf = std::max(1, std::min(64, p.leaf_size));
+  const bool refine = sym && split_mode(p.prec);
+  const int nworkers = std::max(1, std::min(p.workers, 32));
   const char* venv = std::getenv("EIGDC_VERBOSE");
-  const bool verbose = venv && venv[0] == '1';
+  // scratch: solve-level buffers, plus (single worker) the node scratch for
+  // the root size right behind them
   Arena meas(nullptr);
-  SolveWork w;
-  const size_t need = carve_solve(meas, n, w, p.prec);
-  ensure_ws(h, need);
+  SolveMain w;
+  NodeWork nw;
+  carve_main(meas, n, refine, w);
+  const size_t main_bytes = meas.used;
+  if (nworkers == 1) carve_node(meas, n, n, p.prec, nw);
+  ensure_ws(h, meas.used);
   Arena arena(h->ws);
-  carve_solve(arena, n, w, p.prec);
+  carve_main(arena, n, refine, w);
+  char* node_base = h->ws + main_bytes;
+  SolveShared S;
+  S.n = n;
+  S.ldu = ldu;
+  S.leaf = std::max(1, std::min(64, p.leaf_size));
+  S.sym = sym;
+  S.verbose = venv && venv[0] == '1';
+  S.Acur = w.Acur;
+  S.dU = dU;
+  S.p = p;
   // split precision: FP32-level iterates, so the R-test and the split test
   // are read at that level; the FP64 refinement at the end restores accuracy
-  eig_params_t pp = p;
-  if (split_mode(p.prec)) pp.split_tol = std::max(p.split_tol, 1e-3);
-  eig_solve_info_t inf;
-  std::memset(&inf, 0, sizeof(inf));
+  S.pp = p;
+  if (split_mode(p.prec)) S.pp.split_tol = std::max(p.split_tol, 1e-3);
+  std::memset(&S.inf, 0, sizeof(S.inf));
   // working copy of A; global U = I
   CK(copy_matrix(s, n, n, dA, lda, w.Acur, n));
   CK(fill_identity_block(s, n, n, dU, ldu, 0));
@@ -735,115 +1049,31 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
     CK(cudaStreamSynchronize(s));
     if (*hf) {
       h->err = "input contains NaN or Inf";
-      inf.status = EIG_NONFINITE;
-      if (info) *info = inf;
+      S.inf.status = EIG_NONFINITE;
+      if (info) *info = S.inf;
       return EIG_NONFINITE;
     }
   }
   double lo0, hi0;
   gershgorin_interval(h, w.Acur, n, n, w.dtmp, lo0, hi0);
-  std::vector<Node> stack{Node{0, n, lo0, hi0, ROOT_NODE, 0}};
-  std::vector<LeafDesc> leaves;
-  std::vector<double> diag, hscores;
-  const double tau = p.tau > 0 ? p.tau : -1.0;
-  const int gsplit_max = 1;
-  (void)gsplit_max;
-  int status = EIG_OK;
-  while (!stack.empty() && status == EIG_OK) {
-    Node nd = stack.back();
-    stack.pop_back();
-    inf.nodes++;
-    inf.max_depth = std::max(inf.max_depth, nd.depth);
-    const int m = nd.m;
-    double* An = w.Acur + nd.off + (size_t)nd.off * n;
-    if (m <= leaf) {
-      leaves.push_back(LeafDesc{nd.off, m, (int)leaves.size() * 64 * 64});
-      continue;
-    }
-    int attempt = 0, fails = 0;
-    bool done = false;
-    while (!done) {
-      eig_region_t rg;
-      if (!sym && p.root_unit_circle && nd.id == ROOT_NODE && attempt == 0) {
-        rg.kind = EIG_REGION_UNIT_CIRCLE;
-        rg.c_or_sigma = 0.0;
-        rg.r_or_s = 1.0;
-      } else {
-        node_diag(h, w.Acur, n, nd.off, m, diag);
-        double sigma, sc;
-        choose_shift(diag, nd.lo, nd.hi, p.seed, nd.id, attempt, sigma, sc);
-        rg.kind = EIG_REGION_LINE;
-        rg.c_or_sigma = sigma;
-        rg.r_or_s = sc;
-      }
-      const double tau_m = tau > 0 ? tau : (split_mode(p.prec) ? 1e-5 : default_tau(m));
-      IRSOut ir = run_irs(h, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(p.prec));
-      inf.total_iters += ir.iters;
-      inf.flops += ir.iters * flops_irs_iter(m);
-      SplitOut so = run_split(h, w.split, m, ir.Ap, ir.Bp, m, An, n, sym, nd.id, attempt, pp,
-                              ir.converged, hscores);
-      inf.flops += (so.draw + 1) * (flops_grurv(m) + flops_similarity(m));
-      if (verbose)
-        std::fprintf(stderr,
-                     "[eigdc] node off=%d m=%d depth=%d attempt=%d region=%d (%.6g, %.6g) "
-                     "iters=%d conv=%d ratio=%.3g k=%d e=%.3g rank=%d draw=%d accepted=%d\n",
-                     nd.off, m, nd.depth, attempt, rg.kind, rg.c_or_sigma, rg.r_or_s, ir.iters,
-                     (int)ir.converged, ir.last_ratio, so.k, so.e, so.rank, so.draw,
-                     (int)so.accepted);
-      if (so.accepted) {
-        const int k = so.k;
-        // U[:, off:off+m] <- U[:, off:off+m] Q ; node block <- A^
-        CK(gemm(s, false, false, n, m, m, 1.0, dU + (size_t)nd.off * ldu, ldu, w.split.Ucur, m,
-                0.0, w.Unode, n));
-        CK(copy_matrix(s, n, m, w.Unode, n, dU + (size_t)nd.off * ldu, ldu));
-        inf.flops += 2.0 * n * (double)m * m;
-        CK(copy_matrix(s, m, m, w.split.Ahat, m, An, n));
-        double lo1, hi1, lo2, hi2;
-        double* A11 = An;
-        double* A22 = An + k + (size_t)k * n;
-        if (rg.kind == EIG_REGION_LINE) {
-          lo1 = rg.c_or_sigma;
-          hi1 = nd.hi;
-          lo2 = nd.lo;
-          hi2 = rg.c_or_sigma;
-        } else {
-          gershgorin_interval(h, A11, n, k, w.dtmp, lo1, hi1);
-          gershgorin_interval(h, A22, n, m - k, w.dtmp, lo2, hi2);
-        }
-        if (!sym) {
-          double g1l, g1h, g2l, g2h;
-          gershgorin_interval(h, A11, n, k, w.dtmp, g1l, g1h);
-          gershgorin_interval(h, A22, n, m - k, w.dtmp, g2l, g2h);
-          lo1 = std::max(lo1, g1l);
-          hi1 = std::min(hi1, g1h);
-          lo2 = std::max(lo2, g2l);
-          hi2 = std::min(hi2, g2h);
-          if (lo1 >= hi1) { lo1 = g1l; hi1 = g1h; }
-          if (lo2 >= hi2) { lo2 = g2l; hi2 = g2h; }
-        }
-        inf.splits++;
-        stack.push_back(Node{nd.off + k, m - k, lo2, hi2, child_node(nd.id, 1), nd.depth + 1});
-        stack.push_back(Node{nd.off, k, lo1, hi1, child_node(nd.id, 0), nd.depth + 1});
-        done = true;
-        continue;
-      }
-      inf.failed_attempts++;
-      if (rg.kind == EIG_REGION_LINE && ir.converged) {
-        if (so.rank == 0) nd.hi = rg.c_or_sigma;
-        else if (so.rank == m) nd.lo = rg.c_or_sigma;
-        else fails++;
-      } else {
-        fails++;
-      }
-      attempt++;
-      if (fails > p.max_fail || attempt > 250) {
-        status = EIG_NO_SPLIT;
-        h->err = "no split found for a node of size " + std::to_string(m);
-        break;
-      }
-    }
+  CK(cudaStreamSynchronize(s));
+  S.queue.push_back(Node{0, n, lo0, hi0, ROOT_NODE, 0});
+  S.outstanding = 1;
+  if (nworkers == 1) {
+    worker_loop(h, S, false, node_base);
+  } else {
+    ensure_workers(h, nworkers);
+    std::vector<std::thread> threads;
+    for (int i = 0; i < nworkers; ++i)
+      threads.emplace_back(worker_loop, h->workers[i], std::ref(S), true, nullptr);
+    for (auto& t : threads) t.join();
+    CK(cudaSetDevice(h->device));
   }
+  int status = S.status;
+  eig_solve_info_t inf = S.inf;
+  if (status != EIG_OK) h->err = S.err;
   if (status == EIG_OK) {
+    std::vector<LeafDesc>& leaves = S.leaves;
     inf.leaves = (int)leaves.size();
     CK(cudaMemcpyAsync(w.ddesc, leaves.data(), sizeof(LeafDesc) * leaves.size(),
                        cudaMemcpyHostToDevice, s));
@@ -860,9 +1090,8 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
       status = EIG_NO_CONVERGENCE;
       h->err = "a leaf solver did not converge";
     }
-    if (sym && split_mode(p.prec)) {
-      inf.flops += refine_symmetric(h, n, dA, lda, dU, ldu, w.wtmp, w.irs.Aj, w.irs.An, w.irs.Bj,
-                                    w.irs.Bn, w.split.nbits);
+    if (refine) {
+      inf.flops += refine_symmetric(h, n, dA, lda, dU, ldu, w.wtmp, w.G, w.AU, w.S, w.E, w.bits);
     }
     if (sym) {
       // eigenvalues ascending with their vectors
@@ -891,8 +1120,8 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
     } else {
       // T = U^T A U with the quasi-triangular pattern of the leaves
       const int gs = gemm_choose_splits(n, n, n);
-      CK(gemm(s, false, false, n, n, n, 1.0, dA, lda, dU, ldu, 0.0, w.Unode, n, gs, w.irs.gpart));
-      CK(gemm(s, true, false, n, n, n, 1.0, dU, ldu, w.Unode, n, 0.0, w.sortbuf, n, gs, w.irs.gpart));
+      CK(gemm(s, false, false, n, n, n, 1.0, dA, lda, dU, ldu, 0.0, w.Tbuf, n, gs, w.gpart));
+      CK(gemm(s, true, false, n, n, n, 1.0, dU, ldu, w.Tbuf, n, 0.0, w.sortbuf, n, gs, w.gpart));
       inf.flops += 4.0 * (double)n * n * n;
       CK(zero_lower_quasi(s, n, w.sortbuf, n, dwi));
       CK(copy_matrix(s, n, n, w.sortbuf, n, dA, lda));
@@ -935,6 +1164,7 @@ void eig_default_params(eig_params_t* p) {
   p->nb = 0;
   p->v_draws = 4;
   p->root_unit_circle = 1;
+  p->workers = 8;
 }
 
 int eig_create(eig_handle_t* out, int device, void* stream) {
@@ -959,6 +1189,13 @@ int eig_destroy(eig_handle_t h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  for (eig_handle_s* w : h->workers) {
+    cudaStreamSynchronize(w->stream);
+    if (w->ws) cudaFree(w->ws);
+    if (w->pinned) cudaFreeHost(w->pinned);
+    cudaStreamDestroy(w->stream);
+    delete w;
+  }
   if (h->ws) cudaFree(h->ws);
   if (h->lastR) cudaFree(h->lastR);
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -974,8 +1211,11 @@ int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
   if (!h || !bytes || n < 0) return EIG_ERR_ARG;
   (void)kind;
   Arena a(nullptr);
-  SolveWork w;
-  *bytes = carve_solve(a, n, w);
+  SolveMain w;
+  NodeWork nw;
+  carve_main(a, n, true, w);
+  carve_node(a, n, n, EIG_SPLIT_BF16X3, nw);
+  *bytes = a.used;
   return EIG_OK;
 }
 
@@ -1118,6 +1358,64 @@ int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
   const eig_params_t p = params_or_default(params);
   check_params(h, p);
   return solve_impl(h, kind, n, dA, lda, dwr, dwi, dU, ldu, p, info);
+  API_END
+}
+
+int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double* const* dA,
+                      const int* lda, double* const* dwr, double* const* dwi, double* const* dU,
+                      const int* ldu, const eig_params_t* params, int* status,
+                      eig_solve_info_t* infos) {
+  API_BEGIN
+  REQUIRE(kind == EIG_KIND_SYM || kind == EIG_KIND_NONSYM, "unknown kind");
+  REQUIRE(count >= 0, "count < 0");
+  REQUIRE(count == 0 || (n && dA && lda && dwr && dU && ldu && status), "NULL array");
+  REQUIRE(kind == EIG_KIND_SYM || count == 0 || dwi, "dwi is NULL");
+  for (int i = 0; i < count; ++i) {
+    REQUIRE(n[i] >= 1 && dA[i] && lda[i] >= n[i] && dwr[i] && dU[i] && ldu[i] >= n[i],
+            "invalid problem " + std::to_string(i));
+    REQUIRE(kind == EIG_KIND_SYM || dwi[i], "dwi[" + std::to_string(i) + "] is NULL");
+  }
+  eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  const int nworkers = std::max(1, std::min(p.workers, 32));
+  p.workers = 1;   // each problem runs sequentially inside its worker
+  CK(cudaStreamSynchronize(h->stream));   // inputs written on the caller's stream
+  ensure_workers(h, nworkers);
+  // largest problems first
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::atomic<int> next{0};
+  auto work = [&](eig_handle_t hw) {
+    cudaSetDevice(hw->device);
+    while (true) {
+      const int t = next.fetch_add(1);
+      if (t >= count) return;
+      const int i = order[t];
+      eig_solve_info_t inf;
+      std::memset(&inf, 0, sizeof(inf));
+      int rc;
+      try {
+        hw->err.clear();
+        rc = solve_impl(hw, kind, n[i], dA[i], lda[i], dwr[i], dwi ? dwi[i] : nullptr, dU[i],
+                        ldu[i], p, &inf);
+      } catch (Fail f) {
+        rc = f.code;
+      }
+      status[i] = rc;
+      if (infos) infos[i] = inf;
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int i = 0; i < nworkers; ++i) threads.emplace_back(work, h->workers[i]);
+  for (auto& t : threads) t.join();
+  CK(cudaSetDevice(h->device));
+  for (int i = 0; i < count; ++i)
+    if (status[i] != EIG_OK) {
+      h->err = "problem " + std::to_string(i) + " returned " + std::to_string(status[i]);
+      return status[i] < 0 ? status[i] : EIG_OK;
+    }
+  return EIG_OK;
   API_END
 }
 

@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
                 ("split_tol", ctypes.c_double), ("leaf_size", ctypes.c_int),
                 ("prec", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("max_fail", ctypes.c_int), ("nb", ctypes.c_int),
-                ("v_draws", ctypes.c_int), ("root_unit_circle", ctypes.c_int)]
+                ("v_draws", ctypes.c_int), ("root_unit_circle", ctypes.c_int),
+                ("workers", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -87,6 +88,8 @@ _SIGNATURES = {
                        ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
     "eig_solve": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
                        ctypes.POINTER(SolveInfo)]),
+    "eig_solve_batched": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Params),
+                               _P, _P]),
     "eig_qr": (_I, [_P, _I, _I, _P, _I, _P, _I, _P, _I]),
     "eig_gaussian": (_I, [_P, _I, _I, _U64, _I, _U64, _I, _P, _I]),
     "eig_haar": (_I, [_P, _I, _U64, _I, _U64, _I, _P, _I]),
@@ -218,6 +221,28 @@ def eig_solve(h, kind, n, dA, lda, dwr, dwi, dU, ldu, params):
     rc = lib().eig_solve(h.ptr, kind, n, _ptr(dA), lda, _ptr(dwr), _ptr(dwi), _ptr(dU), ldu,
                          ctypes.byref(params), ctypes.byref(info))
     return rc, info
+
+
+def eig_solve_batched(h, kind, ns, dAs, ldas, dwrs, dwis, dUs, ldus, params):
+    """Host arrays built here from Python lists; returns (rc, status array, infos)."""
+    count = len(ns)
+    I = ctypes.c_int * max(count, 1)
+    Pp = ctypes.c_void_p * max(count, 1)
+    n_a = I(*ns)
+    lda_a = I(*ldas)
+    ldu_a = I(*ldus)
+    A_a = Pp(*[t.data_ptr() for t in dAs])
+    wr_a = Pp(*[t.data_ptr() for t in dwrs])
+    wi_a = Pp(*[t.data_ptr() for t in dwis]) if dwis is not None else None
+    U_a = Pp(*[t.data_ptr() for t in dUs])
+    st = I()
+    infos = (SolveInfo * max(count, 1))()
+    rc = lib().eig_solve_batched(h.ptr, kind, count, ctypes.cast(n_a, _P), ctypes.cast(A_a, _P),
+                                 ctypes.cast(lda_a, _P), ctypes.cast(wr_a, _P),
+                                 ctypes.cast(wi_a, _P) if wi_a is not None else None,
+                                 ctypes.cast(U_a, _P), ctypes.cast(ldu_a, _P),
+                                 ctypes.byref(params), ctypes.cast(st, _P), ctypes.cast(infos, _P))
+    return rc, [st[i] for i in range(count)], [infos[i] for i in range(count)]
 
 
 def eig_qr(h, m, n, dX, ldx, dQ, ldq, dR, ldr):
