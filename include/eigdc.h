@@ -44,6 +44,7 @@ typedef struct eig_handle_s* eig_handle_t;
 #define EIG_NO_SPLIT 2        /* repeated failure to split a node (Sec. 3.3-3.5) */
 #define EIG_NEAR_SINGULAR_PENCIL 3 /* pencil strategy found no dividing circle (Sec. 3.5) */
 #define EIG_NONFINITE 4       /* NaN/Inf met in an input or an iterate */
+#define EIG_TIMEOUT 5         /* eig_server_wait: the request did not finish in time */
 
 /* arithmetic of the contractions */
 #define EIG_FP64 0
@@ -74,7 +75,9 @@ typedef struct {
 typedef struct {
   double tau;        /* IRS stopping ratio ||R_j - R_{j-1}||_1 <= tau ||R_{j-1}||_1; <= 0: default */
   int maxit;         /* IRS runs j = 0..maxit (Algorithm 3, "until j > maxit") */
-  double split_tol;  /* accept a split when ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) <= split_tol */
+  double split_tol;  /* accept a split when ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) <= split_tol;
+                        <= 0: max(1e-12, 16 n 2^-53) for a node of size n (the FP64 rounding
+                        floor of that ratio grows like n u); split precision: >= 1e-3 */
   int leaf_size;     /* nodes of at most this size go to the leaf solver (<= 64) */
   int prec;          /* EIG_FP64 or EIG_SPLIT_BF16X3 */
   uint64_t seed;     /* Philox key of every draw of the method */
@@ -92,7 +95,8 @@ typedef struct {
   int converged;        /* 1 if the R-test fired */
   int k;                /* chosen block size (eig_split) */
   double split_residual;/* ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) at k */
-  int rank;             /* numerical rank of R2 in RURV(A_p) */
+  int rank;             /* RURV rank: #{|R2_ii| > 1e-8 max|R1_ii|}, R2 of RURV(A_p), R1 of the
+                           RQ step on A_p + B_p (A_p measured against A_p + B_p) */
   int draw;             /* Haar draw that was used (0-based) */
 } eig_step_info_t;
 
@@ -108,7 +112,7 @@ typedef struct {
 } eig_solve_info_t;
 
 /* Defaults: tau = max(1e-14, 4 sqrt(n) 2^-53) at call time, maxit = 60,
- * split_tol = 1e-12, leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
+ * split_tol = 0 (automatic), leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
  * v_draws = 4, root_unit_circle = 1, workers = 8. */
 void eig_default_params(eig_params_t* p);
 
@@ -177,6 +181,36 @@ int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double*
                       const int* lda, double* const* dwr, double* const* dwi, double* const* dU,
                       const int* ldu, const eig_params_t* params, int* status,
                       eig_solve_info_t* infos);
+
+/* ------------------------------------------------------------- serving
+ * A request server: `workers` host threads, each with its own CUDA stream
+ * and workspace, take submitted requests in arrival order as soon as a worker
+ * is free and the request's device footprint (the workspace eig_solve needs
+ * for its n) fits the HBM budget together with the running requests; a
+ * request is always admitted when nothing runs.  Requests that arrive while
+ * others run are admitted as slots and memory free up, and their work overlaps
+ * on the device.  Each request's result is identical to eig_solve with
+ * workers = 1 on the same input. */
+typedef struct eig_server_s* eig_server_t;
+int eig_server_create(eig_server_t* srv, int device, int workers, double hbm_budget_gb);
+/* Queue a request (kind, n, buffers as in eig_solve).  The input dA must be
+ * complete on the device (the caller synchronizes the stream that wrote it);
+ * the buffers stay owned by the caller and must live until the request is
+ * done.  *ticket identifies the request. */
+int eig_server_submit(eig_server_t srv, int kind, int n, double* dA, int lda, double* dwr,
+                      double* dwi, double* dU, int ldu, const eig_params_t* params,
+                      uint64_t* ticket);
+/* *done = 1 once finished; then *status, times[0..2] = queue wait, service,
+ * latency (seconds, host steady clock) and *info are filled (each may be NULL). */
+int eig_server_poll(eig_server_t srv, uint64_t ticket, int* done, int* status, double* times,
+                    eig_solve_info_t* info);
+/* Block until the request is done (EIG_TIMEOUT after timeout_s seconds). */
+int eig_server_wait(eig_server_t srv, uint64_t ticket, double timeout_s, int* status);
+int eig_server_stats(eig_server_t srv, unsigned long long* completed, unsigned long long* pending,
+                     double* reserved_gb, double* peak_reserved_gb);
+/* Stop the workers (a running request finishes first, queued ones are
+ * dropped) and free everything. */
+int eig_server_destroy(eig_server_t srv);
 
 /* ------------------------------------------------------ building blocks
  * The steps of the path, exposed so each can be checked on its own. */

@@ -86,9 +86,17 @@ def splitter_left(Ap, Bp, V):
     return U_cur, R1, R2
 
 
-def numerical_rank(R, rel_tol=1e-8):
-    """Count of |R_ii| above rel_tol * max |R_ii| (RURV rank decision)."""
-    d = np.abs(np.diag(R))
-    if d.size == 0 or d.max() == 0.0:
+def numerical_rank(R2, R1, rel_tol=1e-8):
+    """RURV rank decision: #{|R2_ii| > rel_tol * max_i |R1_ii|}.
+
+    R2 is the triangular factor of RURV(A_p) and R1 that of the RQ step on
+    A_p + B_p.  The splitter's matrix is (A_p + B_p)^{-1} A_p (Sec. 3.2), so
+    A_p's singular values are measured against the size of A_p + B_p, of which
+    max |R1_ii| is the scale (reading; the paper leaves the rank decision
+    implicit).  A_p negligible next to B_p (every eigenvalue inside) gives 0.
+    """
+    d2 = np.abs(np.diag(R2))
+    scale = float(np.max(np.abs(np.diag(R1)))) if R1.size else 0.0
+    if d2.size == 0 or scale == 0.0:
         return 0
-    return int(np.sum(d > rel_tol * d.max()))
+    return int(np.sum(d2 > rel_tol * scale))

@@ -16,7 +16,11 @@ Readings (paper silent or other sources):
     and half-width of [lo, hi] and xi a Philox uniform of the node;
   * line scale s = R (the paper assumes ||A|| = O(1), Sec. 3.3);
   * the side of an unsplit node is read from the numerical rank of R2 in
-    RURV(A_p): rank 0 means no eigenvalue right of x, rank n none left of it;
+    RURV(A_p), measured against |A_p + B_p| (rurv.numerical_rank): rank 0
+    means no eigenvalue right of x, rank n none left of it;
+  * split_tol None means max(1e-12, 16 n u): the rounding floor of
+    ||E21||_1 / ||A||_1 after an FP64 step grows about like n u (measured
+    4-5 n u at n = 2048 and 4096);
   * a split is accepted when 0 < k < n and e(k) <= split_tol; after max_fail
     unproductive attempts the solve stops with status NO_SPLIT;
   * Theorem 2.1 holds with high probability only: when IRS converged and the
@@ -54,7 +58,7 @@ def split_from_irs(A, B, res, res_t, seed, stream, attempt, draw, symmetric):
     n = A.shape[0]
     V = haar(n, seed, stream, attempt_code(attempt, draw), PURPOSE_HAAR)
     QR_, R1, R2 = splitter_right(res.Ap, res.Bp, V)
-    rank = numerical_rank(R2)
+    rank = numerical_rank(R2, R1)
     out = dict(QR=QR_, rank=rank, R1=R1, R2=R2, draw=draw)
     if B is None:
         Ahat = QR_.T @ A @ QR_
@@ -72,12 +76,19 @@ def split_from_irs(A, B, res, res_t, seed, stream, attempt, draw, symmetric):
     return out
 
 
+def default_split_tol(n):
+    """max(1e-12, 16 n u), u = 2^-53 (see the module docstring)."""
+    return max(1e-12, 16.0 * n * 2.0 ** -53)
+
+
 def divide_step(A, B=None, region=(REGION_UNIT_CIRCLE, 0.0, 1.0), seed=0,
                 stream=ROOT_NODE, attempt=0, tau=None, maxit=60,
-                symmetric=False, split_tol=1e-12, record_R=False, v_draws=4):
+                symmetric=False, split_tol=None, record_R=False, v_draws=4):
     """One step of RSEP (symmetric) / RNEP (B None) / RGNEP (B given)."""
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
+    if split_tol is None:
+        split_tol = default_split_tol(n)
     kind, c, r = region
     Am, Bm = region_map(A, B, kind, c, r)
     res = irs(Am, Bm, tau=tau, maxit=maxit, record_R=record_R)
@@ -134,6 +145,7 @@ class SolveInfo:
 
 def _recurse(A, seed, leaf_size, tau, maxit, split_tol, max_fail, symmetric,
              root_unit_circle, info):
+    # split_tol None: automatic per node size (default_split_tol)
     """Shared recursion; returns (Q, blocks) with A = Q T Q^T block structure."""
     n = A.shape[0]
     Q = np.eye(n)
@@ -202,7 +214,7 @@ def _recurse(A, seed, leaf_size, tau, maxit, split_tol, max_fail, symmetric,
     return Q, leaves, True
 
 
-def eig_sym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=1e-12, max_fail=8):
+def eig_sym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None, max_fail=8):
     """(w ascending, U, info) for symmetric A by RSEP recursion + Jacobi leaves."""
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -220,7 +232,7 @@ def eig_sym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=1e-12, max_fa
     return w[order], Q[:, order], info
 
 
-def schur_nonsym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=1e-12,
+def schur_nonsym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
                  max_fail=8, root_unit_circle=True):
     """(T, Q, wr, wi, info): A = Q T Q^T, T quasi-triangular (RNEP + Francis)."""
     A = np.asarray(A, dtype=np.float64)

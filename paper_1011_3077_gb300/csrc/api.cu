@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <condition_variable>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -441,6 +442,15 @@ static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64) {
   return a.used - start;
 }
 
+// split_tol <= 0: max(1e-12, 16 n u), the rounding floor of ||E21||_1/||A||_1
+// after an FP64 step grows about like n u (measured 4-5 n u at n = 2048 and
+// 4096); split precision: at least 1e-3 (FP32-level iterates, refined later).
+static double effective_split_tol(const eig_params_t& p, int n) {
+  double t = p.split_tol > 0 ? p.split_tol : std::max(1e-12, 16.0 * n * 0x1p-53);
+  if (split_mode(p.prec)) t = std::max(t, 1e-3);
+  return t;
+}
+
 // Tie rule (paper silent): smallest e(k); exact ties -> k closest to n/2,
 // then the smaller k.
 static int choose_k(const double* e, int n) {
@@ -500,13 +510,13 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
     mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, true, n, n, n, 1.0, Ap, ldp, w.Vh, n, 0.0, w.X, n,
        gsplit, w.gpart);
     qr_explicit(h, w.qr, n, n, w.X, n, w.U, n, w.R2, n);
-    CK(count_rank(s, n, w.R2, n, 1e-8, w.rank));
     // RQ(U^T (A_p + B_p)) by reversal: Z = (J Y)^T = Q~ R~, U_cur = Q~ J
     CK(add_matrices(s, n, n, Ap, ldp, Bp, ldp, w.S, n));
     mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.U, n, w.S, n, 0.0, w.Y, n,
        gsplit, w.gpart);
     CK(reverse_transpose(s, n, w.Y, n, w.Z, n));
-    qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, nullptr, 0);
+    qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, w.G, n);   // R~ (diag: R1 reversed) into G
+    CK(count_rank(s, n, w.R2, n, w.G, n, 1e-8, w.rank));
     CK(reverse_columns(s, n, n, w.Qt, n, w.Ucur, n));
     // similarity and split test
     mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, false, n, n, n, 1.0, A, lda, w.Ucur, n, 0.0, w.tmp,
@@ -541,7 +551,7 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
       out.k = 0;
       out.e = 0.0;
     }
-    out.accepted = irs_converged && out.k > 0 && out.k < n && out.e <= p.split_tol;
+    out.accepted = irs_converged && out.k > 0 && out.k < n && out.e <= effective_split_tol(p, n);
     if (out.accepted || !irs_converged || rank == 0 || rank == n) break;
   }
   return out;
@@ -1036,7 +1046,6 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
   // split precision: FP32-level iterates, so the R-test and the split test
   // are read at that level; the FP64 refinement at the end restores accuracy
   S.pp = p;
-  if (split_mode(p.prec)) S.pp.split_tol = std::max(p.split_tol, 1e-3);
   std::memset(&S.inf, 0, sizeof(S.inf));
   // working copy of A; global U = I
   CK(copy_matrix(s, n, n, dA, lda, w.Acur, n));
@@ -1156,7 +1165,7 @@ void eig_default_params(eig_params_t* p) {
   if (!p) return;
   p->tau = 0.0;
   p->maxit = 60;
-  p->split_tol = 1e-12;
+  p->split_tol = 0.0;
   p->leaf_size = 64;
   p->prec = EIG_FP64;
   p->seed = 0;
@@ -1527,6 +1536,248 @@ int eig_gemm_split(eig_handle_t h, int ta, int tb, int m, int n, int k, double a
   }
   return EIG_OK;
   API_END
+}
+
+}  // extern "C"
+
+// =================================================================== serving
+// A request server over the same solver: worker threads, each with its own
+// CUDA stream and workspace, take requests in arrival order as soon as a
+// worker is free and the request's device footprint fits the HBM budget
+// (continuous batching: requests that arrive while others run are admitted
+// as slots and memory free up, and their work overlaps on the device).
+namespace {
+
+struct Request {
+  uint64_t ticket;
+  int kind, n, lda, ldu;
+  double *dA, *dwr, *dwi, *dU;
+  eig_params_t p;
+  size_t footprint;
+  double t_submit = 0, t_start = 0, t_end = 0;
+  int status = EIG_OK;
+  bool done = false;
+  eig_solve_info_t info;
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+size_t solve_footprint(int n, int kind, int prec) {
+  Arena a(nullptr);
+  SolveMain w;
+  NodeWork nw;
+  carve_main(a, n, kind == EIG_KIND_SYM && split_mode(prec), w);
+  carve_node(a, n, n, prec, nw);
+  return a.used;
+}
+
+}  // namespace
+
+struct eig_server_s {
+  int device = 0;
+  size_t budget = 0;
+  size_t reserved = 0, peak_reserved = 0;
+  uint64_t next_ticket = 1;
+  uint64_t completed = 0;
+  bool stop = false;
+  std::vector<eig_handle_s*> workers;
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request*> queue;
+  std::vector<Request*> all;
+};
+
+static void server_worker(eig_server_s* S, eig_handle_s* hw) {
+  cudaSetDevice(hw->device);
+  while (true) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      S->cv_work.wait(lock, [&] {
+        if (S->stop) return true;
+        if (S->queue.empty()) return false;
+        Request* h = S->queue.front();
+        return S->reserved == 0 || S->reserved + h->footprint <= S->budget;
+      });
+      if (S->stop) return;
+      r = S->queue.front();
+      S->queue.pop_front();
+      S->reserved += r->footprint;
+      S->peak_reserved = std::max(S->peak_reserved, S->reserved);
+      r->t_start = now_s();
+    }
+    int rc;
+    eig_solve_info_t inf;
+    std::memset(&inf, 0, sizeof(inf));
+    try {
+      hw->err.clear();
+      rc = solve_impl(hw, r->kind, r->n, r->dA, r->lda, r->dwr, r->dwi, r->dU, r->ldu, r->p, &inf);
+    } catch (Fail f) {
+      rc = f.code;
+    }
+    // keep a worker's scratch only while it is small: the budget counts
+    // running requests, so large idle workspaces are returned
+    if (hw->ws_bytes > ((size_t)1 << 30)) {
+      cudaStreamSynchronize(hw->stream);
+      cudaFree(hw->ws);
+      hw->ws = nullptr;
+      hw->ws_bytes = 0;
+    }
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      r->status = rc;
+      r->info = inf;
+      r->t_end = now_s();
+      r->done = true;
+      S->reserved -= r->footprint;
+      S->completed++;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+extern "C" {
+
+int eig_server_create(eig_server_t* out, int device, int workers, double hbm_budget_gb) {
+  if (!out || workers < 1 || workers > 64 || !(hbm_budget_gb > 0)) return EIG_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return EIG_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return EIG_ERR_CUDA;
+  panel_init();
+  eig_server_s* S = new eig_server_s();
+  S->device = device;
+  S->budget = (size_t)(hbm_budget_gb * 1e9);
+  for (int i = 0; i < workers; ++i) {
+    eig_handle_s* w = new eig_handle_s();
+    w->device = device;
+    if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete w;
+      break;
+    }
+    S->workers.push_back(w);
+  }
+  if (S->workers.empty()) {
+    delete S;
+    return EIG_ERR_CUDA;
+  }
+  for (eig_handle_s* w : S->workers) S->threads.emplace_back(server_worker, S, w);
+  *out = S;
+  return EIG_OK;
+}
+
+int eig_server_submit(eig_server_t S, int kind, int n, double* dA, int lda, double* dwr,
+                      double* dwi, double* dU, int ldu, const eig_params_t* params,
+                      uint64_t* ticket) {
+  if (!S || !ticket) return EIG_ERR_ARG;
+  if ((kind != EIG_KIND_SYM && kind != EIG_KIND_NONSYM) || n < 1 || !dA || lda < n || !dwr ||
+      !dU || ldu < n || (kind == EIG_KIND_NONSYM && !dwi))
+    return EIG_ERR_ARG;
+  Request* r = new Request();
+  r->kind = kind;
+  r->n = n;
+  r->dA = dA;
+  r->lda = lda;
+  r->dwr = dwr;
+  r->dwi = dwi;
+  r->dU = dU;
+  r->ldu = ldu;
+  eig_default_params(&r->p);
+  if (params) r->p = *params;
+  r->p.workers = 1;
+  if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
+      (r->p.prec != EIG_FP64 && r->p.prec != EIG_SPLIT_BF16X3)) {
+    delete r;
+    return EIG_ERR_ARG;
+  }
+  r->footprint = solve_footprint(n, kind, r->p.prec);
+  std::memset(&r->info, 0, sizeof(r->info));
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    r->ticket = S->next_ticket++;
+    r->t_submit = now_s();
+    S->queue.push_back(r);
+    S->all.push_back(r);
+    *ticket = r->ticket;
+  }
+  S->cv_work.notify_all();
+  return EIG_OK;
+}
+
+static Request* find_request(eig_server_s* S, uint64_t ticket) {
+  if (ticket == 0 || ticket > S->all.size()) return nullptr;
+  return S->all[ticket - 1];
+}
+
+int eig_server_poll(eig_server_t S, uint64_t ticket, int* done, int* status, double* times,
+                    eig_solve_info_t* info) {
+  if (!S || !done) return EIG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  Request* r = find_request(S, ticket);
+  if (!r) return EIG_ERR_ARG;
+  *done = r->done ? 1 : 0;
+  if (r->done) {
+    if (status) *status = r->status;
+    if (times) {
+      times[0] = r->t_start - r->t_submit;   // queue wait
+      times[1] = r->t_end - r->t_start;      // service
+      times[2] = r->t_end - r->t_submit;     // latency
+    }
+    if (info) *info = r->info;
+  }
+  return EIG_OK;
+}
+
+int eig_server_wait(eig_server_t S, uint64_t ticket, double timeout_s, int* status) {
+  if (!S) return EIG_ERR_ARG;
+  std::unique_lock<std::mutex> lock(S->mu);
+  Request* r = find_request(S, ticket);
+  if (!r) return EIG_ERR_ARG;
+  const bool ok = S->cv_done.wait_for(lock, std::chrono::duration<double>(timeout_s),
+                                      [&] { return r->done; });
+  if (!ok) return EIG_TIMEOUT;
+  if (status) *status = r->status;
+  return EIG_OK;
+}
+
+int eig_server_stats(eig_server_t S, unsigned long long* completed, unsigned long long* pending,
+                     double* reserved_gb, double* peak_reserved_gb) {
+  if (!S) return EIG_ERR_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  if (completed) *completed = S->completed;
+  if (pending) *pending = S->queue.size();
+  if (reserved_gb) *reserved_gb = S->reserved / 1e9;
+  if (peak_reserved_gb) *peak_reserved_gb = S->peak_reserved / 1e9;
+  return EIG_OK;
+}
+
+int eig_server_destroy(eig_server_t S) {
+  if (!S) return EIG_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->threads) t.join();
+  cudaSetDevice(S->device);
+  for (eig_handle_s* w : S->workers) {
+    cudaStreamSynchronize(w->stream);
+    if (w->ws) cudaFree(w->ws);
+    if (w->pinned) cudaFreeHost(w->pinned);
+    cudaStreamDestroy(w->stream);
+    delete w;
+  }
+  for (Request* r : S->all) delete r;
+  delete S;
+  return EIG_OK;
 }
 
 }  // extern "C"

@@ -85,8 +85,8 @@ cudaError_t split_scores(cudaStream_t s, int n, const double* A, int lda, double
                          double* colpart, double* scores, bool accumulate);
 cudaError_t diag_gershgorin(cudaStream_t s, int n, const double* A, int lda, double* diag,
                             double* lo_hi);
-cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, double rel_tol,
-                       int* rank);
+cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, const double* Sc, int lds,
+                       double rel_tol, int* rank);
 cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const double* wi);
 // FP64 refinement of a symmetric eigendecomposition (n x n packed operands)
 cudaError_t oa_diag(cudaStream_t s, int n, const double* G, const double* S, double* lam,

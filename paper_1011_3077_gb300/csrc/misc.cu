@@ -441,13 +441,17 @@ cudaError_t diag_gershgorin(cudaStream_t s, int n, const double* A, int lda, dou
   return cudaGetLastError();
 }
 
-// Numerical rank: #{i : |R_ii| > rel_tol * max_i |R_ii|} (one CTA).
-__global__ void count_rank_kernel(int n, const double* __restrict__ R, int ldr, double rel_tol,
+// RURV rank decision (one CTA): #{i : |R_ii| > rel_tol * max_i |S_ii|}, with
+// R the factor of RURV(A_p) and S that of the RQ step on A_p + B_p, so A_p is
+// measured against the size of A_p + B_p (the splitter's matrix is
+// (A_p + B_p)^{-1} A_p).
+__global__ void count_rank_kernel(int n, const double* __restrict__ R, int ldr,
+                                  const double* __restrict__ Sc, int lds, double rel_tol,
                                   int* rank) {
   __shared__ double smax[256];
   __shared__ int scnt[256];
   double m = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) m = fmax(m, fabs(R[i + (size_t)i * ldr]));
+  for (int i = threadIdx.x; i < n; i += 256) m = fmax(m, fabs(Sc[i + (size_t)i * lds]));
   smax[threadIdx.x] = m;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -467,9 +471,10 @@ __global__ void count_rank_kernel(int n, const double* __restrict__ R, int ldr, 
   if (threadIdx.x == 0) *rank = scnt[0];
 }
 
-cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, double rel_tol, int* rank) {
+cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, const double* Sc, int lds,
+                       double rel_tol, int* rank) {
   note_launches(1);
-  count_rank_kernel<<<1, 256, 0, s>>>(n, R, ldr, rel_tol, rank);
+  count_rank_kernel<<<1, 256, 0, s>>>(n, R, ldr, Sc, lds, rel_tol, rank);
   return cudaGetLastError();
 }
 

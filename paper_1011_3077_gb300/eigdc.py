@@ -27,6 +27,7 @@ EIG_NO_CONVERGENCE = 1
 EIG_NO_SPLIT = 2
 EIG_NEAR_SINGULAR_PENCIL = 3
 EIG_NONFINITE = 4
+EIG_TIMEOUT = 5
 
 EIG_REGION_UNIT_CIRCLE = 0
 EIG_REGION_CIRCLE = 1
@@ -90,6 +91,16 @@ _SIGNATURES = {
                        ctypes.POINTER(SolveInfo)]),
     "eig_solve_batched": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Params),
                                _P, _P]),
+    "eig_server_create": (_I, [ctypes.POINTER(_P), _I, _I, _D]),
+    "eig_server_submit": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
+                               ctypes.POINTER(_U64)]),
+    "eig_server_poll": (_I, [_P, _U64, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                             ctypes.POINTER(_D), ctypes.POINTER(SolveInfo)]),
+    "eig_server_wait": (_I, [_P, _U64, _D, ctypes.POINTER(_I)]),
+    "eig_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong),
+                              ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(_D),
+                              ctypes.POINTER(_D)]),
+    "eig_server_destroy": (_I, [_P]),
     "eig_qr": (_I, [_P, _I, _I, _P, _I, _P, _I, _P, _I]),
     "eig_gaussian": (_I, [_P, _I, _I, _U64, _I, _U64, _I, _P, _I]),
     "eig_haar": (_I, [_P, _I, _U64, _I, _U64, _I, _P, _I]),
@@ -243,6 +254,66 @@ def eig_solve_batched(h, kind, ns, dAs, ldas, dwrs, dwis, dUs, ldus, params):
                                  ctypes.cast(U_a, _P), ctypes.cast(ldu_a, _P),
                                  ctypes.byref(params), ctypes.cast(st, _P), ctypes.cast(infos, _P))
     return rc, [st[i] for i in range(count)], [infos[i] for i in range(count)]
+
+
+class Server:
+    """eig_server_* wrapper: submit device buffers, poll or wait for completion."""
+
+    def __init__(self, device=0, workers=8, hbm_budget_gb=120.0):
+        self._s = ctypes.c_void_p()
+        rc = lib().eig_server_create(ctypes.byref(self._s), device, workers, hbm_budget_gb)
+        if rc != EIG_OK:
+            raise EigError(rc, "eig_server_create failed")
+        self._keep = {}
+
+    def submit(self, kind, dA, dwr, dwi, dU, params=None):
+        n = int(dA.shape[0])
+        t = ctypes.c_uint64()
+        p = params or default_params()
+        rc = lib().eig_server_submit(self._s, kind, n, _ptr(dA), n, _ptr(dwr), _ptr(dwi),
+                                     _ptr(dU), n, ctypes.byref(p), ctypes.byref(t))
+        if rc != EIG_OK:
+            raise EigError(rc, "eig_server_submit failed")
+        self._keep[t.value] = (dA, dwr, dwi, dU)     # buffers live until done
+        return t.value
+
+    def poll(self, ticket):
+        done = ctypes.c_int()
+        st = ctypes.c_int()
+        times = (ctypes.c_double * 3)()
+        info = SolveInfo()
+        lib().eig_server_poll(self._s, ticket, ctypes.byref(done), ctypes.byref(st), times,
+                              ctypes.byref(info))
+        if not done.value:
+            return None
+        return st.value, (times[0], times[1], times[2]), info
+
+    def wait(self, ticket, timeout_s=600.0):
+        st = ctypes.c_int()
+        rc = lib().eig_server_wait(self._s, ticket, timeout_s, ctypes.byref(st))
+        return rc, st.value
+
+    def stats(self):
+        c = ctypes.c_ulonglong()
+        q = ctypes.c_ulonglong()
+        r = ctypes.c_double()
+        pk = ctypes.c_double()
+        lib().eig_server_stats(self._s, ctypes.byref(c), ctypes.byref(q), ctypes.byref(r),
+                               ctypes.byref(pk))
+        return {"completed": c.value, "pending": q.value, "reserved_gb": r.value,
+                "peak_reserved_gb": pk.value}
+
+    def close(self):
+        if self._s:
+            lib().eig_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def eig_qr(h, m, n, dX, ldx, dQ, ldq, dR, ldr):

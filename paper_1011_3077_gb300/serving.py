@@ -1,0 +1,139 @@
+"""Serving loop: Poisson arrivals of mixed eigenproblems on one GPU.
+
+Requests (symmetric eigendecomposition, nonsymmetric real Schur form) of
+log-uniform size arrive as a Poisson stream and are submitted to the native
+request server (include/eigdc.h, eig_server_*), which admits them under an
+HBM budget as workers free up and overlaps their work on the device.  The
+loop reports throughput and p50/p99 latency (arrival to completion).
+
+Inputs are synthesised on the device before the clock starts (random
+orthogonal similarity of a prescribed spectrum; a library QR draws the
+orthogonal factor -- input generation, not the method).  Nonsymmetric
+requests use the triangular construction with strict-upper scale 0.1/sqrt(n)
+(the reduced-coupling reading of the nonsymmetric workload).
+
+Usage: python -m paper_1011_3077_gb300.serving --rate 200 --count 40
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import eigdc
+
+
+def _orthogonal(n, gen, device):
+    import torch
+    G = torch.randn((n, n), generator=gen, dtype=torch.float64, device=device)
+    Q, R = torch.linalg.qr(G)
+    s = torch.sign(torch.diagonal(R))
+    s[s == 0] = 1.0
+    return Q * s
+
+
+def synthesize(kind, n, seed, device="cuda"):
+    """(dA column-major, reference spectrum) for one request."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    Q = _orthogonal(n, gen, device)
+    if kind == eigdc.EIG_KIND_SYM:
+        lam = torch.rand(n, generator=gen, dtype=torch.float64, device=device) * 2.0 - 1.0
+        A = (Q * lam) @ Q.T
+        A = 0.5 * (A + A.T)
+        ref = torch.sort(lam).values
+    else:
+        h = n // 2
+        mags = torch.cat([0.2 + 0.7 * torch.rand(h, generator=gen, dtype=torch.float64, device=device),
+                          1.1 + 1.9 * torch.rand(n - h, generator=gen, dtype=torch.float64, device=device)])
+        sgn = torch.where(torch.rand(n, generator=gen, device=device) < 0.5, -1.0, 1.0).to(torch.float64)
+        d = (mags * sgn)[torch.randperm(n, generator=gen, device=device)]
+        T = torch.triu(torch.randn((n, n), generator=gen, dtype=torch.float64, device=device)
+                       * (0.1 / math.sqrt(n)), 1) + torch.diag(d)
+        A = Q @ T @ Q.T
+        ref = torch.sort(d).values
+    # column-major storage of A is the row-major storage of A^T
+    return A.T.contiguous(), ref
+
+
+def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.5), workers=8,
+        budget_gb=120.0, prec=eigdc.EIG_FP64, seed=5, device="cuda", verbose=False):
+    import torch
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    kinds = rng.choice([eigdc.EIG_KIND_SYM, eigdc.EIG_KIND_NONSYM], size=count,
+                       p=np.asarray(mix) / np.sum(mix))
+    sizes = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(int)
+    reqs = []
+    for i in range(count):
+        n = int(sizes[i])
+        dA, ref = synthesize(int(kinds[i]), n, seed * 1000003 + i, device)
+        dwr = torch.zeros(n, dtype=torch.float64, device=device)
+        dwi = torch.zeros(n, dtype=torch.float64, device=device)
+        dU = torch.zeros((n, n), dtype=torch.float64, device=device)
+        reqs.append((int(kinds[i]), n, dA, dwr, dwi, dU, ref))
+    torch.cuda.synchronize()
+    srv = eigdc.Server(0, workers, budget_gb)
+    params = eigdc.default_params(seed=seed, prec=prec)
+    tickets = []
+    t0 = time.perf_counter()
+    for i, (kind, n, dA, dwr, dwi, dU, ref) in enumerate(reqs):
+        delay = t0 + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(kind, dA, dwr, dwi, dU, params))
+    statuses, lat, wait, service = [], [], [], []
+    for t in tickets:
+        srv.wait(t, 3600.0)
+        st, times, info = srv.poll(t)
+        statuses.append(st)
+        wait.append(times[0])
+        service.append(times[1])
+        lat.append(times[2])
+    makespan = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    errs = []
+    for (kind, n, dA, dwr, dwi, dU, ref), st in zip(reqs, statuses):
+        if st == 0:
+            w = torch.sort(dwr).values
+            errs.append(float(torch.max(torch.abs(w - ref))))
+    ok = sum(1 for s in statuses if s == 0)
+    out = {
+        "requests": count, "ok": ok, "offered_rate_per_s": rate,
+        "solves_per_s": ok / makespan, "makespan_s": makespan,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "service_s": {"p50": float(np.percentile(service, 50)), "p99": float(np.percentile(service, 99))},
+        "sizes": {"min": int(sizes.min()), "max": int(sizes.max())},
+        "max_eigenvalue_error": max(errs) if errs else None,
+        "peak_reserved_gb": stats["peak_reserved_gb"], "budget_gb": budget_gb,
+        "workers": workers, "precision": "split" if prec else "fp64",
+    }
+    if verbose:
+        print(json.dumps(out))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--count", type=int, default=40)
+    ap.add_argument("--nmin", type=int, default=64)
+    ap.add_argument("--nmax", type=int, default=4096)
+    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--prec", type=int, default=0)
+    ap.add_argument("--seed", type=int, default=5)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    run(a.rate, a.count, a.nmin, a.nmax, workers=a.workers, budget_gb=a.budget_gb, prec=a.prec,
+        seed=a.seed, verbose=True)
+
+
+if __name__ == "__main__":
+    main()

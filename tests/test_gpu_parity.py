@@ -241,6 +241,26 @@ def test_config1_split_matches_oracle(E):
     assert np.max(np.abs(Q.T @ Q - np.eye(n))) <= 1e-13
 
 
+def test_rank_decision_empty_sides_gpu(E):
+    """A line beyond the spectrum: rank 0 (right of everything) or n (left),
+    measured against |A_p + B_p|, as in the oracle."""
+    eigdc, h, torch = E
+    from oracle.solve import divide_step as ods
+    A, lam = workloads.symmetric_uniform(40, seed=2)
+    n = 40
+    for sigma, want in ((18.0, 0), (-18.0, n)):
+        Am, Bm = region_map(A, None, REGION_LINE, sigma, 14.0)
+        dAp, dBp = eigdc.to_device(Am), eigdc.to_device(Bm)
+        rc, info = eigdc.eig_divide_step(h, n, dAp, n, dBp, n, eigdc.Region(0, 0.0, 1.0),
+                                         eigdc.default_params())
+        assert rc == eigdc.EIG_OK
+        dQ = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        rc, si = eigdc.eig_split(h, n, dAp, dBp, n, eigdc.to_device(A), n, dQ, n, 1, 1, 0,
+                                 eigdc.default_params(seed=3))
+        st = ods(A, None, (REGION_LINE, sigma, 14.0), seed=3, stream=1, symmetric=True)
+        assert si.rank == want == st.rank
+
+
 # ------------------------------------------------------------------ whole solves
 @pytest.mark.parametrize("n,leaf", [(1, 64), (2, 64), (64, 64), (150, 40), (300, 64)])
 def test_eig_solve_symmetric(E, n, leaf):

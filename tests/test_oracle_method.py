@@ -221,12 +221,23 @@ def test_splitter_spans_outside_subspace():
     U, R1, R2 = splitter_right(res.Ap, res.Bp, V)
     out = np.abs(lam) > 1.0
     r = int(out.sum())
-    assert numerical_rank(R2) == r
+    assert numerical_rank(R2, R1) == r
     assert subspace_residual(U[:, :r], S[:, out]) < 1e-10
     Ahat = U.T @ A @ U
     assert np.linalg.norm(Ahat[r:, :r]) < 1e-10 * np.linalg.norm(A)
     assert np.allclose(np.sort(np.abs(np.linalg.eigvals(Ahat[:r, :r]))),
                        np.sort(np.abs(lam[out])), atol=1e-9)
+
+
+def test_rank_decision_empty_sides():
+    """A line right of (left of) the whole spectrum gives rank 0 (n): the
+    projector (A_p + B_p)^{-1} A_p of Sec. 3.2 is 0 (I), however small A_p's
+    own singular values are relative to each other."""
+    A, lam = workloads.symmetric_uniform(24, seed=2)
+    for sigma, want in ((18.0, 0), (-18.0, 24)):
+        st = divide_step(A, None, (REGION_LINE, sigma, 14.0), seed=3, symmetric=True)
+        assert st.irs.converged
+        assert st.rank == want
 
 
 # ------------------------------------------------------------------- leaves
