@@ -206,3 +206,43 @@ def real_schur(A, max_iter_per_eig=40):
             return H, Z, wr, wi, False
         _francis_step(H, Z, lo, hi, exceptional=(its % 11 == 10))
     return H, Z, wr, wi, True
+
+
+# ------------------------------------------------------ pencil leaves
+
+def _back_solve_right(A, R):
+    """X with X R = A for upper-triangular R (column-by-column substitution)."""
+    n = R.shape[0]
+    X = np.zeros_like(A)
+    for j in range(n):
+        X[:, j] = (A[:, j] - X[:, :j] @ R[:j, j]) / R[j, j]
+    return X
+
+
+def pencil_schur_leaf(A, B, cond_limit=1e8):
+    """Generalized real Schur form of a small regular pencil (A, B).
+
+    Reading for the leaves of the pencil recursion (the paper leaves small
+    subproblems to "the standard algorithm"): with B well conditioned,
+    M = A B^{-1} has the eigenvalues of the pencil; its real Schur form
+    M = QL TM QL^T and the RQ factorisation QL^T B = R Z give
+        QL^T A Z^T = TM R (quasi-upper-triangular),  QL^T B Z^T = R (upper),
+    i.e. QR_ = Z^T.  B^{-1} is applied through its QR factors and a triangular
+    substitution.  Returns (S, T, QL, QR_, ok); ok is False when
+    max|R_ii| / min|R_ii| of B's QR exceeds cond_limit (near-singular B).
+    """
+    from .householder import qr_explicit, rq_explicit
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    QB, RB = qr_explicit(B)
+    d = np.abs(np.diag(RB))
+    if d.size and (d.min() == 0.0 or d.max() / d.min() > cond_limit):
+        return None, None, None, None, None, False
+    X = _back_solve_right(A, RB)          # A R_B^{-1}
+    M = X @ QB.T                          # A B^{-1}
+    TM, QL, wr, wi, ok = real_schur(M)
+    R, Qrq = rq_explicit(QL.T @ B)
+    QR_ = Qrq.T
+    S = QL.T @ A @ QR_
+    T = QL.T @ B @ QR_
+    return S, T, QL, QR_, wi, ok

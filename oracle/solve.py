@@ -39,7 +39,7 @@ import numpy as np
 from .irs import irs, region_map, norm1, default_tau, REGION_LINE, REGION_UNIT_CIRCLE
 from .rurv import haar, splitter_right, splitter_left, numerical_rank
 from .split import split_test, symmetrise
-from .leaves import jacobi_eig, real_schur
+from .leaves import jacobi_eig, real_schur, pencil_schur_leaf
 from .philox import (uniform_scalar, attempt_code, PURPOSE_SHIFT, PURPOSE_HAAR,
                      PURPOSE_HAAR_LEFT, ROOT_NODE, child_node)
 
@@ -254,6 +254,129 @@ def schur_nonsym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
     T = Q.T @ A @ Q
     T = quasi_triangular_part(T, wi)
     return T, Q, wr, wi, info
+
+
+def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None, max_fail=8):
+    """Generalized real Schur form of a regular pencil by RGNEP recursion.
+
+    Strategy (Sec. 3.5): the root splits on the unit circle; the group
+    outside is handled as the swapped pencil (B, A), whose eigenvalues
+    1/lambda lie inside the unit disk, so every child's spectrum is in the
+    disk of radius 1.  Below the root, real lines Re z = sigma on the interval
+    [-1, 1] of the (possibly swapped) node, with the symmetric strategy's
+    shift and empty-side rules (reading: real lines, as for RNEP).  Leaves by
+    pencil_schur_leaf.  Returns (S, T, QL, QR, alpha_re, alpha_im, beta, info)
+    with QL^T A QR = S quasi-upper-triangular and QL^T B QR = T upper.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    n = A.shape[0]
+    info = SolveInfo()
+    QL = np.eye(n)
+    QRm = np.eye(n)
+    leaves = []
+    work = [(0, n, A.copy(), B.copy(), -1.0, 1.0, False, ROOT_NODE, 0)]
+    while work:
+        off, m, An, Bn, lo, hi, swapped, node, depth = work.pop()
+        info.nodes += 1
+        info.depth = max(info.depth, depth)
+        if m <= leaf_size:
+            leaves.append((off, m, An, Bn))
+            continue
+        attempt = 0
+        fails = 0
+        while True:
+            P, Qm = (Bn, An) if swapped else (An, Bn)
+            if node == ROOT_NODE and attempt == 0:
+                region = (REGION_UNIT_CIRCLE, 0.0, 1.0)
+            else:
+                c = 0.5 * (lo + hi)
+                R = 0.5 * (hi - lo)
+                xi = uniform_scalar(seed, PURPOSE_SHIFT, node, attempt)
+                sigma = c + R * (xi - 0.5)
+                region = (REGION_LINE, sigma, R)
+            st = divide_step(P, Qm, region, seed, node, attempt, tau, maxit,
+                             symmetric=False, split_tol=split_tol)
+            info.iters.append(st.irs.iters)
+            if st.accepted:
+                k = st.k
+                QL[:, off:off + m] = QL[:, off:off + m] @ st.QL
+                QRm[:, off:off + m] = QRm[:, off:off + m] @ st.QR
+                Ah = st.QL.T @ An @ st.QR
+                Bh = st.QL.T @ Bn @ st.QR
+                if region[0] == REGION_UNIT_CIRCLE:
+                    # outside group (leading k) continues swapped
+                    c1 = (-1.0, 1.0, not swapped)
+                    c2 = (-1.0, 1.0, swapped)
+                else:
+                    c1 = (region[1], hi, swapped)
+                    c2 = (lo, region[1], swapped)
+                info.splits += 1
+                work.append((off + k, m - k, Ah[k:, k:].copy(), Bh[k:, k:].copy(), c2[0], c2[1],
+                             c2[2], child_node(node, 1), depth + 1))
+                work.append((off, k, Ah[:k, :k].copy(), Bh[:k, :k].copy(), c1[0], c1[1], c1[2],
+                             child_node(node, 0), depth + 1))
+                break
+            info.failed_attempts += 1
+            if region[0] == REGION_LINE and st.irs.converged and st.rank in (0, m):
+                if st.rank == 0:
+                    hi = region[1]
+                else:
+                    lo = region[1]
+            else:
+                fails += 1
+            attempt += 1
+            if fails > max_fail or attempt > 250:
+                info.status = STATUS_NO_SPLIT
+                return None, None, QL, QRm, None, None, None, info
+    wi_pattern = np.zeros(n)
+    for off, m, An, Bn in leaves:
+        S, T, ZL, ZR, wil, ok = pencil_schur_leaf(An, Bn)
+        if S is None or not ok:
+            info.status = STATUS_NO_CONVERGENCE
+            return None, None, QL, QRm, None, None, None, info
+        QL[:, off:off + m] = QL[:, off:off + m] @ ZL
+        QRm[:, off:off + m] = QRm[:, off:off + m] @ ZR
+        wi_pattern[off:off + m] = wil
+    S = quasi_triangular_part(QL.T @ A @ QRm, wi_pattern)
+    T = np.triu(QL.T @ B @ QRm)
+    ar, ai, be = pencil_eigenvalues(S, T, wi_pattern)
+    return S, T, QL, QRm, ar, ai, be, info
+
+
+def pencil_eigenvalues(S, T, wi):
+    """(alpha_re, alpha_im, beta) from a quasi-triangular S and triangular T:
+    1x1 blocks give (s_ii, 0, t_ii); a 2x2 block (marked by wi[i] > 0 and
+    wi[i+1] = -wi[i]) gives the roots of det(S_blk - z T_blk) = 0 with beta
+    = 1 (alpha = z)."""
+    n = S.shape[0]
+    ar, ai, be = np.zeros(n), np.zeros(n), np.zeros(n)
+    i = 0
+    while i < n:
+        if i + 1 < n and wi[i] > 0.0 and wi[i + 1] == -wi[i]:
+            s = S[i:i + 2, i:i + 2]
+            t = np.triu(T[i:i + 2, i:i + 2])
+            # det(s - z t) = a z^2 + b z + c
+            a = t[0, 0] * t[1, 1]
+            b = -(s[0, 0] * t[1, 1] + s[1, 1] * t[0, 0] - s[1, 0] * t[0, 1])
+            c = s[0, 0] * s[1, 1] - s[0, 1] * s[1, 0]
+            disc = b * b - 4 * a * c
+            if disc < 0:
+                re = -b / (2 * a)
+                im = np.sqrt(-disc) / (2 * abs(a))
+                ar[i], ai[i], be[i] = re, im, 1.0
+                ar[i + 1], ai[i + 1], be[i + 1] = re, -im, 1.0
+            else:
+                r = np.sqrt(disc)
+                z1 = (-b + r) / (2 * a)
+                z2 = (-b - r) / (2 * a)
+                ar[i], be[i] = z1, 1.0
+                ar[i + 1], be[i + 1] = z2, 1.0
+            i += 2
+        else:
+            ar[i], ai[i], be[i] = S[i, i], 0.0, T[i, i]
+            i += 1
+    return ar, ai, be
 
 
 def quasi_triangular_part(T, wi):

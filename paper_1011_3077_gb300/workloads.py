@@ -98,9 +98,9 @@ def batched_symmetric(count=2000, seed=4, nmin=32, nmax=512):
     return mats, spectra
 
 
-def regular_pencil(n, seed=5):
+def regular_pencil(n, seed=5, offdiag_scale=None):
     rng = rng_for(5, seed)
-    T, d = nonsymmetric_triangular(n, rng)
+    T, d = nonsymmetric_triangular(n, rng, offdiag_scale)
     Q = random_orthogonal(n, rng)
     M = Q @ T @ Q.T
     B = np.eye(n) + 0.1 * rng.standard_normal((n, n)) / np.sqrt(n)

@@ -359,3 +359,49 @@ def test_schur_nonsym_config2_small():
     order = np.argsort(wr0.real)
     err = np.abs(got - wr0.real[order])
     assert np.all(err <= 1e-13 * kappa[order] * np.linalg.norm(A, 2) * n + 1e-12)
+
+
+# ------------------------------------------------------------------- pencils
+
+def test_pencil_leaf_generalized_schur():
+    from oracle.leaves import pencil_schur_leaf
+    A, B, d = workloads.regular_pencil(40, seed=1, offdiag_scale=0.1 / np.sqrt(40))
+    S, T, QL, QR, wi, ok = pencil_schur_leaf(A, B)
+    assert ok and np.all(wi == 0.0)
+    assert np.linalg.norm(QL @ S @ QR.T - A) <= 1e-13 * np.linalg.norm(A)
+    assert np.linalg.norm(QL @ T @ QR.T - B) <= 1e-13 * np.linalg.norm(B)
+    assert np.max(np.abs(np.tril(T, -1))) <= 1e-14
+    assert np.max(np.abs(np.tril(S, -1))) <= 1e-13
+    # A = M B => eigenvalues of the pencil are those of M (prescribed)
+    lam = np.diag(S) / np.diag(T)
+    assert np.allclose(np.sort(lam), np.sort(d), atol=1e-11)
+
+
+def test_pencil_leaf_rejects_singular_B():
+    from oracle.leaves import pencil_schur_leaf
+    A = np.eye(5)
+    B = np.diag([1.0, 1.0, 0.0, 1.0, 1.0])
+    assert pencil_schur_leaf(A, B)[-1] is False
+
+
+def test_pencil_schur_recursion_prescribed():
+    from oracle.solve import pencil_schur
+    n = 150
+    A, B, d = workloads.regular_pencil(n, seed=2, offdiag_scale=0.1 / np.sqrt(n))
+    S, T, QL, QR, ar, ai, be, info = pencil_schur(A, B, seed=3, leaf_size=40)
+    assert info.status == STATUS_OK and info.splits >= 3
+    assert np.linalg.norm(A - QL @ S @ QR.T) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(B - QL @ T @ QR.T) <= 1e-12 * np.linalg.norm(B)
+    assert np.linalg.norm(QL.T @ QL - np.eye(n), 2) <= 1e-12
+    assert np.linalg.norm(QR.T @ QR - np.eye(n), 2) <= 1e-12
+    assert np.all(np.tril(T, -1) == 0) and np.all(np.tril(S, -2) == 0)
+    assert np.allclose(np.sort(ar / be), np.sort(d), atol=1e-10)
+
+
+def test_pencil_with_identity_B_matches_standard_problem():
+    from oracle.solve import pencil_schur
+    n = 90
+    A, d, _ = workloads.nonsymmetric_schur(n, seed=6, offdiag_scale=0.1 / np.sqrt(n))
+    S, T, QL, QR, ar, ai, be, info = pencil_schur(A, np.eye(n), seed=1, leaf_size=40)
+    assert info.status == STATUS_OK
+    assert np.allclose(np.sort(ar / be), np.sort(d), atol=1e-10)
