@@ -219,7 +219,15 @@ def _back_solve_right(A, R):
     return X
 
 
-def pencil_schur_leaf(A, B, cond_limit=1e8):
+def _upper_rotation(b10, b11):
+    """2x2 orthogonal Z with [b10, b11] Z = [0, r], r = hypot(b10, b11) >= 0."""
+    r = float(np.hypot(b10, b11))
+    if r == 0.0:
+        return np.eye(2)
+    return np.array([[b11, b10], [-b10, b11]]) / r
+
+
+def pencil_schur_leaf(A, B, cond_limit=1e8, swapped=False):
     """Generalized real Schur form of a small regular pencil (A, B).
 
     Reading for the leaves of the pencil recursion (the paper leaves small
@@ -228,21 +236,44 @@ def pencil_schur_leaf(A, B, cond_limit=1e8):
     M = QL TM QL^T and the RQ factorisation QL^T B = R Z give
         QL^T A Z^T = TM R (quasi-upper-triangular),  QL^T B Z^T = R (upper),
     i.e. QR_ = Z^T.  B^{-1} is applied through its QR factors and a triangular
-    substitution.  Returns (S, T, QL, QR_, ok); ok is False when
-    max|R_ii| / min|R_ii| of B's QR exceeds cond_limit (near-singular B).
+    substitution.
+
+    swapped: the leaf comes from the group the recursion handles as (B, A)
+    (eigenvalues outside the unit circle, Sec. 3.5), where A, not B, is the
+    well-conditioned matrix (B may be singular: infinite eigenvalues).  The
+    same construction is then run on (B, A); it leaves B's blocks of complex
+    pairs 2x2 and A's triangular, so each such block of Q_L^T B Q_R is made
+    upper triangular by one rotation of its two columns of Q_R (A's block
+    becomes a full 2x2 block).
+
+    Returns (S, T, QL, QR_, wi, ok) with S = QL^T A QR_ quasi-upper-triangular
+    and T = QL^T B QR_ upper triangular (up to rounding); wi marks the 2x2
+    blocks (wi[i] > 0, wi[i+1] = -wi[i]).  ok is False when max|R_ii| /
+    min|R_ii| of the factorised matrix's QR exceeds cond_limit.
     """
     from .householder import qr_explicit, rq_explicit
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
-    QB, RB = qr_explicit(B)
+    P, Qm = (B, A) if swapped else (A, B)
+    QB, RB = qr_explicit(Qm)
     d = np.abs(np.diag(RB))
     if d.size and (d.min() == 0.0 or d.max() / d.min() > cond_limit):
         return None, None, None, None, None, False
-    X = _back_solve_right(A, RB)          # A R_B^{-1}
-    M = X @ QB.T                          # A B^{-1}
+    X = _back_solve_right(P, RB)          # P Qm^{-1} = P R^{-1} QB^T
+    M = X @ QB.T
     TM, QL, wr, wi, ok = real_schur(M)
-    R, Qrq = rq_explicit(QL.T @ B)
+    R, Qrq = rq_explicit(QL.T @ Qm)
     QR_ = Qrq.T
+    if swapped:
+        m = A.shape[0]
+        i = 0
+        while i < m - 1:
+            if wi[i] > 0.0 and wi[i + 1] == -wi[i]:
+                blk = QL[:, i:i + 2].T @ B @ QR_[:, i:i + 2]
+                QR_[:, i:i + 2] = QR_[:, i:i + 2] @ _upper_rotation(blk[1, 0], blk[1, 1])
+                i += 2
+            else:
+                i += 1
     S = QL.T @ A @ QR_
     T = QL.T @ B @ QR_
     return S, T, QL, QR_, wi, ok

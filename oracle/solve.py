@@ -265,7 +265,8 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
     disk of radius 1.  Below the root, real lines Re z = sigma on the interval
     [-1, 1] of the (possibly swapped) node, with the symmetric strategy's
     shift and empty-side rules (reading: real lines, as for RNEP).  Leaves by
-    pencil_schur_leaf.  Returns (S, T, QL, QR, alpha_re, alpha_im, beta, info)
+    pencil_schur_leaf in the node's orientation (a swapped leaf factorises A,
+    which is well conditioned there, so infinite eigenvalues are allowed).  Returns (S, T, QL, QR, alpha_re, alpha_im, beta, info)
     with QL^T A QR = S quasi-upper-triangular and QL^T B QR = T upper.
     """
     A = np.asarray(A, dtype=np.float64)
@@ -281,7 +282,7 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
         info.nodes += 1
         info.depth = max(info.depth, depth)
         if m <= leaf_size:
-            leaves.append((off, m, An, Bn))
+            leaves.append((off, m, An, Bn, swapped))
             continue
         attempt = 0
         fails = 0
@@ -330,8 +331,8 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
                 info.status = STATUS_NO_SPLIT
                 return None, None, QL, QRm, None, None, None, info
     wi_pattern = np.zeros(n)
-    for off, m, An, Bn in leaves:
-        S, T, ZL, ZR, wil, ok = pencil_schur_leaf(An, Bn)
+    for off, m, An, Bn, sw in leaves:
+        S, T, ZL, ZR, wil, ok = pencil_schur_leaf(An, Bn, swapped=sw)
         if S is None or not ok:
             info.status = STATUS_NO_CONVERGENCE
             return None, None, QL, QRm, None, None, None, info

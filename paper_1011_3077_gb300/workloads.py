@@ -15,6 +15,10 @@ Workloads (sizes are parameters; the defaults follow the stated configurations):
     (x = sqrt(u1) cos(2 pi u2)), Q Haar.
   * batched_symmetric(count=2000): n log-uniform in [32, 512], lam ~ U[-1, 1].
   * regular_pencil(n): B = I + 0.1 G / sqrt(n), A = (Q T Q^T) B.
+  * pencil_with_infinite(n, n_inf): A = Q1 S Q2^T, B = Q1 T Q2^T with S, T
+    upper triangular; n_inf diagonal pairs (s, t) = (1, 0) with those rows of
+    T zero (a semisimple infinite eigenvalue, singular B), the others (d_i, 1)
+    with d_i as in nonsymmetric_triangular.
   * normal_complex(n): real normal matrix with conjugate pairs a +- ib,
     a, b ~ U[-1.5, 1.5] (the random normal examples of Sec. 3.3.1).
   * near_axis(n=25): real parts +-1e-10, imaginary parts U[-1.5, 1.5].
@@ -105,6 +109,23 @@ def regular_pencil(n, seed=5, offdiag_scale=None):
     M = Q @ T @ Q.T
     B = np.eye(n) + 0.1 * rng.standard_normal((n, n)) / np.sqrt(n)
     return M @ B, B, d
+
+
+def pencil_with_infinite(n, n_inf=2, seed=9, offdiag_scale=None):
+    """(A, B, finite eigenvalues sorted, n_inf) of a regular pencil whose B is
+    singular: det(A - z B) = prod (s_ii - z t_ii) with t_ii = 0 at n_inf
+    positions."""
+    rng = rng_for(9, seed)
+    S, d = nonsymmetric_triangular(n, rng, offdiag_scale)
+    scale = (1.0 / np.sqrt(n)) if offdiag_scale is None else offdiag_scale
+    T = np.triu(rng.standard_normal((n, n)) * scale, 1) + np.eye(n)
+    idx = rng.choice(n, n_inf, replace=False)
+    S[idx, idx] = 1.0
+    T[idx, :] = 0.0       # rank(T) = n - n_inf: the infinite eigenvalue is semisimple
+    finite = np.sort(np.delete(d, idx))
+    Q1 = random_orthogonal(n, rng)
+    Q2 = random_orthogonal(n, rng)
+    return Q1 @ S @ Q2.T, Q1 @ T @ Q2.T, finite, n_inf
 
 
 def _real_normal_from_pairs(re, im, real_eigs, rng):

@@ -405,3 +405,94 @@ def test_pencil_with_identity_B_matches_standard_problem():
     S, T, QL, QR, ar, ai, be, info = pencil_schur(A, np.eye(n), seed=1, leaf_size=40)
     assert info.status == STATUS_OK
     assert np.allclose(np.sort(ar / be), np.sort(d), atol=1e-10)
+
+
+def _pencil_from_blocks(Sm, Tm, seed):
+    rng = np.random.default_rng(seed)
+    Q1 = workloads.random_orthogonal(Sm.shape[0], rng)
+    Q2 = workloads.random_orthogonal(Sm.shape[0], rng)
+    return Q1 @ Sm @ Q2.T, Q1 @ Tm @ Q2.T
+
+
+def test_pencil_leaf_swapped_singular_B_and_pair():
+    """Swapped leaf: all eigenvalues outside the unit circle, one infinite
+    (B singular) and one complex pair 1.5 +- 2i; the unswapped construction
+    must refuse it (B^{-1}), the swapped one must return a generalized real
+    Schur form with T upper triangular and the prescribed (alpha, beta)."""
+    from oracle.leaves import pencil_schur_leaf
+    from oracle.solve import pencil_eigenvalues
+    m = 12
+    rng = np.random.default_rng(11)
+    Sm = np.triu(0.1 * rng.standard_normal((m, m)), 1)
+    Tm = np.triu(0.1 * rng.standard_normal((m, m)), 1) + np.eye(m)
+    real = np.array([2.0, -1.5, 3.0, -2.5, 1.2, -1.1, 2.2, 4.0, -3.0])
+    Sm[np.arange(9), np.arange(9)] = real
+    Sm[9:11, 9:11] = [[1.5, 2.0], [-2.0, 1.5]]
+    Sm[9, 10], Sm[10, 9] = 2.0, -2.0
+    Tm[9, 10] = 0.0
+    Sm[11, 11], Tm[11, 11] = 1.0, 0.0          # infinite eigenvalue
+    A, B = _pencil_from_blocks(Sm, Tm, 12)
+    assert pencil_schur_leaf(A, B)[-1] is False
+    S, T, QL, QR, wi, ok = pencil_schur_leaf(A, B, swapped=True)
+    assert ok
+    nA, nB = np.linalg.norm(A), np.linalg.norm(B)
+    assert np.linalg.norm(QL @ S @ QR.T - A) <= 1e-13 * nA
+    assert np.linalg.norm(QL @ T @ QR.T - B) <= 1e-13 * nB
+    assert np.max(np.abs(np.tril(T, -1))) <= 1e-14 * nB
+    assert np.sum(wi > 0) == 1
+    Sq = S.copy()
+    j = int(np.argmax(wi > 0))
+    Sq[np.tril_indices(m, -1)] = 0.0
+    Sq[j + 1, j] = S[j + 1, j]
+    assert np.max(np.abs(S - Sq)) <= 1e-13 * nA
+    ar, ai, be = pencil_eigenvalues(Sq, np.triu(T), wi)
+    inf = np.abs(be) <= 1e-13 * nB
+    assert np.sum(inf) == 1
+    fin = (ar[~inf] + 1j * ai[~inf]) / be[~inf]
+    want = np.concatenate([real, [1.5 + 2j, 1.5 - 2j]])
+    assert np.allclose(np.sort_complex(fin), np.sort_complex(want), atol=1e-12)
+
+
+def test_upper_rotation_closed_form():
+    from oracle.leaves import _upper_rotation
+    Z = _upper_rotation(3.0, 4.0)
+    assert np.allclose(Z.T @ Z, np.eye(2), atol=1e-16) and np.linalg.det(Z) > 0
+    assert np.allclose(np.array([3.0, 4.0]) @ Z, [0.0, 5.0], atol=1e-15)
+    assert np.array_equal(_upper_rotation(0.0, 0.0), np.eye(2))
+
+
+def test_pencil_schur_infinite_eigenvalues():
+    """Singular B: the root's outside group (with the infinite eigenvalues)
+    is handled swapped down to its leaves; beta = 0 exactly there up to
+    rounding, the finite eigenvalues as prescribed."""
+    from oracle.solve import pencil_schur
+    n = 110
+    A, B, finite, n_inf = workloads.pencil_with_infinite(n, 3, seed=1,
+                                                         offdiag_scale=0.1 / np.sqrt(n))
+    S, T, QL, QR, ar, ai, be, info = pencil_schur(A, B, seed=2, leaf_size=40)
+    assert info.status == STATUS_OK and info.splits >= 2
+    assert np.linalg.norm(A - QL @ S @ QR.T) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(B - QL @ T @ QR.T) <= 1e-12 * np.linalg.norm(B)
+    inf = np.abs(be) <= 1e-12 * np.linalg.norm(B)
+    assert np.sum(inf) == n_inf
+    assert np.all(ai == 0.0)
+    assert np.allclose(np.sort(ar[~inf] / be[~inf]), finite, atol=1e-10)
+
+
+def test_pencil_schur_complex_pairs_both_groups():
+    """A = M B with M real normal (pairs a +- ib, |.| up to ~2): pairs land in
+    swapped and unswapped leaves; (alpha, beta) match eig(M)."""
+    from oracle.solve import pencil_schur
+    n = 100
+    M, _ = workloads.normal_complex(n, seed=5)
+    rng = np.random.default_rng(3)
+    B = np.eye(n) + 0.1 * rng.standard_normal((n, n)) / np.sqrt(n)
+    A = M @ B
+    S, T, QL, QR, ar, ai, be, info = pencil_schur(A, B, seed=4, leaf_size=40)
+    assert info.status == STATUS_OK and info.splits >= 2
+    assert np.linalg.norm(A - QL @ S @ QR.T) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(B - QL @ T @ QR.T) <= 1e-12 * np.linalg.norm(B)
+    got = np.sort_complex((ar + 1j * ai) / be)
+    want = np.sort_complex(np.linalg.eigvals(M))
+    assert np.max(np.abs(got - want)) <= 1e-10
+    assert np.sum(ai != 0) >= 80
