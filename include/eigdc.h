@@ -65,6 +65,7 @@ typedef struct eig_handle_s* eig_handle_t;
 /* problem kinds for eig_solve */
 #define EIG_KIND_SYM 0        /* RSEP recursion (Algorithm 6, Sec. 3.4) */
 #define EIG_KIND_NONSYM 1     /* RNEP recursion (Algorithm 5, Sec. 3.3) */
+#define EIG_KIND_PENCIL 2     /* RGNEP recursion (Algorithm 4, Sec. 3.5): eig_pencil_schur */
 
 typedef struct {
   int kind;
@@ -155,6 +156,44 @@ int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int l
               double* dA, int lda, double* dQ, int ldq, int symmetric,
               uint64_t stream, int attempt, const eig_params_t* params,
               eig_step_info_t* info);
+
+/* Pencil splitters and split test of one RGNEP step (Algorithm 4, lines 2-5):
+ * Q_R = GRURV(2, A_p + B_p, A_p, -1, +1) from the IRS iterates (dApR, dBpR)
+ * of the mapped (A, B); Q_L = GRURV(2, A_pL^T, (A_pL + B_pL)^T, +1, -1) from
+ * the iterates (dApL, dBpL) of the mapped (A^T, B^T) (Haar draw of purpose 6);
+ * A^ = Q_L^T A Q_R, B^ = Q_L^T B Q_R; k minimises ||E21||_1 / ||A||_1 +
+ * ||F21||_1 / ||B||_1.  dA, dB: the ORIGINAL pencil, overwritten with A^, B^;
+ * dQL, dQR (n x n) receive Q_L, Q_R.  FP64 only (EIG_ERR_ARG otherwise).
+ * Returns EIG_NO_SPLIT when no accepted split exists (outputs hold the last
+ * draw); the rank reported is that of the right RURV. */
+int eig_split_pencil(eig_handle_t h, int n, const double* dApR, const double* dBpR,
+                     const double* dApL, const double* dBpL, int ldp, double* dA, int lda,
+                     double* dB, int ldb, double* dQL, int ldql, double* dQR, int ldqr,
+                     uint64_t stream, int attempt, const eig_params_t* params,
+                     eig_step_info_t* info);
+
+/* Generalized real Schur form of a regular pencil (A, B) by the RGNEP
+ * recursion (Algorithm 4 with the strategy of Sec. 3.5): the root divides on
+ * the unit circle, the group outside continues as the swapped pencil (B, A)
+ * (eigenvalues 1/lambda inside the unit disk), later nodes divide on real
+ * lines over [-1, 1].  Leaves (<= leaf_size) are solved in the node's
+ * orientation (P, Q) = (A, B) or (B, A): M = P Q^{-1}, Hessenberg + Francis
+ * on M, then the RQ factor of Q_L^T Q (plus one rotation per complex pair of
+ * a swapped leaf, keeping T triangular).  B may be singular (infinite
+ * eigenvalues go to the swapped side, where A is factorised).
+ * On exit: dA <- S = Q_L^T A Q_R (quasi-upper-triangular, a 2x2 block per
+ * complex pair), dB <- T = Q_L^T B Q_R (upper triangular), dQL,
+ * dQR <- orthogonal (n x n), and the eigenvalues (alphar + i alphai) / beta
+ * (device arrays of n) in block order.  FP64 only (EIG_ERR_ARG otherwise).
+ * Status: EIG_NO_SPLIT (no divide found for a node), EIG_NEAR_SINGULAR_PENCIL
+ * (the matrix a leaf factorises has max/min |r_ii| > 1e8: an eigenvalue
+ * within the leaf's group sits at 0 or infinity of the wrong side, or the
+ * pencil is close to singular), EIG_NO_CONVERGENCE (leaf QR iteration),
+ * EIG_NONFINITE (NaN/Inf input). */
+int eig_pencil_schur(eig_handle_t h, int n, double* dA, int lda, double* dB, int ldb,
+                     double* dQL, int ldql, double* dQR, int ldqr, double* dalphar,
+                     double* dalphai, double* dbeta, const eig_params_t* params,
+                     eig_solve_info_t* info);
 
 /* Full recursive solve (Sec. 3.3 / 3.4 strategies, leaves by cyclic Jacobi or
  * Hessenberg + Francis double-shift QR).

@@ -38,6 +38,7 @@ namespace {
 constexpr int JB_LD_C = 32;   // largest panel width (leading dimension of T)
 constexpr int PURPOSE_HAAR = 4;
 constexpr int PURPOSE_SHIFT = 5;
+constexpr int PURPOSE_HAAR_LEFT = 6;
 constexpr uint64_t ROOT_NODE = 1;
 
 }  // namespace
@@ -404,6 +405,8 @@ static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int ld
 // ---------------------------------------------------------------- split
 struct SplitWork {
   double *G, *Vh, *X, *U, *R2, *S, *Y, *Z, *Qt, *Ucur, *tmp, *Ahat, *scores, *colpart, *gpart;
+  double* QLn = nullptr;    // pencils: left splitter Q_L
+  double* Bhat = nullptr;   // pencils: Q_L^T B Q_R
   unsigned long long* nbits;
   int* rank;
   QRWork qr;
@@ -411,9 +414,14 @@ struct SplitWork {
   void* tcw = nullptr;
 };
 
-static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64) {
+static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64,
+                          bool pencil = false) {
   const size_t start = a.used;
   const size_t nn = (size_t)n * n;
+  if (pencil) {
+    w.QLn = a.take<double>(nn);
+    w.Bhat = a.take<double>(nn);
+  }
   w.G = a.take<double>(nn);
   w.Vh = a.take<double>(nn);
   w.X = a.take<double>(nn);
@@ -488,6 +496,80 @@ static double device_norm1(eig_handle_t h, int rows, int cols, const double* A, 
   return v;
 }
 
+// Q_R = GRURV(2, A_p + B_p, A_p, -1, +1) (Algorithms 4-6) into w.Ucur and the
+// RURV rank of A_p (relative to max |R1_ii|) into w.rank, for Haar draw `code`.
+static void right_splitter(eig_handle_t h, SplitWork& w, int n, const double* Ap,
+                           const double* Bp, int ldp, uint64_t seed, uint64_t stream_id,
+                           int code, int gsplit) {
+  cudaStream_t s = h->stream;
+  // Haar V (Algorithm 1, lines 1-2)
+  CK(gaussian(s, n, n, seed, PURPOSE_HAAR, stream_id, code, w.G, n));
+  qr_explicit(h, w.qr, n, n, w.G, n, w.Vh, n, nullptr, 0);
+  // RURV(A_p): [U, R2] = QR(A_p V^T)
+  mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, true, n, n, n, 1.0, Ap, ldp, w.Vh, n, 0.0, w.X, n,
+     gsplit, w.gpart);
+  qr_explicit(h, w.qr, n, n, w.X, n, w.U, n, w.R2, n);
+  // RQ(U^T (A_p + B_p)) by reversal: Z = (J Y)^T = Q~ R~, U_cur = Q~ J
+  CK(add_matrices(s, n, n, Ap, ldp, Bp, ldp, w.S, n));
+  mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.U, n, w.S, n, 0.0, w.Y, n,
+     gsplit, w.gpart);
+  CK(reverse_transpose(s, n, w.Y, n, w.Z, n));
+  qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, w.G, n);   // R~ (diag: R1 reversed) into G
+  CK(count_rank(s, n, w.R2, n, w.G, n, 1e-8, w.rank));
+  CK(reverse_columns(s, n, n, w.Qt, n, w.Ucur, n));
+}
+
+// Q_L = GRURV(2, A_pL^T, (A_pL + B_pL)^T, +1, -1) (Algorithm 4, left deflating
+// subspace) from the IRS iterates of (A^T, B^T), into w.QLn:
+//   RULV((A_pL + B_pL)^T ^T): X = (A_pL + B_pL) V_L^T = U L (QL via the QR of
+//   the column-reversed X), then Q_L = Q of QR(A_pL^T U).
+static void left_splitter(eig_handle_t h, SplitWork& w, int n, const double* ApL,
+                          const double* BpL, int ldp, uint64_t seed, uint64_t stream_id, int code,
+                          int gsplit) {
+  cudaStream_t s = h->stream;
+  CK(gaussian(s, n, n, seed, PURPOSE_HAAR_LEFT, stream_id, code, w.G, n));
+  qr_explicit(h, w.qr, n, n, w.G, n, w.Vh, n, nullptr, 0);
+  CK(add_matrices(s, n, n, ApL, ldp, BpL, ldp, w.S, n));
+  mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, true, n, n, n, 1.0, w.S, n, w.Vh, n, 0.0, w.X, n,
+     gsplit, w.gpart);
+  CK(reverse_columns(s, n, n, w.X, n, w.Z, n));
+  qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, nullptr, 0);
+  CK(reverse_columns(s, n, n, w.Qt, n, w.U, n));
+  mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, ApL, ldp, w.U, n, 0.0, w.Y, n,
+     gsplit, w.gpart);
+  qr_explicit(h, w.qr, n, n, w.Y, n, w.QLn, n, nullptr, 0);
+}
+
+// Reads the n-1 split scores, the rank and the tensor-core error flag back.
+static void read_split(eig_handle_t h, SplitWork& w, int n, std::vector<double>& hscores,
+                       int& rank) {
+  cudaStream_t s = h->stream;
+  const size_t sbytes = sizeof(double) * std::max(n - 1, 1);
+  char* hb = static_cast<char*>(pinned(h, sbytes + 64));
+  if (n >= 2) CK(cudaMemcpyAsync(hb, w.scores, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hb + sbytes, w.rank, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hb + sbytes + 8, w.qr.q.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int terr;
+  std::memcpy(&terr, hb + sbytes + 8, sizeof(int));
+  if (terr != 0) {
+    h->err = "tensor-core GEMM: a bounded wait timed out";
+    throw Fail{EIG_ERR_CUDA};
+  }
+  if (n >= 2) std::memcpy(hscores.data(), hb, sizeof(double) * (n - 1));
+  std::memcpy(&rank, hb + sbytes, sizeof(int));
+}
+
+static void pick_k(SplitOut& out, const std::vector<double>& hscores, int n) {
+  if (n >= 2) {
+    out.k = choose_k(hscores.data(), n);
+    out.e = hscores[out.k - 1];
+  } else {
+    out.k = 0;
+    out.e = 0.0;
+  }
+}
+
 // Splitter Q = GRURV(2, A_p + B_p, A_p, -1, +1), A^ = Q^T A Q, split test.
 // Results stay in w.Ahat / w.Ucur.
 static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
@@ -503,21 +585,7 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
   CK(cudaMemsetAsync(w.qr.q.tcerr, 0, sizeof(int), s));
   for (int draw = 0; draw < draws; ++draw) {
     const int code = ((attempt & 0x3F) << 2) | (draw & 3);
-    // Haar V (Algorithm 1, lines 1-2)
-    CK(gaussian(s, n, n, p.seed, PURPOSE_HAAR, stream_id, code, w.G, n));
-    qr_explicit(h, w.qr, n, n, w.G, n, w.Vh, n, nullptr, 0);
-    // RURV(A_p): [U, R2] = QR(A_p V^T)
-    mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, true, n, n, n, 1.0, Ap, ldp, w.Vh, n, 0.0, w.X, n,
-       gsplit, w.gpart);
-    qr_explicit(h, w.qr, n, n, w.X, n, w.U, n, w.R2, n);
-    // RQ(U^T (A_p + B_p)) by reversal: Z = (J Y)^T = Q~ R~, U_cur = Q~ J
-    CK(add_matrices(s, n, n, Ap, ldp, Bp, ldp, w.S, n));
-    mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.U, n, w.S, n, 0.0, w.Y, n,
-       gsplit, w.gpart);
-    CK(reverse_transpose(s, n, w.Y, n, w.Z, n));
-    qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, w.G, n);   // R~ (diag: R1 reversed) into G
-    CK(count_rank(s, n, w.R2, n, w.G, n, 1e-8, w.rank));
-    CK(reverse_columns(s, n, n, w.Qt, n, w.Ucur, n));
+    right_splitter(h, w, n, Ap, Bp, ldp, p.seed, stream_id, code, gsplit);
     // similarity and split test
     mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, false, n, n, n, 1.0, A, lda, w.Ucur, n, 0.0, w.tmp,
        n, gsplit, w.gpart);
@@ -525,34 +593,60 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
        w.Ahat, n, gsplit, w.gpart);
     if (symmetric) CK(symmetrize(s, n, w.Ahat, n));
     if (n >= 2) CK(split_scores(s, n, w.Ahat, n, normA > 0 ? 1.0 / normA : 1.0, w.colpart, w.scores, false));
-    const size_t sbytes = sizeof(double) * std::max(n - 1, 1);
-    char* hb = static_cast<char*>(pinned(h, sbytes + 64));
-    if (n >= 2) CK(cudaMemcpyAsync(hb, w.scores, sizeof(double) * (n - 1), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hb + sbytes, w.rank, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hb + sbytes + 8, w.qr.q.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    {
-      int terr;
-      std::memcpy(&terr, hb + sbytes + 8, sizeof(int));
-      if (terr != 0) {
-        h->err = "tensor-core GEMM: a bounded wait timed out";
-        throw Fail{EIG_ERR_CUDA};
-      }
-    }
-    if (n >= 2) std::memcpy(hscores.data(), hb, sizeof(double) * (n - 1));
     int rank;
-    std::memcpy(&rank, hb + sbytes, sizeof(int));
+    read_split(h, w, n, hscores, rank);
     out.rank = rank;
     out.draw = draw;
-    if (n >= 2) {
-      out.k = choose_k(hscores.data(), n);
-      out.e = hscores[out.k - 1];
-    } else {
-      out.k = 0;
-      out.e = 0.0;
-    }
+    pick_k(out, hscores, n);
     out.accepted = irs_converged && out.k > 0 && out.k < n && out.e <= effective_split_tol(p, n);
     if (out.accepted || !irs_converged || rank == 0 || rank == n) break;
+  }
+  return out;
+}
+
+// One RGNEP split (Algorithm 4) from the IRS iterates of (A, B) (right) and
+// of (A^T, B^T) (left): Q_R into w.Ucur, Q_L into w.QLn, A^ = Q_L^T A Q_R
+// into w.Ahat, B^ = Q_L^T B Q_R into w.Bhat.  The score of k is
+// ||E21||_1 / ||A||_1 + ||F21||_1 / ||B||_1.  Acceptance needs both IRS runs
+// converged; redraws (v_draws) stop once the right IRS failed or the rank
+// shows an empty side.
+static SplitOut run_split_pencil(eig_handle_t h, SplitWork& w, int n, const double* ApR,
+                                 const double* BpR, const double* ApL, const double* BpL, int ldp,
+                                 const double* A, int lda, const double* B, int ldb,
+                                 uint64_t stream_id, int attempt, const eig_params_t& p,
+                                 bool conv_right, bool conv_left, std::vector<double>& hscores) {
+  cudaStream_t s = h->stream;
+  const double normA = device_norm1(h, n, n, A, lda, w.nbits);
+  const double normB = device_norm1(h, n, n, B, ldb, w.nbits);
+  const int gsplit = gemm_choose_splits(n, n, n);
+  SplitOut out{0, INFINITY, 0, 0, false};
+  const int draws = std::max(1, p.v_draws);
+  hscores.assign(std::max(n - 1, 0), 0.0);
+  CK(cudaMemsetAsync(w.qr.q.tcerr, 0, sizeof(int), s));
+  for (int draw = 0; draw < draws; ++draw) {
+    const int code = ((attempt & 0x3F) << 2) | (draw & 3);
+    right_splitter(h, w, n, ApR, BpR, ldp, p.seed, stream_id, code, gsplit);
+    left_splitter(h, w, n, ApL, BpL, ldp, p.seed, stream_id, code, gsplit);
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, false, n, n, n, 1.0, A, lda, w.Ucur, n, 0.0, w.tmp,
+       n, gsplit, w.gpart);
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.QLn, n, w.tmp, n, 0.0,
+       w.Ahat, n, gsplit, w.gpart);
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, false, false, n, n, n, 1.0, B, ldb, w.Ucur, n, 0.0, w.tmp,
+       n, gsplit, w.gpart);
+    mm(h, w.prec, w.tcw, w.qr.q.tcerr, true, false, n, n, n, 1.0, w.QLn, n, w.tmp, n, 0.0,
+       w.Bhat, n, gsplit, w.gpart);
+    if (n >= 2) {
+      CK(split_scores(s, n, w.Ahat, n, normA > 0 ? 1.0 / normA : 1.0, w.colpart, w.scores, false));
+      CK(split_scores(s, n, w.Bhat, n, normB > 0 ? 1.0 / normB : 1.0, w.colpart, w.scores, true));
+    }
+    int rank;
+    read_split(h, w, n, hscores, rank);
+    out.rank = rank;
+    out.draw = draw;
+    pick_k(out, hscores, n);
+    out.accepted = conv_right && conv_left && out.k > 0 && out.k < n &&
+                   out.e <= effective_split_tol(p, n);
+    if (out.accepted || !conv_right || rank == 0 || rank == n) break;
   }
   return out;
 }
@@ -597,6 +691,7 @@ struct Node {
   double lo, hi;
   uint64_t id;
   int depth;
+  bool swapped = false;   // pencils: the node is handled as (B, A) (Sec. 3.5)
 };
 
 static void node_diag(eig_handle_t h, const double* Acur, int ld, int off, int m,
@@ -781,14 +876,23 @@ struct NodeWork {
   SplitWork split;
   double* Unode;
   double* dtmp;
+  IRSWork irsL;                      // pencils: IRS of (A^T, B^T)
+  double* At = nullptr;              // pencils: node's (A^T, B^T)
+  double* Bt = nullptr;
 };
 
-static size_t carve_node(Arena& a, int n_total, int m, int prec, NodeWork& w) {
+static size_t carve_node(Arena& a, int n_total, int m, int prec, NodeWork& w,
+                         bool pencil = false) {
   const size_t start = a.used;
   carve_irs(a, m, w.irs, prec);
-  carve_split(a, m, w.split, prec);
+  carve_split(a, m, w.split, prec, pencil);
   w.Unode = a.take<double>((size_t)n_total * m);
   w.dtmp = a.take<double>(2 * (size_t)m + 8);
+  if (pencil) {
+    carve_irs(a, m, w.irsL, prec);
+    w.At = a.take<double>((size_t)m * m);
+    w.Bt = a.take<double>((size_t)m * m);
+  }
   return a.used - start;
 }
 
@@ -799,11 +903,17 @@ struct SolveMain {
   unsigned long long* bits;
   int* status;
   LeafDesc* ddesc;
+  double* Bcur = nullptr;     // pencils: working B
+  double* Zleaf2 = nullptr;   // pencils: right leaf vectors
 };
 
-static size_t carve_main(Arena& a, int n, bool refine, SolveMain& w) {
+static size_t carve_main(Arena& a, int n, bool refine, SolveMain& w, bool pencil = false) {
   const size_t start = a.used;
   const size_t nn = (size_t)n * n;
+  if (pencil) {
+    w.Bcur = a.take<double>(nn);
+    w.Zleaf2 = a.take<double>((size_t)64 * 64 * std::max(1, n));
+  }
   w.Acur = a.take<double>(nn);
   w.wtmp = a.take<double>(2 * (size_t)n + 8);
   w.Zleaf = a.take<double>((size_t)64 * 64 * std::max(1, n));
@@ -826,7 +936,11 @@ struct SolveShared {
   int n = 0, ldu = 0, leaf = 64;
   bool sym = true, verbose = false;
   double* Acur = nullptr;
-  double* dU = nullptr;
+  double* dU = nullptr;        // pencils: Q_L
+  bool pencil = false;
+  double* Bcur = nullptr;
+  double* dQR = nullptr;
+  int ldqr = 0;
   eig_params_t p, pp;
   std::mutex mu;
   std::condition_variable cv;
@@ -959,6 +1073,127 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   }
 }
 
+// One node of the pencil recursion (RGNEP, Algorithm 4; strategy of Sec.
+// 3.5): the root first tries the unit circle; the group outside it (leading
+// k) continues as the swapped pencil (B, A), whose eigenvalues 1/lambda lie
+// inside the unit disk, so every later node splits on real lines Re z =
+// sigma over [lo, hi] within [-1, 1], with the empty-side rule of the
+// symmetric strategy.  Q_L and Q_R of an accepted split update the global
+// left / right Schur vectors and the node's blocks of (A, B).
+static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
+  cudaStream_t s = hw->stream;
+  const int n = S.n, m = nd.m;
+  const eig_params_t& p = S.p;
+  double* An = S.Acur + nd.off + (size_t)nd.off * n;
+  double* Bn = S.Bcur + nd.off + (size_t)nd.off * n;
+  if (m <= S.leaf) {
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.inf.nodes++;
+    S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
+    S.leaves.push_back(LeafDesc{nd.off, m, (int)S.leaves.size() * 64 * 64, nd.swapped ? 1 : 0});
+    return;
+  }
+  Arena arena(base);
+  NodeWork w;
+  carve_node(arena, n, m, p.prec, w, true);
+  const double* P = nd.swapped ? Bn : An;
+  const double* Qm = nd.swapped ? An : Bn;
+  CK2(hw, transpose(s, m, m, P, n, w.At, m));
+  CK2(hw, transpose(s, m, m, Qm, n, w.Bt, m));
+  std::vector<double> hscores;
+  const double tau = p.tau > 0 ? p.tau : default_tau(m);
+  int attempt = 0, fails = 0, iters = 0, failed = 0;
+  double flops = 0.0;
+  while (true) {
+    eig_region_t rg;
+    if (nd.id == ROOT_NODE && attempt == 0) {
+      rg.kind = EIG_REGION_UNIT_CIRCLE;
+      rg.c_or_sigma = 0.0;
+      rg.r_or_s = 1.0;
+    } else {
+      const double c = 0.5 * (nd.lo + nd.hi), R = 0.5 * (nd.hi - nd.lo);
+      const double xi = philox_uniform(p.seed, PURPOSE_SHIFT, nd.id, attempt);
+      rg.kind = EIG_REGION_LINE;
+      rg.c_or_sigma = c + R * (xi - 0.5);
+      rg.r_or_s = R;
+    }
+    IRSOut ir = run_irs(hw, w.irs, m, P, n, Qm, n, rg, tau, p.maxit);
+    IRSOut il = run_irs(hw, w.irsL, m, w.At, m, w.Bt, m, rg, tau, p.maxit);
+    iters += ir.iters;
+    flops += (ir.iters + il.iters) * flops_irs_iter(m);
+    SplitOut so = run_split_pencil(hw, w.split, m, ir.Ap, ir.Bp, il.Ap, il.Bp, m, P, n, Qm, n,
+                                   nd.id, attempt, S.pp, ir.converged, il.converged, hscores);
+    flops += (so.draw + 1) * 2.0 * (flops_grurv(m) + flops_similarity(m));
+    if (S.verbose)
+      std::fprintf(stderr,
+                   "[eigdc] pencil node off=%d m=%d depth=%d swapped=%d attempt=%d region=%d "
+                   "(%.6g, %.6g) iters=%d/%d conv=%d/%d k=%d e=%.3g rank=%d draw=%d accepted=%d\n",
+                   nd.off, m, nd.depth, (int)nd.swapped, attempt, rg.kind, rg.c_or_sigma,
+                   rg.r_or_s, ir.iters, il.iters, (int)ir.converged, (int)il.converged, so.k,
+                   so.e, so.rank, so.draw, (int)so.accepted);
+    if (so.accepted) {
+      const int k = so.k;
+      CK2(hw, gemm(s, false, false, n, m, m, 1.0, S.dU + (size_t)nd.off * S.ldu, S.ldu,
+                   w.split.QLn, m, 0.0, w.Unode, n));
+      CK2(hw, copy_matrix(s, n, m, w.Unode, n, S.dU + (size_t)nd.off * S.ldu, S.ldu));
+      CK2(hw, gemm(s, false, false, n, m, m, 1.0, S.dQR + (size_t)nd.off * S.ldqr, S.ldqr,
+                   w.split.Ucur, m, 0.0, w.Unode, n));
+      CK2(hw, copy_matrix(s, n, m, w.Unode, n, S.dQR + (size_t)nd.off * S.ldqr, S.ldqr));
+      flops += 4.0 * n * (double)m * m;
+      // the split was computed on (P, Qm); write it back in (A, B) order
+      CK2(hw, copy_matrix(s, m, m, w.split.Ahat, m, nd.swapped ? Bn : An, n));
+      CK2(hw, copy_matrix(s, m, m, w.split.Bhat, m, nd.swapped ? An : Bn, n));
+      double lo1, hi1, lo2, hi2;
+      bool sw1, sw2;
+      if (rg.kind == EIG_REGION_UNIT_CIRCLE) {
+        lo1 = lo2 = -1.0;
+        hi1 = hi2 = 1.0;
+        sw1 = !nd.swapped;
+        sw2 = nd.swapped;
+      } else {
+        lo1 = rg.c_or_sigma;
+        hi1 = nd.hi;
+        lo2 = nd.lo;
+        hi2 = rg.c_or_sigma;
+        sw1 = sw2 = nd.swapped;
+      }
+      CK2(hw, cudaStreamSynchronize(s));   // children may run on other streams
+      std::lock_guard<std::mutex> lock(S.mu);
+      S.inf.nodes++;
+      S.inf.splits++;
+      S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
+      S.inf.total_iters += iters;
+      S.inf.failed_attempts += failed;
+      S.inf.flops += flops;
+      S.queue.push_back(Node{nd.off, k, lo1, hi1, child_node(nd.id, 0), nd.depth + 1, sw1});
+      S.queue.push_back(Node{nd.off + k, m - k, lo2, hi2, child_node(nd.id, 1), nd.depth + 1, sw2});
+      S.outstanding += 2;
+      S.cv.notify_all();
+      return;
+    }
+    failed++;
+    if (rg.kind == EIG_REGION_LINE && ir.converged && (so.rank == 0 || so.rank == m)) {
+      if (so.rank == 0) nd.hi = rg.c_or_sigma;
+      else nd.lo = rg.c_or_sigma;
+    } else {
+      fails++;
+    }
+    attempt++;
+    if (fails > p.max_fail || attempt > 250) {
+      std::lock_guard<std::mutex> lock(S.mu);
+      S.inf.nodes++;
+      S.inf.total_iters += iters;
+      S.inf.failed_attempts += failed;
+      S.inf.flops += flops;
+      if (S.status == EIG_OK) {
+        S.status = EIG_NO_SPLIT;
+        S.err = "no split found for a pencil node of size " + std::to_string(m);
+      }
+      return;
+    }
+  }
+}
+
 // Worker loop: take nodes until the tree is finished or a node failed.
 // With own_ws the node scratch is grown in hw's workspace per node; else
 // `fixed_base` (carved for the root size) is used.
@@ -983,10 +1218,11 @@ static void worker_loop(eig_handle_t hw, SolveShared& S, bool own_ws, char* fixe
       if (own_ws && nd.m > S.leaf) {
         Arena meas(nullptr);
         NodeWork tmp;
-        ensure_ws(hw, carve_node(meas, S.n, nd.m, S.p.prec, tmp));
+        ensure_ws(hw, carve_node(meas, S.n, nd.m, S.p.prec, tmp, S.pencil));
         base = hw->ws;
       }
-      process_node(hw, S, nd, base);
+      if (S.pencil) process_pencil_node(hw, S, nd, base);
+      else process_node(hw, S, nd, base);
     } catch (Fail f) {
       std::lock_guard<std::mutex> lock(S.mu);
       if (S.status == EIG_OK) {
@@ -1142,6 +1378,115 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
   return status;
 }
 
+// Generalized real Schur form of a regular pencil (A, B) by the RGNEP
+// recursion (Algorithm 4, Sec. 3.5) and small-pencil leaves (M = A B^{-1},
+// Francis on M, RQ of Q_L^T B).  On exit dA <- S = Q_L^T A Q_R
+// (quasi-upper-triangular), dB <- T = Q_L^T B Q_R (upper), (ar, ai, be) the
+// eigenvalues (ar + i ai) / be in block order.
+static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, int ldb,
+                       double* dQL, int ldql, double* dQR, int ldqr, double* dar, double* dai,
+                       double* dbe, const eig_params_t& p, eig_solve_info_t* info) {
+  cudaStream_t s = h->stream;
+  const int nworkers = std::max(1, std::min(p.workers, 32));
+  const char* venv = std::getenv("EIGDC_VERBOSE");
+  Arena meas(nullptr);
+  SolveMain w;
+  NodeWork nw;
+  carve_main(meas, n, false, w, true);
+  const size_t main_bytes = meas.used;
+  if (nworkers == 1) carve_node(meas, n, n, p.prec, nw, true);
+  ensure_ws(h, meas.used);
+  Arena arena(h->ws);
+  carve_main(arena, n, false, w, true);
+  char* node_base = h->ws + main_bytes;
+  SolveShared S;
+  S.n = n;
+  S.ldu = ldql;
+  S.leaf = std::max(1, std::min(64, p.leaf_size));
+  S.sym = false;
+  S.pencil = true;
+  S.verbose = venv && venv[0] == '1';
+  S.Acur = w.Acur;
+  S.Bcur = w.Bcur;
+  S.dU = dQL;
+  S.dQR = dQR;
+  S.ldqr = ldqr;
+  S.p = p;
+  S.pp = p;
+  std::memset(&S.inf, 0, sizeof(S.inf));
+  CK(copy_matrix(s, n, n, dA, lda, w.Acur, n));
+  CK(copy_matrix(s, n, n, dB, ldb, w.Bcur, n));
+  CK(fill_identity_block(s, n, n, dQL, ldql, 0));
+  CK(fill_identity_block(s, n, n, dQR, ldqr, 0));
+  CK(cudaMemsetAsync(w.status, 0, 8 * sizeof(int), s));
+  CK(nonfinite_check(s, n, n, dA, lda, w.status + 2));
+  CK(nonfinite_check(s, n, n, dB, ldb, w.status + 2));
+  {
+    int* hf = static_cast<int*>(pinned(h, 64));
+    CK(cudaMemcpyAsync(hf, w.status + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*hf) {
+      h->err = "input contains NaN or Inf";
+      S.inf.status = EIG_NONFINITE;
+      if (info) *info = S.inf;
+      return EIG_NONFINITE;
+    }
+  }
+  S.queue.push_back(Node{0, n, -1.0, 1.0, ROOT_NODE, 0, false});
+  S.outstanding = 1;
+  if (nworkers == 1) {
+    worker_loop(h, S, false, node_base);
+  } else {
+    ensure_workers(h, nworkers);
+    std::vector<std::thread> threads;
+    for (int i = 0; i < nworkers; ++i)
+      threads.emplace_back(worker_loop, h->workers[i], std::ref(S), true, nullptr);
+    for (auto& t : threads) t.join();
+    CK(cudaSetDevice(h->device));
+  }
+  int status = S.status;
+  eig_solve_info_t inf = S.inf;
+  if (status != EIG_OK) h->err = S.err;
+  if (status == EIG_OK) {
+    std::vector<LeafDesc>& leaves = S.leaves;
+    const int nl = (int)leaves.size();
+    inf.leaves = nl;
+    double* wr = w.wtmp;
+    double* wi = w.wtmp + n;
+    double* M = w.Tbuf;   // leaves' M = A B^{-1} in the diagonal blocks
+    CK(cudaMemcpyAsync(w.ddesc, leaves.data(), sizeof(LeafDesc) * nl, cudaMemcpyHostToDevice, s));
+    CK(pencil_leaves_phase1(s, nl, w.ddesc, w.Acur, w.Bcur, n, M, w.status));
+    CK(francis_leaves(s, nl, w.ddesc, M, n, wr, wi, w.Zleaf, w.status));
+    CK(pencil_leaves_phase2(s, nl, w.ddesc, w.Acur, w.Bcur, n, wi, w.Zleaf, w.Zleaf2));
+    CK(apply_leaf_vectors(s, nl, w.ddesc, n, dQL, ldql, dQL, ldql, w.Zleaf));
+    CK(apply_leaf_vectors(s, nl, w.ddesc, n, dQR, ldqr, dQR, ldqr, w.Zleaf2));
+    int* hs = static_cast<int*>(pinned(h, 64));
+    CK(cudaMemcpyAsync(hs, w.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs[0] & 2) {
+      status = EIG_NEAR_SINGULAR_PENCIL;
+      h->err = "a leaf pencil has a near-singular B (max/min |r_ii| > 1e8)";
+    } else if (hs[0]) {
+      status = EIG_NO_CONVERGENCE;
+      h->err = "a leaf solver did not converge";
+    }
+    // S = Q_L^T A Q_R, T = Q_L^T B Q_R with the leaves' zero patterns
+    const int gs = gemm_choose_splits(n, n, n);
+    CK(gemm(s, false, false, n, n, n, 1.0, dA, lda, dQR, ldqr, 0.0, w.Tbuf, n, gs, w.gpart));
+    CK(gemm(s, true, false, n, n, n, 1.0, dQL, ldql, w.Tbuf, n, 0.0, dA, lda, gs, w.gpart));
+    CK(gemm(s, false, false, n, n, n, 1.0, dB, ldb, dQR, ldqr, 0.0, w.Tbuf, n, gs, w.gpart));
+    CK(gemm(s, true, false, n, n, n, 1.0, dQL, ldql, w.Tbuf, n, 0.0, dB, ldb, gs, w.gpart));
+    inf.flops += 8.0 * (double)n * n * n;
+    CK(zero_lower_quasi(s, n, dA, lda, wi));
+    CK(upper_triangle(s, n, dB, ldb, dB, ldb));
+    CK(pencil_alpha_beta(s, n, dA, lda, dB, ldb, wi, dar, dai, dbe));
+    CK(cudaStreamSynchronize(s));
+  }
+  inf.status = status;
+  if (info) *info = inf;
+  return status;
+}
+
 static void check_params(eig_handle_t h, const eig_params_t& p) {
   if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0 ||
       (p.prec != EIG_FP64 && p.prec != EIG_SPLIT_BF16X3)) {
@@ -1218,12 +1563,12 @@ unsigned long long eig_kernel_launches(void) { return g_launches.load(); }
 
 int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
   if (!h || !bytes || n < 0) return EIG_ERR_ARG;
-  (void)kind;
   Arena a(nullptr);
   SolveMain w;
   NodeWork nw;
-  carve_main(a, n, true, w);
-  carve_node(a, n, n, EIG_SPLIT_BF16X3, nw);
+  const bool pencil = (kind == EIG_KIND_PENCIL);
+  carve_main(a, n, true, w, pencil);
+  carve_node(a, n, n, pencil ? EIG_FP64 : EIG_SPLIT_BF16X3, nw, pencil);
   *bytes = a.used;
   return EIG_OK;
 }
@@ -1352,6 +1697,66 @@ int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int l
     return EIG_NO_SPLIT;
   }
   return EIG_OK;
+  API_END
+}
+
+int eig_split_pencil(eig_handle_t h, int n, const double* dApR, const double* dBpR,
+                     const double* dApL, const double* dBpL, int ldp, double* dA, int lda,
+                     double* dB, int ldb, double* dQL, int ldql, double* dQR, int ldqr,
+                     uint64_t stream, int attempt, const eig_params_t* params,
+                     eig_step_info_t* info) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dApR && dBpR && dApL && dBpL && ldp >= n, "IRS iterates / ldp invalid");
+  REQUIRE(dA && lda >= n && dB && ldb >= n, "dA / dB invalid");
+  REQUIRE(dQL && ldql >= n && dQR && ldqr >= n, "dQL / dQR invalid");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  REQUIRE(p.prec == EIG_FP64, "pencils are solved in FP64 only");
+  Arena meas(nullptr);
+  SplitWork w;
+  ensure_ws(h, carve_split(meas, n, w, p.prec, true));
+  Arena a(h->ws);
+  carve_split(a, n, w, p.prec, true);
+  std::vector<double> hs;
+  SplitOut so = run_split_pencil(h, w, n, dApR, dBpR, dApL, dBpL, ldp, dA, lda, dB, ldb, stream,
+                                 attempt, p, true, true, hs);
+  cudaStream_t s = h->stream;
+  CK(copy_matrix(s, n, n, w.Ahat, n, dA, lda));
+  CK(copy_matrix(s, n, n, w.Bhat, n, dB, ldb));
+  CK(copy_matrix(s, n, n, w.QLn, n, dQL, ldql));
+  CK(copy_matrix(s, n, n, w.Ucur, n, dQR, ldqr));
+  CK(cudaStreamSynchronize(s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->k = so.k;
+    info->split_residual = so.e;
+    info->rank = so.rank;
+    info->draw = so.draw;
+    info->converged = 1;
+  }
+  if (!so.accepted) {
+    h->err = "no acceptable split";
+    return EIG_NO_SPLIT;
+  }
+  return EIG_OK;
+  API_END
+}
+
+int eig_pencil_schur(eig_handle_t h, int n, double* dA, int lda, double* dB, int ldb,
+                     double* dQL, int ldql, double* dQR, int ldqr, double* dalphar,
+                     double* dalphai, double* dbeta, const eig_params_t* params,
+                     eig_solve_info_t* info) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dA && lda >= n && dB && ldb >= n, "dA / dB invalid");
+  REQUIRE(dQL && ldql >= n && dQR && ldqr >= n, "dQL / dQR invalid");
+  REQUIRE(dalphar && dalphai && dbeta, "eigenvalue outputs are NULL");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  REQUIRE(p.prec == EIG_FP64, "pencils are solved in FP64 only");
+  return pencil_impl(h, n, dA, lda, dB, ldb, dQL, ldql, dQR, ldqr, dalphar, dalphai, dbeta, p,
+                     info);
   API_END
 }
 

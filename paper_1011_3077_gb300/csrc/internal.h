@@ -67,6 +67,9 @@ cudaError_t add_matrices(cudaStream_t s, int rows, int cols, const double* A, in
                          const double* B, int ldb, double* C, int ldc);
 // Z[i][k] = Y[n-1-k][i]   (Z = (J Y)^T)
 cudaError_t reverse_transpose(cudaStream_t s, int n, const double* Y, int ldy, double* Z, int ldz);
+// B (cols x rows, ldb) = A^T
+cudaError_t transpose(cudaStream_t s, int rows, int cols, const double* A, int lda, double* B,
+                      int ldb);
 // B[:, j] = A[:, n-1-j]
 cudaError_t reverse_columns(cudaStream_t s, int rows, int n, const double* A, int lda, double* B,
                             int ldb);
@@ -88,6 +91,10 @@ cudaError_t diag_gershgorin(cudaStream_t s, int n, const double* A, int lda, dou
 cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, const double* Sc, int lds,
                        double rel_tol, int* rank);
 cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const double* wi);
+// (alpha_re, alpha_im, beta) of (S, T) in generalized real Schur form; 2 x 2
+// blocks of S are marked by wi[i] > 0, wi[i+1] = -wi[i]
+cudaError_t pencil_alpha_beta(cudaStream_t s, int n, const double* S, int lds, const double* T,
+                              int ldt, const double* wi, double* ar, double* ai, double* be);
 // FP64 refinement of a symmetric eigendecomposition (n x n packed operands)
 cudaError_t oa_diag(cudaStream_t s, int n, const double* G, const double* S, double* lam,
                     unsigned long long* maxabs);
@@ -105,11 +112,23 @@ struct LeafDesc {
   int off;      // row/col offset of the leaf in the global matrix
   int m;        // size (<= 64)
   int zoff;     // offset of its 64x64 Z slot in the Z buffer (doubles)
+  int swapped = 0;   // pencil leaves: the recursion handled this block as (B, A)
 };
 cudaError_t jacobi_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
                           int lda, double* w, double* Z, int* status);
 cudaError_t francis_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
                            int lda, double* wr, double* wi, double* Z, int* status);
+// Pencil leaves, in the leaf's orientation (P, Q) = (A, B), or (B, A) when
+// swapped: phase 1 writes M = P Q^{-1} into the leaves' diagonal blocks of
+// Mout (status bit 2: Q too ill-conditioned); phase 2 computes the right
+// factor QR from Q and the Schur vectors QL of M (slot of ZL), and for a
+// swapped leaf rotates the column pair of each complex block (wi) so that
+// QL^T B QR stays upper triangular.
+cudaError_t pencil_leaves_phase1(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                                 const double* B, int ld, double* Mout, int* status);
+cudaError_t pencil_leaves_phase2(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                                 const double* B, int ld, const double* wi, const double* ZL,
+                                 double* ZR);
 // U[:, off:off+m] = U[:, off:off+m] * Z_i for each leaf (batched, U is n x n)
 cudaError_t apply_leaf_vectors(cudaStream_t s, int count, const LeafDesc* d_desc, int n,
                                const double* Uin, int ldu_in, double* Uout, int ldu_out,

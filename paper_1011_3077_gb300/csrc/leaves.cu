@@ -435,6 +435,236 @@ cudaError_t francis_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, co
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- pencil leaves
+// Generalized real Schur form of a small regular pencil (A, B) (reading for
+// the leaves of the pencil recursion): with B = QB RB well conditioned,
+// M = A B^{-1} = (A RB^{-1}) QB^T; Francis on M gives M = QL TM QL^T; the RQ
+// factorisation QL^T B = R Z gives QR = Z^T, obtained as the column-reversed Q
+// of QR(B^T QL J) (J the index reversal).  Phase 1 writes M, phase 2 QR.
+constexpr int PL_THREADS = 256;
+
+struct PencilShared {
+  double X[LMAX][LMAX + 1];    // matrix being factorised (R on exit)
+  double V[LMAX][LMAX + 1];    // Householder vectors, V[j][i] = v_j[i] for i >= j
+  double Q[LMAX][LMAX + 1];    // explicit orthogonal factor
+  double W[LMAX][LMAX + 1];    // second operand
+  double beta[LMAX];
+  double red[PL_THREADS / 32];
+};
+
+// Householder QR of S.X (m x m) with explicit Q in S.Q (diag R >= 0).
+__device__ void smem_qr_explicit(PencilShared& S, int m) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      double sigma = 0.0;
+      for (int i = j + 1; i < m; ++i) sigma += S.X[i][j] * S.X[i][j];
+      const double x0 = S.X[j][j];
+      double beta, mu, v0;
+      if (sigma == 0.0) {
+        v0 = 0.0;
+        if (x0 >= 0.0) { beta = 0.0; mu = x0; }
+        else { beta = 2.0; mu = -x0; }
+      } else {
+        mu = sqrt(x0 * x0 + sigma);
+        v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+        beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+      }
+      S.V[j][j] = 1.0;
+      for (int i = j + 1; i < m; ++i) S.V[j][i] = (v0 != 0.0) ? S.X[i][j] / v0 : 0.0;
+      S.beta[j] = beta;
+      S.X[j][j] = mu;
+      for (int i = j + 1; i < m; ++i) S.X[i][j] = 0.0;
+    }
+    __syncthreads();
+    const double beta = S.beta[j];
+    if (beta != 0.0) {
+      for (int c = j + 1 + tid; c < m; c += blockDim.x) {
+        double d = 0.0;
+        for (int i = j; i < m; ++i) d += S.V[j][i] * S.X[i][c];
+        for (int i = j; i < m; ++i) S.X[i][c] -= beta * (S.V[j][i] * d);
+      }
+    }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{m-1} I, applied last reflector first
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, c = idx / m;
+    S.Q[i][c] = (i == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = m - 1; j >= 0; --j) {
+    const double beta = S.beta[j];
+    if (beta != 0.0) {
+      for (int c = tid; c < m; c += blockDim.x) {
+        double d = 0.0;
+        for (int i = j; i < m; ++i) d += S.V[j][i] * S.Q[i][c];
+        for (int i = j; i < m; ++i) S.Q[i][c] -= beta * (S.V[j][i] * d);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Phase 1: M = P Q^{-1} into the diagonal blocks of Mout (ld ldm), (P, Q) =
+// (A, B), or (B, A) for a swapped leaf; status bit 2 when Q's triangular
+// factor has max|r_ii| / min|r_ii| > 1e8.
+__global__ void __launch_bounds__(PL_THREADS)
+pencil_leaf_phase1_kernel(const LeafDesc* __restrict__ desc, const double* __restrict__ A,
+                          const double* __restrict__ B, int ld, double* __restrict__ Mout,
+                          int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PencilShared& S = *reinterpret_cast<PencilShared*>(smem_raw);
+  const LeafDesc d = desc[blockIdx.x];
+  const int m = d.m, off = d.off, tid = threadIdx.x;
+  const double* P = d.swapped ? B : A;
+  const double* Qm = d.swapped ? A : B;
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    S.X[i][j] = Qm[(size_t)(off + i) + (size_t)(off + j) * ld];
+    S.W[i][j] = P[(size_t)(off + i) + (size_t)(off + j) * ld];
+  }
+  __syncthreads();
+  smem_qr_explicit(S, m);
+  __shared__ int bad;
+  if (tid == 0) {
+    double mx = 0.0, mn = INFINITY;
+    for (int i = 0; i < m; ++i) {
+      mx = fmax(mx, fabs(S.X[i][i]));
+      mn = fmin(mn, fabs(S.X[i][i]));
+    }
+    bad = (m > 0 && (mn == 0.0 || mx / mn > 1e8)) ? 1 : 0;
+    if (bad) atomicOr(status, 2);
+  }
+  __syncthreads();
+  if (bad) {
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = idx % m, j = idx / m;
+      Mout[(size_t)(off + i) + (size_t)(off + j) * ld] = 0.0;
+    }
+    return;
+  }
+  // rows of X = A R^{-1} (X R = A), each row independent
+  for (int i = tid; i < m; i += blockDim.x) {
+    for (int j = 0; j < m; ++j) {
+      double t = S.W[i][j];
+      for (int l = 0; l < j; ++l) t -= S.W[i][l] * S.X[l][j];
+      S.W[i][j] = t / S.X[j][j];
+    }
+  }
+  __syncthreads();
+  // M = X Q^T
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, c = idx / m;
+    double t = 0.0;
+    for (int l = 0; l < m; ++l) t = fma(S.W[i][l], S.Q[c][l], t);
+    Mout[(size_t)(off + i) + (size_t)(off + c) * ld] = t;
+  }
+}
+
+// Phase 2: QR = column-reversed Q of QR(Q^T QL J), Q = B (A when swapped),
+// QL = the leaf's Schur vectors (slot in ZL), written to the slot in ZR.  For
+// a swapped leaf each complex block (wi[j] > 0, wi[j+1] = -wi[j]) of
+// QL^T B QR is 2 x 2; the rotation Z with [b10, b11] Z = [0, r] applied to
+// columns j, j+1 of QR makes it upper triangular.
+__global__ void __launch_bounds__(PL_THREADS)
+pencil_leaf_phase2_kernel(const LeafDesc* __restrict__ desc, const double* __restrict__ A,
+                          const double* __restrict__ B, int ld, const double* __restrict__ wi,
+                          const double* __restrict__ ZL, double* __restrict__ ZR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PencilShared& S = *reinterpret_cast<PencilShared*>(smem_raw);
+  const LeafDesc d = desc[blockIdx.x];
+  const int m = d.m, off = d.off, tid = threadIdx.x;
+  const double* Qm = d.swapped ? A : B;
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    S.W[i][j] = Qm[(size_t)(off + i) + (size_t)(off + j) * ld];
+    S.Q[i][j] = ZL[(size_t)d.zoff + i + (size_t)j * LMAX];
+  }
+  __syncthreads();
+  // X = B^T QL J : X[r][j] = sum_i B[i][r] QL[i][m-1-j]
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int r = idx % m, j = idx / m;
+    double t = 0.0;
+    for (int i = 0; i < m; ++i) t = fma(S.W[i][r], S.Q[i][m - 1 - j], t);
+    S.X[r][j] = t;
+  }
+  __syncthreads();
+  smem_qr_explicit(S, m);
+  if (d.swapped) {
+    // X <- QR (column-reversed Q); W <- B block; V <- QL
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = idx % m, j = idx / m;
+      S.X[i][j] = S.Q[i][m - 1 - j];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = idx % m, j = idx / m;
+      S.W[i][j] = B[(size_t)(off + i) + (size_t)(off + j) * ld];
+      S.V[i][j] = ZL[(size_t)d.zoff + i + (size_t)j * LMAX];
+    }
+    __syncthreads();
+    // one thread per complex block; blocks touch disjoint column pairs
+    for (int j = tid; j + 1 < m; j += blockDim.x) {
+      const double wj = wi[off + j], wj1 = wi[off + j + 1];
+      if (!(wj > 0.0 && wj1 == -wj)) continue;
+      // row j+1 of QL^T B times columns j, j+1 of QR
+      double b10 = 0.0, b11 = 0.0;
+      for (int c = 0; c < m; ++c) {
+        double t = 0.0;
+        for (int i = 0; i < m; ++i) t = fma(S.V[i][j + 1], S.W[i][c], t);
+        b10 = fma(t, S.X[c][j], b10);
+        b11 = fma(t, S.X[c][j + 1], b11);
+      }
+      const double r = hypot(b10, b11);
+      if (r == 0.0) continue;
+      const double z00 = b11 / r, z01 = b10 / r, z10 = -b10 / r, z11 = b11 / r;
+      for (int i = 0; i < m; ++i) {
+        const double x0 = S.X[i][j], x1 = S.X[i][j + 1];
+        S.X[i][j] = x0 * z00 + x1 * z10;
+        S.X[i][j + 1] = x0 * z01 + x1 * z11;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      const int i = idx % m, j = idx / m;
+      ZR[(size_t)d.zoff + i + (size_t)j * LMAX] = S.X[i][j];
+    }
+    return;
+  }
+  for (int idx = tid; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    ZR[(size_t)d.zoff + i + (size_t)j * LMAX] = S.Q[i][m - 1 - j];
+  }
+}
+
+cudaError_t pencil_leaves_phase1(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                                 const double* B, int ld, double* Mout, int* status) {
+  if (count == 0) return cudaSuccess;
+  static const bool attr = [] {   // once per process (thread-safe static init)
+    cudaFuncSetAttribute(pencil_leaf_phase1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(PencilShared));
+    cudaFuncSetAttribute(pencil_leaf_phase2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(PencilShared));
+    return true;
+  }();
+  (void)attr;
+  note_launches(1);
+  pencil_leaf_phase1_kernel<<<count, PL_THREADS, sizeof(PencilShared), s>>>(d_desc, A, B, ld, Mout,
+                                                                              status);
+  return cudaGetLastError();
+}
+
+cudaError_t pencil_leaves_phase2(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
+                                 const double* B, int ld, const double* wi, const double* ZL,
+                                 double* ZR) {
+  if (count == 0) return cudaSuccess;
+  note_launches(1);
+  pencil_leaf_phase2_kernel<<<count, PL_THREADS, sizeof(PencilShared), s>>>(d_desc, A, B, ld, wi,
+                                                                              ZL, ZR);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- U * Z
 // For leaf t and a 64-row slab of U: U[rows, off:off+m] <- U[rows, off:off+m] Z_t.
 // Each CTA reads its rows of the leaf's columns into shared memory before

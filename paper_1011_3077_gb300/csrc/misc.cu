@@ -193,6 +193,32 @@ cudaError_t reverse_transpose(cudaStream_t s, int n, const double* Y, int ldy, d
   return cudaGetLastError();
 }
 
+// B (cols x rows) = A^T for A rows x cols, 32 x 32 shared tiles.
+__global__ void transpose_kernel(int rows, int cols, const double* __restrict__ A, int lda,
+                                 double* __restrict__ B, int ldb) {
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int q = ty; q < 32; q += 8) {
+    const int r = r0 + tx, c = c0 + q;
+    if (r < rows && c < cols) tile[q][tx] = A[r + (size_t)c * lda];
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    const int r = r0 + q, c = c0 + tx;     // B(c, r) = A(r, c)
+    if (r < rows && c < cols) B[c + (size_t)r * ldb] = tile[tx][q];
+  }
+}
+
+cudaError_t transpose(cudaStream_t s, int rows, int cols, const double* A, int lda, double* B,
+                      int ldb) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  note_launches(1);
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(rows, cols, A, lda, B, ldb);
+  return cudaGetLastError();
+}
+
 __global__ void reverse_columns_kernel(int rows, int n, const double* __restrict__ A, int lda,
                                        double* __restrict__ B, int ldb) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -494,6 +520,56 @@ cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const do
   if (t == 0) return cudaSuccess;
   note_launches(1);
   zero_lower_quasi_kernel<<<blocks_for(t, 256), 256, 0, s>>>(n, T, ldt, wi);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pencil eigenvalues
+// (alpha_re, alpha_im, beta) of a pencil in generalized real Schur form: S
+// quasi-upper-triangular, T upper triangular.  A 1 x 1 block gives
+// (s_ii, 0, t_ii); a 2 x 2 block, marked by wi[i] > 0 and wi[i+1] = -wi[i],
+// gives the two roots of det(S_blk - z T_blk) = a z^2 + b z + c with beta = 1.
+// One thread per index; both threads of a block evaluate the same quadratic.
+__global__ void pencil_alpha_beta_kernel(int n, const double* __restrict__ S, int lds,
+                                         const double* __restrict__ T, int ldt,
+                                         const double* __restrict__ wi, double* __restrict__ ar,
+                                         double* __restrict__ ai, double* __restrict__ be) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const bool first = i + 1 < n && wi[i] > 0.0 && wi[i + 1] == -wi[i];
+  const bool second = i > 0 && wi[i - 1] > 0.0 && wi[i] == -wi[i - 1];
+  if (!first && !second) {
+    ar[i] = S[i + (size_t)i * lds];
+    ai[i] = 0.0;
+    be[i] = T[i + (size_t)i * ldt];
+    return;
+  }
+  const int j = first ? i : i - 1;
+  const double s00 = S[j + (size_t)j * lds], s01 = S[j + (size_t)(j + 1) * lds];
+  const double s10 = S[j + 1 + (size_t)j * lds], s11 = S[j + 1 + (size_t)(j + 1) * lds];
+  const double t00 = T[j + (size_t)j * ldt], t01 = T[j + (size_t)(j + 1) * ldt];
+  const double t11 = T[j + 1 + (size_t)(j + 1) * ldt];
+  const double a = t00 * t11;
+  const double b = -(s00 * t11 + s11 * t00 - s10 * t01);
+  const double c = s00 * s11 - s01 * s10;
+  const double disc = b * b - 4.0 * a * c;
+  if (disc < 0.0) {
+    const double re = -b / (2.0 * a);
+    const double im = sqrt(-disc) / (2.0 * fabs(a));
+    ar[i] = re;
+    ai[i] = first ? im : -im;
+  } else {
+    const double r = sqrt(disc);
+    ar[i] = (first ? (-b + r) : (-b - r)) / (2.0 * a);
+    ai[i] = 0.0;
+  }
+  be[i] = 1.0;
+}
+
+cudaError_t pencil_alpha_beta(cudaStream_t s, int n, const double* S, int lds, const double* T,
+                              int ldt, const double* wi, double* ar, double* ai, double* be) {
+  if (n == 0) return cudaSuccess;
+  note_launches(1);
+  pencil_alpha_beta_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, S, lds, T, ldt, wi, ar, ai, be);
   return cudaGetLastError();
 }
 

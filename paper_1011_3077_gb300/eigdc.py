@@ -36,8 +36,10 @@ EIG_FP64 = 0
 EIG_SPLIT_BF16X3 = 1
 EIG_KIND_SYM = 0
 EIG_KIND_NONSYM = 1
+EIG_KIND_PENCIL = 2
 PURPOSE_HAAR = 4
 PURPOSE_SHIFT = 5
+PURPOSE_HAAR_LEFT = 6
 ROOT_NODE = 1
 
 
@@ -87,6 +89,10 @@ _SIGNATURES = {
     "eig_last_R": (_I, [_P, _I, _P, _I]),
     "eig_split": (_I, [_P, _I, _P, _P, _I, _P, _I, _P, _I, _I, _U64, _I,
                        ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
+    "eig_split_pencil": (_I, [_P, _I, _P, _P, _P, _P, _I, _P, _I, _P, _I, _P, _I, _P, _I,
+                              _U64, _I, ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
+    "eig_pencil_schur": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P,
+                              ctypes.POINTER(Params), ctypes.POINTER(SolveInfo)]),
     "eig_solve": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
                        ctypes.POINTER(SolveInfo)]),
     "eig_solve_batched": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Params),
@@ -224,6 +230,24 @@ def eig_split(h, n, dAp, dBp, ldp, dA, lda, dQ, ldq, symmetric, stream, attempt,
     rc = lib().eig_split(h.ptr, n, _ptr(dAp), _ptr(dBp), ldp, _ptr(dA), lda, _ptr(dQ), ldq,
                          int(symmetric), int(stream), int(attempt), ctypes.byref(params),
                          ctypes.byref(info))
+    return rc, info
+
+
+def eig_split_pencil(h, n, dApR, dBpR, dApL, dBpL, ldp, dA, lda, dB, ldb, dQL, ldql, dQR, ldqr,
+                     stream, attempt, params):
+    info = StepInfo()
+    rc = lib().eig_split_pencil(h.ptr, n, _ptr(dApR), _ptr(dBpR), _ptr(dApL), _ptr(dBpL), ldp,
+                                _ptr(dA), lda, _ptr(dB), ldb, _ptr(dQL), ldql, _ptr(dQR), ldqr,
+                                int(stream), int(attempt), ctypes.byref(params),
+                                ctypes.byref(info))
+    return rc, info
+
+
+def eig_pencil_schur(h, n, dA, lda, dB, ldb, dQL, ldql, dQR, ldqr, dar, dai, dbe, params):
+    info = SolveInfo()
+    rc = lib().eig_pencil_schur(h.ptr, n, _ptr(dA), lda, _ptr(dB), ldb, _ptr(dQL), ldql,
+                                _ptr(dQR), ldqr, _ptr(dar), _ptr(dai), _ptr(dbe),
+                                ctypes.byref(params), ctypes.byref(info))
     return rc, info
 
 
@@ -381,3 +405,19 @@ def schur_nonsymmetric(h, A, params=None):
     dU = torch.zeros((n, n), dtype=torch.float64, device=dA.device)
     rc, info = eig_solve(h, EIG_KIND_NONSYM, n, dA, n, dwr, dwi, dU, n, params)
     return rc, to_host(dA), to_host(dU), dwr.cpu().numpy(), dwi.cpu().numpy(), info
+
+
+def pencil_schur(h, A, B, params=None):
+    """(rc, S, T, QL, QR, alphar, alphai, beta, info) for a real numpy pencil,
+    through eig_pencil_schur."""
+    import torch
+    n = A.shape[0]
+    params = params or default_params()
+    dA = to_device(A)
+    dB = to_device(B)
+    z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=dA.device)
+    dQL, dQR = z(n, n), z(n, n)
+    dar, dai, dbe = z(n), z(n), z(n)
+    rc, info = eig_pencil_schur(h, n, dA, n, dB, n, dQL, n, dQR, n, dar, dai, dbe, params)
+    return (rc, to_host(dA), to_host(dB), to_host(dQL), to_host(dQR), dar.cpu().numpy(),
+            dai.cpu().numpy(), dbe.cpu().numpy(), info)

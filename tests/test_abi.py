@@ -25,7 +25,8 @@ def built():
 def test_header_declares_the_path():
     names = _declared()
     for must in ("eig_divide_step", "eig_split", "eig_solve", "eig_create", "eig_destroy",
-                 "eig_qr", "eig_haar", "eig_split_test", "eig_gemm"):
+                 "eig_qr", "eig_haar", "eig_split_test", "eig_gemm", "eig_split_pencil",
+                 "eig_pencil_schur"):
         assert must in names
 
 
