@@ -36,7 +36,8 @@ tests/test_oracle_method.py.
 """
 import numpy as np
 
-from .irs import irs, region_map, norm1, default_tau, REGION_LINE, REGION_UNIT_CIRCLE
+from .irs import (irs, region_map, norm1, default_tau, REGION_LINE, REGION_UNIT_CIRCLE,
+                  REGION_CIRCLE)
 from .rurv import haar, splitter_right, splitter_left, numerical_rank
 from .split import split_test, symmetrise
 from .leaves import jacobi_eig, real_schur, pencil_schur_leaf
@@ -256,18 +257,37 @@ def schur_nonsym(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
     return T, Q, wr, wi, info
 
 
+RADIUS_EXP_LIMIT = 512.0     # 2^(+-512): the circle search stops there
+
+
+def _circle_region(r):
+    if r == 1.0:
+        return (REGION_UNIT_CIRCLE, 0.0, 1.0)
+    return (REGION_CIRCLE, 0.0, r)
+
+
 def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None, max_fail=8):
     """Generalized real Schur form of a regular pencil by RGNEP recursion.
 
-    Strategy (Sec. 3.5): the root splits on the unit circle; the group
-    outside is handled as the swapped pencil (B, A), whose eigenvalues
-    1/lambda lie inside the unit disk, so every child's spectrum is in the
-    disk of radius 1.  Below the root, real lines Re z = sigma on the interval
-    [-1, 1] of the (possibly swapped) node, with the symmetric strategy's
-    shift and empty-side rules (reading: real lines, as for RNEP).  Leaves by
-    pencil_schur_leaf in the node's orientation (a swapped leaf factorises A,
-    which is well conditioned there, so infinite eigenvalues are allowed).  Returns (S, T, QL, QR, alpha_re, alpha_im, beta, info)
-    with QL^T A QR = S quasi-upper-triangular and QL^T B QR = T upper.
+    Strategy (Sec. 3.5): the root first divides on circles |z| = r about the
+    origin: r = 1; if every eigenvalue is inside, r = 1/2, 1/4, 1/16, ...
+    (r <- r^2); if every one is outside, r = 2, 4, 16, ...  A circle that
+    divides splits the node: the inside group keeps the orientation and lies
+    in |z| < r, the outside group continues as the swapped pencil (B, A),
+    whose eigenvalues 1/lambda lie in |z| < 1/r.  If the search runs past the
+    last circle holding everything inside (outside), that circle bounds the
+    spectrum (the node is swapped in the second case) and the node goes on
+    with real lines.  Below the root: real lines Re z = sigma over [-b, b], b
+    the bound of the node, sigma uniform in the middle half of [lo, hi], with
+    the empty-side rule of the symmetric strategy (reading: real lines, as
+    for RNEP).  Readings where the paper is silent: a circle whose IRS does
+    not converge, or that splits but fails the split test, is retried with
+    its radius times 2^((2 xi - 1)/4) (xi the node's Philox uniform for the
+    attempt) and counts as a failure; the search stops at 2^(+-512).
+    Leaves by pencil_schur_leaf in the node's orientation (a swapped leaf
+    factorises A, which is well conditioned there, so infinite eigenvalues are
+    allowed).  Returns (S, T, QL, QR, alpha_re, alpha_im, beta, info) with
+    QL^T A QR = S quasi-upper-triangular and QL^T B QR = T upper.
     """
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
@@ -286,10 +306,13 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
             continue
         attempt = 0
         fails = 0
+        circle = node == ROOT_NODE      # circle search phase
+        r, r_prev, direction = 1.0, None, 0
+        r_try = r
         while True:
             P, Qm = (Bn, An) if swapped else (An, Bn)
-            if node == ROOT_NODE and attempt == 0:
-                region = (REGION_UNIT_CIRCLE, 0.0, 1.0)
+            if circle:
+                region = _circle_region(r_try)
             else:
                 c = 0.5 * (lo + hi)
                 R = 0.5 * (hi - lo)
@@ -305,10 +328,11 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
                 QRm[:, off:off + m] = QRm[:, off:off + m] @ st.QR
                 Ah = st.QL.T @ An @ st.QR
                 Bh = st.QL.T @ Bn @ st.QR
-                if region[0] == REGION_UNIT_CIRCLE:
-                    # outside group (leading k) continues swapped
-                    c1 = (-1.0, 1.0, not swapped)
-                    c2 = (-1.0, 1.0, swapped)
+                if circle:
+                    # outside group (leading k) continues swapped, |1/z| < 1/r
+                    rr = region[2]
+                    c1 = (-1.0 / rr, 1.0 / rr, not swapped)
+                    c2 = (-rr, rr, swapped)
                 else:
                     c1 = (region[1], hi, swapped)
                     c2 = (lo, region[1], swapped)
@@ -319,7 +343,31 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
                              child_node(node, 0), depth + 1))
                 break
             info.failed_attempts += 1
-            if region[0] == REGION_LINE and st.irs.converged and st.rank in (0, m):
+            empty = st.irs.converged and st.rank in (0, m)
+            if circle and empty:
+                inside = st.rank == 0
+                if inside and direction > 0:
+                    # all outside r_prev, all inside r: bounded after the swap
+                    swapped, lo, hi, circle = not swapped, -1.0 / r_prev, 1.0 / r_prev, False
+                elif not inside and direction < 0:
+                    # all inside r_prev, all outside r: r_prev bounds them
+                    lo, hi, circle = -r_prev, r_prev, False
+                else:
+                    direction = -1 if inside else 1
+                    r_prev = r
+                    r = (0.5 if inside else 2.0) if r == 1.0 else r * r
+                    if abs(np.log2(r)) > RADIUS_EXP_LIMIT:
+                        if inside:
+                            lo, hi = -r_prev, r_prev
+                        else:
+                            swapped, lo, hi = not swapped, -1.0 / r_prev, 1.0 / r_prev
+                        circle = False
+                r_try = r
+            elif circle:
+                fails += 1
+                xi = uniform_scalar(seed, PURPOSE_SHIFT, node, attempt)
+                r_try = r * 2.0 ** (0.25 * (2.0 * xi - 1.0))
+            elif region[0] == REGION_LINE and empty:
                 if st.rank == 0:
                     hi = region[1]
                 else:

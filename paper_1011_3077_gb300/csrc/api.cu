@@ -1074,12 +1074,18 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
 }
 
 // One node of the pencil recursion (RGNEP, Algorithm 4; strategy of Sec.
-// 3.5): the root first tries the unit circle; the group outside it (leading
-// k) continues as the swapped pencil (B, A), whose eigenvalues 1/lambda lie
-// inside the unit disk, so every later node splits on real lines Re z =
-// sigma over [lo, hi] within [-1, 1], with the empty-side rule of the
-// symmetric strategy.  Q_L and Q_R of an accepted split update the global
-// left / right Schur vectors and the node's blocks of (A, B).
+// 3.5).  The root searches circles |z| = r about the origin: r = 1, then
+// r <- r^2 from 1/2 while every eigenvalue is inside, or from 2 while every
+// one is outside.  A dividing circle splits the node: the inside group keeps
+// its orientation, bounded by r; the outside group (leading k) continues as
+// the swapped pencil (B, A), bounded by 1/r.  Running past the last circle
+// that held everything inside (outside) makes that circle the node's bound
+// (swapping in the second case).  Other nodes divide on real lines Re z =
+// sigma over [lo, hi] with the empty-side rule of the symmetric strategy.
+// A circle whose IRS fails or whose split is rejected is retried with its
+// radius times 2^((2 xi - 1)/4); the search stops at 2^(+-512).  Q_L and Q_R
+// of an accepted split update the global left / right Schur vectors and the
+// node's blocks of (A, B).
 static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   cudaStream_t s = hw->stream;
   const int n = S.n, m = nd.m;
@@ -1096,20 +1102,28 @@ static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* 
   Arena arena(base);
   NodeWork w;
   carve_node(arena, n, m, p.prec, w, true);
-  const double* P = nd.swapped ? Bn : An;
-  const double* Qm = nd.swapped ? An : Bn;
-  CK2(hw, transpose(s, m, m, P, n, w.At, m));
-  CK2(hw, transpose(s, m, m, Qm, n, w.Bt, m));
+  const double* P = nullptr;
+  const double* Qm = nullptr;
   std::vector<double> hscores;
   const double tau = p.tau > 0 ? p.tau : default_tau(m);
   int attempt = 0, fails = 0, iters = 0, failed = 0;
   double flops = 0.0;
+  bool circle = nd.id == ROOT_NODE;
+  double r = 1.0, r_prev = 0.0, r_try = 1.0;
+  int direction = 0;
+  auto orient = [&]() {   // (P, Qm) = (A, B) or (B, A), and their transposes
+    P = nd.swapped ? Bn : An;
+    Qm = nd.swapped ? An : Bn;
+    CK2(hw, transpose(s, m, m, P, n, w.At, m));
+    CK2(hw, transpose(s, m, m, Qm, n, w.Bt, m));
+  };
+  orient();
   while (true) {
     eig_region_t rg;
-    if (nd.id == ROOT_NODE && attempt == 0) {
-      rg.kind = EIG_REGION_UNIT_CIRCLE;
+    if (circle) {
+      rg.kind = r_try == 1.0 ? EIG_REGION_UNIT_CIRCLE : EIG_REGION_CIRCLE;
       rg.c_or_sigma = 0.0;
-      rg.r_or_s = 1.0;
+      rg.r_or_s = r_try;
     } else {
       const double c = 0.5 * (nd.lo + nd.hi), R = 0.5 * (nd.hi - nd.lo);
       const double xi = philox_uniform(p.seed, PURPOSE_SHIFT, nd.id, attempt);
@@ -1145,9 +1159,12 @@ static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* 
       CK2(hw, copy_matrix(s, m, m, w.split.Bhat, m, nd.swapped ? An : Bn, n));
       double lo1, hi1, lo2, hi2;
       bool sw1, sw2;
-      if (rg.kind == EIG_REGION_UNIT_CIRCLE) {
-        lo1 = lo2 = -1.0;
-        hi1 = hi2 = 1.0;
+      if (circle) {
+        const double rr = rg.r_or_s;
+        lo1 = -1.0 / rr;
+        hi1 = 1.0 / rr;
+        lo2 = -rr;
+        hi2 = rr;
         sw1 = !nd.swapped;
         sw2 = nd.swapped;
       } else {
@@ -1172,7 +1189,43 @@ static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* 
       return;
     }
     failed++;
-    if (rg.kind == EIG_REGION_LINE && ir.converged && (so.rank == 0 || so.rank == m)) {
+    const bool empty = ir.converged && (so.rank == 0 || so.rank == m);
+    if (circle && empty) {
+      const bool inside = so.rank == 0;
+      if (inside && direction > 0) {
+        // everything outside r_prev and inside r: bounded once swapped
+        nd.swapped = !nd.swapped;
+        nd.lo = -1.0 / r_prev;
+        nd.hi = 1.0 / r_prev;
+        circle = false;
+        orient();
+      } else if (!inside && direction < 0) {
+        nd.lo = -r_prev;   // everything inside r_prev and outside r
+        nd.hi = r_prev;
+        circle = false;
+      } else {
+        direction = inside ? -1 : 1;
+        r_prev = r;
+        r = (r == 1.0) ? (inside ? 0.5 : 2.0) : r * r;
+        if (std::fabs(std::log2(r)) > 512.0) {
+          if (inside) {
+            nd.lo = -r_prev;
+            nd.hi = r_prev;
+          } else {
+            nd.swapped = !nd.swapped;
+            nd.lo = -1.0 / r_prev;
+            nd.hi = 1.0 / r_prev;
+            orient();
+          }
+          circle = false;
+        }
+      }
+      r_try = r;
+    } else if (circle) {
+      fails++;
+      const double xi = philox_uniform(p.seed, PURPOSE_SHIFT, nd.id, attempt);
+      r_try = r * std::exp2(0.25 * (2.0 * xi - 1.0));
+    } else if (rg.kind == EIG_REGION_LINE && empty) {
       if (so.rank == 0) nd.hi = rg.c_or_sigma;
       else nd.lo = rg.c_or_sigma;
     } else {

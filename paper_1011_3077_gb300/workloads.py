@@ -102,9 +102,15 @@ def batched_symmetric(count=2000, seed=4, nmin=32, nmax=512):
     return mats, spectra
 
 
-def regular_pencil(n, seed=5, offdiag_scale=None):
+def regular_pencil(n, seed=5, offdiag_scale=None, eig_scale=1.0):
+    """(A, B, eigenvalues) with A = (Q T Q^T) B; eig_scale multiplies T (its
+    spectrum and its coupling, so relative conditioning is unchanged), e.g.
+    0.15: every eigenvalue inside |z| < 1/2; 6: every one outside |z| = 1."""
     rng = rng_for(5, seed)
     T, d = nonsymmetric_triangular(n, rng, offdiag_scale)
+    if eig_scale != 1.0:
+        T = T * eig_scale
+        d = d * eig_scale
     Q = random_orthogonal(n, rng)
     M = Q @ T @ Q.T
     B = np.eye(n) + 0.1 * rng.standard_normal((n, n)) / np.sqrt(n)

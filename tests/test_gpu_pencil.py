@@ -158,6 +158,27 @@ def test_pencil_schur_infinite_eigenvalues(E):
     assert np.allclose(np.sort(ar[~inf] / be[~inf]), finite, atol=1e-10)
 
 
+@pytest.mark.parametrize("eig_scale", [0.15, 6.0, 0.05])
+def test_pencil_circle_search_matches_oracle(E, eig_scale):
+    """Spectra entirely inside |z| = 1/2 or outside |z| = 1: the root's circle
+    search (Sec. 3.5) takes the same radii, splits and failed attempts as the
+    oracle."""
+    eigdc, h, torch = E
+    n = 120
+    A, B, d = workloads.regular_pencil(n, seed=3, offdiag_scale=0.1 / np.sqrt(n),
+                                       eig_scale=eig_scale)
+    rc, S, T, QL, QR, ar, ai, be, info = eigdc.pencil_schur(
+        h, A, B, eigdc.default_params(seed=1, leaf_size=40))
+    assert rc == eigdc.EIG_OK
+    _check_form(A, B, S, T, QL, QR, ar, ai, be)
+    So, To, QLo, QRo, aro, aio, beo, io = opencil(A, B, seed=1, leaf_size=40)
+    assert io.status == 0
+    assert info.splits == io.splits and info.nodes == io.nodes
+    assert info.failed_attempts == io.failed_attempts >= 1
+    lam = np.sort(ar / be)
+    assert np.allclose(lam, np.sort(d), rtol=1e-10, atol=1e-10 * np.max(np.abs(d)))
+
+
 def test_pencil_identity_B_matches_standard(E):
     eigdc, h, torch = E
     n = 90

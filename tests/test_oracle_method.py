@@ -496,3 +496,46 @@ def test_pencil_schur_complex_pairs_both_groups():
     want = np.sort_complex(np.linalg.eigvals(M))
     assert np.max(np.abs(got - want)) <= 1e-10
     assert np.sum(ai != 0) >= 80
+
+
+@pytest.mark.parametrize("eig_scale,lo_r,hi_r", [(0.15, 0.03, 0.45), (6.0, 1.2, 18.0)])
+def test_pencil_schur_circle_search(eig_scale, lo_r, hi_r):
+    """Every eigenvalue inside |z| = 1/2 (the search goes 1, 1/2, 1/4) or
+    outside |z| = 1 (1, 2, ...): the root divides on a circle other than the
+    unit circle and the solve still returns the prescribed spectrum."""
+    from oracle.solve import pencil_schur
+    n = 120
+    A, B, d = workloads.regular_pencil(n, seed=3, offdiag_scale=0.1 / np.sqrt(n),
+                                       eig_scale=eig_scale)
+    assert lo_r - 1e-12 <= np.min(np.abs(d)) and np.max(np.abs(d)) <= hi_r + 1e-12
+    S, T, QL, QR, ar, ai, be, info = pencil_schur(A, B, seed=1, leaf_size=40)
+    assert info.status == STATUS_OK and info.splits >= 2
+    assert info.failed_attempts >= 1          # the unit circle did not divide
+    assert np.linalg.norm(A - QL @ S @ QR.T) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(B - QL @ T @ QR.T) <= 1e-12 * np.linalg.norm(B)
+    lam = np.sort(ar / be)
+    assert np.allclose(lam, np.sort(d), rtol=1e-10, atol=1e-10 * np.max(np.abs(d)))
+
+
+def test_pencil_root_circle_sequence():
+    """The radii the root tries follow 2^(-2^k) / 2^(2^k) (Sec. 3.5)."""
+    from oracle import solve as osolve
+    seen = []
+    real = osolve.divide_step
+
+    def spy(P, Qm, region, *a, **kw):
+        if a[1] == osolve.ROOT_NODE:
+            seen.append(region)
+        return real(P, Qm, region, *a, **kw)
+    n = 70
+    A, B, d = workloads.regular_pencil(n, seed=4, offdiag_scale=0.1 / np.sqrt(n), eig_scale=0.05)
+    # |d| in [0.01, 0.15]: 1, 1/2, 1/4 all hold everything; 1/16 = 0.0625 divides
+    osolve.divide_step = spy
+    try:
+        out = osolve.pencil_schur(A, B, seed=2, leaf_size=30)
+    finally:
+        osolve.divide_step = real
+    assert out[-1].status == STATUS_OK
+    radii = [reg[2] for reg in seen]
+    assert radii[:4] == [1.0, 0.5, 0.25, 0.0625]
+    assert seen[0][0] == REGION_UNIT_CIRCLE and all(reg[0] == REGION_CIRCLE for reg in seen[1:4])
