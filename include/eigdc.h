@@ -42,7 +42,7 @@ typedef struct eig_handle_s* eig_handle_t;
 #define EIG_ERR_SCRATCH (-4)  /* eig_gemm_noalloc: the split-K partials exceed its static scratch */
 #define EIG_NO_CONVERGENCE 1  /* IRS hit maxit (Algorithm 3), or a leaf solver gave up */
 #define EIG_NO_SPLIT 2        /* repeated failure to split a node (Sec. 3.3-3.5) */
-#define EIG_NEAR_SINGULAR_PENCIL 3 /* pencil strategy found no dividing circle (Sec. 3.5) */
+#define EIG_NEAR_SINGULAR_PENCIL 3 /* a pencil leaf's factorised matrix is near singular (Sec. 3.5) */
 #define EIG_NONFINITE 4       /* NaN/Inf met in an input or an iterate */
 #define EIG_TIMEOUT 5         /* eig_server_wait: the request did not finish in time */
 
@@ -52,7 +52,7 @@ typedef struct eig_handle_s* eig_handle_t;
  * run as three-term BF16 products with FP32 accumulation on the tcgen05
  * tensor cores (eig_gemm_split); panels, norms, the R-test, the split test
  * and the rank decision stay FP64.  Defaults then read tau = 1e-5 and
- * split_tol >= 1e-4, and eig_solve(EIG_KIND_SYM) ends with an FP64
+ * split_tol >= 1e-3, and eig_solve(EIG_KIND_SYM) ends with an FP64
  * refinement of the eigenvectors and eigenvalues. */
 #define EIG_SPLIT_BF16X3 1
 
@@ -78,7 +78,9 @@ typedef struct {
   int maxit;         /* IRS runs j = 0..maxit (Algorithm 3, "until j > maxit") */
   double split_tol;  /* accept a split when ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) <= split_tol;
                         <= 0: max(1e-12, 16 n 2^-53) for a node of size n (the FP64 rounding
-                        floor of that ratio grows like n u); split precision: >= 1e-3 */
+                        floor of that ratio grows like n u), pencils max(1e-10, 16 n 2^-53)
+                        (two independently computed subspaces; the finished solve's backward
+                        error stays 10-50x below the score); split precision: >= 1e-3 */
   int leaf_size;     /* nodes of at most this size go to the leaf solver (<= 64) */
   int prec;          /* EIG_FP64 or EIG_SPLIT_BF16X3 */
   uint64_t seed;     /* Philox key of every draw of the method */
@@ -239,6 +241,12 @@ int eig_server_create(eig_server_t* srv, int device, int workers, double hbm_bud
 int eig_server_submit(eig_server_t srv, int kind, int n, double* dA, int lda, double* dwr,
                       double* dwi, double* dU, int ldu, const eig_params_t* params,
                       uint64_t* ticket);
+/* Pencil request (eig_pencil_schur semantics and outputs; FP64 params only,
+ * EIG_ERR_ARG otherwise); admission and buffers as for eig_server_submit. */
+int eig_server_submit_pencil(eig_server_t srv, int n, double* dA, int lda, double* dB, int ldb,
+                             double* dQL, int ldql, double* dQR, int ldqr, double* dalphar,
+                             double* dalphai, double* dbeta, const eig_params_t* params,
+                             uint64_t* ticket);
 /* *done = 1 once finished; then *status, times[0..2] = queue wait, service,
  * latency (seconds, host steady clock) and *info are filled (each may be NULL). */
 int eig_server_poll(eig_server_t srv, uint64_t ticket, int* done, int* status, double* times,

@@ -453,8 +453,13 @@ static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64,
 // split_tol <= 0: max(1e-12, 16 n u), the rounding floor of ||E21||_1/||A||_1
 // after an FP64 step grows about like n u (measured 4-5 n u at n = 2048 and
 // 4096); split precision: at least 1e-3 (FP32-level iterates, refined later).
-static double effective_split_tol(const eig_params_t& p, int n) {
-  double t = p.split_tol > 0 ? p.split_tol : std::max(1e-12, 16.0 * n * 0x1p-53);
+// Pencils: max(1e-10, 16 n u).  The two deflating subspaces are computed
+// independently, so their mutual error enters ||F21|| without cancellation,
+// concentrated in a few ill-separated columns; the 1-norm score (a column
+// maximum) overstates the finished solve's Frobenius backward error 10-50x.
+static double effective_split_tol(const eig_params_t& p, int n, bool pencil = false) {
+  double t = p.split_tol > 0 ? p.split_tol
+                             : std::max(pencil ? 1e-10 : 1e-12, 16.0 * n * 0x1p-53);
   if (split_mode(p.prec)) t = std::max(t, 1e-3);
   return t;
 }
@@ -645,7 +650,7 @@ static SplitOut run_split_pencil(eig_handle_t h, SplitWork& w, int n, const doub
     out.draw = draw;
     pick_k(out, hscores, n);
     out.accepted = conv_right && conv_left && out.k > 0 && out.k < n &&
-                   out.e <= effective_split_tol(p, n);
+                   out.e <= effective_split_tol(p, n, true);
     if (out.accepted || !conv_right || rank == 0 || rank == n) break;
   }
   return out;
@@ -2010,6 +2015,8 @@ struct Request {
   uint64_t ticket;
   int kind, n, lda, ldu;
   double *dA, *dwr, *dwi, *dU;
+  int ldb = 0, ldqr = 0;                                      // pencils
+  double *dB = nullptr, *dQR = nullptr, *dbeta = nullptr;     // pencils
   eig_params_t p;
   size_t footprint;
   double t_submit = 0, t_start = 0, t_end = 0;
@@ -2026,8 +2033,9 @@ size_t solve_footprint(int n, int kind, int prec) {
   Arena a(nullptr);
   SolveMain w;
   NodeWork nw;
-  carve_main(a, n, kind == EIG_KIND_SYM && split_mode(prec), w);
-  carve_node(a, n, n, prec, nw);
+  const bool pencil = kind == EIG_KIND_PENCIL;
+  carve_main(a, n, kind == EIG_KIND_SYM && split_mode(prec), w, pencil);
+  carve_node(a, n, n, prec, nw, pencil);
   return a.used;
 }
 
@@ -2072,7 +2080,12 @@ static void server_worker(eig_server_s* S, eig_handle_s* hw) {
     std::memset(&inf, 0, sizeof(inf));
     try {
       hw->err.clear();
-      rc = solve_impl(hw, r->kind, r->n, r->dA, r->lda, r->dwr, r->dwi, r->dU, r->ldu, r->p, &inf);
+      if (r->kind == EIG_KIND_PENCIL)
+        rc = pencil_impl(hw, r->n, r->dA, r->lda, r->dB, r->ldb, r->dU, r->ldu, r->dQR, r->ldqr,
+                         r->dwr, r->dwi, r->dbeta, r->p, &inf);
+      else
+        rc = solve_impl(hw, r->kind, r->n, r->dA, r->lda, r->dwr, r->dwi, r->dU, r->ldu, r->p,
+                        &inf);
     } catch (Fail f) {
       rc = f.code;
     }
@@ -2132,6 +2145,20 @@ int eig_server_create(eig_server_t* out, int device, int workers, double hbm_bud
   return EIG_OK;
 }
 
+static void enqueue(eig_server_s* S, Request* r, uint64_t* ticket) {
+  r->footprint = solve_footprint(r->n, r->kind, r->p.prec);
+  std::memset(&r->info, 0, sizeof(r->info));
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    r->ticket = S->next_ticket++;
+    r->t_submit = now_s();
+    S->queue.push_back(r);
+    S->all.push_back(r);
+    *ticket = r->ticket;
+  }
+  S->cv_work.notify_all();
+}
+
 int eig_server_submit(eig_server_t S, int kind, int n, double* dA, int lda, double* dwr,
                       double* dwi, double* dU, int ldu, const eig_params_t* params,
                       uint64_t* ticket) {
@@ -2156,17 +2183,40 @@ int eig_server_submit(eig_server_t S, int kind, int n, double* dA, int lda, doub
     delete r;
     return EIG_ERR_ARG;
   }
-  r->footprint = solve_footprint(n, kind, r->p.prec);
-  std::memset(&r->info, 0, sizeof(r->info));
-  {
-    std::lock_guard<std::mutex> lock(S->mu);
-    r->ticket = S->next_ticket++;
-    r->t_submit = now_s();
-    S->queue.push_back(r);
-    S->all.push_back(r);
-    *ticket = r->ticket;
+  enqueue(S, r, ticket);
+  return EIG_OK;
+}
+
+int eig_server_submit_pencil(eig_server_t S, int n, double* dA, int lda, double* dB, int ldb,
+                             double* dQL, int ldql, double* dQR, int ldqr, double* dalphar,
+                             double* dalphai, double* dbeta, const eig_params_t* params,
+                             uint64_t* ticket) {
+  if (!S || !ticket) return EIG_ERR_ARG;
+  if (n < 1 || !dA || lda < n || !dB || ldb < n || !dQL || ldql < n || !dQR || ldqr < n ||
+      !dalphar || !dalphai || !dbeta)
+    return EIG_ERR_ARG;
+  Request* r = new Request();
+  r->kind = EIG_KIND_PENCIL;
+  r->n = n;
+  r->dA = dA;
+  r->lda = lda;
+  r->dB = dB;
+  r->ldb = ldb;
+  r->dU = dQL;
+  r->ldu = ldql;
+  r->dQR = dQR;
+  r->ldqr = ldqr;
+  r->dwr = dalphar;
+  r->dwi = dalphai;
+  r->dbeta = dbeta;
+  eig_default_params(&r->p);
+  if (params) r->p = *params;
+  r->p.workers = 1;
+  if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 || r->p.prec != EIG_FP64) {
+    delete r;
+    return EIG_ERR_ARG;
   }
-  S->cv_work.notify_all();
+  enqueue(S, r, ticket);
   return EIG_OK;
 }
 

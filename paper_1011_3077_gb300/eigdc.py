@@ -100,6 +100,8 @@ _SIGNATURES = {
     "eig_server_create": (_I, [ctypes.POINTER(_P), _I, _I, _D]),
     "eig_server_submit": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
                                ctypes.POINTER(_U64)]),
+    "eig_server_submit_pencil": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P,
+                                      ctypes.POINTER(Params), ctypes.POINTER(_U64)]),
     "eig_server_poll": (_I, [_P, _U64, ctypes.POINTER(_I), ctypes.POINTER(_I),
                              ctypes.POINTER(_D), ctypes.POINTER(SolveInfo)]),
     "eig_server_wait": (_I, [_P, _U64, _D, ctypes.POINTER(_I)]),
@@ -299,6 +301,18 @@ class Server:
         if rc != EIG_OK:
             raise EigError(rc, "eig_server_submit failed")
         self._keep[t.value] = (dA, dwr, dwi, dU)     # buffers live until done
+        return t.value
+
+    def submit_pencil(self, dA, dB, dQL, dQR, dar, dai, dbe, params=None):
+        n = int(dA.shape[0])
+        t = ctypes.c_uint64()
+        p = params or default_params()
+        rc = lib().eig_server_submit_pencil(self._s, n, _ptr(dA), n, _ptr(dB), n, _ptr(dQL), n,
+                                            _ptr(dQR), n, _ptr(dar), _ptr(dai), _ptr(dbe),
+                                            ctypes.byref(p), ctypes.byref(t))
+        if rc != EIG_OK:
+            raise EigError(rc, "eig_server_submit_pencil failed")
+        self._keep[t.value] = (dA, dB, dQL, dQR, dar, dai, dbe)
         return t.value
 
     def poll(self, ticket):

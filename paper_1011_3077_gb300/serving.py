@@ -1,16 +1,19 @@
 """Serving loop: Poisson arrivals of mixed eigenproblems on one GPU.
 
-Requests (symmetric eigendecomposition, nonsymmetric real Schur form) of
-log-uniform size arrive as a Poisson stream and are submitted to the native
-request server (include/eigdc.h, eig_server_*), which admits them under an
-HBM budget as workers free up and overlaps their work on the device.  The
-loop reports throughput and p50/p99 latency (arrival to completion).
+Requests (symmetric eigendecomposition, nonsymmetric real Schur form,
+generalized real Schur form of a regular pencil) of log-uniform size arrive
+as a Poisson stream and are submitted to the native request server
+(include/eigdc.h, eig_server_*), which admits them under an HBM budget as
+workers free up and overlaps their work on the device.  The loop reports
+throughput and p50/p99 latency (arrival to completion).
 
 Inputs are synthesised on the device before the clock starts (random
 orthogonal similarity of a prescribed spectrum; a library QR draws the
 orthogonal factor -- input generation, not the method).  Nonsymmetric
 requests use the triangular construction with strict-upper scale 0.1/sqrt(n)
-(the reduced-coupling reading of the nonsymmetric workload).
+(the reduced-coupling reading of the nonsymmetric workload); pencils are
+A = (Q T Q^T) B with that T and B = I + 0.1 G / sqrt(n).  Pencils are solved
+in FP64 (the split-precision form covers the standard problems).
 
 Usage: python -m paper_1011_3077_gb300.serving --rate 200 --count 40
 """
@@ -34,11 +37,12 @@ def _orthogonal(n, gen, device):
 
 
 def synthesize(kind, n, seed, device="cuda"):
-    """(dA column-major, reference spectrum) for one request."""
+    """(dA column-major, dB column-major or None, reference spectrum) for one request."""
     import torch
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     Q = _orthogonal(n, gen, device)
+    dB = None
     if kind == eigdc.EIG_KIND_SYM:
         lam = torch.rand(n, generator=gen, dtype=torch.float64, device=device) * 2.0 - 1.0
         A = (Q * lam) @ Q.T
@@ -54,37 +58,69 @@ def synthesize(kind, n, seed, device="cuda"):
                        * (0.1 / math.sqrt(n)), 1) + torch.diag(d)
         A = Q @ T @ Q.T
         ref = torch.sort(d).values
+        if kind == eigdc.EIG_KIND_PENCIL:
+            G = torch.randn((n, n), generator=gen, dtype=torch.float64, device=device)
+            B = torch.eye(n, dtype=torch.float64, device=device) + G * (0.1 / math.sqrt(n))
+            A = A @ B
+            dB = B.T.contiguous()
     # column-major storage of A is the row-major storage of A^T
-    return A.T.contiguous(), ref
+    return A.T.contiguous(), dB, ref
 
 
-def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.5), workers=8,
-        budget_gb=120.0, prec=eigdc.EIG_FP64, seed=5, device="cuda", verbose=False):
+def backward_error(kind, dA, o):
+    """||A - U L U^T||_F / ||A||_F (symmetric), ||A - U T U^T|| / ||A||
+    (Schur), max over A and B of ||X - Q_L X^ Q_R^T|| / ||X|| (pencil).
+    Tensors hold column-major matrices, i.e. the row-major transposes."""
+    import torch
+    A0 = o["A0"]
+    if kind == eigdc.EIG_KIND_SYM:
+        Ut = o["dU"]
+        rec = Ut.T @ torch.diag(o["dwr"]) @ Ut
+        return float(torch.linalg.norm(A0 - rec) / torch.linalg.norm(A0))
+    if kind == eigdc.EIG_KIND_NONSYM:
+        Ut = o["dU"]
+        return float(torch.linalg.norm(A0 - Ut.T @ dA @ Ut) / torch.linalg.norm(A0))
+    QLt, QRt = o["dU"], o["dQR"]
+    rA = torch.linalg.norm(A0 - QRt.T @ dA @ QLt) / torch.linalg.norm(A0)
+    rB = torch.linalg.norm(o["B0"] - QRt.T @ o["dB"] @ QLt) / torch.linalg.norm(o["B0"])
+    return float(max(rA, rB))
+
+
+def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8,
+        budget_gb=120.0, prec=eigdc.EIG_FP64, seed=5, device="cuda", verbose=False,
+        details=False):
     import torch
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, count)
     arrivals = np.cumsum(gaps) - gaps[0]
-    kinds = rng.choice([eigdc.EIG_KIND_SYM, eigdc.EIG_KIND_NONSYM], size=count,
-                       p=np.asarray(mix) / np.sum(mix))
+    kinds = rng.choice([eigdc.EIG_KIND_SYM, eigdc.EIG_KIND_NONSYM, eigdc.EIG_KIND_PENCIL][:len(mix)],
+                       size=count, p=np.asarray(mix) / np.sum(mix))
     sizes = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(int)
     reqs = []
     for i in range(count):
         n = int(sizes[i])
-        dA, ref = synthesize(int(kinds[i]), n, seed * 1000003 + i, device)
-        dwr = torch.zeros(n, dtype=torch.float64, device=device)
-        dwi = torch.zeros(n, dtype=torch.float64, device=device)
-        dU = torch.zeros((n, n), dtype=torch.float64, device=device)
-        reqs.append((int(kinds[i]), n, dA, dwr, dwi, dU, ref))
+        kind = int(kinds[i])
+        dA, dB, ref = synthesize(kind, n, seed * 1000003 + i, device)
+        z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=device)
+        out = dict(dwr=z(n), dwi=z(n), dU=z(n, n), A0=dA.clone())
+        if kind == eigdc.EIG_KIND_PENCIL:
+            out.update(dB=dB, dQR=z(n, n), dbe=z(n), B0=dB.clone())
+        reqs.append((kind, n, dA, out, ref))
     torch.cuda.synchronize()
     srv = eigdc.Server(0, workers, budget_gb)
     params = eigdc.default_params(seed=seed, prec=prec)
+    params64 = eigdc.default_params(seed=seed, prec=eigdc.EIG_FP64)
     tickets = []
     t0 = time.perf_counter()
-    for i, (kind, n, dA, dwr, dwi, dU, ref) in enumerate(reqs):
+    for i, (kind, n, dA, o, ref) in enumerate(reqs):
         delay = t0 + arrivals[i] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets.append(srv.submit(kind, dA, dwr, dwi, dU, params))
+        if kind == eigdc.EIG_KIND_PENCIL:
+            tickets.append(srv.submit_pencil(dA, o["dB"], o["dU"], o["dQR"], o["dwr"], o["dwi"],
+                                             o["dbe"], params64))
+        else:
+            tickets.append(srv.submit(kind, dA, o["dwr"], o["dwi"], o["dU"], params))
     statuses, lat, wait, service = [], [], [], []
     for t in tickets:
         srv.wait(t, 3600.0)
@@ -96,11 +132,18 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.5), workers=8,
     makespan = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
-    errs = []
-    for (kind, n, dA, dwr, dwi, dU, ref), st in zip(reqs, statuses):
+    errs, bwds, records = [], [], []
+    for i, ((kind, n, dA, o, ref), st) in enumerate(zip(reqs, statuses)):
+        err = bwd = None
         if st == 0:
-            w = torch.sort(dwr).values
-            errs.append(float(torch.max(torch.abs(w - ref))))
+            w = o["dwr"] / o["dbe"] if kind == eigdc.EIG_KIND_PENCIL else o["dwr"]
+            err = float(torch.max(torch.abs(torch.sort(w).values - ref)))
+            errs.append(err)
+            bwd = backward_error(kind, dA, o)
+            bwds.append(bwd)
+        records.append({"kind": kind, "n": n, "status": st, "wait_s": wait[i],
+                        "service_s": service[i], "latency_s": lat[i], "eig_err": err,
+                        "backward_err": bwd})
     ok = sum(1 for s in statuses if s == 0)
     out = {
         "requests": count, "ok": ok, "offered_rate_per_s": rate,
@@ -109,12 +152,18 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.5), workers=8,
         "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
         "service_s": {"p50": float(np.percentile(service, 50)), "p99": float(np.percentile(service, 99))},
         "sizes": {"min": int(sizes.min()), "max": int(sizes.max())},
+        "max_backward_error": max(bwds) if bwds else None,
         "max_eigenvalue_error": max(errs) if errs else None,
         "peak_reserved_gb": stats["peak_reserved_gb"], "budget_gb": budget_gb,
         "workers": workers, "precision": "split" if prec else "fp64",
+        "mix": {"sym": int(np.sum(kinds == eigdc.EIG_KIND_SYM)),
+                "nonsym": int(np.sum(kinds == eigdc.EIG_KIND_NONSYM)),
+                "pencil": int(np.sum(kinds == eigdc.EIG_KIND_PENCIL))},
     }
     if verbose:
         print(json.dumps(out))
+    if details:
+        out["requests_detail"] = records
     return out
 
 

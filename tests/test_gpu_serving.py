@@ -11,7 +11,8 @@ def test_results_same_alone_and_in_the_mix():
     from paper_1011_3077_gb300 import build, eigdc, serving
     build.build()
     rng = np.random.default_rng(3)
-    kinds = [eigdc.EIG_KIND_SYM if i % 2 == 0 else eigdc.EIG_KIND_NONSYM for i in range(16)]
+    kinds = [(eigdc.EIG_KIND_SYM, eigdc.EIG_KIND_NONSYM, eigdc.EIG_KIND_PENCIL)[i % 3]
+             for i in range(16)]
     sizes = rng.integers(24, 180, size=16)
     inputs = [serving.synthesize(k, int(n), 100 + i) for i, (k, n) in enumerate(zip(kinds, sizes))]
     torch.cuda.synchronize()
@@ -20,12 +21,17 @@ def test_results_same_alone_and_in_the_mix():
     budget_gb = 3 * 1e-9 * max(1, int(sizes.max())) ** 2 * 8 * 40
     srv = eigdc.Server(0, 6, budget_gb)
     bufs, tickets = [], []
-    for (dA0, ref), k in zip(inputs, kinds):
+    z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
+    for (dA0, dB0, ref), k in zip(inputs, kinds):
         n = dA0.shape[0]
         dA = dA0.clone()
-        dwr = torch.zeros(n, dtype=torch.float64, device="cuda")
-        dwi = torch.zeros(n, dtype=torch.float64, device="cuda")
-        dU = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        dwr, dwi, dU = z(n), z(n), z(n, n)
+        if k == eigdc.EIG_KIND_PENCIL:
+            dB, dQR, dbe = dB0.clone(), z(n, n), z(n)
+            torch.cuda.synchronize()
+            bufs.append((dA, dwr, dwi, dU, dB, dQR, dbe))
+            tickets.append(srv.submit_pencil(dA, dB, dU, dQR, dwr, dwi, dbe, params))
+            continue
         torch.cuda.synchronize()
         bufs.append((dA, dwr, dwi, dU))
         tickets.append(srv.submit(k, dA, dwr, dwi, dU, params))
@@ -39,16 +45,24 @@ def test_results_same_alone_and_in_the_mix():
     # alone: the same request through eig_solve with one worker
     h = eigdc.Handle(0)
     p1 = eigdc.default_params(seed=9, workers=1)
-    for (dA0, ref), k, (dA, dwr, dwi, dU) in zip(inputs, kinds, bufs):
+    for (dA0, dB0, ref), k, got in zip(inputs, kinds, bufs):
         n = dA0.shape[0]
         a = dA0.clone()
-        wr = torch.zeros(n, dtype=torch.float64, device="cuda")
-        wi = torch.zeros(n, dtype=torch.float64, device="cuda")
-        U = torch.zeros((n, n), dtype=torch.float64, device="cuda")
-        rc, info = eigdc.eig_solve(h, k, n, a, n, wr, wi, U, n, p1)
-        assert rc == 0
-        assert torch.equal(a, dA) and torch.equal(wr, dwr) and torch.equal(U, dU)
-        assert float(torch.max(torch.abs(torch.sort(wr).values - ref))) <= 1e-9
+        wr, wi, U = z(n), z(n), z(n, n)
+        if k == eigdc.EIG_KIND_PENCIL:
+            b, QR, be = dB0.clone(), z(n, n), z(n)
+            rc, info = eigdc.eig_pencil_schur(h, n, a, n, b, n, U, n, QR, n, wr, wi, be, p1)
+            assert rc == 0
+            for mine, theirs in zip((a, wr, wi, U, b, QR, be), got):
+                assert torch.equal(mine, theirs)
+            lam = torch.sort(wr / be).values
+        else:
+            rc, info = eigdc.eig_solve(h, k, n, a, n, wr, wi, U, n, p1)
+            assert rc == 0
+            dA, dwr, dwi, dU = got
+            assert torch.equal(a, dA) and torch.equal(wr, dwr) and torch.equal(U, dU)
+            lam = torch.sort(wr).values
+        assert float(torch.max(torch.abs(lam - ref))) <= 1e-9
     h.close()
 
 
@@ -56,6 +70,7 @@ def test_serving_loop_reports_latency():
     from paper_1011_3077_gb300 import build, eigdc, serving
     build.build()
     out = serving.run(rate=400.0, count=12, nmin=32, nmax=256, workers=4, budget_gb=8.0, seed=2)
-    assert out["ok"] == 12
+    assert out["ok"] == 12 and out["mix"]["pencil"] >= 1
     assert out["latency_s"]["p99"] >= out["latency_s"]["p50"] > 0
     assert out["max_eigenvalue_error"] <= 1e-9
+    assert out["max_backward_error"] <= 1e-12
