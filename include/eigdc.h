@@ -128,6 +128,13 @@ const char* eig_last_error(eig_handle_t h);
 /* Number of CUDA kernels this library has launched in the process so far
  * (instrumentation for benchmarks; no device work). */
 unsigned long long eig_kernel_launches(void);
+/* Event timing of the FP64 GEMM kernel launches (instrumentation for the
+ * roofline of the dominant kernel inside a timed region; no effect on
+ * results).  enable != 0: clear and start recording one event pair per
+ * launch, on the launch's stream.  enable == 0: stop, wait for the recorded
+ * launches and return the summed launch durations (ms), the launch count and
+ * the summed algorithmic flops 2mnk (the outputs may be NULL). */
+int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, double* flops);
 /* Device workspace (bytes) the handle needs for calls on size n. */
 int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes);
 

@@ -1619,6 +1619,14 @@ const char* eig_last_error(eig_handle_t h) { return h ? h->err.c_str() : "null h
 
 unsigned long long eig_kernel_launches(void) { return g_launches.load(); }
 
+int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, double* flops) {
+  if (enable) {
+    gemm_timing_start();
+    return EIG_OK;
+  }
+  return gemm_timing_stop(total_ms, launches, flops) == cudaSuccess ? EIG_OK : EIG_ERR_CUDA;
+}
+
 int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
   if (!h || !bytes || n < 0) return EIG_ERR_ARG;
   Arena a(nullptr);

@@ -67,6 +67,9 @@ cudaError_t add_matrices(cudaStream_t s, int rows, int cols, const double* A, in
                          const double* B, int ldb, double* C, int ldc);
 // Z[i][k] = Y[n-1-k][i]   (Z = (J Y)^T)
 cudaError_t reverse_transpose(cudaStream_t s, int n, const double* Y, int ldy, double* Z, int ldz);
+// Opt-in event timing of the FP64 GEMM launches (instrumentation).
+void gemm_timing_start();
+cudaError_t gemm_timing_stop(double* total_ms, unsigned long long* launches, double* flops);
 // B (cols x rows, ldb) = A^T
 cudaError_t transpose(cudaStream_t s, int rows, int cols, const double* A, int lda, double* B,
                       int ldb);

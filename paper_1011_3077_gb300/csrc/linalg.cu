@@ -12,6 +12,10 @@
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <vector>
 #include <stdint.h>
 
 #include "internal.h"
@@ -191,11 +195,76 @@ int gemm_choose_splits(int m, int n, int k) {
   return best;
 }
 
+// ------------------------------------------------------------ launch timing
+// Opt-in CUDA-event timing of every dgemm_kernel launch, for the roofline of
+// the dominant kernel measured inside a timed region.  Off by default; when
+// on, each launch records one event before and one after it on its stream.
+namespace {
+struct TimedLaunch {
+  cudaEvent_t a, b;
+  double flops;
+};
+std::mutex g_tmu;
+std::atomic<bool> g_timing{false};
+std::vector<TimedLaunch> g_timed;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {   // g_tmu held
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+void gemm_timing_start() {
+  std::lock_guard<std::mutex> lock(g_tmu);
+  for (TimedLaunch& t : g_timed) {
+    g_event_pool.push_back(t.a);
+    g_event_pool.push_back(t.b);
+  }
+  g_timed.clear();
+  g_timing.store(true);
+}
+
+cudaError_t gemm_timing_stop(double* total_ms, unsigned long long* launches, double* flops) {
+  g_timing.store(false);
+  std::lock_guard<std::mutex> lock(g_tmu);
+  double ms = 0.0, fl = 0.0;
+  for (TimedLaunch& t : g_timed) {
+    cudaError_t e = cudaEventSynchronize(t.b);
+    if (e != cudaSuccess) return e;
+    float x = 0.0f;
+    e = cudaEventElapsedTime(&x, t.a, t.b);
+    if (e != cudaSuccess) return e;
+    ms += x;
+    fl += t.flops;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = g_timed.size();
+  if (flops) *flops = fl;
+  return cudaSuccess;
+}
+
 template <bool TA, bool TB>
 static void launch_dgemm(cudaStream_t s, int m, int n, int k, int splits, int kchunk, double alpha,
                          const double* A, int lda, const double* B, int ldb, double beta,
                          double* C, int ldc, double* part) {
   note_launches(1);
+  TimedLaunch tl{nullptr, nullptr, 2.0 * m * (double)n * k};
+  if (g_timing.load(std::memory_order_relaxed)) {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    tl.a = take_event();
+    tl.b = take_event();
+    if (tl.a) cudaEventRecord(tl.a, s);
+  }
   if (narrow_tile(m)) {
     dim3 grid((m + 31) / 32, (n + 127) / 128, splits);
     dgemm_kernel<TA, TB, 32, 128><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta,
@@ -204,6 +273,11 @@ static void launch_dgemm(cudaStream_t s, int m, int n, int k, int splits, int kc
     dim3 grid((m + 63) / 64, (n + 63) / 64, splits);
     dgemm_kernel<TA, TB, 64, 64><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta,
                                                            C, ldc, kchunk, part);
+  }
+  if (tl.a && tl.b) {
+    cudaEventRecord(tl.b, s);
+    std::lock_guard<std::mutex> lock(g_tmu);
+    g_timed.push_back(tl);
   }
 }
 

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "eig_destroy": (_I, [_P]),
     "eig_last_error": (ctypes.c_char_p, [_P]),
     "eig_kernel_launches": (ctypes.c_ulonglong, []),
+    "eig_gemm_timing": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong),
+                             ctypes.POINTER(_D)]),
     "eig_workspace_size": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "eig_divide_step": (_I, [_P, _I, _P, _I, _P, _I, ctypes.POINTER(Region),
                              ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
@@ -214,6 +216,21 @@ def ld(t):
 
 def eig_kernel_launches():
     return int(lib().eig_kernel_launches())
+
+
+def eig_gemm_timing_start():
+    rc = lib().eig_gemm_timing(1, None, None, None)
+    if rc != EIG_OK:
+        raise EigError(rc, "eig_gemm_timing start failed")
+
+
+def eig_gemm_timing_stop():
+    """(summed launch ms, launches, summed flops) of the FP64 GEMMs since start."""
+    ms, cnt, fl = ctypes.c_double(), ctypes.c_ulonglong(), ctypes.c_double()
+    rc = lib().eig_gemm_timing(0, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(fl))
+    if rc != EIG_OK:
+        raise EigError(rc, "eig_gemm_timing stop failed")
+    return ms.value, int(cnt.value), fl.value
 
 
 def eig_divide_step(h, n, dA, lda, dB, ldb, region, params):
