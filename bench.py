@@ -50,6 +50,11 @@ def parse():
                     help="strict-upper scale of T in units of 1/sqrt(n) (1.0 = the exact "
                          "construction, whose eigenvalues are too ill-conditioned to split "
                          "in FP64 at n=2048; 0.1 = the documented reduced-coupling variant)")
+    ap.add_argument("--prec", type=int, default=0, choices=[0, 2],
+                    help="0: FP64 contractions on the DFMA pipe; 2: FP64-accurate contractions "
+                         "on the tensor cores (error-free nine-digit BF16 split)")
+    ap.add_argument("--workers", type=int, default=8,
+                    help="host workers of the node-parallel recursion (own CUDA streams)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -66,7 +71,9 @@ def config(n, args):
     return {"workload": "nonsymmetric real Schur, A = Q T Q^T, n=%d, T strict upper "
                         "N(0, (%g/sqrt(n))^2), full recursion to 64x64 leaves, unit-circle "
                         "root split then Moebius lines" % (n, args.coupling),
-            "n": n, "coupling": args.coupling, "leaf_size": 64, "precision": "fp64",
+            "n": n, "coupling": args.coupling, "leaf_size": 64,
+            "precision": "fp64" if args.prec == 0 else "fp64 (tensor-core error-free split)",
+            "workers": args.workers,
             "l2": "flushed between timed steps (512 MiB write)",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
 
@@ -209,7 +216,7 @@ def main():
     h = eigdc.Handle(local, stream)
     n = args.n
     A, d = workload(n, rank, args.coupling)
-    params = eigdc.default_params(seed=0, leaf_size=64)
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
     dA0 = eigdc.to_device(A, dev)
     dA = torch.empty_like(dA0)
     dwr = torch.zeros(n, dtype=torch.float64, device=dev)

@@ -55,6 +55,17 @@ typedef struct eig_handle_s* eig_handle_t;
  * split_tol >= 1e-3, and eig_solve(EIG_KIND_SYM) ends with an FP64
  * refinement of the eigenvectors and eigenvalues. */
 #define EIG_SPLIT_BF16X3 1
+/* FP64-accurate contractions on the tensor cores: every GEMM of the path
+ * (reflector products, complement products, splitter, similarity) splits its
+ * FP64 operands error-free into nine 6-bit digits per row / column (power-of-
+ * two scaled, stored exactly as BF16), multiplies the digit pairs of weight
+ * levels 0..9 with tcgen05.mma into one FP32 TMEM accumulator per level, exact
+ * because each 448-wide K chunk keeps every partial sum an integer below 2^24,
+ * and drains the levels into FP64 (eig_gemm_fp64tc).  Error ~ K 2^-53 of
+ * max|row| max|column|, like an FP64 GEMM; every other setting (tau,
+ * split_tol, no refinement) is that of EIG_FP64.  Small products stay on the
+ * FP64 kernel. */
+#define EIG_FP64_TC 2
 
 /* regions (Sec. 3.1 unit circle; Sec. 3.3 line via the Moebius map
  * f(z) = (z - sigma + s)/(z - sigma - s); Sec. 3.5 circles |z - c| = r) */
@@ -172,7 +183,8 @@ int eig_split(eig_handle_t h, int n, const double* dAp, const double* dBp, int l
  * the iterates (dApL, dBpL) of the mapped (A^T, B^T) (Haar draw of purpose 6);
  * A^ = Q_L^T A Q_R, B^ = Q_L^T B Q_R; k minimises ||E21||_1 / ||A||_1 +
  * ||F21||_1 / ||B||_1.  dA, dB: the ORIGINAL pencil, overwritten with A^, B^;
- * dQL, dQR (n x n) receive Q_L, Q_R.  FP64 only (EIG_ERR_ARG otherwise).
+ * dQL, dQR (n x n) receive Q_L, Q_R.  EIG_FP64 or EIG_FP64_TC only (EIG_ERR_ARG
+ * otherwise).
  * Returns EIG_NO_SPLIT when no accepted split exists (outputs hold the last
  * draw); the rank reported is that of the right RURV. */
 int eig_split_pencil(eig_handle_t h, int n, const double* dApR, const double* dBpR,
@@ -193,7 +205,8 @@ int eig_split_pencil(eig_handle_t h, int n, const double* dApR, const double* dB
  * On exit: dA <- S = Q_L^T A Q_R (quasi-upper-triangular, a 2x2 block per
  * complex pair), dB <- T = Q_L^T B Q_R (upper triangular), dQL,
  * dQR <- orthogonal (n x n), and the eigenvalues (alphar + i alphai) / beta
- * (device arrays of n) in block order.  FP64 only (EIG_ERR_ARG otherwise).
+ * (device arrays of n) in block order.  EIG_FP64 or EIG_FP64_TC only (EIG_ERR_ARG
+ * otherwise).
  * Status: EIG_NO_SPLIT (no divide found for a node), EIG_NEAR_SINGULAR_PENCIL
  * (the matrix a leaf factorises has max/min |r_ii| > 1e8: an eigenvalue
  * within the leaf's group sits at 0 or infinity of the wrong side, or the
@@ -248,8 +261,8 @@ int eig_server_create(eig_server_t* srv, int device, int workers, double hbm_bud
 int eig_server_submit(eig_server_t srv, int kind, int n, double* dA, int lda, double* dwr,
                       double* dwi, double* dU, int ldu, const eig_params_t* params,
                       uint64_t* ticket);
-/* Pencil request (eig_pencil_schur semantics and outputs; FP64 params only,
- * EIG_ERR_ARG otherwise); admission and buffers as for eig_server_submit. */
+/* Pencil request (eig_pencil_schur semantics and outputs; EIG_FP64 or
+ * EIG_FP64_TC params only, EIG_ERR_ARG otherwise); admission and buffers as for eig_server_submit. */
 int eig_server_submit_pencil(eig_server_t srv, int n, double* dA, int lda, double* dB, int ldb,
                              double* dQL, int ldql, double* dQR, int ldqr, double* dalphar,
                              double* dalphai, double* dbeta, const eig_params_t* params,
@@ -299,6 +312,12 @@ int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
              const double* dA, int lda, const double* dB, int ldb, double beta,
              double* dC, int ldc);
 
+/* C = alpha op(A) op(B) + beta C with the FP64-accurate tensor-core split of
+ * EIG_FP64_TC (device pointers, column-major; op = transpose when t != 0).
+ * Returns EIG_ERR_CUDA if a bounded wait of the kernel timed out. */
+int eig_gemm_fp64tc(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+                    const double* dA, int lda, const double* dB, int ldb, double beta, double* dC,
+                    int ldc);
 /* C = alpha op(A) op(B) + beta C in the split-precision form of the
  * contractions: FP64 operands split into three BF16 planes (hi + mid + lo),
  * the six plane products of weight >= 2^-16 accumulated in FP32 on the

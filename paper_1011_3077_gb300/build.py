@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeigdc.so")
-SOURCES = ["linalg.cu", "misc.cu", "leaves.cu", "tc_gemm.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["linalg.cu", "misc.cu", "leaves.cu", "tc_gemm.cu", "tcx_gemm.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -36,7 +36,7 @@ def _stale(obj, src):
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "internal.h"),
+    deps = [src, os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_ptx.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "eigdc.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

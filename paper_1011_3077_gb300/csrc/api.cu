@@ -156,20 +156,47 @@ struct QRBufs {
 };
 
 static bool split_mode(int prec) { return prec == EIG_SPLIT_BF16X3; }
+// contractions on the tensor cores: BF16 x 3 (FP32-level) or the FP64-accurate split
+static bool tc_path(int prec) { return prec == EIG_SPLIT_BF16X3 || prec == EIG_FP64_TC; }
+
+static size_t tc_ws_bytes(int prec, int m, int n, int k) {
+  if (prec == EIG_SPLIT_BF16X3) return tc_gemm_workspace_bytes(m, n, k);
+  if (prec == EIG_FP64_TC) return tcx_gemm_workspace_bytes(m, n, k);
+  return 0;
+}
+
+// Products below this size stay on the FP64 DFMA kernel in EIG_FP64_TC mode:
+// the digit split costs a pass over both operands and three launches.
+static bool tcx_worth(int m, int n, int k) {
+  return m >= 64 && n >= 16 && k >= 64 && (double)m * n * k >= 16777216.0;
+}
+
+// Tensor-core product C = alpha op(A) op(B) + beta C in the arithmetic of prec
+// (tc_path(prec)); small FP64_TC products use the DFMA kernel without split-K.
+static cudaError_t tcmm(cudaStream_t s, int prec, bool ta, bool tb, int m, int n, int k,
+                        double alpha, const double* A, int lda, const double* B, int ldb,
+                        double beta, double* C, int ldc, void* ws, int* err) {
+  if (prec == EIG_FP64_TC) {
+    if (!tcx_worth(m, n, k))
+      return gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 1, nullptr);
+    return tcx_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
+  }
+  return tc_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
+}
 
 // C = alpha op(A) op(B) + beta C in the arithmetic of `prec`.
 static void mm(eig_handle_t h, int prec, void* tcw, int* tcerr, bool ta, bool tb, int m, int n,
                int k, double alpha, const double* A, int lda, const double* B, int ldb,
                double beta, double* C, int ldc, int splits, double* part) {
-  if (split_mode(prec))
-    CK(tc_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
+  if (tc_path(prec))
+    CK(tcmm(h->stream, prec, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
   else
     CK(gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, splits, part));
 }
 
 // BF16 plane scratch of the reflector products of an m x n QR.
-static size_t tcw_qr_bytes(int m, int n) {
-  return std::max(tc_gemm_workspace_bytes(n, JB_LD_C, m), tc_gemm_workspace_bytes(m, n, JB_LD_C));
+static size_t tcw_qr_bytes(int prec, int m, int n) {
+  return std::max(tc_ws_bytes(prec, n, JB_LD_C, m), tc_ws_bytes(prec, m, n, JB_LD_C));
 }
 
 constexpr int JB_LD = 32;
@@ -194,13 +221,13 @@ static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
     if (nc > 0) {
       const int mb = m - j0;
       double* C = q.W + j0 + (size_t)(j0 + jb) * q.ldw;
-      if (split_mode(q.prec)) {
+      if (tc_path(q.prec)) {
         // (V^T C)^T = C^T V on the tensor cores (M = nc rows, N = jb)
-        CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
-                   q.tcerr));
+        CK(tcmm(s, q.prec, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part, nc,
+                q.tcw, q.tcerr));
         CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk, true));
-        CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw, q.tcw,
-                   q.tcerr));
+        CK(tcmm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw,
+                q.tcw, q.tcerr));
       } else {
         int sp = gemm_choose_splits(jb, nc, mb);
         sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
@@ -229,12 +256,12 @@ static void apply_q(eig_handle_t h, int m, int nref, int jbmax, QRBufs& q, doubl
     if (nc <= 0) continue;
     double* Yb = Y + j0 + (size_t)c0 * ldy;
     const double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
-    if (split_mode(q.prec)) {
-      CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
-                 q.tcerr));
+    if (tc_path(q.prec)) {
+      CK(tcmm(s, q.prec, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc,
+              q.tcw, q.tcerr));
       CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, false, q.Wk, true));
-      CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy, q.tcw,
-                 q.tcerr));
+      CK(tcmm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy,
+              q.tcw, q.tcerr));
       continue;
     }
     int sp = gemm_choose_splits(jb, nc, mb);
@@ -261,7 +288,7 @@ static size_t carve_qr(Arena& a, int m, int n, QRWork& w, int prec = EIG_FP64) {
   w.q.Wk = a.take<double>((size_t)JB_LD * n);
   w.q.part = a.take<double>(qr_part_doubles(m, n));
   w.q.prec = prec;
-  w.q.tcw = split_mode(prec) ? (void*)a.take<char>(tcw_qr_bytes(m, n)) : nullptr;
+  w.q.tcw = tc_path(prec) ? (void*)a.take<char>(tcw_qr_bytes(prec, m, n)) : nullptr;
   w.q.tcerr = a.take<int>(4);
   return a.used - start;
 }
@@ -305,8 +332,8 @@ static size_t carve_irs(Arena& a, int n, IRSWork& w, int prec = EIG_FP64) {
   w.prec = prec;
   // one plane buffer serves the QR's reflector products and the complement
   // products (they run one after the other on the stream)
-  w.tcw = split_mode(prec) ? (void*)a.take<char>(std::max(tc_gemm_workspace_bytes(n, n, n),
-                                                          tcw_qr_bytes(2 * n, n)))
+  w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(tc_ws_bytes(prec, n, n, n),
+                                                       tcw_qr_bytes(prec, 2 * n, n)))
                            : nullptr;
   carve_qr(a, 2 * n, n, w.qr, EIG_FP64);
   w.qr.q.prec = prec;
@@ -441,8 +468,8 @@ static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64,
   w.nbits = a.take<unsigned long long>(4);
   w.rank = a.take<int>(4);
   w.prec = prec;
-  w.tcw = split_mode(prec) ? (void*)a.take<char>(std::max(tc_gemm_workspace_bytes(n, n, n),
-                                                          tcw_qr_bytes(n, n)))
+  w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(tc_ws_bytes(prec, n, n, n),
+                                                       tcw_qr_bytes(prec, n, n)))
                            : nullptr;
   carve_qr(a, n, n, w.qr, EIG_FP64);
   w.qr.q.prec = prec;
@@ -976,6 +1003,7 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   Arena arena(base);
   NodeWork w;
   carve_node(arena, n, m, p.prec, w);
+  const auto t_node = std::chrono::steady_clock::now();
   std::vector<double> diag, hscores;
   const double tau = p.tau > 0 ? p.tau : -1.0;
   int attempt = 0, fails = 0;
@@ -1005,10 +1033,13 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
     if (S.verbose)
       std::fprintf(stderr,
                    "[eigdc] node off=%d m=%d depth=%d attempt=%d region=%d (%.6g, %.6g) "
-                   "iters=%d conv=%d ratio=%.3g k=%d e=%.3g rank=%d draw=%d accepted=%d\n",
+                   "iters=%d conv=%d ratio=%.3g k=%d e=%.3g rank=%d draw=%d accepted=%d "
+                   "t=%.4f s\n",
                    nd.off, m, nd.depth, attempt, rg.kind, rg.c_or_sigma, rg.r_or_s, ir.iters,
                    (int)ir.converged, ir.last_ratio, so.k, so.e, so.rank, so.draw,
-                   (int)so.accepted);
+                   (int)so.accepted,
+                   std::chrono::duration<double>(std::chrono::steady_clock::now() - t_node)
+                       .count());
     if (so.accepted) {
       const int k = so.k;
       // U[:, off:off+m] <- U[:, off:off+m] Q ; node block <- A^
@@ -1547,7 +1578,7 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
 
 static void check_params(eig_handle_t h, const eig_params_t& p) {
   if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0 ||
-      (p.prec != EIG_FP64 && p.prec != EIG_SPLIT_BF16X3)) {
+      (p.prec != EIG_FP64 && p.prec != EIG_SPLIT_BF16X3 && p.prec != EIG_FP64_TC)) {
     h->err = "invalid eig_params_t";
     throw Fail{EIG_ERR_ARG};
   }
@@ -1634,7 +1665,12 @@ int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
   NodeWork nw;
   const bool pencil = (kind == EIG_KIND_PENCIL);
   carve_main(a, n, true, w, pencil);
-  carve_node(a, n, n, pencil ? EIG_FP64 : EIG_SPLIT_BF16X3, nw, pencil);
+  // the largest node scratch over the precision modes
+  Arena b1(nullptr), b2(nullptr);
+  NodeWork nw2;
+  carve_node(b1, n, n, EIG_SPLIT_BF16X3, nw, pencil);
+  carve_node(b2, n, n, EIG_FP64_TC, nw2, pencil);
+  a.used += std::max(b1.used, b2.used);
   *bytes = a.used;
   return EIG_OK;
 }
@@ -1778,7 +1814,8 @@ int eig_split_pencil(eig_handle_t h, int n, const double* dApR, const double* dB
   REQUIRE(dQL && ldql >= n && dQR && ldqr >= n, "dQL / dQR invalid");
   const eig_params_t p = params_or_default(params);
   check_params(h, p);
-  REQUIRE(p.prec == EIG_FP64, "pencils are solved in FP64 only");
+  REQUIRE(p.prec == EIG_FP64 || p.prec == EIG_FP64_TC,
+          "pencils are solved in FP64 (EIG_FP64 or EIG_FP64_TC) only");
   Arena meas(nullptr);
   SplitWork w;
   ensure_ws(h, carve_split(meas, n, w, p.prec, true));
@@ -1820,7 +1857,8 @@ int eig_pencil_schur(eig_handle_t h, int n, double* dA, int lda, double* dB, int
   REQUIRE(dalphar && dalphai && dbeta, "eigenvalue outputs are NULL");
   const eig_params_t p = params_or_default(params);
   check_params(h, p);
-  REQUIRE(p.prec == EIG_FP64, "pencils are solved in FP64 only");
+  REQUIRE(p.prec == EIG_FP64 || p.prec == EIG_FP64_TC,
+          "pencils are solved in FP64 (EIG_FP64 or EIG_FP64_TC) only");
   return pencil_impl(h, n, dA, lda, dB, ldb, dQL, ldql, dQR, ldqr, dalphar, dalphai, dbeta, p,
                      info);
   API_END
@@ -1982,6 +2020,29 @@ int eig_gemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha, 
   CK(gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, sp,
           reinterpret_cast<double*>(h->ws)));
   CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_gemm_fp64tc(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+                    const double* dA, int lda, const double* dB, int ldb, double beta, double* dC,
+                    int ldc) {
+  API_BEGIN
+  REQUIRE(m >= 0 && n >= 0 && k >= 0 && dC && ldc >= std::max(m, 1), "invalid arguments");
+  REQUIRE(lda >= std::max(1, ta ? k : m) && ldb >= std::max(1, tb ? n : k), "invalid ld");
+  const size_t need = tcx_gemm_workspace_bytes(m, n, k) + 256;
+  ensure_ws(h, need);
+  int* derr = reinterpret_cast<int*>(h->ws + need - 256);
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
+  CK(tcx_gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, h->ws,
+              derr));
+  int* hf = static_cast<int*>(pinned(h, 64));
+  CK(cudaMemcpyAsync(hf, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (*hf) {
+    h->err = "tensor-core GEMM: a bounded wait timed out (flag " + std::to_string(*hf) + ")";
+    return EIG_ERR_CUDA;
+  }
   return EIG_OK;
   API_END
 }
@@ -2187,7 +2248,7 @@ int eig_server_submit(eig_server_t S, int kind, int n, double* dA, int lda, doub
   if (params) r->p = *params;
   r->p.workers = 1;
   if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
-      (r->p.prec != EIG_FP64 && r->p.prec != EIG_SPLIT_BF16X3)) {
+      (r->p.prec != EIG_FP64 && r->p.prec != EIG_SPLIT_BF16X3 && r->p.prec != EIG_FP64_TC)) {
     delete r;
     return EIG_ERR_ARG;
   }
@@ -2220,7 +2281,8 @@ int eig_server_submit_pencil(eig_server_t S, int n, double* dA, int lda, double*
   eig_default_params(&r->p);
   if (params) r->p = *params;
   r->p.workers = 1;
-  if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 || r->p.prec != EIG_FP64) {
+  if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
+      (r->p.prec != EIG_FP64 && r->p.prec != EIG_FP64_TC)) {
     delete r;
     return EIG_ERR_ARG;
   }

@@ -34,6 +34,7 @@ EIG_REGION_CIRCLE = 1
 EIG_REGION_LINE = 2
 EIG_FP64 = 0
 EIG_SPLIT_BF16X3 = 1
+EIG_FP64_TC = 2
 EIG_KIND_SYM = 0
 EIG_KIND_NONSYM = 1
 EIG_KIND_PENCIL = 2
@@ -118,6 +119,7 @@ _SIGNATURES = {
                             ctypes.POINTER(_D), _P]),
     "eig_gemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_split": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+    "eig_gemm_fp64tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
 }
 
@@ -401,6 +403,11 @@ def eig_gemm(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
 
 def eig_gemm_split(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
     return h.check(lib().eig_gemm_split(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
+                                        _ptr(dB), ldb, beta, _ptr(dC), ldc))
+
+
+def eig_gemm_fp64tc(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
+    return h.check(lib().eig_gemm_fp64tc(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
                                         _ptr(dB), ldb, beta, _ptr(dC), ldc))
 
 
