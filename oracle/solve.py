@@ -395,18 +395,92 @@ def pencil_schur(A, B, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=None,
             return None, None, QL, QRm, None, None, None, info
         QL[:, off:off + m] = QL[:, off:off + m] @ ZL
         QRm[:, off:off + m] = QRm[:, off:off + m] @ ZR
-        wi_pattern[off:off + m] = wil
-    S = quasi_triangular_part(QL.T @ A @ QRm, wi_pattern)
-    T = np.triu(QL.T @ B @ QRm)
+        wi_pattern[off:off + m] = np.asarray(wil, dtype=np.float64)
+    Sf = QL.T @ A @ QRm
+    Tf = QL.T @ B @ QRm
+    if split_real_pairs(Sf, Tf, QL, QRm, wi_pattern):
+        Sf = QL.T @ A @ QRm
+        Tf = QL.T @ B @ QRm
+    S = quasi_triangular_part(Sf, wi_pattern)
+    T = np.triu(Tf)
     ar, ai, be = pencil_eigenvalues(S, T, wi_pattern)
     return S, T, QL, QRm, ar, ai, be, info
+
+
+def pair_quadratic(s, t):
+    """Coefficients (a, b, c) of det(s - z t) = a z^2 + b z + c for a 2 x 2
+    block s and an upper triangular t; the reversed polynomial c w^2 + b w + a
+    has the roots w = 1/z (the swapped block (t, s))."""
+    a = t[0, 0] * t[1, 1]
+    b = -(s[0, 0] * t[1, 1] + s[1, 1] * t[0, 0] - s[1, 0] * t[0, 1])
+    c = s[0, 0] * s[1, 1] - s[0, 1] * s[1, 0]
+    return a, b, c
+
+
+def _rotation_from(vec):
+    """2 x 2 rotation whose first column is vec / |vec| (identity for vec = 0)."""
+    r = float(np.hypot(vec[0], vec[1]))
+    if r == 0.0:
+        return np.eye(2)
+    x0, x1 = vec[0] / r, vec[1] / r
+    return np.array([[x0, -x1], [x1, x0]])
+
+
+def split_real_pairs(S, T, QL, QR, wi):
+    """Split the 2 x 2 blocks marked as complex pairs (wi[i] > 0, wi[i+1] =
+    -wi[i]) whose generalized eigenvalues are real, in place on QL, QR, wi.
+
+    A leaf's Francis iteration can leave two nearly equal real eigenvalues of
+    M (for instance a multiple eigenvalue at infinity seen as mu = 0 in a
+    swapped leaf) as a 2 x 2 block with a tiny imaginary part; in the (S, T)
+    frame that block may have real eigenvalues, which a generalized real Schur
+    form keeps in 1 x 1 blocks.  For a real eigenvalue alpha/beta (taken in
+    the orientation with the larger leading coefficient), x spans the null
+    space of beta S2 - alpha T2 (orthogonal to its larger row), Z rotates e1
+    onto x and Q rotates e1 onto S2 x (or T2 x): Q^T S2 Z and Q^T T2 Z are then
+    upper triangular.  Returns True if a block was split."""
+    n = S.shape[0]
+    changed = False
+    i = 0
+    while i < n - 1:
+        if not (wi[i] > 0.0 and wi[i + 1] == -wi[i]):
+            i += 1
+            continue
+        s = S[i:i + 2, i:i + 2]
+        t = np.triu(T[i:i + 2, i:i + 2])
+        a, b, c = pair_quadratic(s, t)
+        disc = b * b - 4.0 * a * c
+        if disc < 0.0 or (a == 0.0 and c == 0.0):
+            i += 2
+            continue
+        r = np.sqrt(disc)
+        q = -0.5 * (b + (r if b >= 0.0 else -r))     # the larger-magnitude root term
+        if abs(a) >= abs(c):
+            alpha, beta = (q / a if q != 0.0 else 0.0), 1.0
+        else:
+            alpha, beta = 1.0, (q / c if q != 0.0 else 0.0)
+        N = beta * s - alpha * t
+        row = N[0] if np.hypot(*N[0]) >= np.hypot(*N[1]) else N[1]
+        Z = _rotation_from(np.array([-row[1], row[0]]))
+        x = Z[:, 0]
+        u, v = s @ x, t @ x
+        Q = _rotation_from(u if np.hypot(*u) >= np.hypot(*v) else v)
+        QR[:, i:i + 2] = QR[:, i:i + 2] @ Z
+        QL[:, i:i + 2] = QL[:, i:i + 2] @ Q
+        wi[i] = wi[i + 1] = 0.0
+        changed = True
+        i += 2
+    return changed
 
 
 def pencil_eigenvalues(S, T, wi):
     """(alpha_re, alpha_im, beta) from a quasi-triangular S and triangular T:
     1x1 blocks give (s_ii, 0, t_ii); a 2x2 block (marked by wi[i] > 0 and
-    wi[i+1] = -wi[i]) gives the roots of det(S_blk - z T_blk) = 0 with beta
-    = 1 (alpha = z)."""
+    wi[i+1] = -wi[i]) gives its roots of det(S_blk - z T_blk) = 0, solved in
+    the orientation with the larger leading coefficient: z = alpha with
+    beta = 1 if |det T_blk| >= |det S_blk|, else the roots w = p +- i q of the
+    swapped block give alpha = p -+ i q, beta = p^2 + q^2 (z = alpha / beta).
+    The first index of a pair carries the positive imaginary part."""
     n = S.shape[0]
     ar, ai, be = np.zeros(n), np.zeros(n), np.zeros(n)
     i = 0
@@ -414,22 +488,26 @@ def pencil_eigenvalues(S, T, wi):
         if i + 1 < n and wi[i] > 0.0 and wi[i + 1] == -wi[i]:
             s = S[i:i + 2, i:i + 2]
             t = np.triu(T[i:i + 2, i:i + 2])
-            # det(s - z t) = a z^2 + b z + c
-            a = t[0, 0] * t[1, 1]
-            b = -(s[0, 0] * t[1, 1] + s[1, 1] * t[0, 0] - s[1, 0] * t[0, 1])
-            c = s[0, 0] * s[1, 1] - s[0, 1] * s[1, 0]
+            a, b, c = pair_quadratic(s, t)
             disc = b * b - 4 * a * c
+            lead, const = (a, c) if abs(a) >= abs(c) else (c, a)
             if disc < 0:
-                re = -b / (2 * a)
-                im = np.sqrt(-disc) / (2 * abs(a))
-                ar[i], ai[i], be[i] = re, im, 1.0
-                ar[i + 1], ai[i + 1], be[i + 1] = re, -im, 1.0
+                re = -b / (2 * lead)
+                im = np.sqrt(-disc) / (2 * abs(lead))
+                if abs(a) >= abs(c):
+                    vals = [(re, im, 1.0), (re, -im, 1.0)]
+                else:
+                    m2 = re * re + im * im
+                    vals = [(re, im, m2), (re, -im, m2)]
             else:
                 r = np.sqrt(disc)
-                z1 = (-b + r) / (2 * a)
-                z2 = (-b - r) / (2 * a)
-                ar[i], be[i] = z1, 1.0
-                ar[i + 1], be[i + 1] = z2, 1.0
+                w1 = (-b + r) / (2 * lead)
+                w2 = (-b - r) / (2 * lead)
+                if abs(a) >= abs(c):
+                    vals = [(w1, 0.0, 1.0), (w2, 0.0, 1.0)]
+                else:
+                    vals = [(1.0, 0.0, w1), (1.0, 0.0, w2)]
+            (ar[i], ai[i], be[i]), (ar[i + 1], ai[i + 1], be[i + 1]) = vals
             i += 2
         else:
             ar[i], ai[i], be[i] = S[i, i], 0.0, T[i, i]

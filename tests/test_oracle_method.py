@@ -539,3 +539,50 @@ def test_pencil_root_circle_sequence():
     radii = [reg[2] for reg in seen]
     assert radii[:4] == [1.0, 0.5, 0.25, 0.0625]
     assert seen[0][0] == REGION_UNIT_CIRCLE and all(reg[0] == REGION_CIRCLE for reg in seen[1:4])
+
+
+@pytest.mark.parametrize("s,t", [
+    ([[2.0, 1.0], [0.5, 3.0]], [[1.0, 0.2], [0.0, 1.0]]),       # two finite real eigenvalues
+    ([[1.0, 2.0], [0.7, -1.0]], [[1.0, 0.3], [0.0, 0.0]]),      # one infinite eigenvalue
+    ([[0.0, 1.0], [0.0, 0.0]], [[1.0, 0.0], [0.0, 1.0]])])      # Jordan block at 0
+def test_split_real_pairs_triangularises(s, t):
+    """A 2 x 2 block marked as a pair but with real generalized eigenvalues is
+    split: both factors become upper triangular, the orthogonal factors stay
+    orthogonal, and det(S - z T) keeps its roots."""
+    from oracle.solve import split_real_pairs, pair_quadratic
+    n = 4
+    rng = np.random.default_rng(2)
+    S = np.triu(rng.standard_normal((n, n)))
+    T = np.triu(rng.standard_normal((n, n))) + 2 * np.eye(n)
+    S[1:3, 1:3] = s
+    T[1:3, 1:3] = t
+    QL, QR = np.eye(n), np.eye(n)
+    wi = np.array([0.0, 1.0, -1.0, 0.0])
+    a0, b0, c0 = pair_quadratic(np.array(s), np.array(t))
+    assert split_real_pairs(S, T, QL, QR, wi)
+    assert np.all(wi == 0.0)
+    S2, T2 = QL.T @ S @ QR, QL.T @ T @ QR
+    assert abs(S2[2, 1]) <= 1e-15 * np.abs(S).max() and abs(T2[2, 1]) <= 1e-15 * np.abs(T).max()
+    assert np.allclose(QL.T @ QL, np.eye(n), atol=1e-15) and np.allclose(QR.T @ QR, np.eye(n), atol=1e-15)
+    # det(S2 - z T2) restricted to the block = product of the 1 x 1 factors
+    a1 = T2[1, 1] * T2[2, 2]
+    b1 = -(S2[1, 1] * T2[2, 2] + S2[2, 2] * T2[1, 1])
+    c1 = S2[1, 1] * S2[2, 2]
+    scale = max(abs(a0), abs(b0), abs(c0))
+    # the rotations have determinant 1, so the quadratic is unchanged
+    assert np.allclose([a1, b1, c1], [a0, b0, c0], atol=1e-14 * scale)
+
+
+def test_pair_eigenvalues_with_near_singular_T():
+    """Complex pair +- i / eps from s = [[0, 1], [-1, 0]], t = eps I: the swapped
+    orientation gives beta = eps^2 and alpha = -+ i eps exactly."""
+    from oracle.solve import pencil_eigenvalues
+    eps = 1e-9
+    S = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    T = eps * np.eye(2)
+    ar, ai, be = pencil_eigenvalues(S, T, np.array([1.0, -1.0]))
+    assert np.allclose(be, [eps * eps, eps * eps], rtol=1e-15)
+    lam = (ar + 1j * ai) / be
+    assert np.allclose(np.sort_complex(lam), np.sort_complex(np.array([1j / eps, -1j / eps])),
+                       rtol=1e-14)
+    assert ai[0] > 0 and ai[1] == -ai[0]
