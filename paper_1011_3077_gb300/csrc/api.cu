@@ -165,31 +165,25 @@ static size_t tc_ws_bytes(int prec, int m, int n, int k) {
   return 0;
 }
 
-// Products below this size stay on the FP64 DFMA kernel in EIG_FP64_TC mode:
-// the digit split costs a pass over both operands and three launches.
+// Products that stay on the FP64 DFMA kernel in EIG_FP64_TC mode: the digit
+// split costs a pass over both operands and three launches, and a 128 x 48
+// tile with nine digit planes per operand needs every dimension of a few
+// hundred to pay (measured: 5.8x DFMA at 4096^3, 3.1x at 1024^3, slower on the
+// rank-32 reflector products 2048 x 32 x 4096 and 4096 x 2048 x 32).
 static bool tcx_worth(int m, int n, int k) {
-  return m >= 64 && n >= 16 && k >= 64 && (double)m * n * k >= 16777216.0;
+  return m >= 128 && n >= 128 && k >= 128 && (double)m * n * k >= 33554432.0;
 }
 
-// Tensor-core product C = alpha op(A) op(B) + beta C in the arithmetic of prec
-// (tc_path(prec)); small FP64_TC products use the DFMA kernel without split-K.
-static cudaError_t tcmm(cudaStream_t s, int prec, bool ta, bool tb, int m, int n, int k,
-                        double alpha, const double* A, int lda, const double* B, int ldb,
-                        double beta, double* C, int ldc, void* ws, int* err) {
-  if (prec == EIG_FP64_TC) {
-    if (!tcx_worth(m, n, k))
-      return gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, 1, nullptr);
-    return tcx_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
-  }
-  return tc_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
-}
-
-// C = alpha op(A) op(B) + beta C in the arithmetic of `prec`.
+// C = alpha op(A) op(B) + beta C in the arithmetic of `prec`: BF16 x 3 on the
+// tensor cores (split precision), the FP64-accurate tensor-core split for
+// large products (EIG_FP64_TC), else the FP64 DFMA kernel with split-K.
 static void mm(eig_handle_t h, int prec, void* tcw, int* tcerr, bool ta, bool tb, int m, int n,
                int k, double alpha, const double* A, int lda, const double* B, int ldb,
                double beta, double* C, int ldc, int splits, double* part) {
-  if (tc_path(prec))
-    CK(tcmm(h->stream, prec, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
+  if (split_mode(prec))
+    CK(tc_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
+  else if (prec == EIG_FP64_TC && tcx_worth(m, n, k))
+    CK(tcx_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
   else
     CK(gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, splits, part));
 }
@@ -221,13 +215,13 @@ static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
     if (nc > 0) {
       const int mb = m - j0;
       double* C = q.W + j0 + (size_t)(j0 + jb) * q.ldw;
-      if (tc_path(q.prec)) {
+      if (split_mode(q.prec)) {
         // (V^T C)^T = C^T V on the tensor cores (M = nc rows, N = jb)
-        CK(tcmm(s, q.prec, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part, nc,
-                q.tcw, q.tcerr));
+        CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
+                   q.tcerr));
         CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk, true));
-        CK(tcmm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw,
-                q.tcw, q.tcerr));
+        CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw, q.tcw,
+                   q.tcerr));
       } else {
         int sp = gemm_choose_splits(jb, nc, mb);
         sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
@@ -256,12 +250,12 @@ static void apply_q(eig_handle_t h, int m, int nref, int jbmax, QRBufs& q, doubl
     if (nc <= 0) continue;
     double* Yb = Y + j0 + (size_t)c0 * ldy;
     const double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
-    if (tc_path(q.prec)) {
-      CK(tcmm(s, q.prec, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc,
-              q.tcw, q.tcerr));
+    if (split_mode(q.prec)) {
+      CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
+                 q.tcerr));
       CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, false, q.Wk, true));
-      CK(tcmm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy,
-              q.tcw, q.tcerr));
+      CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy, q.tcw,
+                 q.tcerr));
       continue;
     }
     int sp = gemm_choose_splits(jb, nc, mb);
@@ -288,7 +282,7 @@ static size_t carve_qr(Arena& a, int m, int n, QRWork& w, int prec = EIG_FP64) {
   w.q.Wk = a.take<double>((size_t)JB_LD * n);
   w.q.part = a.take<double>(qr_part_doubles(m, n));
   w.q.prec = prec;
-  w.q.tcw = tc_path(prec) ? (void*)a.take<char>(tcw_qr_bytes(prec, m, n)) : nullptr;
+  w.q.tcw = split_mode(prec) ? (void*)a.take<char>(tcw_qr_bytes(prec, m, n)) : nullptr;
   w.q.tcerr = a.take<int>(4);
   return a.used - start;
 }
@@ -333,7 +327,7 @@ static size_t carve_irs(Arena& a, int n, IRSWork& w, int prec = EIG_FP64) {
   // one plane buffer serves the QR's reflector products and the complement
   // products (they run one after the other on the stream)
   w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(tc_ws_bytes(prec, n, n, n),
-                                                       tcw_qr_bytes(prec, 2 * n, n)))
+                                                       split_mode(prec) ? tcw_qr_bytes(prec, 2 * n, n) : 0))
                            : nullptr;
   carve_qr(a, 2 * n, n, w.qr, EIG_FP64);
   w.qr.q.prec = prec;
@@ -469,7 +463,7 @@ static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64,
   w.rank = a.take<int>(4);
   w.prec = prec;
   w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(tc_ws_bytes(prec, n, n, n),
-                                                       tcw_qr_bytes(prec, n, n)))
+                                                       split_mode(prec) ? tcw_qr_bytes(prec, n, n) : 0))
                            : nullptr;
   carve_qr(a, n, n, w.qr, EIG_FP64);
   w.qr.q.prec = prec;
@@ -1566,6 +1560,12 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
     CK(gemm(s, false, false, n, n, n, 1.0, dB, ldb, dQR, ldqr, 0.0, w.Tbuf, n, gs, w.gpart));
     CK(gemm(s, true, false, n, n, n, 1.0, dQL, ldql, w.Tbuf, n, 0.0, dB, ldb, gs, w.gpart));
     inf.flops += 8.0 * (double)n * n * n;
+    {
+      // 2 x 2 blocks of real generalized eigenvalues become 1 x 1 blocks
+      int* hfl = static_cast<int*>(pinned(h, 64));
+      CK(pencil_split_real_pairs(s, n, dA, lda, dB, ldb, dQL, ldql, dQR, ldqr, wi, w.sortbuf,
+                                 reinterpret_cast<int*>(w.Zleaf2), w.status + 4, hfl));
+    }
     CK(zero_lower_quasi(s, n, dA, lda, wi));
     CK(upper_triangle(s, n, dB, ldb, dB, ldb));
     CK(pencil_alpha_beta(s, n, dA, lda, dB, ldb, wi, dar, dai, dbe));

@@ -101,6 +101,13 @@ cudaError_t diag_gershgorin(cudaStream_t s, int n, const double* A, int lda, dou
 cudaError_t count_rank(cudaStream_t s, int n, const double* R, int ldr, const double* Sc, int lds,
                        double rel_tol, int* rank);
 cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const double* wi);
+// Split the 2 x 2 blocks of (S, T) marked as complex pairs in wi whose
+// generalized eigenvalues are real (rotations applied to S, T, QL, QR; wi
+// updated).  scratch: 5n doubles; act: n ints; flag: device int; hflag:
+// pinned host int, set to 1 if any block was split.
+cudaError_t pencil_split_real_pairs(cudaStream_t s, int n, double* S, int lds, double* T, int ldt,
+                                    double* QL, int ldql, double* QR, int ldqr, double* wi,
+                                    double* scratch, int* act, int* flag, int* hflag);
 // (alpha_re, alpha_im, beta) of (S, T) in generalized real Schur form; 2 x 2
 // blocks of S are marked by wi[i] > 0, wi[i+1] = -wi[i]
 cudaError_t pencil_alpha_beta(cudaStream_t s, int n, const double* S, int lds, const double* T,

