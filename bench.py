@@ -50,9 +50,12 @@ def parse():
                     help="strict-upper scale of T in units of 1/sqrt(n) (1.0 = the exact "
                          "construction, whose eigenvalues are too ill-conditioned to split "
                          "in FP64 at n=2048; 0.1 = the documented reduced-coupling variant)")
-    ap.add_argument("--prec", type=int, default=0, choices=[0, 2],
-                    help="0: FP64 contractions on the DFMA pipe; 2: FP64-accurate contractions "
-                         "on the tensor cores (error-free nine-digit BF16 split)")
+    ap.add_argument("--prec", type=int, default=2, choices=[0, 2],
+                    help="2: FP64-accurate contractions on the tensor cores (error-free "
+                         "nine-digit BF16 split) for the large products; 0: every contraction "
+                         "on the FP64 DFMA pipe")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 path beside the tensor-core one")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -224,23 +227,24 @@ def main():
     dU = torch.zeros((n, n), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    def step(p=params):
         dA.copy_(dA0)
-        rc, info = eigdc.eig_solve(h, eigdc.EIG_KIND_NONSYM, n, dA, n, dwr, dwi, dU, n, params)
+        rc, info = eigdc.eig_solve(h, eigdc.EIG_KIND_NONSYM, n, dA, n, dwr, dwi, dU, n, p)
         if rc != eigdc.EIG_OK:
             raise RuntimeError("eig_solve failed: %d %s" % (rc, h.last_error()))
         return info
 
+    def backward_error():
+        # matrices are stored transposed (row-major view of column-major data)
+        T = dA.double()
+        R = dA0 - (dU.t() @ T.t() @ dU).t()
+        return float(torch.sqrt((R * R).sum()) / torch.sqrt((dA0 * dA0).sum()))
+
     for _ in range(max(args.warmup, 0)):
         info = step()
     # accuracy of the result (evaluation only, outside the timed region)
-    T = dA.double()
     Ut = dU
-    At = dA0
-    # matrices are stored transposed (row-major view of column-major data):
-    # A = U T U^T  <=>  A^T = U^T... work on the stored transposes directly
-    R = At - (Ut.t() @ T.t() @ Ut).t()
-    bwd = float(torch.sqrt((R * R).sum()) / torch.sqrt((At * At).sum()))
+    bwd = backward_error()
     # ||U^T U - I||_2 by power iteration on the symmetric residual
     Eo = Ut @ Ut.t() - torch.eye(n, dtype=torch.float64, device=dev)
     v = torch.ones(n, dtype=torch.float64, device=dev) / np.sqrt(n)
@@ -309,6 +313,31 @@ def main():
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": solves / (float(te.item()) / 1e3), "unit": "solves/s",
                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * (2 * n * n + 2 * n)}
+
+    # the plain FP64 path (every contraction on the DFMA pipe) on the same
+    # workload, timed the same way, for the metric's "vs plain FP64"
+    plain = None
+    if args.prec != 0 and not args.no_fp64_compare:
+        p64 = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=0)
+        step(p64)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ps, pe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ps.record(stream)
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            step(p64)
+        pe.record(stream)
+        torch.cuda.synchronize()
+        p_ms = ps.elapsed_time(pe)
+        tp = torch.tensor([p_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(tp, op=dist.ReduceOp.MAX)
+        p_ms = float(tp.item())
+        plain = {"value": solves / (p_ms / 1e3), "unit": "solves/s",
+                 "ms_per_step": p_ms / args.steps, "backward_error": backward_error(),
+                 "speedup_of_value": value / (solves / (p_ms / 1e3))}
 
     # roofline of the dominant kernel, the FP64 GEMM (dgemm_kernel): every
     # launch of the timed region was bracketed by CUDA events on its own
@@ -380,7 +409,7 @@ def main():
                                "total_iters": infos[-1].total_iters, "leaves": infos[-1].leaves,
                                "max_depth": infos[-1].max_depth},
                 "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roofline,
-                "e2e": e2e, "cpu_baseline": cpu}
+                "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain}
         print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

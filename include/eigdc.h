@@ -55,16 +55,17 @@ typedef struct eig_handle_s* eig_handle_t;
  * split_tol >= 1e-3, and eig_solve(EIG_KIND_SYM) ends with an FP64
  * refinement of the eigenvectors and eigenvalues. */
 #define EIG_SPLIT_BF16X3 1
-/* FP64-accurate contractions on the tensor cores: every GEMM of the path
- * (reflector products, complement products, splitter, similarity) splits its
- * FP64 operands error-free into nine 6-bit digits per row / column (power-of-
- * two scaled, stored exactly as BF16), multiplies the digit pairs of weight
- * levels 0..9 with tcgen05.mma into one FP32 TMEM accumulator per level, exact
- * because each 448-wide K chunk keeps every partial sum an integer below 2^24,
- * and drains the levels into FP64 (eig_gemm_fp64tc).  Error ~ K 2^-53 of
- * max|row| max|column|, like an FP64 GEMM; every other setting (tau,
- * split_tol, no refinement) is that of EIG_FP64.  Small products stay on the
- * FP64 kernel. */
+/* FP64-accurate contractions on the tensor cores: the large products of the
+ * path (complement products of the squarings, splitter, similarity; every
+ * dimension >= 128) split their FP64 operands error-free into nine 6-bit
+ * digits per row / column (power-of-two scaled, stored exactly as BF16),
+ * multiply the digit pairs of weight levels 0..9 with tcgen05.mma into one
+ * FP32 TMEM accumulator per level, exact because each 448-wide K chunk keeps
+ * every partial sum an integer below 2^24, and drain the levels into FP64
+ * (eig_gemm_fp64tc).  Error ~ K 2^-53 of max|row| max|column|, like an FP64
+ * GEMM; the rank-32 reflector products of the panels stay on the FP64 DFMA
+ * kernel, and every other setting (tau, split_tol, no refinement) is that of
+ * EIG_FP64. */
 #define EIG_FP64_TC 2
 
 /* regions (Sec. 3.1 unit circle; Sec. 3.3 line via the Moebius map
