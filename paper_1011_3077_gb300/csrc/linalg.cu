@@ -341,10 +341,9 @@ constexpr int PQ_GROUPS = PQ_THREADS / 32;
 constexpr size_t PQ_SMEM_LIMIT = 220 * 1024;
 
 struct PanelScratch {
-  double red_sig[2][2];
-  double red_dot[2][PQ_MAXJB];
+  double red[2][2][PQ_MAXJB];   // [parity][0: partial dots P'_k, 1: pivot row a_k(c)][k]
+  double comb[2][PQ_MAXJB];     // cluster sums of red[par]
   double grp[PQ_GROUPS][PQ_MAXJB + 1];
-  double wsum[PQ_THREADS / 32];
   double dk[PQ_MAXJB];
   double bc[4];
   double taus[PQ_MAXJB];
@@ -383,75 +382,23 @@ panel_qr_kernel(int m, int jb, double* __restrict__ P, int ldp, double* __restri
   __syncthreads();
   cluster.sync();   // every CTA of the cluster is resident before any DSMEM access
 
+  // One cluster reduction per column.  With x the column below and at the
+  // pivot, v_c = 1 and v_r = x_r / v0 (r > c), every needed product follows
+  // from the unnormalised partials P'_k = sum_{r > c} x_r a_k(r) (k = c gives
+  // sigma = sum_{r > c} x_r^2) and the pivot row a_k(c):
+  //   v^T a_k = a_k(c) + P'_k / v0   (update of column k > c; for k < c the
+  //   same expression with the stored reflector v_k gives v^T v_k for T).
   for (int c = 0; c < jb; ++c) {
     const int par = c & 1;
     double* colc = slab + c * rs_pad;
-    // ---- A: partial sum of squares below the pivot, pivot value
-    double s = 0.0;
-    for (int r = tid; r < rcount; r += PQ_THREADS) {
-      if (r0 + r > c) {
-        const double x = colc[r];
-        s = fma(x, x, s);
-      }
-    }
-    s = warp_sum(s);
-    if (lane == 0) sc->wsum[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < PQ_THREADS / 32; ++w) t += sc->wsum[w];
-      sc->red_sig[par][0] = t;
-      sc->red_sig[par][1] = (c >= r0 && c < r0 + rcount) ? colc[c - r0] : 0.0;
-    }
-    cluster.sync();
-    // ---- B: combine the CS partials (lane q reads rank q; fixed shuffle tree,
-    //      so every CTA gets bit-identical scalars), form the reflector
-    if (warp == 0) {
-      double sg = 0.0, xv = 0.0;
-      if (lane < CS) {
-        const double* rq = cluster.map_shared_rank(&sc->red_sig[0][0], lane);
-        sg = rq[par * 2 + 0];
-        xv = rq[par * 2 + 1];
-      }
-      const double sigma = warp_sum(sg);
-      const double x0 = warp_sum(xv);
-      if (lane == 0) {
-        double beta, mu, v0;
-        if (sigma == 0.0) {
-          v0 = 0.0;                          // v = e1 (nothing below the pivot)
-          if (x0 >= 0.0) { beta = 0.0; mu = x0; }
-          else { beta = 2.0; mu = -x0; }
-        } else {
-          mu = sqrt(x0 * x0 + sigma);
-          v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
-          beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
-        }
-        sc->bc[0] = beta;
-        sc->bc[1] = mu;
-        sc->bc[2] = v0;
-        sc->taus[c] = beta;
-      }
-    }
-    __syncthreads();
-    const double beta = sc->bc[0];
-    const double mu = sc->bc[1];
-    const double v0 = sc->bc[2];
-    for (int r = tid; r < rcount; r += PQ_THREADS) {
-      if (r0 + r > c) colc[r] = (v0 != 0.0) ? colc[r] / v0 : 0.0;
-    }
-    __syncthreads();
+    // ---- partials of this CTA's rows: thread (k = lane, g = warp)
     {
-      const int k = lane;          // column of the dot product
-      const int g = warp;          // row group
+      const int k = lane, g = warp;
       double d = 0.0;
-      if (k < jb && k != c) {
+      if (k < jb) {
         const double* colk = slab + k * rs_pad;
         for (int r = g; r < rcount; r += PQ_GROUPS) {
-          const int gr = r0 + r;
-          if (gr >= c) {
-            const double w = (gr == c) ? 1.0 : colc[r];
-            d = fma(w, colk[r], d);
-          }
+          if (r0 + r > c) d = fma(colc[r], colk[r], d);
         }
       }
       sc->grp[g][k] = d;
@@ -460,27 +407,50 @@ panel_qr_kernel(int m, int jb, double* __restrict__ P, int ldp, double* __restri
     if (tid < PQ_MAXJB) {
       double t = 0.0;
       for (int g = 0; g < PQ_GROUPS; ++g) t += sc->grp[g][tid];
-      sc->red_dot[par][tid] = t;
+      sc->red[par][0][tid] = t;
+      const bool own = (c >= r0 && c < r0 + rcount);
+      sc->red[par][1][tid] = (own && tid < jb) ? slab[tid * rs_pad + (c - r0)] : 0.0;
     }
     cluster.sync();
-    // ---- C: combine dots (thread (k, g) reads ranks g and g + 8 in parallel,
-    //      then a fixed-order sum over g), update, extend T
-    {
-      const int k = lane, g = warp;
+    // ---- cluster sums in rank order (bit-identical in every CTA)
+    if (tid < 2 * PQ_MAXJB) {
+      const int w = tid / PQ_MAXJB, k = tid % PQ_MAXJB;
       double t = 0.0;
-      if (k < jb) {
-        for (int q = g; q < CS; q += PQ_GROUPS) {
-          const double* rq = cluster.map_shared_rank(&sc->red_dot[0][0], q);
-          t += rq[par * PQ_MAXJB + k];
-        }
+      for (int q = 0; q < CS; ++q) {
+        const double* rq = cluster.map_shared_rank(&sc->red[0][0][0], q);
+        t += rq[(par * 2 + w) * PQ_MAXJB + k];
       }
-      sc->grp[g][k] = t;
+      sc->comb[w][k] = t;
     }
     __syncthreads();
+    if (tid == 0) {
+      const double sigma = sc->comb[0][c];
+      const double x0 = sc->comb[1][c];
+      double beta, mu, v0;
+      if (sigma == 0.0) {
+        v0 = 0.0;                          // v = e1 (nothing below the pivot)
+        if (x0 >= 0.0) { beta = 0.0; mu = x0; }
+        else { beta = 2.0; mu = -x0; }
+      } else {
+        mu = sqrt(x0 * x0 + sigma);
+        v0 = (x0 <= 0.0) ? (x0 - mu) : (-sigma / (x0 + mu));
+        beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+      }
+      sc->bc[0] = beta;
+      sc->bc[1] = mu;
+      sc->bc[2] = v0;
+      sc->taus[c] = beta;
+    }
+    __syncthreads();
+    const double beta = sc->bc[0];
+    const double mu = sc->bc[1];
+    const double v0 = sc->bc[2];
     if (tid < jb) {
-      double t = 0.0;
-      for (int g = 0; g < PQ_GROUPS; ++g) t += sc->grp[g][tid];
-      sc->dk[tid] = t;
+      const double pk = sc->comb[0][tid];
+      sc->dk[tid] = sc->comb[1][tid] + ((v0 != 0.0) ? pk / v0 : 0.0);
+    }
+    for (int r = tid; r < rcount; r += PQ_THREADS) {
+      if (r0 + r > c) colc[r] = (v0 != 0.0) ? colc[r] / v0 : 0.0;
     }
     __syncthreads();
     if (beta != 0.0) {
