@@ -12,8 +12,10 @@ orthogonal similarity of a prescribed spectrum; a library QR draws the
 orthogonal factor -- input generation, not the method).  Nonsymmetric
 requests use the triangular construction with strict-upper scale 0.1/sqrt(n)
 (the reduced-coupling reading of the nonsymmetric workload); pencils are
-A = (Q T Q^T) B with that T and B = I + 0.1 G / sqrt(n).  Pencils are solved
-in FP64 (the split-precision form covers the standard problems).
+A = (Q T Q^T) B with that T and B = I + 0.1 G / sqrt(n).  By default every
+request runs in EIG_FP64_TC (FP64 in and out, the large products on the
+tensor cores through the error-free split); pencils run in EIG_FP64_TC or
+EIG_FP64 (the BF16 x 3 form covers the standard problems only).
 
 Usage: python -m paper_1011_3077_gb300.serving --rate 200 --count 40
 """
@@ -87,7 +89,7 @@ def backward_error(kind, dA, o):
 
 
 def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8,
-        budget_gb=120.0, prec=eigdc.EIG_FP64, seed=5, device="cuda", verbose=False,
+        budget_gb=120.0, prec=eigdc.EIG_FP64_TC, seed=5, device="cuda", verbose=False,
         details=False):
     import torch
     rng = np.random.default_rng(seed)
@@ -109,7 +111,8 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
     torch.cuda.synchronize()
     srv = eigdc.Server(0, workers, budget_gb)
     params = eigdc.default_params(seed=seed, prec=prec)
-    params64 = eigdc.default_params(seed=seed, prec=eigdc.EIG_FP64)
+    params64 = eigdc.default_params(
+        seed=seed, prec=prec if prec in (eigdc.EIG_FP64, eigdc.EIG_FP64_TC) else eigdc.EIG_FP64)
     tickets = []
     t0 = time.perf_counter()
     for i, (kind, n, dA, o, ref) in enumerate(reqs):
@@ -155,7 +158,9 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
         "max_backward_error": max(bwds) if bwds else None,
         "max_eigenvalue_error": max(errs) if errs else None,
         "peak_reserved_gb": stats["peak_reserved_gb"], "budget_gb": budget_gb,
-        "workers": workers, "precision": "split" if prec else "fp64",
+        "workers": workers,
+        "precision": {eigdc.EIG_FP64: "fp64", eigdc.EIG_SPLIT_BF16X3: "bf16x3 split",
+                      eigdc.EIG_FP64_TC: "fp64 (tensor-core error-free split)"}[prec],
         "mix": {"sym": int(np.sum(kinds == eigdc.EIG_KIND_SYM)),
                 "nonsym": int(np.sum(kinds == eigdc.EIG_KIND_NONSYM)),
                 "pencil": int(np.sum(kinds == eigdc.EIG_KIND_PENCIL))},
@@ -175,7 +180,7 @@ def main():
     ap.add_argument("--nmax", type=int, default=4096)
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=120.0)
-    ap.add_argument("--prec", type=int, default=0)
+    ap.add_argument("--prec", type=int, default=2)
     ap.add_argument("--seed", type=int, default=5)
     a = ap.parse_args()
     from . import build
