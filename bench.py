@@ -58,6 +58,11 @@ def parse():
                     help="skip timing the plain FP64 path beside the tensor-core one")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
+    ap.add_argument("--workload", default="schur", choices=["schur", "batched"],
+                    help="schur: one nonsymmetric n x n solve per step (default); batched: "
+                         "--count independent symmetric problems, n log-uniform in [32, 512], "
+                         "solved by eig_solve_batched per step")
+    ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -194,6 +199,91 @@ def traffic_per_launch(per_launch_flops):
     return rec["dram_bytes_per_flop"] * per_launch_flops
 
 
+def batched_arm(args, torch, eigdc, h, dev, stream, world):
+    """Many independent symmetric problems per step (n log-uniform in [32, 512],
+    lambda ~ U[-1, 1], random orthogonal similarity), one eig_solve_batched
+    call: the problems run on the handle's host workers, each with its own CUDA
+    stream.  The call returns after every problem is solved, so CUDA events on
+    the handle's stream around it bracket the whole batch."""
+    from paper_1011_3077_gb300 import serving
+    rng = np.random.default_rng(0xE16D0004 + int(os.environ.get("RANK", "0")))
+    sizes = np.rint(np.exp(rng.uniform(np.log(32), np.log(512), args.count))).astype(int)
+    A0, refs = [], []
+    for i, n in enumerate(sizes):
+        dA, _, ref = serving.synthesize(eigdc.EIG_KIND_SYM, int(n), 7919 * i + 11, dev)
+        A0.append(dA)
+        refs.append(ref)
+    work = [a.clone() for a in A0]
+    wr = [torch.zeros(int(n), dtype=torch.float64, device=dev) for n in sizes]
+    Us = [torch.zeros((int(n), int(n)), dtype=torch.float64, device=dev) for n in sizes]
+    ns = [int(n) for n in sizes]
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for a, b in zip(work, A0):
+            a.copy_(b)
+        rc, st, infos = eigdc.eig_solve_batched(h, eigdc.EIG_KIND_SYM, ns, work, ns, wr, None, Us,
+                                                ns, params)
+        if rc != eigdc.EIG_OK or any(x != 0 for x in st):
+            raise RuntimeError("eig_solve_batched failed: %d %s" % (rc, h.last_error()))
+        return infos
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = eigdc.eig_kernel_launches()
+    ms = []
+    flops = 0.0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            flops += sum(x.flops for x in infos)
+    launches = eigdc.eig_kernel_launches() - l0
+    total_ms = float(sum(ms))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    solves = args.count * args.steps * world
+    # accuracy of the last step (outside the timed region)
+    eig_err = max(float(torch.max(torch.abs(w - r))) for w, r in zip(wr, refs))
+    bwd = 0.0
+    for j in np.linspace(0, args.count - 1, 25).astype(int):
+        A, U, w = A0[j], Us[j], wr[j]
+        R = A - U.t() @ torch.diag(w) @ U
+        bwd = max(bwd, float(torch.linalg.norm(R) / torch.linalg.norm(A)))
+    line = {"metric": METRIC, "value": solves / (total_ms / 1e3), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched symmetric eigendecompositions, %d independent "
+                                   "problems, n log-uniform in [32, 512], lambda ~ U[-1, 1]"
+                                   % args.count,
+                       "count": args.count, "n_min": int(sizes.min()), "n_max": int(sizes.max()),
+                       "sum_n2": int(np.sum(sizes.astype(np.int64) ** 2)),
+                       "workers": args.workers,
+                       "precision": "fp64" if args.prec == 0 else
+                                    "fp64 (tensor-core error-free split)",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "gflops": flops * world / (total_ms / 1e3) / 1e9,
+            "max_eigenvalue_error": eig_err, "backward_error_sample25": bwd,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
+            "e2e": None, "cpu_baseline": None}
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -217,6 +307,12 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream(dev)
     h = eigdc.Handle(local, stream)
+    if args.workload == "batched":
+        batched_arm(args, torch, eigdc, h, dev, stream, world)
+        h.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
     n = args.n
     A, d = workload(n, rank, args.coupling)
     params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
