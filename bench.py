@@ -184,6 +184,23 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(ms, device, world):
+    """Slowest rank's time (ms): every rank's timed region ends when the last
+    one does, so whole-job throughput divides all ranks' units by it."""
+    import torch
+    if world <= 1:
+        return float(ms)
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms_max, world):
+    """Units of all ranks (independent replicas) per second of the slowest rank."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def traffic_per_launch(per_launch_flops):
     """DRAM bytes per dgemm launch from the committed ncu capture (bytes per
     algorithmic flop, scaled to this run's average launch), or None when the
@@ -249,12 +266,7 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
             ms.append(e0.elapsed_time(e1))
             flops += sum(x.flops for x in infos)
     launches = eigdc.eig_kernel_launches() - l0
-    total_ms = float(sum(ms))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), dev, world)
     solves = args.count * args.steps * world
     # accuracy of the last step (outside the timed region)
     eig_err = max(float(torch.max(torch.abs(w - r))) for w, r in zip(wr, refs))
@@ -263,7 +275,8 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
         A, U, w = A0[j], Us[j], wr[j]
         R = A - U.t() @ torch.diag(w) @ U
         bwd = max(bwd, float(torch.linalg.norm(R) / torch.linalg.norm(A)))
-    line = {"metric": METRIC, "value": solves / (total_ms / 1e3), "unit": "solves/s",
+    line = {"metric": METRIC, "value": whole_job_rate(args.count * args.steps, total_ms, world),
+            "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -373,13 +386,9 @@ def main():
     if world > 1:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(step_ms))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev, world)
     solves = args.steps * world
-    value = solves / (total_ms / 1e3)
+    value = whole_job_rate(args.steps, total_ms, world)
     flops = float(np.mean([i.flops for i in infos]))
     gflops = flops * solves / (total_ms / 1e3) / 1e9
 
@@ -403,11 +412,8 @@ def main():
             hw[1].copy_(dwi, non_blocking=True)
         e_e.record(stream)
         torch.cuda.synchronize()
-        e_ms = e_s.elapsed_time(e_e)
-        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": solves / (float(te.item()) / 1e3), "unit": "solves/s",
+        e_ms = max_over_ranks(e_s.elapsed_time(e_e), dev, world)
+        e2e = {"value": whole_job_rate(args.steps, e_ms, world), "unit": "solves/s",
                "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * (2 * n * n + 2 * n)}
 
     # the plain FP64 path (every contraction on the DFMA pipe) on the same
@@ -426,14 +432,11 @@ def main():
             step(p64)
         pe.record(stream)
         torch.cuda.synchronize()
-        p_ms = ps.elapsed_time(pe)
-        tp = torch.tensor([p_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(tp, op=dist.ReduceOp.MAX)
-        p_ms = float(tp.item())
-        plain = {"value": solves / (p_ms / 1e3), "unit": "solves/s",
+        p_ms = max_over_ranks(ps.elapsed_time(pe), dev, world)
+        p_val = whole_job_rate(args.steps, p_ms, world)
+        plain = {"value": p_val, "unit": "solves/s",
                  "ms_per_step": p_ms / args.steps, "backward_error": backward_error(),
-                 "speedup_of_value": value / (solves / (p_ms / 1e3))}
+                 "speedup_of_value": value / p_val}
 
     # roofline of the dominant kernel, the FP64 GEMM (dgemm_kernel): every
     # launch of the timed region was bracketed by CUDA events on its own
