@@ -15,6 +15,8 @@ Workloads (sizes are parameters; the defaults follow the stated configurations):
     (x = sqrt(u1) cos(2 pi u2)), Q Haar.
   * batched_symmetric(count=2000): n log-uniform in [32, 512], lam ~ U[-1, 1].
   * regular_pencil(n): B = I + 0.1 G / sqrt(n), A = (Q T Q^T) B.
+  * svd_matrix(m, n): A = U diag(s) V^T, s ~ U[0.05, 1], U and V random
+    orthonormal.
   * pencil_with_infinite(n, n_inf): A = Q1 S Q2^T, B = Q1 T Q2^T with S, T
     upper triangular; n_inf diagonal pairs (s, t) = (1, 0) with those rows of
     T zero (a semisimple infinite eigenvalue, singular B), the others (d_i, 1)
@@ -115,6 +117,17 @@ def regular_pencil(n, seed=5, offdiag_scale=None, eig_scale=1.0):
     M = Q @ T @ Q.T
     B = np.eye(n) + 0.1 * rng.standard_normal((n, n)) / np.sqrt(n)
     return M @ B, B, d
+
+
+def svd_matrix(m, n, seed=10, lo=0.05, hi=1.0):
+    """(A, singular values descending): A = U diag(s) V^T with U, V random
+    orthonormal (m x r, n x r), r = min(m, n), s ~ U[lo, hi]."""
+    rng = rng_for(10, seed)
+    r = min(m, n)
+    s = np.sort(rng.uniform(lo, hi, r))[::-1]
+    U = random_orthogonal(m, rng)[:, :r]
+    V = random_orthogonal(n, rng)[:, :r]
+    return (U * s) @ V.T, s
 
 
 def pencil_with_infinite(n, n_inf=2, seed=9, offdiag_scale=None):

@@ -586,3 +586,25 @@ def test_pair_eigenvalues_with_near_singular_T():
     assert np.allclose(np.sort_complex(lam), np.sort_complex(np.array([1j / eps, -1j / eps])),
                        rtol=1e-14)
     assert ai[0] > 0 and ai[1] == -ai[0]
+
+
+@pytest.mark.parametrize("m,n", [(60, 40), (45, 70), (80, 80)])
+def test_oracle_svd_through_embedding(m, n):
+    """Singular values as the positive eigenvalues of [[0, A], [A^T, 0]]
+    (Sec. 3.2): prescribed s recovered, agreement with the library SVD,
+    A = U S V^T, orthonormal U and V."""
+    from oracle.svd import svd, embed
+    A, s0 = workloads.svd_matrix(m, n, seed=m + n)
+    s, U, V, info = svd(A, seed=2, leaf_size=32)
+    assert info.status == STATUS_OK
+    r = min(m, n)
+    assert np.allclose(s, s0, atol=1e-12)
+    assert np.allclose(s, np.linalg.svd(A, compute_uv=False)[:r], atol=1e-12)
+    assert np.linalg.norm(A - (U * s) @ V.T) <= 1e-12 * np.linalg.norm(A)
+    assert np.linalg.norm(U.T @ U - np.eye(r)) <= 1e-12
+    assert np.linalg.norm(V.T @ V - np.eye(r)) <= 1e-12
+    # the embedding is symmetric with the +- pairing of its spectrum
+    H = embed(A)
+    assert np.array_equal(H, H.T)
+    ev = np.linalg.eigvalsh(H)
+    assert np.allclose(np.sort(np.abs(ev))[::-1][:2 * r:2], s0, atol=1e-12)
