@@ -58,10 +58,11 @@ def parse():
                     help="skip timing the plain FP64 path beside the tensor-core one")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
-    ap.add_argument("--workload", default="schur", choices=["schur", "batched"],
+    ap.add_argument("--workload", default="schur", choices=["schur", "batched", "svd"],
                     help="schur: one nonsymmetric n x n solve per step (default); batched: "
                          "--count independent symmetric problems, n log-uniform in [32, 512], "
-                         "solved by eig_solve_batched per step")
+                         "solved by eig_solve_batched per step; svd: singular values and "
+                         "vectors of one n x n matrix per step (eig_svd)")
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -297,6 +298,68 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
         print(json.dumps(line), flush=True)
 
 
+def svd_arm(args, torch, eigdc, h, dev, stream, world):
+    """One n x n SVD per step through the symmetric embedding (eig_svd):
+    A = U diag(s) V^T with s ~ U[0.05, 1], U and V random orthogonal."""
+    from paper_1011_3077_gb300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    n = args.n
+    A, s0 = workloads.svd_matrix(n, n, seed=20 + rank)
+    dA = eigdc.to_device(A, dev)
+    dS = torch.zeros(n, dtype=torch.float64, device=dev)
+    dU = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    dV = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        rc, info = eigdc.eig_svd(h, n, n, dA, n, dS, dU, n, dV, n, params)
+        if rc != eigdc.EIG_OK:
+            raise RuntimeError("eig_svd failed: %d %s" % (rc, h.last_error()))
+        return info
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    l0 = eigdc.eig_kernel_launches()
+    ms, flops = [], 0.0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            flops += info.flops
+    launches = eigdc.eig_kernel_launches() - l0
+    total_ms = max_over_ranks(sum(ms), dev, world)
+    # accuracy (column-major tensors hold the transposes)
+    U, V, s = dU.t(), dV.t(), dS
+    At = torch.from_numpy(A).to(dev)
+    bwd = float(torch.linalg.norm(At - (U * s) @ V.t()) / torch.linalg.norm(At))
+    I = torch.eye(n, dtype=torch.float64, device=dev)
+    orth = max(float(torch.linalg.norm(U.t() @ U - I)), float(torch.linalg.norm(V.t() @ V - I)))
+    err = float(torch.max(torch.abs(s - torch.from_numpy(s0.copy()).to(dev))))
+    line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "SVD of A = U diag(s) V^T, n=%d, s ~ U[0.05, 1], through the "
+                                   "symmetric embedding of order 2n" % n,
+                       "n": n, "workers": args.workers,
+                       "precision": "fp64" if args.prec == 0 else
+                                    "fp64 (tensor-core error-free split)",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "gflops": flops * world / (total_ms / 1e3) / 1e9, "singular_value_error": err,
+            "backward_error": bwd, "orthogonality_frobenius": orth,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
+            "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -320,8 +383,9 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream(dev)
     h = eigdc.Handle(local, stream)
-    if args.workload == "batched":
-        batched_arm(args, torch, eigdc, h, dev, stream, world)
+    if args.workload in ("batched", "svd"):
+        (batched_arm if args.workload == "batched" else svd_arm)(args, torch, eigdc, h, dev,
+                                                                 stream, world)
         h.close()
         if world > 1:
             dist.destroy_process_group()

@@ -230,6 +230,18 @@ int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
               double* dwi, double* dU, int ldu, const eig_params_t* params,
               eig_solve_info_t* info);
 
+/* Singular value decomposition through the symmetric eigensolver (RSVD,
+ * Sec. 3.2): the embedding H = [[0, A], [A^T, 0]] of order m + n goes through
+ * the RSEP recursion (eig_solve, EIG_KIND_SYM, with params); its min(m, n)
+ * largest eigenvalues are the singular values, and the two halves of their
+ * eigenvectors, times sqrt(2), the left and right singular vectors.
+ * dA (m x n) is not modified; dS (min(m, n)) <- singular values descending;
+ * dU (m x min(m, n)), dV (n x min(m, n)) <- orthonormal singular vectors
+ * (vectors of zero singular values are not determined).  The handle holds
+ * 2 (m + n)^2 + (m + n) doubles for H and its eigenvectors. */
+int eig_svd(eig_handle_t h, int m, int n, const double* dA, int lda, double* dS, double* dU,
+            int ldu, double* dV, int ldv, const eig_params_t* params, eig_solve_info_t* info);
+
 /* Batched solves of independent problems (the units of parallelism of
  * Sec. 4.3, here spread over the handle's host workers, each with its own
  * CUDA stream; problems run largest first, each sequentially inside one

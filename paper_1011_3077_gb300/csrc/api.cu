@@ -54,6 +54,8 @@ struct eig_handle_s {
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
   std::vector<eig_handle_s*> workers;   // sub-handles of the node / batch executor
+  char* aux = nullptr;                  // caller-level buffers (SVD embedding), grown on demand
+  size_t aux_bytes = 0;
 };
 
 namespace {
@@ -1640,6 +1642,7 @@ int eig_destroy(eig_handle_t h) {
     delete w;
   }
   if (h->ws) cudaFree(h->ws);
+  if (h->aux) cudaFree(h->aux);
   if (h->lastR) cudaFree(h->lastR);
   if (h->pinned) cudaFreeHost(h->pinned);
   delete h;
@@ -1876,6 +1879,41 @@ int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
   const eig_params_t p = params_or_default(params);
   check_params(h, p);
   return solve_impl(h, kind, n, dA, lda, dwr, dwi, dU, ldu, p, info);
+  API_END
+}
+
+int eig_svd(eig_handle_t h, int m, int n, const double* dA, int lda, double* dS, double* dU,
+            int ldu, double* dV, int ldv, const eig_params_t* params, eig_solve_info_t* info) {
+  API_BEGIN
+  REQUIRE(m >= 1 && n >= 1, "m and n must be >= 1");
+  REQUIRE(dA && lda >= m, "dA / lda invalid");
+  REQUIRE(dS && dU && ldu >= m && dV && ldv >= n, "dS / dU / dV invalid");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  const int N = m + n;
+  const size_t nn = (size_t)N * N;
+  const size_t bytes = sizeof(double) * (2 * nn + N + 32);
+  if (bytes > h->aux_bytes) {
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->aux) cudaFree(h->aux);
+    h->aux = nullptr;
+    h->aux_bytes = 0;
+    if (cudaMalloc(&h->aux, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->err = "SVD buffer allocation failed";
+      return EIG_ERR_NOMEM;
+    }
+    h->aux_bytes = bytes;
+  }
+  double* H = reinterpret_cast<double*>(h->aux);
+  double* W = H + nn;
+  double* w = W + nn;
+  CK(svd_embed(h->stream, m, n, dA, lda, H, N));
+  const int st = solve_impl(h, EIG_KIND_SYM, N, H, N, w, nullptr, W, N, p, info);
+  if (st != EIG_OK) return st;
+  CK(svd_extract(h->stream, m, n, W, N, w, dS, dU, ldu, dV, ldv));
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
   API_END
 }
 

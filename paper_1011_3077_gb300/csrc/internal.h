@@ -108,6 +108,11 @@ cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const do
 cudaError_t pencil_split_real_pairs(cudaStream_t s, int n, double* S, int lds, double* T, int ldt,
                                     double* QL, int ldql, double* QR, int ldqr, double* wi,
                                     double* scratch, int* act, int* flag, int* hflag);
+// SVD through the symmetric embedding: H = [[0, A], [A^T, 0]]; singular
+// triplets from the r = min(m, n) largest eigenpairs of H.
+cudaError_t svd_embed(cudaStream_t s, int m, int n, const double* A, int lda, double* H, int ldh);
+cudaError_t svd_extract(cudaStream_t s, int m, int n, const double* W, int ldw, const double* w,
+                        double* S, double* U, int ldu, double* V, int ldv);
 // (alpha_re, alpha_im, beta) of (S, T) in generalized real Schur form; 2 x 2
 // blocks of S are marked by wi[i] > 0, wi[i+1] = -wi[i]
 cudaError_t pencil_alpha_beta(cudaStream_t s, int n, const double* S, int lds, const double* T,

@@ -5,6 +5,8 @@
 // (Sec. 4.2.1), Gershgorin data for the strategies of Sec. 3.3-3.4, and small
 // reshaping kernels (index reversal for RQ / QL).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 #include <stdint.h>
 
@@ -520,6 +522,55 @@ cudaError_t zero_lower_quasi(cudaStream_t s, int n, double* T, int ldt, const do
   if (t == 0) return cudaSuccess;
   note_launches(1);
   zero_lower_quasi_kernel<<<blocks_for(t, 256), 256, 0, s>>>(n, T, ldt, wi);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- SVD embedding
+// H (N x N, N = m + n) = [[0, A], [A^T, 0]] for A (m x n).
+__global__ void svd_embed_kernel(int m, int n, const double* __restrict__ A, int lda,
+                                 double* __restrict__ H, int ldh) {
+  const int N = m + n;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)N * N) return;
+  const int i = (int)(idx % N), j = (int)(idx / N);
+  double v = 0.0;
+  if (i < m && j >= m) v = A[i + (size_t)(j - m) * lda];
+  else if (i >= m && j < m) v = A[j + (size_t)(i - m) * lda];
+  H[i + (size_t)j * ldh] = v;
+}
+
+cudaError_t svd_embed(cudaStream_t s, int m, int n, const double* A, int lda, double* H, int ldh) {
+  const size_t t = (size_t)(m + n) * (m + n);
+  if (t == 0) return cudaSuccess;
+  note_launches(1);
+  svd_embed_kernel<<<blocks_for(t, 256), 256, 0, s>>>(m, n, A, lda, H, ldh);
+  return cudaGetLastError();
+}
+
+// From the eigenpairs of H (eigenvalues ascending in w, vectors in W): the
+// r = min(m, n) largest, descending, as singular values S[j] = w[N-1-j] with
+// U[:, j] = sqrt(2) W[0:m, N-1-j] and V[:, j] = sqrt(2) W[m:N, N-1-j].
+__global__ void svd_extract_kernel(int m, int n, int r, const double* __restrict__ W, int ldw,
+                                   const double* __restrict__ w, double* __restrict__ S,
+                                   double* __restrict__ U, int ldu, double* __restrict__ V,
+                                   int ldv) {
+  const int N = m + n;
+  const int j = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = N - 1 - j;
+  const double s2 = 1.4142135623730951;   // sqrt(2), correctly rounded
+  if (i == 0) S[j] = w[c];
+  if (i < m) U[i + (size_t)j * ldu] = s2 * W[i + (size_t)c * ldw];
+  if (i < n) V[i + (size_t)j * ldv] = s2 * W[m + i + (size_t)c * ldw];
+}
+
+cudaError_t svd_extract(cudaStream_t s, int m, int n, const double* W, int ldw, const double* w,
+                        double* S, double* U, int ldu, double* V, int ldv) {
+  const int r = std::min(m, n);
+  if (r == 0) return cudaSuccess;
+  dim3 grid((std::max(m, n) + 127) / 128, r);
+  note_launches(1);
+  svd_extract_kernel<<<grid, 128, 0, s>>>(m, n, r, W, ldw, w, S, U, ldu, V, ldv);
   return cudaGetLastError();
 }
 

@@ -98,6 +98,8 @@ _SIGNATURES = {
                               ctypes.POINTER(Params), ctypes.POINTER(SolveInfo)]),
     "eig_solve": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
                        ctypes.POINTER(SolveInfo)]),
+    "eig_svd": (_I, [_P, _I, _I, _P, _I, _P, _P, _I, _P, _I, ctypes.POINTER(Params),
+                     ctypes.POINTER(SolveInfo)]),
     "eig_solve_batched": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Params),
                                _P, _P]),
     "eig_server_create": (_I, [ctypes.POINTER(_P), _I, _I, _D]),
@@ -459,3 +461,24 @@ def pencil_schur(h, A, B, params=None):
     rc, info = eig_pencil_schur(h, n, dA, n, dB, n, dQL, n, dQR, n, dar, dai, dbe, params)
     return (rc, to_host(dA), to_host(dB), to_host(dQL), to_host(dQR), dar.cpu().numpy(),
             dai.cpu().numpy(), dbe.cpu().numpy(), info)
+
+
+def eig_svd(h, m, n, dA, lda, dS, dU, ldu, dV, ldv, params):
+    info = SolveInfo()
+    rc = lib().eig_svd(h.ptr, m, n, _ptr(dA), lda, _ptr(dS), _ptr(dU), ldu, _ptr(dV), ldv,
+                       ctypes.byref(params), ctypes.byref(info))
+    return rc, info
+
+
+def svd(h, A, params=None):
+    """(rc, s descending, U, V, info) for a real numpy matrix, through eig_svd."""
+    import torch
+    m, n = A.shape
+    r = min(m, n)
+    params = params or default_params()
+    dA = to_device(A)
+    dS = torch.zeros(r, dtype=torch.float64, device=dA.device)
+    dU = torch.zeros((r, m), dtype=torch.float64, device=dA.device)   # column-major m x r
+    dV = torch.zeros((r, n), dtype=torch.float64, device=dA.device)
+    rc, info = eig_svd(h, m, n, dA, m, dS, dU, m, dV, n, params)
+    return rc, dS.cpu().numpy(), dU.cpu().numpy().T.copy(), dV.cpu().numpy().T.copy(), info
