@@ -56,6 +56,9 @@ def parse():
                          "on the FP64 DFMA pipe")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path beside the tensor-core one")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="capture the IRS squarings as CUDA graphs (the bench process does no "
+                         "device-wide synchronisation while a solve runs)")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
     ap.add_argument("--workload", default="schur", choices=["schur", "batched", "svd"],
@@ -235,7 +238,8 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
     wr = [torch.zeros(int(n), dtype=torch.float64, device=dev) for n in sizes]
     Us = [torch.zeros((int(n), int(n)), dtype=torch.float64, device=dev) for n in sizes]
     ns = [int(n) for n in sizes]
-    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec,
+                                  graphs=args.graphs)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -309,7 +313,8 @@ def svd_arm(args, torch, eigdc, h, dev, stream, world):
     dS = torch.zeros(n, dtype=torch.float64, device=dev)
     dU = torch.zeros((n, n), dtype=torch.float64, device=dev)
     dV = torch.zeros((n, n), dtype=torch.float64, device=dev)
-    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec,
+                                  graphs=args.graphs)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -392,7 +397,8 @@ def main():
         return
     n = args.n
     A, d = workload(n, rank, args.coupling)
-    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec)
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec,
+                                  graphs=args.graphs)
     dA0 = eigdc.to_device(A, dev)
     dA = torch.empty_like(dA0)
     dwr = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -484,7 +490,8 @@ def main():
     # workload, timed the same way, for the metric's "vs plain FP64"
     plain = None
     if args.prec != 0 and not args.no_fp64_compare:
-        p64 = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=0)
+        p64 = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=0,
+                                   graphs=args.graphs)
         step(p64)
         if world > 1:
             dist.barrier()
@@ -545,6 +552,9 @@ def main():
                 "peak_note": "measured sustained bf16 %.1f TF/s x nominal FP64/BF16 ratio "
                              "1.25/2250 (%s)" % (bf16, peak_src),
                 "launches": g_cnt, "per_launch_flops": per_launch_flops,
+                "timed_set": "every eagerly launched dgemm_kernel of the timed region" +
+                             ("; launches replayed from the IRS squarings' CUDA graphs are "
+                              "not individually timed" if args.graphs else ""),
                 "launch_ms": g_ms_sum / g_cnt if g_cnt else None,
                 "isolated": {"shape": "%d x %d x %d (TN)" % (n, n, n), "launch_ms": g_ms,
                              "achieved": iso_achieved, "peak": bf16_burst * ratio,

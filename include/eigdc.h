@@ -102,6 +102,10 @@ typedef struct {
   int root_unit_circle; /* eig_solve nonsymmetric: split the root on |z| = 1 */
   int workers;       /* eig_solve: host workers (each with its own CUDA stream) that process
                         independent nodes of the recursion concurrently; 1 = sequential */
+  int graphs;        /* 1: capture the repeated launch sequence of the IRS squarings as CUDA
+                        graphs (per worker stream, cached on the handle) and replay them; the
+                        caller must not synchronize the whole device (cudaDeviceSynchronize)
+                        from another thread while the call runs.  0 (default): plain launches */
 } eig_params_t;
 
 typedef struct {
@@ -128,7 +132,7 @@ typedef struct {
 
 /* Defaults: tau = max(1e-14, 4 sqrt(n) 2^-53) at call time, maxit = 60,
  * split_tol = 0 (automatic), leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
- * v_draws = 4, root_unit_circle = 1, workers = 8. */
+ * v_draws = 4, root_unit_circle = 1, workers = 8, graphs = 0. */
 void eig_default_params(eig_params_t* p);
 
 /* Create a handle bound to CUDA device `device` and stream `stream`

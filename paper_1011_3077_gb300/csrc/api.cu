@@ -56,7 +56,21 @@ struct eig_handle_s {
   std::vector<eig_handle_s*> workers;   // sub-handles of the node / batch executor
   char* aux = nullptr;                  // caller-level buffers (SVD embedding), grown on demand
   size_t aux_bytes = 0;
+  // CUDA graphs of the IRS squaring, keyed by the workspace it runs in
+  struct IrsGraph {
+    const void* base;
+    int n, prec, parity;
+    cudaGraphExec_t exec;
+    unsigned long long kernels;
+  };
+  std::vector<IrsGraph> graphs;
+  bool graphs_off = false;
 };
+
+static void clear_graphs(eig_handle_s* h) {
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+}
 
 namespace {
 
@@ -104,6 +118,7 @@ struct Arena {
 static void ensure_ws(eig_handle_t h, size_t bytes) {
   if (bytes <= h->ws_bytes) return;
   CK(cudaStreamSynchronize(h->stream));
+  clear_graphs(h);   // the graphs hold pointers into the old workspace
   if (h->ws) cudaFree(h->ws);
   h->ws = nullptr;
   h->ws_bytes = 0;
@@ -352,7 +367,7 @@ static double default_tau(int n) { return std::max(1e-14, 4.0 * std::sqrt((doubl
 // quadratically (the FP32-level floor of the split-precision iterates).
 static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int lda, const double* B,
                       int ldb, const eig_region_t& rg, double tau, int maxit,
-                      bool stagnate = false) {
+                      bool stagnate = false, bool use_graphs = false) {
   cudaStream_t s = h->stream;
   const size_t nn = (size_t)n * n;
   QRBufs& q = w.qr.q;
@@ -370,24 +385,87 @@ static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int ld
   CK(cudaMemsetAsync(q.tcerr, 0, sizeof(int), s));
   IRSOut out{0, false, 0.0, nullptr, nullptr, nullptr};
   bool have_prev = false;
-  for (int j = 0;; ++j) {
+  // Device work of one squaring: QR of the stack, R_j (and the R-test sums),
+  // the complement [Q12; Q22] = Q [0; I], A_{j+1}, B_{j+1}, the next stack.
+  auto squaring = [&](bool prev) {
     const int jbmax = geqrf(h, 2 * n, n, q);
-    if (have_prev) {
+    if (prev) {
       CK(cudaMemsetAsync(w.sums, 0, 2 * sizeof(unsigned long long), s));
       CK(r_extract_diff(s, n, q.W, q.ldw, Rc, Rp, w.sums));
     } else {
       CK(r_extract_diff(s, n, q.W, q.ldw, Rc, nullptr, nullptr));
     }
-    // [Q12; Q22]: the last n columns of the 2n x 2n orthogonal factor
     CK(fill_identity_block(s, 2 * n, n, w.Y, 2 * n, n));
     apply_q(h, 2 * n, n, jbmax, q, w.Y, 2 * n, n, false);
     mm(h, w.prec, w.tcw, q.tcerr, true, false, n, n, n, 1.0, w.Y, 2 * n, Aj, n, 0.0, An, n, gsplit,
        w.gpart);
     mm(h, w.prec, w.tcw, q.tcerr, true, false, n, n, n, 1.0, w.Y + n, 2 * n, Bj, n, 0.0, Bn, n,
        gsplit, w.gpart);
+    CK(stack_pencil(s, n, An, Bn, q.W));
+  };
+  // From the second squaring on, the launch sequence repeats with the buffer
+  // pairs alternating: it is captured once per parity as a CUDA graph (cached
+  // on the handle for this workspace and size) and replayed.  Streams that
+  // cannot be captured (the legacy default stream) launch eagerly.
+  const bool graphs = use_graphs && (s != nullptr) && !h->graphs_off;
+  auto run_graph = [&](int parity) {
+    for (auto& g : h->graphs) {
+      if (g.base == w.Aj && g.n == n && g.prec == w.prec && g.parity == parity) {
+        CK(cudaGraphLaunch(g.exec, s));
+        note_launches(g.kernels);
+        return;
+      }
+    }
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs_off = true;
+      squaring(true);
+      return;
+    }
+    try {
+      squaring(true);
+    } catch (Fail&) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;   // kernel nodes: the launches of one replay
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (e == cudaSuccess && graph) {
+      size_t nn = 0;
+      e = cudaGraphGetNodes(graph, nullptr, &nn);
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+      for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+          ++kernels;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !exec) {
+      // capture unavailable here: launch eagerly from now on
+      cudaGetLastError();
+      h->graphs_off = true;
+      squaring(true);
+      return;
+    }
+    if (h->graphs.size() >= 96) clear_graphs(h);
+    // the first launch's kernels were counted while capturing; replays add
+    // `kernels` each
+    h->graphs.push_back({w.Aj, n, w.prec, parity, exec, kernels});
+    CK(cudaGraphLaunch(exec, s));
+  };
+  for (int j = 0;; ++j) {
+    if (j == 0 || !graphs) squaring(have_prev);
+    else run_graph(j & 1);
     std::swap(Aj, An);
     std::swap(Bj, Bn);
-    CK(stack_pencil(s, n, Aj, Bj, q.W));
     if (have_prev) {
       CK(cudaMemcpyAsync(hsum, w.sums, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(&hsum[2], q.tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1020,7 +1098,8 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
       rg.r_or_s = sc;
     }
     const double tau_m = tau > 0 ? tau : (split_mode(p.prec) ? 1e-5 : default_tau(m));
-    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(p.prec));
+    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(p.prec),
+                        p.graphs != 0);
     iters += ir.iters;
     flops += ir.iters * flops_irs_iter(m);
     SplitOut so = run_split(hw, w.split, m, ir.Ap, ir.Bp, m, An, n, S.sym, nd.id, attempt, S.pp,
@@ -1163,8 +1242,8 @@ static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* 
       rg.c_or_sigma = c + R * (xi - 0.5);
       rg.r_or_s = R;
     }
-    IRSOut ir = run_irs(hw, w.irs, m, P, n, Qm, n, rg, tau, p.maxit);
-    IRSOut il = run_irs(hw, w.irsL, m, w.At, m, w.Bt, m, rg, tau, p.maxit);
+    IRSOut ir = run_irs(hw, w.irs, m, P, n, Qm, n, rg, tau, p.maxit, false, p.graphs != 0);
+    IRSOut il = run_irs(hw, w.irsL, m, w.At, m, w.Bt, m, rg, tau, p.maxit, false, p.graphs != 0);
     iters += ir.iters;
     flops += (ir.iters + il.iters) * flops_irs_iter(m);
     SplitOut so = run_split_pencil(hw, w.split, m, ir.Ap, ir.Bp, il.Ap, il.Bp, m, P, n, Qm, n,
@@ -1610,6 +1689,7 @@ void eig_default_params(eig_params_t* p) {
   p->v_draws = 4;
   p->root_unit_circle = 1;
   p->workers = 8;
+  p->graphs = 0;
 }
 
 int eig_create(eig_handle_t* out, int device, void* stream) {
@@ -1638,9 +1718,11 @@ int eig_destroy(eig_handle_t h) {
     cudaStreamSynchronize(w->stream);
     if (w->ws) cudaFree(w->ws);
     if (w->pinned) cudaFreeHost(w->pinned);
+    clear_graphs(w);
     cudaStreamDestroy(w->stream);
     delete w;
   }
+  clear_graphs(h);
   if (h->ws) cudaFree(h->ws);
   if (h->aux) cudaFree(h->aux);
   if (h->lastR) cudaFree(h->lastR);
@@ -2285,6 +2367,7 @@ int eig_server_submit(eig_server_t S, int kind, int n, double* dA, int lda, doub
   eig_default_params(&r->p);
   if (params) r->p = *params;
   r->p.workers = 1;
+  r->p.graphs = 0;   // the caller keeps running CUDA work while requests are served
   if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
       (r->p.prec != EIG_FP64 && r->p.prec != EIG_SPLIT_BF16X3 && r->p.prec != EIG_FP64_TC)) {
     delete r;
@@ -2319,6 +2402,7 @@ int eig_server_submit_pencil(eig_server_t S, int n, double* dA, int lda, double*
   eig_default_params(&r->p);
   if (params) r->p = *params;
   r->p.workers = 1;
+  r->p.graphs = 0;
   if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
       (r->p.prec != EIG_FP64 && r->p.prec != EIG_FP64_TC)) {
     delete r;
@@ -2388,6 +2472,7 @@ int eig_server_destroy(eig_server_t S) {
     cudaStreamSynchronize(w->stream);
     if (w->ws) cudaFree(w->ws);
     if (w->pinned) cudaFreeHost(w->pinned);
+    clear_graphs(w);
     cudaStreamDestroy(w->stream);
     delete w;
   }

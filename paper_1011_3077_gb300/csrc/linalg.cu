@@ -259,7 +259,11 @@ static void launch_dgemm(cudaStream_t s, int m, int n, int k, int splits, int kc
                          double* C, int ldc, double* part) {
   note_launches(1);
   TimedLaunch tl{nullptr, nullptr, 2.0 * m * (double)n * k};
-  if (g_timing.load(std::memory_order_relaxed)) {
+  // launches being captured into a CUDA graph are not timed (their events
+  // would become graph nodes); the timed set is the eagerly launched ones
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (g_timing.load(std::memory_order_relaxed) &&
+      cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
     std::lock_guard<std::mutex> lock(g_tmu);
     tl.a = take_event();
     tl.b = take_event();

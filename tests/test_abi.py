@@ -46,7 +46,7 @@ def test_default_params_host_only(built):
     from paper_1011_3077_gb300 import eigdc
     p = eigdc.default_params()
     assert p.maxit == 60 and p.split_tol == 0.0 and p.leaf_size == 64 and p.v_draws == 4
-    assert p.workers == 8
+    assert p.workers == 8 and p.graphs == 0
 
 
 def test_struct_layout_matches_c_compiler(built, tmp_path):
