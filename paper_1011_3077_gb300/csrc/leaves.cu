@@ -424,12 +424,12 @@ francis_kernel(const LeafDesc* __restrict__ desc, const double* __restrict__ A, 
 cudaError_t francis_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
                            int lda, double* wr, double* wi, double* Z, int* status) {
   if (count == 0) return cudaSuccess;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {   // once per process (thread-safe static init)
     cudaFuncSetAttribute(francis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(FrancisShared));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   note_launches(1);
   francis_kernel<<<count, 128, sizeof(FrancisShared), s>>>(d_desc, A, lda, wr, wi, Z, status);
   return cudaGetLastError();

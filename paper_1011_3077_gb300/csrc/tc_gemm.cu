@@ -197,21 +197,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------ host side
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-static bool encode_fn() {
-  if (g_encode) return true;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                       &q) != cudaSuccess ||
-      q != cudaDriverEntryPointSuccess || fn == nullptr) {
-    cudaGetLastError();
-    return false;
-  }
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return true;
+// The driver's tensor-map encoder, looked up once (thread-safe static init);
+// nullptr when the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fnp = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || fn == nullptr) {
+      cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  return fnp;
 }
+
+static bool encode_fn() { return encoder() != nullptr; }
 
 // 3-D tensor map over K-major BF16 planes: (k, row, plane), box 64 x box_rows x 1,
 // 128-byte swizzle.
@@ -221,7 +224,7 @@ bool make_plane_map(CUtensorMap* map, void* base, int rows, int kp, int box_rows
   cuuint64_t strides[2] = {(cuuint64_t)kp * 2, (cuuint64_t)kp * 2 * (cuuint64_t)rows};
   cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
+  const CUresult r = encoder()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -263,12 +266,12 @@ cudaError_t tc_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, doubl
   if (!make_plane_map(&ta_map, pa, m, kp, TC_BM, TC_PLANES) ||
       !make_plane_map(&tb_map, pb, n, kp, TC_BN, TC_PLANES))
     return cudaErrorInvalidValue;
-  static bool attr = false;
   const size_t smem = sizeof(TcSmem) + 1024;
-  if (!attr) {
+  static const bool attr = [smem] {   // once per process (thread-safe static init)
     cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   dim3 grid((m + TC_BM - 1) / TC_BM, (n + TC_BN - 1) / TC_BN);
   note_launches(1);
   tc_gemm_kernel<<<grid, TC_THREADS, smem, s>>>(ta_map, tb_map, m, n, k, alpha, beta, C, ldc, err);
