@@ -124,7 +124,6 @@ cudaError_t oa_offmax(cudaStream_t s, int n, const double* G, const double* S,
                       unsigned long long* bits);
 cudaError_t oa_correction(cudaStream_t s, int n, const double* G, const double* S,
                           const double* lam, double delta, double* E);
-cudaError_t rayleigh(cudaStream_t s, int n, const double* X, const double* AX, double* lam);
 cudaError_t add_inplace(cudaStream_t s, size_t count, double* X, const double* D);
 
 // ------------------------------------------------------------- leaves.cu

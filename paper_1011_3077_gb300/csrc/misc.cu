@@ -837,50 +837,4 @@ cudaError_t add_inplace(cudaStream_t s, size_t count, double* X, const double* D
   return cudaGetLastError();
 }
 
-__global__ void rayleigh_kernel(int n, const double* __restrict__ X, const double* __restrict__ AX,
-                                double* __restrict__ lam) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  double num = 0.0, den = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    const double x = X[i + (size_t)warp * n];
-    num = fma(x, AX[i + (size_t)warp * n], num);
-    den = fma(x, x, den);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    num += __shfl_xor_sync(0xffffffffu, num, o);
-    den += __shfl_xor_sync(0xffffffffu, den, o);
-  }
-  if (lane == 0) lam[warp] = num / den;
-}
-
-cudaError_t oa_diag(cudaStream_t s, int n, const double* G, const double* S, double* lam,
-                    unsigned long long* maxabs) {
-  note_launches(1);
-  oa_diag_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, G, S, lam, maxabs);
-  return cudaGetLastError();
-}
-
-cudaError_t oa_offmax(cudaStream_t s, int n, const double* G, const double* S,
-                      unsigned long long* bits) {
-  note_launches(1);
-  oa_offmax_kernel<<<blocks_for((size_t)n * n, 256), 256, 0, s>>>(n, G, S, bits);
-  return cudaGetLastError();
-}
-
-cudaError_t oa_correction(cudaStream_t s, int n, const double* G, const double* S,
-                          const double* lam, double delta, double* E) {
-  note_launches(1);
-  oa_correction_kernel<<<blocks_for((size_t)n * n, 256), 256, 0, s>>>(n, G, S, lam, delta, E);
-  return cudaGetLastError();
-}
-
-cudaError_t rayleigh(cudaStream_t s, int n, const double* X, const double* AX, double* lam) {
-  note_launches(1);
-  rayleigh_kernel<<<blocks_for((size_t)n * 32, 256), 256, 0, s>>>(n, X, AX, lam);
-  return cudaGetLastError();
-}
-
 }  // namespace eigdc
