@@ -59,7 +59,8 @@ def build(verbose=False, force=False):
                 if verbose and out.strip():
                     print(out)
     if force or jobs or not os.path.exists(LIB):
-        _run([nvcc] + ARCH + ["-shared", "-o", LIB] + objs)
+        # --no-undefined: a missing definition fails the link, not the first load
+        _run([nvcc] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", LIB] + objs)
     return LIB
 
 

@@ -837,4 +837,25 @@ cudaError_t add_inplace(cudaStream_t s, size_t count, double* X, const double* D
   return cudaGetLastError();
 }
 
+cudaError_t oa_diag(cudaStream_t s, int n, const double* G, const double* S, double* lam,
+                    unsigned long long* maxabs) {
+  note_launches(1);
+  oa_diag_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, G, S, lam, maxabs);
+  return cudaGetLastError();
+}
+
+cudaError_t oa_offmax(cudaStream_t s, int n, const double* G, const double* S,
+                      unsigned long long* bits) {
+  note_launches(1);
+  oa_offmax_kernel<<<blocks_for((size_t)n * n, 256), 256, 0, s>>>(n, G, S, bits);
+  return cudaGetLastError();
+}
+
+cudaError_t oa_correction(cudaStream_t s, int n, const double* G, const double* S,
+                          const double* lam, double delta, double* E) {
+  note_launches(1);
+  oa_correction_kernel<<<blocks_for((size_t)n * n, 256), 256, 0, s>>>(n, G, S, lam, delta, E);
+  return cudaGetLastError();
+}
+
 }  // namespace eigdc
