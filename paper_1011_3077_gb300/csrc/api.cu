@@ -1,12 +1,18 @@
 // C-ABI of libeigdc and the host-side drivers of the divide-and-conquer path
 // (Ballard, Demmel, Dumitriu, arXiv 1011.3077):
 //   blocked Householder QR (Sec. 3 intro) -> IRS (Algorithm 3) -> GRURV
-//   splitter (Algorithm 2 with k = 2, exponents (-1, +1)) -> similarity and
-//   split test (Algorithms 5 / 6, Sec. 4.2.1) -> recursion (Sec. 3.3 / 3.4).
-// Every arithmetic step runs in the sm_103a kernels of linalg.cu, misc.cu and
-// leaves.cu; the host only orders launches, reads the convergence ratio once
-// per squaring, the chosen k / rank once per split, and takes the strategy
-// decisions (shift, interval) of the recursion.
+//   splitters (Algorithm 2 with k = 2; the left one of pencils, Algorithm 4)
+//   -> similarity and split test (Algorithms 4-6, Sec. 4.2.1) -> recursion
+//   (Sec. 3.3-3.5: lines, the pencil circle search and swap) -> leaves;
+//   the SVD through the symmetric embedding (Sec. 3.2).
+// Around it: the node-parallel executor (host workers with their own CUDA
+// streams), batched solves, CUDA graphs of the squarings, the request
+// server, and the precision modes (FP64, the FP64-accurate tensor-core split,
+// BF16 x 3 with FP64 refinement).
+// Every arithmetic step runs in the sm_103a kernels of linalg.cu, misc.cu,
+// leaves.cu, tc_gemm.cu and tcx_gemm.cu; the host only orders launches, reads
+// the convergence ratio once per squaring, the chosen k / rank once per
+// split, and takes the strategy decisions (shift, interval, circle, swap).
 #include <cuda_runtime.h>
 
 #include <algorithm>

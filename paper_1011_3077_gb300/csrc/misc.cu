@@ -2,8 +2,11 @@
 // region map + stacking (Sec. 3.3 Moebius map, Algorithm 3 stacking), the
 // R-difference convergence norms (Algorithm 3), the Philox Gaussian draw
 // (Algorithm 1, line 1), the split-test prefix-sum / max reduction
-// (Sec. 4.2.1), Gershgorin data for the strategies of Sec. 3.3-3.4, and small
-// reshaping kernels (index reversal for RQ / QL).
+// (Sec. 4.2.1), Gershgorin data for the strategies of Sec. 3.3-3.4, small
+// reshaping kernels (index reversal for RQ / QL, transposes), the kernels of
+// the FP64 refinement of the BF16 x 3 form, the SVD embedding (Sec. 3.2) and
+// the generalized Schur assembly of pencils (2 x 2 pair splitting, alpha /
+// beta).
 #include <cuda_runtime.h>
 
 #include <algorithm>
