@@ -608,3 +608,35 @@ def test_oracle_svd_through_embedding(m, n):
     assert np.array_equal(H, H.T)
     ev = np.linalg.eigvalsh(H)
     assert np.allclose(np.sort(np.abs(ev))[::-1][:2 * r:2], s0, atol=1e-12)
+
+
+def test_trevc_two_by_two_closed_form():
+    from oracle.trevc import triangular_eigenvectors
+    a, b, d = 0.7, -1.3, 2.1
+    X = triangular_eigenvectors(np.array([[a, b], [0.0, d]]))
+    assert np.allclose(X, [[1.0, b / (d - a)], [0.0, 1.0]], atol=1e-16)
+
+
+@pytest.mark.parametrize("kind", ["real", "complex"])
+def test_trevc_eigenvectors_of_schur_form(kind):
+    """Eigenvectors from the oracle's real Schur form: A V = V L to rounding
+    (scaled by the eigenvalue condition), and each V column parallel to the
+    library eigenvector of the same eigenvalue."""
+    from oracle.trevc import eigenvectors
+    n = 70
+    if kind == "real":
+        A, d, _ = workloads.nonsymmetric_schur(n, seed=11, offdiag_scale=0.1 / np.sqrt(n))
+    else:
+        A, _ = workloads.normal_complex(n, seed=4)
+    T, Q, wr, wi, info = schur_nonsym(A, seed=1, leaf_size=32)
+    assert info.status == STATUS_OK
+    lam, V = eigenvectors(T, Q, wi)
+    ref = wr + 1j * wi
+    assert max(np.min(np.abs(ref - x)) for x in lam) <= 1e-12
+    R = A @ V - V * lam
+    assert np.linalg.norm(R) <= 1e-11 * np.linalg.norm(A) * np.sqrt(n)
+    w_ref, V_ref = np.linalg.eig(A)
+    for j in range(n):
+        k = int(np.argmin(np.abs(w_ref - lam[j])))
+        cosang = abs(np.vdot(V_ref[:, k], V[:, j])) / np.linalg.norm(V_ref[:, k])
+        assert cosang >= 1.0 - 1e-8
