@@ -1483,6 +1483,8 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
       threads.emplace_back(worker_loop, h->workers[i], std::ref(S), true, nullptr);
     for (auto& t : threads) t.join();
     CK(cudaSetDevice(h->device));
+    // a worker that stopped on an error may have left launches in flight
+    for (int i = 0; i < nworkers; ++i) CK(cudaStreamSynchronize(h->workers[i]->stream));
   }
   int status = S.status;
   eig_solve_info_t inf = S.inf;
@@ -1613,6 +1615,8 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
       threads.emplace_back(worker_loop, h->workers[i], std::ref(S), true, nullptr);
     for (auto& t : threads) t.join();
     CK(cudaSetDevice(h->device));
+    // a worker that stopped on an error may have left launches in flight
+    for (int i = 0; i < nworkers; ++i) CK(cudaStreamSynchronize(h->workers[i]->stream));
   }
   int status = S.status;
   eig_solve_info_t inf = S.inf;
@@ -2054,6 +2058,7 @@ int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double*
   for (int i = 0; i < nworkers; ++i) threads.emplace_back(work, h->workers[i]);
   for (auto& t : threads) t.join();
   CK(cudaSetDevice(h->device));
+  for (int i = 0; i < nworkers; ++i) CK(cudaStreamSynchronize(h->workers[i]->stream));
   for (int i = 0; i < count; ++i)
     if (status[i] != EIG_OK) {
       h->err = "problem " + std::to_string(i) + " returned " + std::to_string(status[i]);
