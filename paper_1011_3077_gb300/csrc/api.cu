@@ -2289,6 +2289,9 @@ static void server_worker(eig_server_s* S, eig_handle_s* hw) {
     } catch (Fail f) {
       rc = f.code;
     }
+    // nothing of this request may still run once it is reported done (a
+    // failed solve can stop with launches in flight)
+    cudaStreamSynchronize(hw->stream);
     // keep a worker's scratch only while it is small: the budget counts
     // running requests, so large idle workspaces are returned
     if (hw->ws_bytes > ((size_t)1 << 30)) {
