@@ -27,6 +27,12 @@ Modules
              cyclic Jacobi, Hessenberg + Francis double-shift QR.
   solve      One divide step (RSEP / RNEP / RGNEP) and the recursive drivers
              (Sec. 3.3-3.5 strategies).
+  svd        RSVD through the symmetric embedding (Sec. 3.2).
+  trevc      Eigenvectors from the Schur form (the eigenvector section).
+  complex_qr   Complex Householder QR / RQ and the Haar unitary.
+  complex_leaf Complex Hessenberg + single-shift QR (complex Schur leaves).
+  cplane     The complex-plane strategy of Sec. 3.3: lines at random angles,
+             the 2-step radius shrink and convex enclosures of clusters.
 
 Parity status of each function is stated in its docstring; functions with no
 independent pin say "parity unpinned".

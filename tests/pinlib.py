@@ -76,3 +76,43 @@ def subspace_residual(U1, X):
     """||(I - U1 U1^T) X||_2 / ||X||_2 for U1 with orthonormal columns."""
     P = X - U1 @ (U1.T @ X)
     return np.linalg.norm(P, 2) / np.linalg.norm(X, 2)
+
+
+def cholesky_upper_c(M):
+    """Upper-triangular R, real positive diagonal, R^H R = M (Hermitian M)."""
+    M = np.asarray(M, dtype=np.complex128)
+    n = M.shape[0]
+    R = np.zeros((n, n), dtype=np.complex128)
+    for j in range(n):
+        s = (M[j, j] - np.vdot(R[:j, j], R[:j, j])).real
+        R[j, j] = np.sqrt(s)
+        for k in range(j + 1, n):
+            R[j, k] = (M[j, k] - np.vdot(R[:j, j], R[:j, k])) / R[j, j]
+    return R
+
+
+def ld_solve_c(A, B):
+    """A^{-1} B over C by Gaussian elimination with partial pivoting in long double."""
+    A = np.array(A, dtype=np.clongdouble)
+    B = np.array(B, dtype=np.clongdouble)
+    if B.ndim == 1:
+        B = B[:, None]
+    n = A.shape[0]
+    M = np.concatenate([A, B], axis=1)
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(M[k:, k])))
+        if p != k:
+            M[[k, p]] = M[[p, k]]
+        for i in range(k + 1, n):
+            f = M[i, k] / M[k, k]
+            M[i, k:] -= f * M[k, k:]
+    X = np.zeros((n, B.shape[1]), dtype=np.clongdouble)
+    for i in range(n - 1, -1, -1):
+        X[i] = (M[i, n:] - M[i, i + 1:n] @ X[i + 1:]) / M[i, i]
+    return X
+
+
+def subspace_residual_c(U1, X):
+    """||(I - U1 U1^H) X||_2 / ||X||_2 for U1 with orthonormal columns (complex)."""
+    P = X - U1 @ (U1.conj().T @ X)
+    return np.linalg.norm(P, 2) / np.linalg.norm(X, 2)
