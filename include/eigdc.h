@@ -369,6 +369,66 @@ int eig_gemm_noalloc(void* stream, int ta, int tb, int m, int n, int k, double a
                      const double* dA, int lda, const double* dB, int ldb, double beta,
                      double* dC, int ldc);
 
+/* ------------------------------------------------------ complex-plane strategy
+ * Sec. 3.3: splitting lines at random angles.  The line {z : Re(conj(w) z) = t}
+ * (|w| = 1) is mapped to the unit circle by the rotated Moebius map
+ * (A - w (t - s) I, A - w (t + s) I); IRS, GRURV, the similarity and the split
+ * test then run in complex arithmetic, so eigenvalues that no real line
+ * separates (a spectrum along the imaginary axis, conjugate pairs) split too.
+ * Complex arrays are interleaved (re, im) FP64 pairs, column-major, with
+ * leading dimensions counted in complex elements.
+ */
+#define EIG_MAX_HALFPLANES 8
+
+/* A convex region {|z - c| <= R} cut by half-planes Re(conj(w_i) z) >= t_i that
+ * holds the eigenvalues of a cluster no line could split (the convex
+ * enclosures of pseudospectra remarked on in Sec. 3.3).  At most the
+ * EIG_MAX_HALFPLANES most recent half-planes are kept; fewer half-planes give
+ * a larger region that still holds the cluster. */
+typedef struct {
+  int offset, size;   /* the cluster's diagonal block T(offset:offset+size, ...) */
+  double c_re, c_im, R;
+  int nhp;
+  double w_re[EIG_MAX_HALFPLANES], w_im[EIG_MAX_HALFPLANES], t[EIG_MAX_HALFPLANES];
+} eig_enclosure_t;
+
+/* Complex Schur form A = U T U^H (T upper triangular, w = diag(T)) of an
+ * n x n complex matrix by the recursion of Sec. 3.3: a disk holding the
+ * spectrum (Gershgorin about tr(A)/n), lines at a random angle and offset
+ * within half the radius (Philox purpose 8 of the node and attempt), chops of
+ * empty half-planes, the 2-step radius shrink (the next line perpendicular to
+ * the chord; the region moves to its enclosing circle, radius at most
+ * sin(5 pi/12) R), Gershgorin disks of the blocks after a split, and complex
+ * Hessenberg + single-shift QR leaves (leaf_size <= 64).
+ *   - dA (lda >= n), dT (ldt >= n), dU (ldu >= n): device, complex; dw: device,
+ *     n complex.  dA is not modified.
+ *   - params: tau, maxit, split_tol (0: max(1e-12, 16 n 2^-53)), leaf_size,
+ *     seed, max_fail, v_draws are used; every contraction runs in FP64.
+ *   - enclose = 1: a node that fails max_fail times is returned as a cluster:
+ *     its block is put in Schur form by the leaf solver and its region is
+ *     written to enc[i] (up to enc_cap entries; *n_enc = number of clusters).
+ *     enclose = 0: such a node stops the solve with EIG_NO_SPLIT.
+ *   - Returns EIG_NO_CONVERGENCE if a leaf's QR iteration ran out of steps. */
+int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* dT, int ldt,
+                      double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,
+                      eig_enclosure_t* enc, int enc_cap, int* n_enc, eig_solve_info_t* info);
+
+/* Host-only helpers of the Sec. 3.3 strategy (no GPU or handle needed).
+ * eig_cplane_enclosing_circle: a circle (m, r) holding the region
+ * {|z - c| <= R} cut by the nhp half-planes Re(conj(w_i) z) >= t_i: the
+ * smallest circle through the region's corners when it also holds the
+ * region's boundary arcs, else the disk itself.
+ * eig_cplane_draw_line: the line (w, t) of attempt `attempt` at node `node`:
+ * w = e^{2 pi i u2} (or i * pw when perpendicular != 0), t = R (u1 - 1/2) +
+ * Re(conj(w) c), (u1, u2) the Philox pair of purpose 8.  Both return EIG_OK or
+ * EIG_ERR_ARG (NULL output, negative count or radius). */
+int eig_cplane_enclosing_circle(double c_re, double c_im, double R, int nhp, const double* w_re,
+                                const double* w_im, const double* t, double* m_re, double* m_im,
+                                double* r);
+int eig_cplane_draw_line(uint64_t seed, uint64_t node, int attempt, double c_re, double c_im,
+                         double R, int perpendicular, double pw_re, double pw_im, double* w_re,
+                         double* w_im, double* t);
+
 #ifdef __cplusplus
 }
 #endif

@@ -798,6 +798,7 @@ static uint64_t child_node(uint64_t parent, int side) {
   return splitmix64(2 * parent + (uint64_t)side + 1);
 }
 
+
 struct Node {
   int off, m;
   double lo, hi;
@@ -1683,6 +1684,22 @@ static eig_params_t params_or_default(const eig_params_t* p) {
 
 }  // namespace
 
+// Host helpers shared with the complex-plane driver (cplane.cu).
+void eigdc::philox_pair_host(uint64_t seed, int purpose, uint64_t stream, int attempt, double* u1,
+                             double* u2) {
+  uint32_t c[4] = {0u, ((uint32_t)(attempt & 0xFF) << 8) | ((uint32_t)(purpose & 0xFFFF) << 16),
+                   (uint32_t)(stream & 0xFFFFFFFFull), (uint32_t)(stream >> 32)};
+  philox_host(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  const uint64_t m1 = ((uint64_t)c[0] << 20) | (c[1] >> 12);
+  const uint64_t m2 = ((uint64_t)c[2] << 20) | (c[3] >> 12);
+  *u1 = ((double)m1 + 0.5) * 0x1p-52;
+  *u2 = (double)m2 * 0x1p-52;
+}
+
+uint64_t eigdc::child_node_id(uint64_t parent, int side) { return child_node(parent, side); }
+
+int eigdc::choose_k_host(const double* e, int n) { return choose_k(e, n); }
+
 // =================================================================== C-ABI
 extern "C" {
 
@@ -1971,6 +1988,47 @@ int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
   const eig_params_t p = params_or_default(params);
   check_params(h, p);
   return solve_impl(h, kind, n, dA, lda, dwr, dwi, dU, ldu, p, info);
+  API_END
+}
+
+int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* dT, int ldt,
+                      double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,
+                      eig_enclosure_t* enc, int enc_cap, int* n_enc, eig_solve_info_t* info) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dA && lda >= n, "dA / lda invalid");
+  REQUIRE(dT && ldt >= n && dU && ldu >= n && dw, "dT / dU / dw invalid");
+  REQUIRE(enc_cap >= 0 && (enc_cap == 0 || enc), "enc / enc_cap invalid");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  REQUIRE(p.leaf_size <= 64, "leaf_size must be <= 64");
+  std::vector<CplaneCluster> cl;
+  std::string err;
+  const int rc = cplane_schur(h->stream, n, dA, lda, dT, ldt, dU, ldu, dw, p, enclose != 0, &cl,
+                              info, &err);
+  if (rc < 0) {
+    h->err = err;
+    return rc;
+  }
+  if (n_enc) *n_enc = (int)cl.size();
+  for (int i = 0; i < (int)cl.size() && i < enc_cap; ++i) {
+    eig_enclosure_t& e = enc[i];
+    std::memset(&e, 0, sizeof(e));
+    e.offset = cl[i].off;
+    e.size = cl[i].m;
+    e.c_re = cl[i].cr;
+    e.c_im = cl[i].ci;
+    e.R = cl[i].R;
+    const int nh = (int)cl[i].hp.size();
+    const int first = std::max(0, nh - EIG_MAX_HALFPLANES);
+    e.nhp = nh - first;
+    for (int j = first; j < nh; ++j) {
+      e.w_re[j - first] = cl[i].hp[j].wr;
+      e.w_im[j - first] = cl[i].hp[j].wi;
+      e.t[j - first] = cl[i].hp[j].t;
+    }
+  }
+  return rc;
   API_END
 }
 

@@ -1,0 +1,1380 @@
+// Complex-plane strategy for the nonsymmetric problem (Sec. 3.3) on sm_103a.
+//
+// Splitting lines at random angles separate eigenvalues that real lines
+// cannot (a conjugate pair, a spectrum along the imaginary axis), so this
+// path runs in complex arithmetic.  Complex matrices are interleaved
+// (re, im) FP64 pairs, column-major, leading dimensions in complex elements.
+//
+// One step on the line {z : Re(conj(w) z) = t}, |w| = 1, scale s:
+//   (A_0, B_0) = (A - w (t - s) I, A - w (t + s) I)   rotated Moebius map;
+//   IRS over C (Algorithm 3): QR of [B_j; -A_j], A_{j+1} = Q12^H A_j,
+//   B_{j+1} = Q22^H B_j, until ||R_j - R_{j-1}||_1 <= tau ||R_{j-1}||_1;
+//   splitter Q = GRURV(2, A_p + B_p, A_p, -1, +1) with a Haar unitary V
+//   (Algorithm 2): A_p V^H = U R2, then the RQ of U^H (A_p + B_p) through
+//   the QR of (A_p + B_p)^H U J (J reverses columns): Q = Z~ J;
+//   A^ = Q^H A Q and the 1-norm split test (Algorithm 5).
+// The leading k columns of Q span the invariant subspace of the eigenvalues
+// with Re(conj(w) z) > t.
+//
+// QR convention: reflector v = x + e^{i phi} ||x|| e1 (x0 = |x0| e^{i phi}),
+// normalised to u = v / v0 with tau = 1 + |x0| / ||x||, then a diagonal
+// unitary makes diag(R) real and non-negative; that QR is unique, so R_j and
+// the splitter agree with any other implementation of the same definition.
+//
+// Recursion (Sec. 3.3): the disk |z - c| <= R of a node (root: Gershgorin
+// about c = tr(A)/n), a random angle theta = 2 pi u2 and offset
+// a = R (u1 - 1/2) from Philox purpose 8; a step that finds one side empty
+// chops it off; the region (disk cut by the chopped half-planes) moves to its
+// enclosing circle at once when that shrinks the radius to sin(5 pi/12) R or
+// less, else the next line is perpendicular and the second chop recenters
+// (the 2-step rule).  A node that fails max_fail times is a cluster: with
+// `enclose` it is reported with its region (Sec. 3.3 remarks on convex
+// enclosures of pseudospectra) and solved by the leaf solver, otherwise the
+// solve stops with EIG_NO_SPLIT.  Leaves: complex Hessenberg reduction and
+// single-shift QR with Wilkinson shifts, one CTA per leaf.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/eigdc.h"
+#include "internal.h"
+
+namespace eigdc {
+namespace {
+
+typedef double2 zt;
+
+constexpr int PURPOSE_HAAR_RE = 4;
+constexpr int PURPOSE_HAAR_IM = 7;
+constexpr int PURPOSE_LINE = 8;
+constexpr int ZNB = 32;           // panel width of the complex QR (T leading dimension)
+constexpr int ZLEAF_MAX = 64;     // largest leaf of the complex Schur kernel
+constexpr double SHRINK = 0.96592582628906829;   // sin(5 pi / 12)
+
+__host__ __device__ __forceinline__ zt zmk(double r, double i) { return make_double2(r, i); }
+__device__ __forceinline__ zt zadd(zt a, zt b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ zt zsub(zt a, zt b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ zt zconj(zt a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ zt zmul(zt a, zt b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// c + a b
+__device__ __forceinline__ zt zfma(zt a, zt b, zt c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+// c + conj(a) b
+__device__ __forceinline__ zt zcfma(zt a, zt b, zt c) {
+  return make_double2(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ zt zscale(double s, zt a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double zabs(zt a) { return hypot(a.x, a.y); }
+
+int nblocks(long long count, int per) { return (int)((count + per - 1) / per); }
+
+// ------------------------------------------------------------------ ZGEMM
+// C = alpha op(A) op(B) + beta C, op(X) = X or X^H.  64 x 64 tile per CTA,
+// 256 threads, 4 x 4 complex outputs per thread, K slabs of 8 in shared memory.
+constexpr int ZBM = 64, ZBN = 64, ZBK = 8;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) zgemm_kernel(int m, int n, int k, zt alpha,
+                                                    const zt* __restrict__ A, int lda,
+                                                    const zt* __restrict__ B, int ldb, zt beta,
+                                                    zt* __restrict__ C, int ldc) {
+  __shared__ zt As[ZBK][ZBM + 1];
+  __shared__ zt Bs[ZBK][ZBN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.x * ZBM, col0 = blockIdx.y * ZBN;
+  zt acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = zmk(0.0, 0.0);
+  for (int k0 = 0; k0 < k; k0 += ZBK) {
+    for (int e = tid; e < ZBK * ZBM; e += 256) {
+      int r, kk;
+      if (!TA) { r = e % ZBM; kk = e / ZBM; } else { kk = e % ZBK; r = e / ZBK; }
+      const int gr = row0 + r, gk = k0 + kk;
+      zt v = zmk(0.0, 0.0);
+      if (gr < m && gk < k) v = TA ? zconj(A[gk + (size_t)gr * lda]) : A[gr + (size_t)gk * lda];
+      As[kk][r] = v;
+    }
+    for (int e = tid; e < ZBK * ZBN; e += 256) {
+      int c, kk;
+      if (!TB) { kk = e % ZBK; c = e / ZBK; } else { c = e % ZBN; kk = e / ZBN; }
+      const int gc = col0 + c, gk = k0 + kk;
+      zt v = zmk(0.0, 0.0);
+      if (gc < n && gk < k) v = TB ? zconj(B[gc + (size_t)gk * ldb]) : B[gk + (size_t)gc * ldb];
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ZBK; ++kk) {
+      zt a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = zfma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  const bool use_c = beta.x != 0.0 || beta.y != 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c >= n) continue;
+      zt v = zmul(alpha, acc[i][j]);
+      if (use_c) v = zfma(beta, C[r + (size_t)c * ldc], v);
+      C[r + (size_t)c * ldc] = v;
+    }
+  }
+}
+
+cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, zt alpha, const zt* A,
+                  int lda, const zt* B, int ldb, zt beta, zt* C, int ldc) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  dim3 g(nblocks(m, ZBM), nblocks(n, ZBN));
+  note_launches(1);
+  if (!ta && !tb) zgemm_kernel<false, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta && !tb) zgemm_kernel<true, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!ta && tb) zgemm_kernel<false, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  else zgemm_kernel<true, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ elementwise
+// B = A (rows x cols)
+__global__ void zcopy_kernel(int rows, int cols, const zt* __restrict__ A, int lda,
+                             zt* __restrict__ B, int ldb) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int i = (int)(e % rows), j = (int)(e / rows);
+  B[i + (size_t)j * ldb] = A[i + (size_t)j * lda];
+}
+
+cudaError_t zcopy(cudaStream_t s, int rows, int cols, const zt* A, int lda, zt* B, int ldb) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  note_launches(1);
+  zcopy_kernel<<<nblocks((long long)rows * cols, 256), 256, 0, s>>>(rows, cols, A, lda, B, ldb);
+  return cudaGetLastError();
+}
+
+// A0 = A - w (t - s) I, B0 = A - w (t + s) I
+__global__ void zline_map_kernel(int n, const zt* __restrict__ A, int lda, zt s0, zt s1,
+                                 zt* __restrict__ A0, zt* __restrict__ B0) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  zt a = A[i + (size_t)j * lda];
+  zt b = a;
+  if (i == j) {
+    a = zsub(a, s0);
+    b = zsub(b, s1);
+  }
+  A0[e] = a;
+  B0[e] = b;
+}
+
+// W (2n x n) = [B; -A]
+__global__ void zstack_kernel(int n, const zt* __restrict__ A, const zt* __restrict__ B,
+                              zt* __restrict__ W) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  const zt a = A[e];
+  W[i + (size_t)j * 2 * n] = B[e];
+  W[n + i + (size_t)j * 2 * n] = zmk(-a.x, -a.y);
+}
+
+// E (rows x cols) = identity block at row offset r0: E_ij = [i - r0 == j]
+__global__ void zident_kernel(int rows, int cols, int r0, zt* __restrict__ E) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int i = (int)(e % rows), j = (int)(e / rows);
+  E[e] = zmk(i - r0 == j ? 1.0 : 0.0, 0.0);
+}
+
+cudaError_t zident(cudaStream_t s, int rows, int cols, int r0, zt* E) {
+  note_launches(1);
+  zident_kernel<<<nblocks((long long)rows * cols, 256), 256, 0, s>>>(rows, cols, r0, E);
+  return cudaGetLastError();
+}
+
+// C = A + B (n x n, packed)
+__global__ void zadd_kernel(long long count, const zt* __restrict__ A, const zt* __restrict__ B,
+                            zt* __restrict__ C) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) C[e] = zadd(A[e], B[e]);
+}
+
+// B = A J (columns reversed), rows x n packed
+__global__ void zrevcols_kernel(int rows, int n, const zt* __restrict__ A, zt* __restrict__ B) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * n) return;
+  const int i = (int)(e % rows), j = (int)(e / rows);
+  B[i + (size_t)(n - 1 - j) * rows] = A[e];
+}
+
+// G = Gre + i Gim
+__global__ void zinterleave_kernel(long long count, const double* __restrict__ re,
+                                   const double* __restrict__ im, zt* __restrict__ G) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) G[e] = zmk(re[e], im[e]);
+}
+
+// M = |A| (n x n packed, real)
+__global__ void zabs_kernel(long long count, const zt* __restrict__ A, double* __restrict__ M) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) M[e] = zabs(A[e]);
+}
+
+// T = upper triangle of A (n x n), zero below; w = diag(A)
+__global__ void ztriu_kernel(int n, const zt* __restrict__ A, int lda, zt* __restrict__ T, int ldt,
+                             zt* __restrict__ w) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  const zt v = A[i + (size_t)j * lda];
+  T[i + (size_t)j * ldt] = i <= j ? v : zmk(0.0, 0.0);
+  if (i == j && w) w[i] = v;
+}
+
+// colsum[j] = sum_i |A_ij - [i == j] c| for j < cols; one CTA per column, fixed order.
+__global__ void zcolabs_kernel(int rows, int cols, const zt* __restrict__ A, int lda, zt c,
+                               double* __restrict__ colsum) {
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < rows; i += 256) {
+    zt v = A[i + (size_t)j * lda];
+    if (i == j) v = zsub(v, c);
+    acc += zabs(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    colsum[j] = t;
+  }
+}
+
+// rowsum[i] = sum_j |A_ij - [i == j] c|
+__global__ void zrowabs_kernel(int n, const zt* __restrict__ A, int lda, zt c,
+                               double* __restrict__ rowsum) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < n; ++j) {
+    zt v = A[i + (size_t)j * lda];
+    if (i == j) v = zsub(v, c);
+    acc += zabs(v);
+  }
+  rowsum[i] = acc;
+}
+
+// colsum[j] = sum_i |A_ij - B_ij| (upper triangles of two n x n R factors)
+__global__ void zcoldiff_kernel(int n, const zt* __restrict__ A, const zt* __restrict__ B,
+                                double* __restrict__ colsum) {
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += zabs(zsub(A[i + (size_t)j * n], B[i + (size_t)j * n]));
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    colsum[j] = t;
+  }
+}
+
+// ------------------------------------------------------------------ complex QR
+// Panel factorisation of the m x jb panel P in place (one CTA, 512 threads):
+// R on and above the diagonal (before the phase fix), u below it (u_j = 1
+// implicit), tau[j] real.
+constexpr int ZP_THREADS = 256;
+constexpr int ZP_WARPS = ZP_THREADS / 32;
+
+__device__ double zp_block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < ZP_WARPS; ++w) t += red[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(ZP_THREADS) zpanel_kernel(int m, int jb, zt* __restrict__ P,
+                                                            int ldp, double* __restrict__ tau) {
+  __shared__ double red[ZP_WARPS];
+  __shared__ zt part[ZP_WARPS][ZNB + 1];
+  __shared__ zt dots[ZNB];
+  __shared__ zt s_inv_v0;
+  __shared__ double s_tau;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < jb; ++j) {
+    zt* x = P + (size_t)j * ldp;
+    double ss = 0.0;
+    for (int r = j + tid; r < m; r += ZP_THREADS) ss += x[r].x * x[r].x + x[r].y * x[r].y;
+    ss = zp_block_sum(ss, red);
+    if (tid == 0) {
+      const double nrm = sqrt(ss);
+      const zt x0 = x[j];
+      const double a0 = zabs(x0);
+      if (nrm == 0.0) {
+        s_tau = 0.0;
+        s_inv_v0 = zmk(0.0, 0.0);
+      } else {
+        const zt ph = a0 > 0.0 ? zmk(x0.x / a0, x0.y / a0) : zmk(1.0, 0.0);
+        const double mag = a0 + nrm;                 // v0 = ph (|x0| + ||x||)
+        s_inv_v0 = zmk(ph.x / mag, -ph.y / mag);     // 1 / v0 = conj(ph) / mag
+        s_tau = mag / nrm;                           // 1 + |x0| / ||x||
+        x[j] = zmk(-ph.x * nrm, -ph.y * nrm);        // beta = -ph ||x||
+      }
+      tau[j] = s_tau;
+    }
+    __syncthreads();
+    const double tj = s_tau;
+    if (tj == 0.0) continue;                         // uniform across the block
+    const zt iv = s_inv_v0;
+    for (int r = j + 1 + tid; r < m; r += ZP_THREADS) x[r] = zmul(x[r], iv);
+    __syncthreads();
+    const int nc = jb - j - 1;
+    if (nc <= 0) continue;
+    // dots_c = sum_r conj(u_r) P[r, j+1+c]
+    zt acc[ZNB];
+#pragma unroll
+    for (int c = 0; c < ZNB; ++c) acc[c] = zmk(0.0, 0.0);
+    for (int r = j + tid; r < m; r += ZP_THREADS) {
+      const zt u = r == j ? zmk(1.0, 0.0) : x[r];
+#pragma unroll
+      for (int c = 0; c < ZNB; ++c)
+        if (c < nc) acc[c] = zcfma(u, P[r + (size_t)(j + 1 + c) * ldp], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < ZNB; ++c) {
+      if (c < nc) {
+        double re = acc[c].x, im = acc[c].y;
+        for (int o = 16; o > 0; o >>= 1) {
+          re += __shfl_down_sync(0xffffffffu, re, o);
+          im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) part[warp][c] = zmk(re, im);
+      }
+    }
+    __syncthreads();
+    if (tid < nc) {
+      zt t = zmk(0.0, 0.0);
+      for (int w = 0; w < ZP_WARPS; ++w) t = zadd(t, part[w][tid]);
+      dots[tid] = zscale(tj, t);
+    }
+    __syncthreads();
+    for (int r = j + tid; r < m; r += ZP_THREADS) {
+      const zt u = r == j ? zmk(1.0, 0.0) : x[r];
+      for (int c = 0; c < nc; ++c) {
+        zt* pc = P + r + (size_t)(j + 1 + c) * ldp;
+        *pc = zsub(*pc, zmul(u, dots[c]));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// V (m x jb) explicit: 1 on the diagonal, 0 above, u below (from the panel).
+__global__ void zextract_v_kernel(int m, int jb, const zt* __restrict__ P, int ldp,
+                                  zt* __restrict__ V, int ldv) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * jb) return;
+  const int r = (int)(e % m), c = (int)(e / m);
+  V[r + (size_t)c * ldv] = r < c ? zmk(0.0, 0.0) : (r == c ? zmk(1.0, 0.0) : P[r + (size_t)c * ldp]);
+}
+
+// Partial Gram matrices of V over chunks of 64 rows: part[chunk][i + 32 j] = sum conj(V_ri) V_rj.
+__global__ void __launch_bounds__(1024) zgram_kernel(int m, int jb, const zt* __restrict__ V,
+                                                     int ldv, zt* __restrict__ part) {
+  __shared__ zt Vs[64][ZNB + 1];
+  const int r0 = blockIdx.x * 64;
+  for (int e = threadIdx.x; e < 64 * ZNB; e += 1024) {
+    const int r = e % 64, c = e / 64;
+    Vs[r][c] = (r0 + r < m && c < jb) ? V[r0 + r + (size_t)c * ldv] : zmk(0.0, 0.0);
+  }
+  __syncthreads();
+  const int i = threadIdx.x % 32, j = threadIdx.x / 32;
+  zt s = zmk(0.0, 0.0);
+  for (int r = 0; r < 64; ++r) s = zcfma(Vs[r][i], Vs[r][j], s);
+  part[(size_t)blockIdx.x * 1024 + i + 32 * j] = s;
+}
+
+// T (jb x jb upper, ld ZNB) of H_0 .. H_{jb-1} = I - V T V^H from the Gram partials:
+// T_cc = tau_c, T(0:c, c) = -tau_c T(0:c, 0:c) G(0:c, c).
+__global__ void __launch_bounds__(1024) zlarft_kernel(int nchunks, int jb, const zt* __restrict__ part,
+                                                      const double* __restrict__ tau,
+                                                      zt* __restrict__ T) {
+  __shared__ zt G[ZNB][ZNB + 1];
+  __shared__ zt Ts[ZNB][ZNB + 1];
+  const int i = threadIdx.x % 32, j = threadIdx.x / 32;
+  zt s = zmk(0.0, 0.0);
+  for (int ch = 0; ch < nchunks; ++ch) s = zadd(s, part[(size_t)ch * 1024 + i + 32 * j]);
+  G[i][j] = s;
+  Ts[i][j] = zmk(0.0, 0.0);
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    if (threadIdx.x < c) {
+      const int r = threadIdx.x;
+      zt acc = zmk(0.0, 0.0);
+      for (int q = r; q < c; ++q) acc = zfma(Ts[r][q], G[q][c], acc);
+      Ts[r][c] = zscale(-tau[c], acc);
+    } else if (threadIdx.x == c) {
+      Ts[c][c] = zmk(tau[c], 0.0);
+    }
+    __syncthreads();
+  }
+  T[i + ZNB * j] = (i < jb && j < jb) ? Ts[i][j] : zmk(0.0, 0.0);
+}
+
+// R (n x n, ld ldr) = D^H triu(P(0:n, 0:n)) with D = diag(phase of P_jj); phases[j] = D_jj.
+__global__ void zr_extract_kernel(int n, const zt* __restrict__ P, int ldp, zt* __restrict__ R,
+                                  int ldr, zt* __restrict__ phases) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e % n), j = (int)(e / n);
+  const zt d = P[i + (size_t)i * ldp];
+  const double ad = zabs(d);
+  const zt ph = ad > 0.0 ? zmk(d.x / ad, d.y / ad) : zmk(1.0, 0.0);
+  zt v = zmk(0.0, 0.0);
+  if (i < j) v = zmul(zconj(ph), P[i + (size_t)j * ldp]);
+  else if (i == j) v = zmk(ad, 0.0);
+  if (R) R[i + (size_t)j * ldr] = v;
+  if (j == 0 && phases) phases[i] = ph;
+}
+
+// rows 0..n-1 of E (rows x cols, packed) scaled by phases
+__global__ void zscale_rows_kernel(int rows, int cols, int n, const zt* __restrict__ ph,
+                                   zt* __restrict__ E) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int i = (int)(e % rows);
+  if (i < n) E[e] = zmul(ph[i], E[e]);
+}
+
+// Workspace of one complex QR of an m x n matrix (m >= n).
+struct ZQR {
+  zt* V;        // m x n explicit reflectors (column block p holds rows p*ZNB.. meaningful)
+  zt* T;        // ZNB x n: T of each panel
+  double* tau;  // n
+  zt* phases;   // n
+  zt* W1;       // ZNB x n
+  zt* W2;       // ZNB x n
+  zt* gram;     // ceil(m / 64) x 1024
+  int m, n;
+};
+
+// Householder QR of P (m x n, ld ldp) in place; R (phase-fixed) to R if given.
+cudaError_t zgeqrf(cudaStream_t s, int m, int n, zt* P, int ldp, const ZQR& q, zt* R, int ldr) {
+  const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0), mone = zmk(-1.0, 0.0);
+  for (int j0 = 0; j0 < n; j0 += ZNB) {
+    const int jb = std::min(ZNB, n - j0);
+    const int mm = m - j0;
+    zt* Pp = P + j0 + (size_t)j0 * ldp;
+    note_launches(1);
+    zpanel_kernel<<<1, ZP_THREADS, 0, s>>>(mm, jb, Pp, ldp, q.tau + j0);
+    zt* Vp = q.V + j0 + (size_t)j0 * m;
+    note_launches(1);
+    zextract_v_kernel<<<nblocks((long long)mm * jb, 256), 256, 0, s>>>(mm, jb, Pp, ldp, Vp, m);
+    const int nch = nblocks(mm, 64);
+    note_launches(1);
+    zgram_kernel<<<nch, 1024, 0, s>>>(mm, jb, Vp, m, q.gram);
+    zt* Tp = q.T + (size_t)j0 * ZNB;
+    note_launches(1);
+    zlarft_kernel<<<1, 1024, 0, s>>>(nch, jb, q.gram, q.tau + j0, Tp);
+    const int nc = n - j0 - jb;
+    if (nc > 0) {
+      zt* C = P + j0 + (size_t)(j0 + jb) * ldp;
+      cudaError_t e;
+      if ((e = zgemm(s, true, false, jb, nc, mm, one, Vp, m, C, ldp, zero, q.W1, ZNB)) != cudaSuccess) return e;
+      if ((e = zgemm(s, true, false, jb, nc, jb, one, Tp, ZNB, q.W1, ZNB, zero, q.W2, ZNB)) != cudaSuccess) return e;
+      if ((e = zgemm(s, false, false, mm, nc, jb, mone, Vp, m, q.W2, ZNB, one, C, ldp)) != cudaSuccess) return e;
+    }
+  }
+  note_launches(1);
+  zr_extract_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, P, ldp, R, ldr, q.phases);
+  return cudaGetLastError();
+}
+
+// E <- Q E for the Q of the last zgeqrf (E is m x c, packed); phase_fix
+// applies the diagonal unitary first (needed when E touches the first n rows).
+cudaError_t zapply_q(cudaStream_t s, const ZQR& q, zt* E, int c, bool phase_fix) {
+  const int m = q.m, n = q.n;
+  const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0), mone = zmk(-1.0, 0.0);
+  if (phase_fix) {
+    note_launches(1);
+    zscale_rows_kernel<<<nblocks((long long)m * c, 256), 256, 0, s>>>(m, c, n, q.phases, E);
+  }
+  const int np = nblocks(n, ZNB);
+  for (int p = np - 1; p >= 0; --p) {
+    const int j0 = p * ZNB, jb = std::min(ZNB, n - j0), mm = m - j0;
+    const zt* Vp = q.V + j0 + (size_t)j0 * m;
+    const zt* Tp = q.T + (size_t)j0 * ZNB;
+    zt* Ep = E + j0;
+    cudaError_t e;
+    if ((e = zgemm(s, true, false, jb, c, mm, one, Vp, m, Ep, m, zero, q.W1, ZNB)) != cudaSuccess) return e;
+    if ((e = zgemm(s, false, false, jb, c, jb, one, Tp, ZNB, q.W1, ZNB, zero, q.W2, ZNB)) != cudaSuccess) return e;
+    if ((e = zgemm(s, false, false, mm, c, jb, mone, Vp, m, q.W2, ZNB, one, Ep, m)) != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ complex Schur leaves
+struct ZLeafDesc {
+  int m;
+  const zt* A;   // m x m, ld lda
+  int lda;
+  zt* T;         // m x m, ld m
+  zt* Z;         // m x m, ld m
+  int* status;   // 0 ok, 1 iteration budget spent
+};
+
+__device__ void zleaf_givens(zt a, zt b, zt* G) {
+  const double rho = sqrt(a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y);
+  if (rho == 0.0) {
+    G[0] = zmk(1.0, 0.0); G[1] = zmk(0.0, 0.0); G[2] = zmk(0.0, 0.0); G[3] = zmk(1.0, 0.0);
+    return;
+  }
+  // G = [[conj a, conj b], [-b, a]] / rho, row-major G[0] G[1] / G[2] G[3]
+  G[0] = zmk(a.x / rho, -a.y / rho);
+  G[1] = zmk(b.x / rho, -b.y / rho);
+  G[2] = zmk(-b.x / rho, -b.y / rho);
+  G[3] = zmk(a.x / rho, a.y / rho);
+}
+
+// H <- G_k H G_k^H on indices (k, k+1), Z <- Z G_k^H (all threads take part).
+__device__ void zleaf_rotate(int m, zt (*H)[ZLEAF_MAX + 1], zt (*Z)[ZLEAF_MAX + 1], int k,
+                             const zt* G) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    const zt h0 = H[k][c], h1 = H[k + 1][c];
+    H[k][c] = zfma(G[0], h0, zmul(G[1], h1));
+    H[k + 1][c] = zfma(G[2], h0, zmul(G[3], h1));
+  }
+  __syncthreads();
+  // right multiplication by G^H: [x0, x1] G^H = [x0 conj(G0) + x1 conj(G1), x0 conj(G2) + x1 conj(G3)]
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    const zt h0 = H[r][k], h1 = H[r][k + 1];
+    H[r][k] = zadd(zmul(h0, zconj(G[0])), zmul(h1, zconj(G[1])));
+    H[r][k + 1] = zadd(zmul(h0, zconj(G[2])), zmul(h1, zconj(G[3])));
+    const zt z0 = Z[r][k], z1 = Z[r][k + 1];
+    Z[r][k] = zadd(zmul(z0, zconj(G[0])), zmul(z1, zconj(G[1])));
+    Z[r][k + 1] = zadd(zmul(z0, zconj(G[2])), zmul(z1, zconj(G[3])));
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __restrict__ desc) {
+  extern __shared__ zt zsm[];
+  zt (*H)[ZLEAF_MAX + 1] = reinterpret_cast<zt (*)[ZLEAF_MAX + 1]>(zsm);
+  zt (*Z)[ZLEAF_MAX + 1] = reinterpret_cast<zt (*)[ZLEAF_MAX + 1]>(zsm + ZLEAF_MAX * (ZLEAF_MAX + 1));
+  __shared__ zt u[ZLEAF_MAX];
+  __shared__ zt dots[ZLEAF_MAX];
+  __shared__ zt G[4];
+  __shared__ double s_tau;
+  __shared__ int s_lo, s_hi, s_act;
+  const ZLeafDesc d = desc[blockIdx.x];
+  const int m = d.m;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    H[i][j] = d.A[i + (size_t)j * d.lda];
+    Z[i][j] = zmk(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  // Householder reduction to Hessenberg form (the reflector convention of the QR)
+  for (int k = 0; k + 2 < m; ++k) {
+    if (tid == 0) {
+      double ss = 0.0;
+      for (int r = k + 1; r < m; ++r) ss += H[r][k].x * H[r][k].x + H[r][k].y * H[r][k].y;
+      const double nrm = sqrt(ss);
+      const zt x0 = H[k + 1][k];
+      const double a0 = zabs(x0);
+      if (nrm == 0.0) {
+        s_tau = 0.0;
+      } else {
+        const zt ph = a0 > 0.0 ? zmk(x0.x / a0, x0.y / a0) : zmk(1.0, 0.0);
+        const double mag = a0 + nrm;
+        const zt iv = zmk(ph.x / mag, -ph.y / mag);
+        s_tau = mag / nrm;
+        u[k + 1] = zmk(1.0, 0.0);
+        for (int r = k + 2; r < m; ++r) u[r] = zmul(H[r][k], iv);
+      }
+    }
+    __syncthreads();
+    const double tk = s_tau;
+    if (tk == 0.0) continue;
+    // left: H(k+1:, :) -= tau u (u^H H(k+1:, :))
+    for (int c = tid; c < m; c += blockDim.x) {
+      zt acc = zmk(0.0, 0.0);
+      for (int r = k + 1; r < m; ++r) acc = zcfma(u[r], H[r][c], acc);
+      dots[c] = zscale(tk, acc);
+    }
+    __syncthreads();
+    for (int e = tid; e < (m - k - 1) * m; e += blockDim.x) {
+      const int r = k + 1 + e % (m - k - 1), c = e / (m - k - 1);
+      H[r][c] = zsub(H[r][c], zmul(u[r], dots[c]));
+    }
+    __syncthreads();
+    // right: H(:, k+1:) -= tau (H(:, k+1:) u) u^H, same for Z
+    for (int r = tid; r < m; r += blockDim.x) {
+      zt ah = zmk(0.0, 0.0), az = zmk(0.0, 0.0);
+      for (int c = k + 1; c < m; ++c) {
+        ah = zfma(H[r][c], u[c], ah);
+        az = zfma(Z[r][c], u[c], az);
+      }
+      ah = zscale(tk, ah);
+      az = zscale(tk, az);
+      for (int c = k + 1; c < m; ++c) {
+        H[r][c] = zsub(H[r][c], zmul(ah, zconj(u[c])));
+        Z[r][c] = zsub(Z[r][c], zmul(az, zconj(u[c])));
+      }
+    }
+    __syncthreads();
+    for (int r = k + 2 + tid; r < m; r += blockDim.x) H[r][k] = zmk(0.0, 0.0);
+    __syncthreads();
+  }
+  // single-shift QR with deflation, Wilkinson and exceptional shifts
+  int hi = m - 1, its = 0, budget = 40 * max(m, 1);
+  int ok = 1;
+  while (hi > 0) {
+    if (tid == 0) {
+      int lo = hi;
+      while (lo > 0) {
+        double scale = zabs(H[lo - 1][lo - 1]) + zabs(H[lo][lo]);
+        if (scale == 0.0) {
+          scale = 0.0;
+          for (int a = lo - 1; a <= hi; ++a)
+            for (int b = lo - 1; b <= hi; ++b) scale += zabs(H[a][b]);
+        }
+        if (zabs(H[lo][lo - 1]) <= 0x1p-53 * scale) {
+          H[lo][lo - 1] = zmk(0.0, 0.0);
+          break;
+        }
+        --lo;
+      }
+      s_lo = lo;
+      s_act = 0;
+      if (lo == hi) {
+        s_hi = hi - 1;
+      } else {
+        s_hi = hi;
+        s_act = 1;
+        ++its;
+        --budget;
+        zt mu;
+        if (its % 10 == 0) {
+          mu = zadd(H[hi][hi], zmk(0.75 * zabs(H[hi][hi - 1]), 0.0));
+        } else {
+          const zt a = H[hi - 1][hi - 1], b = H[hi - 1][hi], c = H[hi][hi - 1], dd = H[hi][hi];
+          const zt tr2 = zscale(0.5, zadd(a, dd));
+          const zt hd = zscale(0.5, zsub(a, dd));
+          const zt disc2 = zadd(zmul(hd, hd), zmul(b, c));
+          // principal complex square root
+          const double r = zabs(disc2);
+          double sr = sqrt(0.5 * (r + disc2.x));
+          double si = sqrt(0.5 * fmax(r - disc2.x, 0.0));
+          if (disc2.y < 0.0) si = -si;
+          const zt disc = zmk(sr, si);
+          const zt l1 = zadd(tr2, disc), l2 = zsub(tr2, disc);
+          mu = zabs(zsub(l1, dd)) <= zabs(zsub(l2, dd)) ? l1 : l2;
+        }
+        zleaf_givens(zsub(H[lo][lo], mu), H[lo + 1][lo], G);
+      }
+      if (budget < 0) s_act = 2;
+    }
+    __syncthreads();
+    const int act = s_act, lo = s_lo;
+    if (act == 2) {
+      ok = 0;
+      break;
+    }
+    if (act == 0) {
+      hi = s_hi;
+      if (tid == 0) its = 0;
+      __syncthreads();
+      continue;
+    }
+    zleaf_rotate(m, H, Z, lo, G);
+    for (int k = lo + 1; k < hi; ++k) {
+      if (tid == 0) zleaf_givens(H[k][k - 1], H[k + 1][k - 1], G);
+      __syncthreads();
+      zleaf_rotate(m, H, Z, k, G);
+      if (tid == 0) H[k + 1][k - 1] = zmk(0.0, 0.0);
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    d.T[i + (size_t)j * m] = i <= j ? H[i][j] : zmk(0.0, 0.0);
+    d.Z[i + (size_t)j * m] = Z[i][j];
+  }
+  if (tid == 0) *d.status = ok ? 0 : 1;
+}
+
+// trace of A (n x n): one CTA, fixed summation order
+__global__ void ztrace_kernel(int n, const zt* __restrict__ A, int lda, zt* __restrict__ out) {
+  __shared__ zt red[256];
+  zt acc = zmk(0.0, 0.0);
+  for (int i = threadIdx.x; i < n; i += 256) acc = zadd(acc, A[i + (size_t)i * lda]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    zt t = zmk(0.0, 0.0);
+    for (int i = 0; i < 256; ++i) t = zadd(t, red[i]);
+    *out = t;
+  }
+}
+
+// U (rows x cols, ld ldu) = identity
+__global__ void zident_ld_kernel(int rows, int cols, zt* __restrict__ U, int ldu) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int i = (int)(e % rows), j = (int)(e / rows);
+  U[i + (size_t)j * ldu] = zmk(i == j ? 1.0 : 0.0, 0.0);
+}
+
+// ------------------------------------------------------------------ geometry (host)
+struct HalfPlane {
+  double wr, wi, t;   // {z : Re(conj(w) z) >= t}
+};
+
+struct Region {
+  double cr = 0.0, ci = 0.0, R = 0.0;
+  std::vector<HalfPlane> hp;
+  bool contains(double zr, double zi, double slack = 1e-12) const {
+    const double tol = slack * std::max({R, std::hypot(cr, ci), 1e-300});
+    if (std::hypot(zr - cr, zi - ci) > R + tol) return false;
+    for (const HalfPlane& h : hp)
+      if (h.wr * zr + h.wi * zi < h.t - tol) return false;
+    return true;
+  }
+};
+
+struct Pt {
+  double x, y;
+};
+
+void line_circle(const Region& g, const HalfPlane& h, std::vector<Pt>& out) {
+  const double d = h.t - (h.wr * g.cr + h.wi * g.ci);
+  if (std::fabs(d) > g.R) return;
+  const double hh = std::sqrt(std::max(g.R * g.R - d * d, 0.0));
+  const double fx = g.cr + h.wr * d, fy = g.ci + h.wi * d;
+  // i w = (-wi, wr)
+  out.push_back({fx - h.wi * hh, fy + h.wr * hh});
+  out.push_back({fx + h.wi * hh, fy - h.wr * hh});
+}
+
+bool line_line(const HalfPlane& a, const HalfPlane& b, Pt* p) {
+  const double det = a.wr * b.wi - a.wi * b.wr;
+  if (std::fabs(det) < 1e-14) return false;
+  p->x = (a.t * b.wi - a.wi * b.t) / det;
+  p->y = (a.wr * b.t - a.t * b.wr) / det;
+  return true;
+}
+
+bool circle3(Pt p, Pt q, Pt r, Pt* m, double* rad) {
+  const double d = 2.0 * (p.x * (q.y - r.y) + q.x * (r.y - p.y) + r.x * (p.y - q.y));
+  if (std::fabs(d) < 1e-300) return false;
+  const double pp = p.x * p.x + p.y * p.y, qq = q.x * q.x + q.y * q.y, rr = r.x * r.x + r.y * r.y;
+  m->x = (pp * (q.y - r.y) + qq * (r.y - p.y) + rr * (p.y - q.y)) / d;
+  m->y = (pp * (r.x - q.x) + qq * (p.x - r.x) + rr * (q.x - p.x)) / d;
+  *rad = std::hypot(p.x - m->x, p.y - m->y);
+  return true;
+}
+
+// Smallest circle through a few points: every pair as a diameter and every
+// triple's circumcircle, the smallest that holds all points.
+bool min_circle(const std::vector<Pt>& pts, Pt* m, double* rad) {
+  if (pts.empty()) return false;
+  if (pts.size() == 1) {
+    *m = pts[0];
+    *rad = 0.0;
+    return true;
+  }
+  bool have = false;
+  auto consider = [&](Pt c, double r) {
+    const double tol = 1e-12 * std::max(r, 1e-300);
+    for (const Pt& p : pts)
+      if (std::hypot(p.x - c.x, p.y - c.y) > r + tol) return;
+    if (!have || r < *rad) {
+      have = true;
+      *m = c;
+      *rad = r;
+    }
+  };
+  const size_t np = pts.size();
+  for (size_t i = 0; i < np; ++i)
+    for (size_t j = i + 1; j < np; ++j) {
+      consider({0.5 * (pts[i].x + pts[j].x), 0.5 * (pts[i].y + pts[j].y)},
+               0.5 * std::hypot(pts[i].x - pts[j].x, pts[i].y - pts[j].y));
+      for (size_t k = j + 1; k < np; ++k) {
+        Pt c;
+        double r;
+        if (circle3(pts[i], pts[j], pts[k], &c, &r)) consider(c, r);
+      }
+    }
+  return have;
+}
+
+// Circle holding the region: the smallest circle through its corners when it
+// also holds the boundary arc (the point of the circle opposite its centre,
+// if that point is in the region); otherwise the disk itself.
+void enclosing_circle(const Region& g, double* mr, double* mi, double* rad) {
+  *mr = g.cr;
+  *mi = g.ci;
+  *rad = g.R;
+  if (g.hp.empty()) return;
+  std::vector<Pt> corners, tmp;
+  for (size_t i = 0; i < g.hp.size(); ++i) {
+    tmp.clear();
+    line_circle(g, g.hp[i], tmp);
+    for (const Pt& p : tmp)
+      if (g.contains(p.x, p.y)) corners.push_back(p);
+    for (size_t j = i + 1; j < g.hp.size(); ++j) {
+      Pt p;
+      if (line_line(g.hp[i], g.hp[j], &p) && g.contains(p.x, p.y)) corners.push_back(p);
+    }
+  }
+  Pt m;
+  double r;
+  if (!min_circle(corners, &m, &r)) return;
+  if (r >= g.R || (m.x == g.cr && m.y == g.ci)) return;
+  const double dx = m.x - g.cr, dy = m.y - g.ci, dn = std::hypot(dx, dy);
+  const double fx = g.cr - g.R * dx / dn, fy = g.ci - g.R * dy / dn;
+  if (g.contains(fx, fy) && std::hypot(fx - m.x, fy - m.y) > r * (1.0 + 1e-12)) return;
+  *mr = m.x;
+  *mi = m.y;
+  *rad = r;
+}
+
+// The attempt's line: angle 2 pi u2 (or perpendicular to `perp`), offset R (u1 - 1/2).
+HalfPlane draw_line(const Region& g, uint64_t seed, uint64_t node, int attempt, bool has_perp,
+                    double pr, double pi_) {
+  double u1, u2;
+  philox_pair_host(seed, PURPOSE_LINE, node, attempt, &u1, &u2);
+  HalfPlane h;
+  if (has_perp) {
+    h.wr = -pi_;   // i w
+    h.wi = pr;
+  } else {
+    const double th = 2.0 * 3.14159265358979323846 * u2;
+    h.wr = std::cos(th);
+    h.wi = std::sin(th);
+  }
+  const double a = g.R * (u1 - 0.5);
+  h.t = a + (h.wr * g.cr + h.wi * g.ci);
+  return h;
+}
+
+// ------------------------------------------------------------------ driver (host)
+struct ZFail {
+  int code;
+};
+
+struct CDriver {
+  cudaStream_t s;
+  std::string* err;
+  std::vector<void*> owned;    // stream-ordered allocations freed at the end
+
+  void check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+      *err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+      throw ZFail{EIG_ERR_CUDA};
+    }
+  }
+  template <class T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 256), s) != cudaSuccess) {
+      cudaGetLastError();
+      *err = "complex-plane workspace allocation failed";
+      throw ZFail{EIG_ERR_NOMEM};
+    }
+    owned.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void release(void* p) {
+    for (size_t i = 0; i < owned.size(); ++i)
+      if (owned[i] == p) {
+        cudaFreeAsync(p, s);
+        owned.erase(owned.begin() + (long)i);
+        return;
+      }
+  }
+  ~CDriver() {
+    cudaStreamSynchronize(s);
+    for (void* p : owned) cudaFreeAsync(p, s);
+    cudaStreamSynchronize(s);
+  }
+  void sync() { check(cudaStreamSynchronize(s), "stream synchronize"); }
+};
+
+// Buffers of one divide step, sized for nodes of up to `cap` rows.
+struct StepBufs {
+  int cap = 0;
+  zt *A0, *B0, *A1, *B1, *W, *E, *Ra, *Rb;
+  zt *Vh, *X, *U, *Ur, *S, *Z, *Q, *AQ, *Ahat, *R1, *R2, *tmp;
+  double *Gre, *Gim, *absA, *colpart, *scores, *col1, *col2;
+  ZQR q;   // V (2 cap x cap), T, tau, phases, W1, W2, gram
+};
+
+void make_bufs(CDriver& D, StepBufs& b, int cap) {
+  const size_t c2 = (size_t)cap * cap;
+  b.cap = cap;
+  b.A0 = D.alloc<zt>(c2); b.B0 = D.alloc<zt>(c2); b.A1 = D.alloc<zt>(c2); b.B1 = D.alloc<zt>(c2);
+  b.W = D.alloc<zt>(2 * c2); b.E = D.alloc<zt>(2 * c2);
+  b.Ra = D.alloc<zt>(c2); b.Rb = D.alloc<zt>(c2);
+  b.Vh = D.alloc<zt>(c2); b.X = D.alloc<zt>(c2); b.U = D.alloc<zt>(c2); b.Ur = D.alloc<zt>(c2);
+  b.S = D.alloc<zt>(c2); b.Z = D.alloc<zt>(c2); b.Q = D.alloc<zt>(c2); b.AQ = D.alloc<zt>(c2);
+  b.Ahat = D.alloc<zt>(c2); b.R1 = D.alloc<zt>(c2); b.R2 = D.alloc<zt>(c2);
+  b.tmp = D.alloc<zt>(c2);
+  b.Gre = D.alloc<double>(c2); b.Gim = D.alloc<double>(c2); b.absA = D.alloc<double>(c2);
+  const int nrb = (cap + 31) / 32;
+  b.colpart = D.alloc<double>((size_t)(nrb + 1) * cap + 8);
+  b.scores = D.alloc<double>(cap + 1);
+  b.col1 = D.alloc<double>(cap + 1);
+  b.col2 = D.alloc<double>(cap + 1);
+  b.q.V = D.alloc<zt>(2 * c2);
+  b.q.T = D.alloc<zt>((size_t)ZNB * cap);
+  b.q.tau = D.alloc<double>(cap);
+  b.q.phases = D.alloc<zt>(cap);
+  b.q.W1 = D.alloc<zt>((size_t)ZNB * cap);
+  b.q.W2 = D.alloc<zt>((size_t)ZNB * cap);
+  b.q.gram = D.alloc<zt>((size_t)nblocks(2 * cap, 64) * 1024);
+}
+
+ZQR qr_view(const StepBufs& b, int m, int n) {
+  ZQR q = b.q;
+  q.m = m;
+  q.n = n;
+  return q;
+}
+
+// ||A||_1 of an m x m packed matrix (host max of the column sums)
+double host_norm1(CDriver& D, StepBufs& b, int m, const zt* A, int lda, std::vector<double>& h) {
+  note_launches(1);
+  zcolabs_kernel<<<m, 256, 0, D.s>>>(m, m, A, lda, zmk(0.0, 0.0), b.col1);
+  h.resize(m);
+  D.check(cudaMemcpyAsync(h.data(), b.col1, sizeof(double) * m, cudaMemcpyDeviceToHost, D.s), "norm1 copy");
+  D.sync();
+  double mx = 0.0;
+  for (double v : h) mx = std::max(mx, v);
+  return mx;
+}
+
+// Gershgorin disk of A (m x m, ld lda) about c = tr(A)/m
+Region gershgorin_disk(CDriver& D, StepBufs& b, int m, const zt* A, int lda) {
+  note_launches(1);
+  ztrace_kernel<<<1, 256, 0, D.s>>>(m, A, lda, reinterpret_cast<zt*>(b.col2));
+  double tr[2];
+  D.check(cudaMemcpyAsync(tr, b.col2, sizeof(double) * 2, cudaMemcpyDeviceToHost, D.s), "trace copy");
+  D.sync();
+  const zt c = zmk(tr[0] / m, tr[1] / m);
+  note_launches(2);
+  zcolabs_kernel<<<m, 256, 0, D.s>>>(m, m, A, lda, c, b.col1);
+  zrowabs_kernel<<<nblocks(m, 128), 128, 0, D.s>>>(m, A, lda, c, b.col2);
+  std::vector<double> h1(m), h2(m);
+  D.check(cudaMemcpyAsync(h1.data(), b.col1, sizeof(double) * m, cudaMemcpyDeviceToHost, D.s), "gersh copy");
+  D.check(cudaMemcpyAsync(h2.data(), b.col2, sizeof(double) * m, cudaMemcpyDeviceToHost, D.s), "gersh copy");
+  D.sync();
+  double cm = 0.0, rm = 0.0;
+  for (int i = 0; i < m; ++i) {
+    cm = std::max(cm, h1[i]);
+    rm = std::max(rm, h2[i]);
+  }
+  Region g;
+  g.cr = c.x;
+  g.ci = c.y;
+  g.R = std::min(rm, cm);
+  return g;
+}
+
+struct CIrs {
+  int iters;
+  bool converged;
+  const zt* Ap;
+  const zt* Bp;
+};
+
+// Algorithm 3 over C on (A_0, B_0) already in b.A0, b.B0 (m x m packed).
+CIrs cirs(CDriver& D, StepBufs& b, int m, double tau, int maxit) {
+  const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
+  zt *Aj = b.A0, *Bj = b.B0, *An = b.A1, *Bn = b.B1;
+  zt *Rc = b.Ra, *Rp = b.Rb;
+  const ZQR q = qr_view(b, 2 * m, m);
+  bool have_prev = false;
+  std::vector<double> h1(m), h2(m);
+  int j = 0;
+  while (true) {
+    note_launches(1);
+    zstack_kernel<<<nblocks((long long)m * m, 256), 256, 0, D.s>>>(m, Aj, Bj, b.W);
+    D.check(zgeqrf(D.s, 2 * m, m, b.W, 2 * m, q, Rc, m), "IRS QR");
+    D.check(zident(D.s, 2 * m, m, m, b.E), "IRS complement");
+    D.check(zapply_q(D.s, q, b.E, m, false), "IRS complement");
+    D.check(zgemm(D.s, true, false, m, m, m, one, b.E, 2 * m, Aj, m, zero, An, m), "IRS A");
+    D.check(zgemm(D.s, true, false, m, m, m, one, b.E + m, 2 * m, Bj, m, zero, Bn, m), "IRS B");
+    if (have_prev) {
+      note_launches(2);
+      zcoldiff_kernel<<<m, 256, 0, D.s>>>(m, Rc, Rp, b.col1);
+      zcolabs_kernel<<<m, 256, 0, D.s>>>(m, m, Rp, m, zmk(0.0, 0.0), b.col2);
+      D.check(cudaMemcpyAsync(h1.data(), b.col1, sizeof(double) * m, cudaMemcpyDeviceToHost, D.s), "ratio copy");
+      D.check(cudaMemcpyAsync(h2.data(), b.col2, sizeof(double) * m, cudaMemcpyDeviceToHost, D.s), "ratio copy");
+      D.sync();
+      double num = 0.0, den = 0.0;
+      for (int i = 0; i < m; ++i) {
+        num = std::max(num, h1[i]);
+        den = std::max(den, h2[i]);
+      }
+      const double ratio = den > 0.0 ? num / den : (num == 0.0 ? 0.0 : INFINITY);
+      if (ratio <= tau) return {j + 1, true, An, Bn};
+    }
+    std::swap(Rc, Rp);
+    have_prev = true;
+    std::swap(Aj, An);
+    std::swap(Bj, Bn);
+    ++j;
+    if (j > maxit) return {j, false, Aj, Bj};
+  }
+}
+
+// Explicit unitary factor of the last zgeqrf (m x m) into Qout.
+void explicit_q(CDriver& D, const ZQR& q, zt* Qout) {
+  D.check(zident(D.s, q.m, q.n, 0, Qout), "explicit Q");
+  D.check(zapply_q(D.s, q, Qout, q.n, true), "explicit Q");
+}
+
+struct CStepOut {
+  bool accepted = false;
+  bool converged = false;
+  int k = 0, rank = 0, iters = 0, draw = 0;
+  double e = INFINITY;
+};
+
+// One step on the line (w, t) with scale sc for the node matrix A (m x m
+// packed).  The splitter lands in b.Q and A^ in b.Ahat.
+CStepOut line_step(CDriver& D, StepBufs& b, int m, const zt* A, const HalfPlane& L, double sc,
+                   uint64_t seed, uint64_t node, int attempt, double tau, int maxit,
+                   double split_tol, int v_draws) {
+  const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
+  const size_t mm = (size_t)m * m;
+  CStepOut out;
+  const zt s0 = zmk(L.wr * (L.t - sc), L.wi * (L.t - sc));
+  const zt s1 = zmk(L.wr * (L.t + sc), L.wi * (L.t + sc));
+  note_launches(1);
+  zline_map_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>(m, A, m, s0, s1, b.A0, b.B0);
+  const CIrs irs = cirs(D, b, m, tau, maxit);
+  out.iters = irs.iters;
+  out.converged = irs.converged;
+  std::vector<double> hv;
+  const double normA = host_norm1(D, b, m, A, m, hv);
+  const ZQR q = qr_view(b, m, m);
+  std::vector<double> hs(std::max(m - 1, 1)), d1(2 * (size_t)m), d2(2 * (size_t)m);
+  const int draws = std::max(1, v_draws);
+  for (int draw = 0; draw < draws; ++draw) {
+    const int code = ((attempt & 0x3F) << 2) | (draw & 3);
+    // Haar unitary V from the complex Ginibre draw
+    D.check(gaussian(D.s, m, m, seed, PURPOSE_HAAR_RE, node, code, b.Gre, m), "Haar draw");
+    D.check(gaussian(D.s, m, m, seed, PURPOSE_HAAR_IM, node, code, b.Gim, m), "Haar draw");
+    note_launches(1);
+    zinterleave_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>((long long)mm, b.Gre, b.Gim, b.X);
+    D.check(zgeqrf(D.s, m, m, b.X, m, q, nullptr, m), "Haar QR");
+    explicit_q(D, q, b.Vh);
+    // RURV(A_p): A_p V^H = U R2
+    D.check(zgemm(D.s, false, true, m, m, m, one, irs.Ap, m, b.Vh, m, zero, b.X, m), "A_p V^H");
+    D.check(zgeqrf(D.s, m, m, b.X, m, q, b.R2, m), "RURV QR");
+    explicit_q(D, q, b.U);
+    // RQ of U^H (A_p + B_p) through the QR of (A_p + B_p)^H U J
+    note_launches(2);
+    zadd_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>((long long)mm, irs.Ap, irs.Bp, b.S);
+    zrevcols_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>(m, m, b.U, b.Ur);
+    D.check(zgemm(D.s, true, false, m, m, m, one, b.S, m, b.Ur, m, zero, b.Z, m), "(A_p+B_p)^H U J");
+    D.check(zgeqrf(D.s, m, m, b.Z, m, q, b.R1, m), "RQ via QR");
+    explicit_q(D, q, b.Ur);
+    note_launches(1);
+    zrevcols_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>(m, m, b.Ur, b.Q);
+    // similarity and split test
+    D.check(zgemm(D.s, false, false, m, m, m, one, A, m, b.Q, m, zero, b.AQ, m), "A Q");
+    D.check(zgemm(D.s, true, false, m, m, m, one, b.Q, m, b.AQ, m, zero, b.Ahat, m), "Q^H A Q");
+    note_launches(1);
+    zabs_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>((long long)mm, b.Ahat, b.absA);
+    if (m >= 2)
+      D.check(split_scores(D.s, m, b.absA, m, normA > 0.0 ? 1.0 / normA : 1.0, b.colpart, b.scores,
+                           false), "split scores");
+    D.check(cudaMemcpy2DAsync(d1.data(), 2 * sizeof(double), b.R1, (m + 1) * sizeof(zt),
+                              2 * sizeof(double), m, cudaMemcpyDeviceToHost, D.s), "diag copy");
+    D.check(cudaMemcpy2DAsync(d2.data(), 2 * sizeof(double), b.R2, (m + 1) * sizeof(zt),
+                              2 * sizeof(double), m, cudaMemcpyDeviceToHost, D.s), "diag copy");
+    if (m >= 2)
+      D.check(cudaMemcpyAsync(hs.data(), b.scores, sizeof(double) * (m - 1), cudaMemcpyDeviceToHost, D.s),
+              "scores copy");
+    D.sync();
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i) scale = std::max(scale, std::hypot(d1[2 * i], d1[2 * i + 1]));
+    int rank = 0;
+    if (scale > 0.0)
+      for (int i = 0; i < m; ++i)
+        if (std::hypot(d2[2 * i], d2[2 * i + 1]) > 1e-8 * scale) ++rank;
+    out.rank = rank;
+    out.draw = draw;
+    if (m >= 2) {
+      out.k = choose_k_host(hs.data(), m);
+      out.e = hs[out.k - 1];
+    } else {
+      out.k = 0;
+      out.e = 0.0;
+    }
+    out.accepted = irs.converged && out.k > 0 && out.k < m && out.e <= split_tol;
+    if (out.accepted || !irs.converged || rank == 0 || rank == m) break;
+  }
+  return out;
+}
+
+struct CNode {
+  int off, m;
+  zt* A;   // m x m packed, owned
+  Region reg;
+  uint64_t id;
+  int depth;
+};
+
+struct CLeaf {
+  int off, m;
+  zt* A;
+};
+
+}  // namespace
+
+// Complex Schur form A = U T U^H by the complex-plane recursion (Sec. 3.3).
+int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_, int ldt,
+                 double* dU_, int ldu, double* dw_, const eig_params_t& p, bool enclose,
+                 std::vector<CplaneCluster>* clusters, eig_solve_info_t* info, std::string* err) {
+  const zt* dA = reinterpret_cast<const zt*>(dA_);
+  zt* dT = reinterpret_cast<zt*>(dT_);
+  zt* dU = reinterpret_cast<zt*>(dU_);
+  zt* dw = reinterpret_cast<zt*>(dw_);
+  const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
+  eig_solve_info_t inf;
+  std::memset(&inf, 0, sizeof(inf));
+  int status = EIG_OK;
+  try {
+    CDriver D{s, err, {}};
+    const int leaf = std::max(1, std::min(p.leaf_size > 0 ? p.leaf_size : 64, ZLEAF_MAX));
+    StepBufs b;
+    if (n > leaf) make_bufs(D, b, n);
+    zt* tmpU = D.alloc<zt>((size_t)n * n);
+    note_launches(1);
+    zident_ld_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, n, dU, ldu);
+    zt* root = D.alloc<zt>((size_t)n * n);
+    D.check(zcopy(s, n, n, dA, lda, root, n), "input copy");
+    std::vector<CNode> work;
+    std::vector<CLeaf> leaves;
+    {
+      CNode r{0, n, root, Region(), 1ull, 0};
+      if (n > leaf) r.reg = gershgorin_disk(D, b, n, root, n);
+      work.push_back(r);
+    }
+    while (!work.empty() && status == EIG_OK) {
+      CNode nd = work.back();
+      work.pop_back();
+      inf.nodes += 1;
+      inf.max_depth = std::max(inf.max_depth, nd.depth);
+      if (nd.m <= leaf) {
+        leaves.push_back({nd.off, nd.m, nd.A});
+        continue;
+      }
+      const int m = nd.m;
+      const double tau = p.tau > 0.0 ? p.tau : std::max(1e-14, 4.0 * std::sqrt((double)m) * 0x1p-53);
+      const double stol = p.split_tol > 0.0 ? p.split_tol : std::max(1e-12, 16.0 * m * 0x1p-53);
+      const int maxit = p.maxit;
+      const int max_fail = p.max_fail;
+      int attempt = 0, fails = 0;
+      bool has_perp = false;
+      double pr = 0.0, pi_ = 0.0;
+      Region reg = nd.reg;
+      while (true) {
+        if (!(reg.R > 0.0)) {
+          leaves.push_back({nd.off, m, nd.A});
+          break;
+        }
+        const HalfPlane L = draw_line(reg, p.seed, nd.id, attempt, has_perp, pr, pi_);
+        const CStepOut st = line_step(D, b, m, nd.A, L, reg.R, p.seed, nd.id, attempt, tau, maxit,
+                                      stol, p.v_draws);
+        inf.total_iters += st.iters;
+        if (st.accepted) {
+          const int k = st.k;
+          D.check(zgemm(s, false, false, n, m, m, one, dU + (size_t)nd.off * ldu, ldu, b.Q, m, zero,
+                        tmpU, n), "U update");
+          D.check(zcopy(s, n, m, tmpU, n, dU + (size_t)nd.off * ldu, ldu), "U update");
+          zt* A11 = D.alloc<zt>((size_t)k * k);
+          zt* A22 = D.alloc<zt>((size_t)(m - k) * (m - k));
+          D.check(zcopy(s, k, k, b.Ahat, m, A11, k), "block copy");
+          D.check(zcopy(s, m - k, m - k, b.Ahat + k + (size_t)k * m, m, A22, m - k), "block copy");
+          Region r1 = reg, r2 = reg;
+          r1.hp.push_back(L);
+          r2.hp.push_back({-L.wr, -L.wi, -L.t});
+          Region kids[2];
+          zt* blocks[2] = {A11, A22};
+          const int sizes[2] = {k, m - k};
+          const Region* sides[2] = {&r1, &r2};
+          for (int c = 0; c < 2; ++c) {
+            Region g;
+            if (sizes[c] > leaf) g = gershgorin_disk(D, b, sizes[c], blocks[c], sizes[c]);
+            double er, ei, eR;
+            enclosing_circle(*sides[c], &er, &ei, &eR);
+            if (sizes[c] > leaf && g.R <= eR) {
+              kids[c] = g;
+            } else {
+              kids[c].cr = er;
+              kids[c].ci = ei;
+              kids[c].R = eR;
+            }
+          }
+          inf.splits += 1;
+          work.push_back({nd.off + k, m - k, A22, kids[1], child_node_id(nd.id, 1), nd.depth + 1});
+          work.push_back({nd.off, k, A11, kids[0], child_node_id(nd.id, 0), nd.depth + 1});
+          D.release(nd.A);
+          break;
+        }
+        inf.failed_attempts += 1;
+        if (st.converged && (st.rank == 0 || st.rank == m)) {
+          reg.hp.push_back(st.rank == m ? L : HalfPlane{-L.wr, -L.wi, -L.t});
+          double er, ei, eR;
+          enclosing_circle(reg, &er, &ei, &eR);
+          if (eR <= SHRINK * reg.R) {
+            reg = Region();
+            reg.cr = er; reg.ci = ei; reg.R = eR;
+            has_perp = false;
+          } else if (!has_perp) {
+            has_perp = true;
+            pr = L.wr;
+            pi_ = L.wi;
+          } else {
+            if (eR < reg.R) {
+              reg = Region();
+              reg.cr = er; reg.ci = ei; reg.R = eR;
+            }
+            has_perp = false;
+          }
+        } else {
+          fails += 1;
+          has_perp = false;
+        }
+        attempt += 1;
+        if (fails > max_fail || attempt > 250) {
+          if (enclose) {
+            if (clusters) clusters->push_back({nd.off, m, reg.cr, reg.ci, reg.R, {}});
+            if (clusters)
+              for (const HalfPlane& h : reg.hp) clusters->back().hp.push_back({h.wr, h.wi, h.t});
+            leaves.push_back({nd.off, m, nd.A});
+            break;
+          }
+          status = EIG_NO_SPLIT;
+          break;
+        }
+      }
+    }
+    if (status == EIG_OK) {
+      // leaves: complex Schur per CTA, then U[:, off:off+m] <- U[:, off:off+m] Z_leaf
+      const int nl = (int)leaves.size();
+      inf.leaves = nl;
+      std::vector<ZLeafDesc> hd(nl);
+      std::vector<zt*> Zs(nl);
+      int* dstat = D.alloc<int>(std::max(nl, 1));
+      for (int i = 0; i < nl; ++i) {
+        const int m = leaves[i].m;
+        zt* TZ = D.alloc<zt>(2 * (size_t)m * m);
+        Zs[i] = TZ + (size_t)m * m;
+        hd[i] = {m, leaves[i].A, m, TZ, Zs[i], dstat + i};
+      }
+      ZLeafDesc* dd = D.alloc<ZLeafDesc>(std::max(nl, 1));
+      D.check(cudaMemcpyAsync(dd, hd.data(), sizeof(ZLeafDesc) * nl, cudaMemcpyHostToDevice, s), "leaf descriptors");
+      const int smem = 2 * ZLEAF_MAX * (ZLEAF_MAX + 1) * (int)sizeof(zt);
+      D.check(cudaFuncSetAttribute(zschur_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+              "leaf attribute");
+      if (nl > 0) {
+        note_launches(1);
+        zschur_leaf_kernel<<<nl, 256, smem, s>>>(dd);
+        D.check(cudaGetLastError(), "leaf launch");
+      }
+      for (int i = 0; i < nl; ++i) {
+        const int off = leaves[i].off, m = leaves[i].m;
+        D.check(zgemm(s, false, false, n, m, m, one, dU + (size_t)off * ldu, ldu, Zs[i], m, zero, tmpU, n),
+                "leaf U update");
+        D.check(zcopy(s, n, m, tmpU, n, dU + (size_t)off * ldu, ldu), "leaf U update");
+      }
+      std::vector<int> hst(std::max(nl, 1));
+      if (nl > 0)
+        D.check(cudaMemcpyAsync(hst.data(), dstat, sizeof(int) * nl, cudaMemcpyDeviceToHost, s), "leaf status");
+      // T = triu(U^H A U), w = diag(T)
+      zt* AU = D.alloc<zt>((size_t)n * n);
+      D.check(zgemm(s, false, false, n, n, n, one, dA, lda, dU, ldu, zero, AU, n), "A U");
+      D.check(zgemm(s, true, false, n, n, n, one, dU, ldu, AU, n, zero, tmpU, n), "U^H A U");
+      note_launches(1);
+      ztriu_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, tmpU, n, dT, ldt, dw);
+      D.check(cudaGetLastError(), "triangle");
+      D.sync();
+      for (int i = 0; i < nl; ++i)
+        if (hst[i] != 0) status = EIG_NO_CONVERGENCE;
+    }
+    D.sync();
+  } catch (ZFail f) {
+    status = f.code;
+  }
+  inf.status = status;
+  if (info) *info = inf;
+  return status;
+}
+}  // namespace eigdc
+
+// ------------------------------------------------------------------ host-only C-ABI helpers
+extern "C" int eig_cplane_enclosing_circle(double c_re, double c_im, double R, int nhp,
+                                           const double* w_re, const double* w_im,
+                                           const double* t, double* m_re, double* m_im,
+                                           double* r) {
+  if (nhp < 0 || (nhp > 0 && (!w_re || !w_im || !t)) || !m_re || !m_im || !r || !(R >= 0.0))
+    return EIG_ERR_ARG;
+  eigdc::Region g;
+  g.cr = c_re;
+  g.ci = c_im;
+  g.R = R;
+  for (int i = 0; i < nhp; ++i) g.hp.push_back({w_re[i], w_im[i], t[i]});
+  eigdc::enclosing_circle(g, m_re, m_im, r);
+  return EIG_OK;
+}
+
+extern "C" int eig_cplane_draw_line(uint64_t seed, uint64_t node, int attempt, double c_re,
+                                    double c_im, double R, int perpendicular, double pw_re,
+                                    double pw_im, double* w_re, double* w_im, double* t) {
+  if (!w_re || !w_im || !t || !(R >= 0.0)) return EIG_ERR_ARG;
+  eigdc::Region g;
+  g.cr = c_re;
+  g.ci = c_im;
+  g.R = R;
+  const eigdc::HalfPlane h = eigdc::draw_line(g, seed, node, attempt, perpendicular != 0, pw_re, pw_im);
+  *w_re = h.wr;
+  *w_im = h.wi;
+  *t = h.t;
+  return EIG_OK;
+}

@@ -5,11 +5,25 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
+#include "../../include/eigdc.h"
+
 namespace eigdc {
 
 // Running count of kernel launches made by this library (all launchers add
 // to it); read through eig_kernel_launches().
 void note_launches(unsigned long long k);
+
+// ------------------------------------------------------------- api.cu host helpers
+// (u1, u2) of Philox pair 0 of (purpose, stream, attempt): u1 in (0, 1), u2 in [0, 1).
+void philox_pair_host(uint64_t seed, int purpose, uint64_t stream, int attempt, double* u1,
+                      double* u2);
+// Philox stream id of child `side` (0 or 1) of a recursion node.
+uint64_t child_node_id(uint64_t parent, int side);
+// Block size of the smallest score e[k-1], k = 1..n-1 (ties: closest to n/2, then smaller k).
+int choose_k_host(const double* e, int n);
 
 // ------------------------------------------------------------- linalg.cu
 // C = alpha op(A) op(B) + beta C, column-major FP64.  When splits > 1 the K
@@ -154,5 +168,22 @@ cudaError_t pencil_leaves_phase2(cudaStream_t s, int count, const LeafDesc* d_de
 cudaError_t apply_leaf_vectors(cudaStream_t s, int count, const LeafDesc* d_desc, int n,
                                const double* Uin, int ldu_in, double* Uout, int ldu_out,
                                const double* Z);
+
+// ------------------------------------------------------------- cplane.cu
+// Complex-plane recursion (Sec. 3.3).  Complex arrays are interleaved (re, im)
+// FP64 pairs, column-major, leading dimensions in complex elements.
+struct CplaneHalfPlane {
+  double wr, wi, t;   // {z : Re(conj(w) z) >= t}
+};
+struct CplaneCluster {
+  int off, m;                          // diagonal block of T
+  double cr, ci, R;                    // disk
+  std::vector<CplaneHalfPlane> hp;     // half-planes cutting it
+};
+// A = U T U^H with T upper triangular, w = diag(T).  Returns an EIG_* status;
+// on a negative status *err holds the message.
+int cplane_schur(cudaStream_t s, int n, const double* dA, int lda, double* dT, int ldt,
+                 double* dU, int ldu, double* dw, const eig_params_t& p, bool enclose,
+                 std::vector<CplaneCluster>* clusters, eig_solve_info_t* info, std::string* err);
 
 }  // namespace eigdc

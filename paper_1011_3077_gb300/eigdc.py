@@ -41,7 +41,10 @@ EIG_KIND_PENCIL = 2
 PURPOSE_HAAR = 4
 PURPOSE_SHIFT = 5
 PURPOSE_HAAR_LEFT = 6
+PURPOSE_HAAR_IMAG = 7
+PURPOSE_LINE = 8
 ROOT_NODE = 1
+EIG_MAX_HALFPLANES = 8
 
 
 class Region(ctypes.Structure):
@@ -70,6 +73,20 @@ class SolveInfo(ctypes.Structure):
                 ("max_depth", ctypes.c_int), ("total_iters", ctypes.c_int),
                 ("failed_attempts", ctypes.c_int), ("leaves", ctypes.c_int),
                 ("flops", ctypes.c_double)]
+
+
+class Enclosure(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int), ("size", ctypes.c_int),
+                ("c_re", ctypes.c_double), ("c_im", ctypes.c_double), ("R", ctypes.c_double),
+                ("nhp", ctypes.c_int),
+                ("w_re", ctypes.c_double * EIG_MAX_HALFPLANES),
+                ("w_im", ctypes.c_double * EIG_MAX_HALFPLANES),
+                ("t", ctypes.c_double * EIG_MAX_HALFPLANES)]
+
+    def region(self):
+        """(centre, radius, [(w, t), ...]) with complex centre and normals."""
+        hps = [(complex(self.w_re[i], self.w_im[i]), self.t[i]) for i in range(self.nhp)]
+        return complex(self.c_re, self.c_im), self.R, hps
 
 
 _lib = None
@@ -123,6 +140,14 @@ _SIGNATURES = {
     "eig_gemm_split": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_fp64tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+    "eig_schur_complex": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(Params), _I,
+                               ctypes.POINTER(Enclosure), _I, ctypes.POINTER(_I),
+                               ctypes.POINTER(SolveInfo)]),
+    "eig_cplane_enclosing_circle": (_I, [_D, _D, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                         ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                         ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "eig_cplane_draw_line": (_I, [_U64, _U64, _I, _D, _D, _D, _I, _D, _D, ctypes.POINTER(_D),
+                                  ctypes.POINTER(_D), ctypes.POINTER(_D)]),
 }
 
 EXPORTED = tuple(_SIGNATURES)
@@ -482,3 +507,65 @@ def svd(h, A, params=None):
     dV = torch.zeros((r, n), dtype=torch.float64, device=dA.device)
     rc, info = eig_svd(h, m, n, dA, m, dS, dU, m, dV, n, params)
     return rc, dS.cpu().numpy(), dU.cpu().numpy().T.copy(), dV.cpu().numpy().T.copy(), info
+
+
+# ----------------------------------------------------------------- complex-plane strategy
+
+def to_device_complex(A, device="cuda"):
+    """numpy (rows x cols) -> torch complex128 tensor holding A column-major (interleaved)."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(A, dtype=np.complex128).T)).to(device)
+
+
+def eig_schur_complex(h, n, dA, lda, dT, ldt, dU, ldu, dw, params, enclose=False, enc_cap=16):
+    """Complex Schur form through the C-ABI; returns (rc, info, enclosures)."""
+    info = SolveInfo()
+    enc = (Enclosure * max(enc_cap, 1))()
+    n_enc = ctypes.c_int(0)
+    rc = lib().eig_schur_complex(h.ptr, n, _ptr(dA), lda, _ptr(dT), ldt, _ptr(dU), ldu, _ptr(dw),
+                                 ctypes.byref(params), 1 if enclose else 0, enc, enc_cap,
+                                 ctypes.byref(n_enc), ctypes.byref(info))
+    return rc, info, [enc[i] for i in range(min(n_enc.value, enc_cap))]
+
+
+def schur_complex(h, A, params=None, enclose=False):
+    """(rc, T, U, w, info, enclosures) for a numpy matrix: A = U T U^H (Sec. 3.3)."""
+    import torch
+    n = A.shape[0]
+    params = params or default_params()
+    dA = to_device_complex(A)
+    z = lambda *shape: torch.zeros(shape, dtype=torch.complex128, device=dA.device)
+    dT, dU, dw = z(n, n), z(n, n), z(n)
+    rc, info, enc = eig_schur_complex(h, n, dA, n, dT, n, dU, n, dw, params, enclose)
+    return (rc, dT.cpu().numpy().T.copy(), dU.cpu().numpy().T.copy(), dw.cpu().numpy(), info,
+            enc)
+
+
+def cplane_enclosing_circle(c, R, halfplanes):
+    """Host-only: (centre, radius) of a circle holding {|z - c| <= R} cut by the
+    half-planes Re(conj(w) z) >= t given as [(w, t), ...]."""
+    k = len(halfplanes)
+    arr = ctypes.c_double * max(k, 1)
+    wr = arr(*[complex(w).real for w, _ in halfplanes])
+    wi = arr(*[complex(w).imag for w, _ in halfplanes])
+    tt = arr(*[float(t) for _, t in halfplanes])
+    mr, mi, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().eig_cplane_enclosing_circle(complex(c).real, complex(c).imag, float(R), k, wr, wi,
+                                           tt, ctypes.byref(mr), ctypes.byref(mi),
+                                           ctypes.byref(r))
+    if rc != EIG_OK:
+        raise EigError(rc, "eig_cplane_enclosing_circle: invalid argument")
+    return complex(mr.value, mi.value), r.value
+
+
+def cplane_draw_line(seed, node, attempt, c, R, perpendicular_to=None):
+    """Host-only: the (w, t) of the strategy's line for (seed, node, attempt)."""
+    pw = complex(perpendicular_to) if perpendicular_to is not None else 0j
+    wr, wi, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib().eig_cplane_draw_line(int(seed), int(node), int(attempt), complex(c).real,
+                                    complex(c).imag, float(R),
+                                    0 if perpendicular_to is None else 1, pw.real, pw.imag,
+                                    ctypes.byref(wr), ctypes.byref(wi), ctypes.byref(t))
+    if rc != EIG_OK:
+        raise EigError(rc, "eig_cplane_draw_line: invalid argument")
+    return complex(wr.value, wi.value), t.value

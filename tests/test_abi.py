@@ -60,15 +60,17 @@ def test_struct_layout_matches_c_compiler(built, tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "eigdc.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(eig_params_t),'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(eig_params_t),'
         ' sizeof(eig_region_t), sizeof(eig_step_info_t), sizeof(eig_solve_info_t),'
         ' offsetof(eig_params_t, seed), offsetof(eig_params_t, root_unit_circle),'
-        ' offsetof(eig_solve_info_t, flops)); return 0;}\n')
+        ' offsetof(eig_solve_info_t, flops), sizeof(eig_enclosure_t),'
+        ' offsetof(eig_enclosure_t, nhp), offsetof(eig_enclosure_t, t)); return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(eigdc.Params), ctypes.sizeof(eigdc.Region),
             ctypes.sizeof(eigdc.StepInfo), ctypes.sizeof(eigdc.SolveInfo),
             eigdc.Params.seed.offset, eigdc.Params.root_unit_circle.offset,
-            eigdc.SolveInfo.flops.offset]
+            eigdc.SolveInfo.flops.offset, ctypes.sizeof(eigdc.Enclosure),
+            eigdc.Enclosure.nhp.offset, eigdc.Enclosure.t.offset]
     assert got == want
