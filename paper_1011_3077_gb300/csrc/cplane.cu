@@ -446,7 +446,8 @@ __global__ void __launch_bounds__(1024) zlarft_kernel(int nchunks, int jb, const
     }
     __syncthreads();
   }
-  T[i + ZNB * j] = (i < jb && j < jb) ? Ts[i][j] : zmk(0.0, 0.0);
+  // only the jb columns of this panel exist in the caller's T (ZNB x n)
+  if (j < jb) T[i + ZNB * j] = i < jb ? Ts[i][j] : zmk(0.0, 0.0);
 }
 
 // R (n x n, ld ldr) = D^H triu(P(0:n, 0:n)) with D = diag(phase of P_jj); phases[j] = D_jj.
@@ -597,6 +598,10 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
   const ZLeafDesc d = desc[blockIdx.x];
   const int m = d.m;
   const int tid = threadIdx.x;
+  if (m < 1 || m > ZLEAF_MAX) {   // the shared arrays hold at most ZLEAF_MAX rows
+    if (tid == 0) *d.status = 1;
+    return;
+  }
   for (int e = tid; e < m * m; e += blockDim.x) {
     const int i = e % m, j = e / m;
     H[i][j] = d.A[i + (size_t)j * d.lda];
@@ -957,7 +962,7 @@ void make_bufs(CDriver& D, StepBufs& b, int cap) {
   b.col1 = D.alloc<double>(cap + 1);
   b.col2 = D.alloc<double>(cap + 1);
   b.q.V = D.alloc<zt>(2 * c2);
-  b.q.T = D.alloc<zt>((size_t)ZNB * cap);
+  b.q.T = D.alloc<zt>((size_t)ZNB * (nblocks(cap, ZNB) * ZNB));
   b.q.tau = D.alloc<double>(cap);
   b.q.phases = D.alloc<zt>(cap);
   b.q.W1 = D.alloc<zt>((size_t)ZNB * cap);
@@ -1215,7 +1220,9 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
       Region reg = nd.reg;
       while (true) {
         if (!(reg.R > 0.0)) {
-          leaves.push_back({nd.off, m, nd.A});
+          // every row and column sum of |A - cI| is zero: A = cI is already
+          // triangular (U stays, T = U^H A U below)
+          D.release(nd.A);
           break;
         }
         const HalfPlane L = draw_line(reg, p.seed, nd.id, attempt, has_perp, pr, pi_);
@@ -1284,11 +1291,15 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
         attempt += 1;
         if (fails > max_fail || attempt > 250) {
           if (enclose) {
-            if (clusters) clusters->push_back({nd.off, m, reg.cr, reg.ci, reg.R, {}});
-            if (clusters)
+            if (clusters) {
+              clusters->push_back({nd.off, m, reg.cr, reg.ci, reg.R, {}});
               for (const HalfPlane& h : reg.hp) clusters->back().hp.push_back({h.wr, h.wi, h.t});
-            leaves.push_back({nd.off, m, nd.A});
-            break;
+            }
+            if (m <= ZLEAF_MAX) {
+              leaves.push_back({nd.off, m, nd.A});
+              break;
+            }
+            // the leaf kernel cannot take the cluster: reported, not triangularised
           }
           status = EIG_NO_SPLIT;
           break;

@@ -1,0 +1,135 @@
+"""GPU parity of the complex-plane strategy (Sec. 3.3) through eig_schur_complex.
+
+Same inputs, seeds and Philox counters as the oracle (oracle/cplane.py): the
+recursion takes the same lines, so the split counts agree, the eigenvalues
+agree to the oracle's own accuracy, and the GPU result meets the targets of
+the oracle pins -- T upper triangular, ||U^H U - I|| <= 1e-12,
+||A - U T U^H||_F / ||A||_F <= 1e-13 -- and reports the same cluster
+enclosures for the Jordan example.
+
+These tests have not yet run on a GB300: the module is skipped until the
+first hardware run of the complex path.
+"""
+import numpy as np
+import pytest
+
+from oracle.cplane import schur_complex_plane
+from oracle.solve import STATUS_OK, STATUS_NO_SPLIT
+from paper_1011_3077_gb300 import workloads
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skip(reason="complex path: first hardware run pending")]
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    from paper_1011_3077_gb300 import build, eigdc
+    build.build()
+    h = eigdc.Handle(0)
+    yield eigdc, h, torch
+    torch.cuda.synchronize()
+    h.close()
+
+
+def _crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _prescribed(lam, rng, coupling=0.25):
+    n = len(lam)
+    S = np.eye(n) + coupling * _crandn(rng, n, n) / np.sqrt(2 * n)
+    return S @ np.diag(lam) @ np.linalg.inv(S)
+
+
+def _match(got, want):
+    got = list(np.asarray(got, dtype=np.complex128))
+    worst = 0.0
+    for z in want:
+        i = int(np.argmin([abs(g - z) for g in got]))
+        worst = max(worst, abs(got[i] - z))
+        got.pop(i)
+    return worst
+
+
+def _check(A, T, U, tol=1e-13):
+    n = A.shape[0]
+    assert np.abs(np.tril(T, -1)).max(initial=0.0) == 0.0
+    assert np.abs(U.conj().T @ U - np.eye(n)).max() <= 1e-12
+    assert np.linalg.norm(U @ T @ U.conj().T - A) <= tol * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("n,leaf", [(40, 8), (100, 16), (300, 64)])
+def test_prescribed_complex_spectrum(E, n, leaf):
+    eigdc, h, torch = E
+    rng = np.random.default_rng(71 + n)
+    lam = _crandn(rng, n)
+    A = _prescribed(lam, rng)
+    p = eigdc.default_params(seed=2, leaf_size=leaf)
+    rc, T, U, w, info, _ = eigdc.schur_complex(h, A, p)
+    assert rc == eigdc.EIG_OK and info.splits >= 1
+    _check(A, T, U)
+    assert _match(w, lam) <= 1e-10
+    if n <= 100:
+        To, Uo, wo, io = schur_complex_plane(A, seed=2, leaf_size=leaf)
+        assert io.status == STATUS_OK
+        assert info.splits == io.splits and info.nodes == io.nodes
+        assert _match(w, wo) <= 1e-11
+
+
+def test_eigenvalues_near_the_imaginary_axis(E):
+    eigdc, h, torch = E
+    A = workloads.near_axis(25)
+    p = eigdc.default_params(seed=3, leaf_size=4)
+    rc, T, U, w, info, _ = eigdc.schur_complex(h, A, p)
+    assert rc == eigdc.EIG_OK
+    _check(A, T, U)
+    To, Uo, wo, io = schur_complex_plane(A, seed=3, leaf_size=4)
+    assert info.splits == io.splits
+    assert _match(w, wo) <= 1e-12
+
+
+def test_jordan_cluster_enclosure(E):
+    eigdc, h, torch = E
+    A = workloads.jordan_hard(32)
+    p = eigdc.default_params(seed=1, leaf_size=4)
+    rc, T, U, w, info, enc = eigdc.schur_complex(h, A, p, enclose=True)
+    assert rc == eigdc.EIG_OK
+    _check(A, T, U, 1e-12)
+    To, Uo, wo, io = schur_complex_plane(A, seed=1, leaf_size=4, enclose=True)
+    assert len(enc) == len(io.clusters)
+    for e, (off, m, reg) in zip(enc, io.clusters):
+        assert (e.offset, e.size) == (off, m)
+        c, R, hps = e.region()
+        assert abs(c - reg.c) <= 1e-8 * (1 + abs(reg.c)) and abs(R - reg.R) <= 1e-8 * reg.R
+    cl = [e for e in enc if abs(0.1 - e.region()[0]) <= e.region()[1]]
+    assert len(cl) == 1
+    rc2, _, _, _, info2, _ = eigdc.schur_complex(h, A, p, enclose=False)
+    assert rc2 == eigdc.EIG_NO_SPLIT
+
+
+def test_small_and_degenerate_inputs(E):
+    eigdc, h, torch = E
+    p = eigdc.default_params(seed=0, leaf_size=64)
+    rng = np.random.default_rng(5)
+    A = _crandn(rng, 50, 50)                      # one leaf
+    rc, T, U, w, info, _ = eigdc.schur_complex(h, A, p)
+    assert rc == eigdc.EIG_OK
+    _check(A, T, U)
+    assert _match(w, np.linalg.eigvals(A)) <= 1e-11
+    A1 = np.array([[2.0 - 1.0j]])
+    rc, T, U, w, info, _ = eigdc.schur_complex(h, A1, p)
+    assert rc == eigdc.EIG_OK and abs(w[0] - A1[0, 0]) == 0.0
+    Ac = (0.5 + 0.25j) * np.eye(80)               # Gershgorin radius 0
+    rc, T, U, w, info, _ = eigdc.schur_complex(h, Ac, eigdc.default_params(leaf_size=16))
+    assert rc == eigdc.EIG_OK and np.abs(w - (0.5 + 0.25j)).max() <= 1e-15
+
+
+def test_argument_errors(E):
+    eigdc, h, torch = E
+    dA = torch.zeros((4, 4), dtype=torch.complex128, device="cuda")
+    p = eigdc.default_params(leaf_size=65)
+    rc, info, enc = eigdc.eig_schur_complex(h, 4, dA, 4, dA, 4, dA, 4, dA, p)
+    assert rc == eigdc.EIG_ERR_ARG
+    rc, info, enc = eigdc.eig_schur_complex(h, 4, dA, 3, dA, 4, dA, 4, dA, eigdc.default_params())
+    assert rc == eigdc.EIG_ERR_ARG
