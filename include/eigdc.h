@@ -369,6 +369,23 @@ int eig_gemm_noalloc(void* stream, int ta, int tb, int m, int n, int k, double a
                      const double* dA, int lda, const double* dB, int ldb, double beta,
                      double* dC, int ldc);
 
+/* ------------------------------------------------------ eigenvectors
+ * Eigenvectors from the Schur form (the eigenvector section and its blocked
+ * form): for A = Q T Q^T as eig_solve (EIG_KIND_NONSYM) returns it -- T
+ * quasi-upper-triangular in standard form, wi the imaginary parts -- each
+ * 2 x 2 block is made triangular by the unitary whose first column is the
+ * block's eigenvector, then Tc X = X diag(Tc) is solved for the upper
+ * triangular X (X_jj = 1) by the recurrence
+ *   X_ij = (T_ij X_jj + sum_{k=i+1}^{j-1} T_ik X_kj) / (T_jj - T_ii),
+ * in blocks of 32 whose off-diagonal right-hand sides are complex GEMMs.
+ *   - dT (ldt >= n), dQ (ldq >= n), dwi (n): device, real, not modified.
+ *   - dV (ldv >= n): device, complex (interleaved), receives unit 2-norm
+ *     eigenvectors, A V = V diag(lam); dlam: device, n complex eigenvalues.
+ *   - The eigenvalues must be distinct (the recurrence divides by their
+ *     differences); equal ones give non-finite vectors. */
+int eig_eigenvectors(eig_handle_t h, int n, const double* dT, int ldt, const double* dQ, int ldq,
+                     const double* dwi, double* dV, int ldv, double* dlam);
+
 /* ------------------------------------------------------ complex-plane strategy
  * Sec. 3.3: splitting lines at random angles.  The line {z : Re(conj(w) z) = t}
  * (|w| = 1) is mapped to the unit circle by the rotated Moebius map

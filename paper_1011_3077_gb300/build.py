@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeigdc.so")
 SOURCES = ["linalg.cu", "misc.cu", "leaves.cu", "tc_gemm.cu", "tcx_gemm.cu", "api.cu", "noalloc.cu",
-           "cplane.cu"]
+           "cplane.cu", "trevc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -1991,6 +1991,19 @@ int eig_solve(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
   API_END
 }
 
+int eig_eigenvectors(eig_handle_t h, int n, const double* dT, int ldt, const double* dQ, int ldq,
+                     const double* dwi, double* dV, int ldv, double* dlam) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dT && ldt >= n && dQ && ldq >= n && dwi, "dT / dQ / dwi invalid");
+  REQUIRE(dV && ldv >= n && dlam, "dV / dlam invalid");
+  std::string err;
+  const int rc = trevc(h->stream, n, dT, ldt, dQ, ldq, dwi, dV, ldv, dlam, &err);
+  if (rc < 0) h->err = err;
+  return rc;
+  API_END
+}
+
 int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* dT, int ldt,
                       double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,
                       eig_enclosure_t* enc, int enc_cap, int* n_enc, eig_solve_info_t* info) {

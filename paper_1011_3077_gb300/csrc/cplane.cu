@@ -142,8 +142,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int m, int n, int k, zt alph
   }
 }
 
-cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, zt alpha, const zt* A,
-                  int lda, const zt* B, int ldb, zt beta, zt* C, int ldc) {
+}  // namespace
+
+cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double2 alpha,
+                  const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C,
+                  int ldc) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   dim3 g(nblocks(m, ZBM), nblocks(n, ZBN));
   note_launches(1);
@@ -153,6 +156,8 @@ cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, zt alph
   else zgemm_kernel<true, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
   return cudaGetLastError();
 }
+
+namespace {
 
 // ------------------------------------------------------------------ elementwise
 // B = A (rows x cols)

@@ -180,10 +180,21 @@ struct CplaneCluster {
   double cr, ci, R;                    // disk
   std::vector<CplaneHalfPlane> hp;     // half-planes cutting it
 };
+// C = alpha op(A) op(B) + beta C over C (op = X or X^H), DFMA, 64 x 64 tiles.
+cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double2 alpha,
+                  const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C,
+                  int ldc);
 // A = U T U^H with T upper triangular, w = diag(T).  Returns an EIG_* status;
 // on a negative status *err holds the message.
 int cplane_schur(cudaStream_t s, int n, const double* dA, int lda, double* dT, int ldt,
                  double* dU, int ldu, double* dw, const eig_params_t& p, bool enclose,
                  std::vector<CplaneCluster>* clusters, eig_solve_info_t* info, std::string* err);
+
+// ------------------------------------------------------------- trevc.cu
+// Eigenvectors of A = Q T Q^T from the real Schur form (T quasi-triangular in
+// standard form, wi the imaginary parts): V (n x n complex, unit columns) and
+// lam (n complex).  Returns an EIG_* status.
+int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, int ldq,
+          const double* dwi, double* dV, int ldv, double* dlam, std::string* err);
 
 }  // namespace eigdc

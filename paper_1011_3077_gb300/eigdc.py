@@ -140,6 +140,7 @@ _SIGNATURES = {
     "eig_gemm_split": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_fp64tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+    "eig_eigenvectors": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, _P]),
     "eig_schur_complex": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(Params), _I,
                                ctypes.POINTER(Enclosure), _I, ctypes.POINTER(_I),
                                ctypes.POINTER(SolveInfo)]),
@@ -507,6 +508,25 @@ def svd(h, A, params=None):
     dV = torch.zeros((r, n), dtype=torch.float64, device=dA.device)
     rc, info = eig_svd(h, m, n, dA, m, dS, dU, m, dV, n, params)
     return rc, dS.cpu().numpy(), dU.cpu().numpy().T.copy(), dV.cpu().numpy().T.copy(), info
+
+
+# ----------------------------------------------------------------- eigenvectors
+
+def eig_eigenvectors(h, n, dT, ldt, dQ, ldq, dwi, dV, ldv, dlam):
+    return lib().eig_eigenvectors(h.ptr, n, _ptr(dT), ldt, _ptr(dQ), ldq, _ptr(dwi), _ptr(dV),
+                                  ldv, _ptr(dlam))
+
+
+def eigenvectors(h, T, Q, wi):
+    """(rc, lam, V) for a real Schur form (T, Q, wi) as schur_nonsymmetric returns it."""
+    import torch
+    n = T.shape[0]
+    dT, dQ = to_device(T), to_device(Q)
+    dwi = torch.from_numpy(np.ascontiguousarray(wi, dtype=np.float64)).to(dT.device)
+    dV = torch.zeros((n, n), dtype=torch.complex128, device=dT.device)
+    dlam = torch.zeros(n, dtype=torch.complex128, device=dT.device)
+    rc = eig_eigenvectors(h, n, dT, n, dQ, n, dwi, dV, n, dlam)
+    return rc, dlam.cpu().numpy(), dV.cpu().numpy().T.copy()
 
 
 # ----------------------------------------------------------------- complex-plane strategy
