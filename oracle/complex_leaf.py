@@ -49,7 +49,8 @@ def givens(a, b):
     rho = float(np.sqrt(abs(a) ** 2 + abs(b) ** 2))
     if rho == 0.0:
         return np.eye(2, dtype=np.complex128)
-    return np.array([[np.conj(a), np.conj(b)], [-b, a]], dtype=np.complex128) / rho
+    G = np.array([[np.conj(a), np.conj(b)], [-b, a]], dtype=np.complex128)
+    return G.real / rho + 1j * (G.imag / rho)   # no reciprocal of a subnormal rho
 
 
 def _apply(H, Z, k, G):

@@ -48,7 +48,10 @@ def chouse(x):
     if nrm == 0.0:
         return None, 0.0 + 0.0j
     x0 = x[0]
-    ph = x0 / abs(x0) if x0 != 0 else 1.0 + 0.0j
+    a0 = abs(x0)
+    # real and imaginary parts divided separately: numpy's complex-by-real
+    # division goes through a reciprocal that overflows for a subnormal |x0|
+    ph = complex(x0.real / a0, x0.imag / a0) if a0 > 0 else 1.0 + 0.0j
     v = x.copy()
     v[0] = x0 + ph * nrm
     return v, -ph * nrm
@@ -103,7 +106,8 @@ def cqr_factor(X):
     d = np.diag(R).copy()
     phases = np.ones(n, dtype=np.complex128)
     nz = np.abs(d) > 0.0
-    phases[nz] = d[nz] / np.abs(d[nz])
+    ad = np.abs(d[nz])
+    phases[nz] = d[nz].real / ad + 1j * (d[nz].imag / ad)
     R = phases.conj()[:, None] * R
     R[np.arange(n), np.arange(n)] = np.abs(d)
     return CQRFactors(vs, phases, R, m)
