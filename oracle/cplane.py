@@ -333,7 +333,8 @@ def enclosing_circle(region):
     # the distance from m to a point of the boundary circle grows monotonically
     # towards the point opposite m; if that point is in the region it is the
     # farthest one, otherwise the farthest region point on an arc is an arc end
-    far = c - R * (m - c) / abs(m - c)
+    dm = m - c
+    far = c - R * complex(dm.real / abs(dm), dm.imag / abs(dm))
     if region.contains(far) and abs(far - m) > r * (1.0 + 1e-12):
         return c, R
     return m, r
@@ -365,7 +366,7 @@ class CInfo:
         self.failed_attempts = 0   # attempts that did not split (chops included)
         self.chops = 0
         self.recenters = []        # (node, old radius, new radius, "one chop" | "two chops")
-        self.lines = []            # (node, attempt, w, t, outcome, disk centre, disk radius)
+        self.lines = []            # (node, attempt, w, t, outcome, disk centre, disk radius, rank)
         self.clusters = []         # (offset, size, Region)
 
 
@@ -430,7 +431,7 @@ def schur_complex_plane(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=N
                     ce, Re = enclosing_circle(rr)
                     kids.append(Region(cg, Rg) if Rg <= Re else Region(ce, Re))
                 info.splits += 1
-                info.lines.append((node, attempt, w, t, "split", region.c, region.R))
+                info.lines.append((node, attempt, w, t, "split", region.c, region.R, st.rank))
                 work.append((off + k, m - k, A22, kids[1], child_node(node, 1), depth + 1))
                 work.append((off, k, A11, kids[0], child_node(node, 0), depth + 1))
                 break
@@ -438,7 +439,7 @@ def schur_complex_plane(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=N
             if st.irs.converged and st.rank in (0, m):
                 # nothing on one side of the line: chop it off
                 info.chops += 1
-                info.lines.append((node, attempt, w, t, "chop", region.c, region.R))
+                info.lines.append((node, attempt, w, t, "chop", region.c, region.R, st.rank))
                 keep = (w, t) if st.rank == m else (-w, -t)
                 region.halfplanes.append(keep)
                 cn, rn = enclosing_circle(region)
@@ -455,7 +456,7 @@ def schur_complex_plane(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=N
                     pending = None
             else:
                 fails += 1
-                info.lines.append((node, attempt, w, t, "fail", region.c, region.R))
+                info.lines.append((node, attempt, w, t, "fail", region.c, region.R, st.rank))
                 pending = None
             attempt += 1
             if fails > max_fail or attempt > max_attempts:

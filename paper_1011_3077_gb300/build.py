@@ -38,6 +38,7 @@ def _stale(obj, src):
         return True
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_ptx.cuh"),
+            os.path.join(CSRC, "cplane_strategy.h"),
             os.path.join(os.path.dirname(HERE), "include", "eigdc.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

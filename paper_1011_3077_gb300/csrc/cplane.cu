@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "../../include/eigdc.h"
+#include "cplane_strategy.h"
 #include "internal.h"
 
 namespace eigdc {
@@ -53,7 +54,6 @@ constexpr int PURPOSE_HAAR_IM = 7;
 constexpr int PURPOSE_LINE = 8;
 constexpr int ZNB = 32;           // panel width of the complex QR (T leading dimension)
 constexpr int ZLEAF_MAX = 64;     // largest leaf of the complex Schur kernel
-constexpr double SHRINK = 0.96592582628906829;   // sin(5 pi / 12)
 
 __host__ __device__ __forceinline__ zt zmk(double r, double i) { return make_double2(r, i); }
 __device__ __forceinline__ zt zadd(zt a, zt b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -766,136 +766,14 @@ __global__ void zident_ld_kernel(int rows, int cols, zt* __restrict__ U, int ldu
 }
 
 // ------------------------------------------------------------------ geometry (host)
-struct HalfPlane {
-  double wr, wi, t;   // {z : Re(conj(w) z) >= t}
-};
+// Region, enclosing circle, lines and the per-node plan: cplane_strategy.h.
 
-struct Region {
-  double cr = 0.0, ci = 0.0, R = 0.0;
-  std::vector<HalfPlane> hp;
-  bool contains(double zr, double zi, double slack = 1e-12) const {
-    const double tol = slack * std::max({R, std::hypot(cr, ci), 1e-300});
-    if (std::hypot(zr - cr, zi - ci) > R + tol) return false;
-    for (const HalfPlane& h : hp)
-      if (h.wr * zr + h.wi * zi < h.t - tol) return false;
-    return true;
-  }
-};
-
-struct Pt {
-  double x, y;
-};
-
-void line_circle(const Region& g, const HalfPlane& h, std::vector<Pt>& out) {
-  const double d = h.t - (h.wr * g.cr + h.wi * g.ci);
-  if (std::fabs(d) > g.R) return;
-  const double hh = std::sqrt(std::max(g.R * g.R - d * d, 0.0));
-  const double fx = g.cr + h.wr * d, fy = g.ci + h.wi * d;
-  // i w = (-wi, wr)
-  out.push_back({fx - h.wi * hh, fy + h.wr * hh});
-  out.push_back({fx + h.wi * hh, fy - h.wr * hh});
-}
-
-bool line_line(const HalfPlane& a, const HalfPlane& b, Pt* p) {
-  const double det = a.wr * b.wi - a.wi * b.wr;
-  if (std::fabs(det) < 1e-14) return false;
-  p->x = (a.t * b.wi - a.wi * b.t) / det;
-  p->y = (a.wr * b.t - a.t * b.wr) / det;
-  return true;
-}
-
-bool circle3(Pt p, Pt q, Pt r, Pt* m, double* rad) {
-  const double d = 2.0 * (p.x * (q.y - r.y) + q.x * (r.y - p.y) + r.x * (p.y - q.y));
-  if (std::fabs(d) < 1e-300) return false;
-  const double pp = p.x * p.x + p.y * p.y, qq = q.x * q.x + q.y * q.y, rr = r.x * r.x + r.y * r.y;
-  m->x = (pp * (q.y - r.y) + qq * (r.y - p.y) + rr * (p.y - q.y)) / d;
-  m->y = (pp * (r.x - q.x) + qq * (p.x - r.x) + rr * (q.x - p.x)) / d;
-  *rad = std::hypot(p.x - m->x, p.y - m->y);
-  return true;
-}
-
-// Smallest circle through a few points: every pair as a diameter and every
-// triple's circumcircle, the smallest that holds all points.
-bool min_circle(const std::vector<Pt>& pts, Pt* m, double* rad) {
-  if (pts.empty()) return false;
-  if (pts.size() == 1) {
-    *m = pts[0];
-    *rad = 0.0;
-    return true;
-  }
-  bool have = false;
-  auto consider = [&](Pt c, double r) {
-    const double tol = 1e-12 * std::max(r, 1e-300);
-    for (const Pt& p : pts)
-      if (std::hypot(p.x - c.x, p.y - c.y) > r + tol) return;
-    if (!have || r < *rad) {
-      have = true;
-      *m = c;
-      *rad = r;
-    }
-  };
-  const size_t np = pts.size();
-  for (size_t i = 0; i < np; ++i)
-    for (size_t j = i + 1; j < np; ++j) {
-      consider({0.5 * (pts[i].x + pts[j].x), 0.5 * (pts[i].y + pts[j].y)},
-               0.5 * std::hypot(pts[i].x - pts[j].x, pts[i].y - pts[j].y));
-      for (size_t k = j + 1; k < np; ++k) {
-        Pt c;
-        double r;
-        if (circle3(pts[i], pts[j], pts[k], &c, &r)) consider(c, r);
-      }
-    }
-  return have;
-}
-
-// Circle holding the region: the smallest circle through its corners when it
-// also holds the boundary arc (the point of the circle opposite its centre,
-// if that point is in the region); otherwise the disk itself.
-void enclosing_circle(const Region& g, double* mr, double* mi, double* rad) {
-  *mr = g.cr;
-  *mi = g.ci;
-  *rad = g.R;
-  if (g.hp.empty()) return;
-  std::vector<Pt> corners, tmp;
-  for (size_t i = 0; i < g.hp.size(); ++i) {
-    tmp.clear();
-    line_circle(g, g.hp[i], tmp);
-    for (const Pt& p : tmp)
-      if (g.contains(p.x, p.y)) corners.push_back(p);
-    for (size_t j = i + 1; j < g.hp.size(); ++j) {
-      Pt p;
-      if (line_line(g.hp[i], g.hp[j], &p) && g.contains(p.x, p.y)) corners.push_back(p);
-    }
-  }
-  Pt m;
-  double r;
-  if (!min_circle(corners, &m, &r)) return;
-  if (r >= g.R || (m.x == g.cr && m.y == g.ci)) return;
-  const double dx = m.x - g.cr, dy = m.y - g.ci, dn = std::hypot(dx, dy);
-  const double fx = g.cr - g.R * dx / dn, fy = g.ci - g.R * dy / dn;
-  if (g.contains(fx, fy) && std::hypot(fx - m.x, fy - m.y) > r * (1.0 + 1e-12)) return;
-  *mr = m.x;
-  *mi = m.y;
-  *rad = r;
-}
-
-// The attempt's line: angle 2 pi u2 (or perpendicular to `perp`), offset R (u1 - 1/2).
+// The attempt's line from the Philox pair of purpose PURPOSE_LINE.
 HalfPlane draw_line(const Region& g, uint64_t seed, uint64_t node, int attempt, bool has_perp,
                     double pr, double pi_) {
   double u1, u2;
   philox_pair_host(seed, PURPOSE_LINE, node, attempt, &u1, &u2);
-  HalfPlane h;
-  if (has_perp) {
-    h.wr = -pi_;   // i w
-    h.wi = pr;
-  } else {
-    const double th = 2.0 * 3.14159265358979323846 * u2;
-    h.wr = std::cos(th);
-    h.wi = std::sin(th);
-  }
-  const double a = g.R * (u1 - 0.5);
-  h.t = a + (h.wr * g.cr + h.wi * g.ci);
-  return h;
+  return make_line(g, u1, u2, has_perp, pr, pi_);
 }
 
 // ------------------------------------------------------------------ driver (host)
@@ -1218,21 +1096,20 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
       const double tau = p.tau > 0.0 ? p.tau : std::max(1e-14, 4.0 * std::sqrt((double)m) * 0x1p-53);
       const double stol = p.split_tol > 0.0 ? p.split_tol : std::max(1e-12, 16.0 * m * 0x1p-53);
       const int maxit = p.maxit;
-      const int max_fail = p.max_fail;
-      int attempt = 0, fails = 0;
-      bool has_perp = false;
-      double pr = 0.0, pi_ = 0.0;
-      Region reg = nd.reg;
+      NodePlan plan;
+      plan.reg = nd.reg;
+      plan.max_fail = p.max_fail;
       while (true) {
-        if (!(reg.R > 0.0)) {
+        if (!(plan.reg.R > 0.0)) {
           // every row and column sum of |A - cI| is zero: A = cI is already
           // triangular (U stays, T = U^H A U below)
           D.release(nd.A);
           break;
         }
-        const HalfPlane L = draw_line(reg, p.seed, nd.id, attempt, has_perp, pr, pi_);
-        const CStepOut st = line_step(D, b, m, nd.A, L, reg.R, p.seed, nd.id, attempt, tau, maxit,
-                                      stol, p.v_draws);
+        const HalfPlane L = draw_line(plan.reg, p.seed, nd.id, plan.attempt, plan.has_perp, plan.pr,
+                                      plan.pi_);
+        const CStepOut st = line_step(D, b, m, nd.A, L, plan.reg.R, p.seed, nd.id, plan.attempt, tau,
+                                      maxit, stol, p.v_draws);
         inf.total_iters += st.iters;
         if (st.accepted) {
           const int k = st.k;
@@ -1243,62 +1120,23 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
           zt* A22 = D.alloc<zt>((size_t)(m - k) * (m - k));
           D.check(zcopy(s, k, k, b.Ahat, m, A11, k), "block copy");
           D.check(zcopy(s, m - k, m - k, b.Ahat + k + (size_t)k * m, m, A22, m - k), "block copy");
-          Region r1 = reg, r2 = reg;
-          r1.hp.push_back(L);
-          r2.hp.push_back({-L.wr, -L.wi, -L.t});
-          Region kids[2];
-          zt* blocks[2] = {A11, A22};
-          const int sizes[2] = {k, m - k};
-          const Region* sides[2] = {&r1, &r2};
-          for (int c = 0; c < 2; ++c) {
-            Region g;
-            if (sizes[c] > leaf) g = gershgorin_disk(D, b, sizes[c], blocks[c], sizes[c]);
-            double er, ei, eR;
-            enclosing_circle(*sides[c], &er, &ei, &eR);
-            if (sizes[c] > leaf && g.R <= eR) {
-              kids[c] = g;
-            } else {
-              kids[c].cr = er;
-              kids[c].ci = ei;
-              kids[c].R = eR;
-            }
-          }
+          Region g0, g1, kid0, kid1;
+          if (k > leaf) g0 = gershgorin_disk(D, b, k, A11, k);
+          if (m - k > leaf) g1 = gershgorin_disk(D, b, m - k, A22, m - k);
+          child_regions(plan.reg, L, k > leaf ? &g0 : nullptr, m - k > leaf ? &g1 : nullptr, &kid0,
+                        &kid1);
           inf.splits += 1;
-          work.push_back({nd.off + k, m - k, A22, kids[1], child_node_id(nd.id, 1), nd.depth + 1});
-          work.push_back({nd.off, k, A11, kids[0], child_node_id(nd.id, 0), nd.depth + 1});
+          work.push_back({nd.off + k, m - k, A22, kid1, child_node_id(nd.id, 1), nd.depth + 1});
+          work.push_back({nd.off, k, A11, kid0, child_node_id(nd.id, 0), nd.depth + 1});
           D.release(nd.A);
           break;
         }
         inf.failed_attempts += 1;
-        if (st.converged && (st.rank == 0 || st.rank == m)) {
-          reg.hp.push_back(st.rank == m ? L : HalfPlane{-L.wr, -L.wi, -L.t});
-          double er, ei, eR;
-          enclosing_circle(reg, &er, &ei, &eR);
-          if (eR <= SHRINK * reg.R) {
-            reg = Region();
-            reg.cr = er; reg.ci = ei; reg.R = eR;
-            has_perp = false;
-          } else if (!has_perp) {
-            has_perp = true;
-            pr = L.wr;
-            pi_ = L.wi;
-          } else {
-            if (eR < reg.R) {
-              reg = Region();
-              reg.cr = er; reg.ci = ei; reg.R = eR;
-            }
-            has_perp = false;
-          }
-        } else {
-          fails += 1;
-          has_perp = false;
-        }
-        attempt += 1;
-        if (fails > max_fail || attempt > 250) {
+        if (plan.after_nonsplit(L, st.converged, st.rank, m)) {
           if (enclose) {
             if (clusters) {
-              clusters->push_back({nd.off, m, reg.cr, reg.ci, reg.R, {}});
-              for (const HalfPlane& h : reg.hp) clusters->back().hp.push_back({h.wr, h.wi, h.t});
+              clusters->push_back({nd.off, m, plan.reg.cr, plan.reg.ci, plan.reg.R, {}});
+              for (const HalfPlane& h : plan.reg.hp) clusters->back().hp.push_back({h.wr, h.wi, h.t});
             }
             if (m <= ZLEAF_MAX) {
               leaves.push_back({nd.off, m, nd.A});

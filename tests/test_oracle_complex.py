@@ -321,7 +321,7 @@ def test_driver_prescribed_complex_spectrum():
     _check_schur(A, T, U, 1e-13)
     assert _match(w, lam) < 1e-10
     # every line lies at most R/2 from the centre of its disk
-    for (_, _, wl, t, _, c, R) in info.lines:
+    for (_, _, wl, t, _, c, R, _) in info.lines:
         assert abs(t - (np.conj(wl) * c).real) <= 0.5 * R * (1 + 1e-12)
 
 
@@ -376,8 +376,8 @@ def test_driver_two_step_rule_on_a_loose_disk():
     # after a chop that did not move the disk, the next line of the node is perpendicular
     lines = info.lines
     for i in range(len(lines) - 1):
-        node, att, wl, _, outcome, c, R = lines[i]
-        nn, natt, wn, _, _, cn, Rn = lines[i + 1]
+        node, att, wl, _, outcome, c, R, _ = lines[i]
+        nn, natt, wn, _, _, cn, Rn, _ = lines[i + 1]
         if outcome == "chop" and nn == node and cn == c and Rn == R:
             prev_perp = i > 0 and lines[i - 1][0] == node and lines[i - 1][4] == "chop" \
                 and lines[i - 1][5] == c and lines[i - 1][6] == R
