@@ -61,11 +61,13 @@ def parse():
                          "device-wide synchronisation while a solve runs)")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
-    ap.add_argument("--workload", default="schur", choices=["schur", "batched", "svd"],
+    ap.add_argument("--workload", default="schur", choices=["schur", "batched", "svd", "cplane"],
                     help="schur: one nonsymmetric n x n solve per step (default); batched: "
                          "--count independent symmetric problems, n log-uniform in [32, 512], "
                          "solved by eig_solve_batched per step; svd: singular values and "
-                         "vectors of one n x n matrix per step (eig_svd)")
+                         "vectors of one n x n matrix per step (eig_svd); cplane: the complex "
+                         "Schur form of one n x n matrix per step by lines at random angles "
+                         "(eig_schur_complex)")
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -365,6 +367,65 @@ def svd_arm(args, torch, eigdc, h, dev, stream, world):
         print(json.dumps(line), flush=True)
 
 
+def cplane_arm(args, torch, eigdc, h, dev, stream, world):
+    """One complex Schur form per step by the complex-plane strategy of Sec. 3.3
+    (eig_schur_complex): a real normal matrix with complex pairs a +- ib,
+    a, b ~ U[-1.5, 1.5] (the random normal examples of Sec. 3.3.1)."""
+    from paper_1011_3077_gb300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    n = args.n
+    A, _ = workloads.normal_complex(n, seed=30 + rank)
+    dA = eigdc.to_device_complex(A, dev)
+    dT = torch.zeros((n, n), dtype=torch.complex128, device=dev)
+    dU = torch.zeros((n, n), dtype=torch.complex128, device=dev)
+    dw = torch.zeros(n, dtype=torch.complex128, device=dev)
+    params = eigdc.default_params(seed=0, leaf_size=64)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        rc, info, _ = eigdc.eig_schur_complex(h, n, dA, n, dT, n, dU, n, dw, params)
+        if rc != eigdc.EIG_OK:
+            raise RuntimeError("eig_schur_complex failed: %d %s" % (rc, h.last_error()))
+        return info
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    l0 = eigdc.eig_kernel_launches()
+    ms = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    launches = eigdc.eig_kernel_launches() - l0
+    total_ms = max_over_ranks(sum(ms), dev, world)
+    # column-major tensors hold the transposes
+    U, T = dU.t(), dT.t()
+    Ac = torch.from_numpy(A.astype(np.complex128)).to(dev)
+    bwd = float(torch.linalg.norm(Ac - U @ T @ U.conj().t()) / torch.linalg.norm(Ac))
+    I = torch.eye(n, dtype=torch.complex128, device=dev)
+    orth = float(torch.linalg.norm(U.conj().t() @ U - I))
+    line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "complex Schur form by lines at random angles (Sec. 3.3), "
+                                   "real normal matrix with pairs a +- ib, a, b ~ U[-1.5, 1.5], "
+                                   "n=%d, 64x64 complex leaves" % n,
+                       "n": n, "l2": "flushed between timed steps (512 MiB write)"},
+            "splits": info.splits, "nodes": info.nodes, "squarings": info.total_iters,
+            "backward_error": bwd, "orthogonality_frobenius": orth,
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
+            "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -388,9 +449,9 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream(dev)
     h = eigdc.Handle(local, stream)
-    if args.workload in ("batched", "svd"):
-        (batched_arm if args.workload == "batched" else svd_arm)(args, torch, eigdc, h, dev,
-                                                                 stream, world)
+    if args.workload in ("batched", "svd", "cplane"):
+        arm = {"batched": batched_arm, "svd": svd_arm, "cplane": cplane_arm}[args.workload]
+        arm(args, torch, eigdc, h, dev, stream, world)
         h.close()
         if world > 1:
             dist.destroy_process_group()
