@@ -415,7 +415,9 @@ typedef struct {
  * within half the radius (Philox purpose 8 of the node and attempt), chops of
  * empty half-planes, the 2-step radius shrink (the next line perpendicular to
  * the chord; the region moves to its enclosing circle, radius at most
- * sin(5 pi/12) R), Gershgorin disks of the blocks after a split, and complex
+ * sin(5 pi/12) R), after a split the smaller of each block's disk
+ * |z - c| <= ||A_ii - c I||_F (c its mean eigenvalue) and the enclosing circle
+ * of its side, and complex
  * Hessenberg + single-shift QR leaves (leaf_size <= 64).
  *   - dA (lda >= n), dT (ldt >= n), dU (ldu >= n): device, complex; dw: device,
  *     n complex.  dA is not modified.

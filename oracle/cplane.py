@@ -28,10 +28,16 @@ A^ = Q^H A Q and the block size k minimising ||E21||_1 / ||A||_1
 eigenvalues with Re(conj(w) z) > t.
 
 Readings (paper silent):
-  * Gershgorin disk about the mean eigenvalue c = tr(A)/n, radius the smaller
-    of the row and the column bound of A - c I; after a split a child takes
-    the smaller of its Gershgorin disk and the smallest circle enclosing the
-    parent region cut by the child's side of the line;
+  * root: the Gershgorin disk about the mean eigenvalue c = tr(A)/n, radius
+    the smaller of the row and the column bound of A - c I.  After a split a
+    child takes the smaller of the disk |z - c| <= ||A_ii - c I||_F (c its
+    mean eigenvalue) and the smallest circle enclosing the parent region cut
+    by the child's side of the line.  Sec. 3.3 names Gershgorin bounds there;
+    but the splitter's trailing columns span the complementary invariant
+    subspace in a basis that rounding picks (A_p is numerically rank
+    deficient, so the QR of A_p V^H fixes only its leading columns), and a
+    Gershgorin radius changes with that basis while the Frobenius norm and the
+    trace do not;
   * draws: u1, u2 of the Philox pair of purpose PURPOSE_LINE for the node
     and attempt; theta = 2 pi u2, a = R (u1 - 1/2); the perpendicular line
     of the 2-step rule uses w' = i w and the same a rule;
@@ -354,6 +360,19 @@ def gershgorin_disk(A):
     return c, min(row, col)
 
 
+def frobenius_disk(A):
+    """(c, R): c = tr(A)/n, R = ||A - c I||_F, a disk holding the spectrum.
+
+    Unlike the Gershgorin radius, R does not change under a unitary change of
+    basis, so it does not depend on which orthonormal basis of its invariant
+    subspace a block was computed in (see the module docstring)."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    c = complex(np.trace(A) / n)
+    D = A - c * np.eye(n)
+    return c, float(np.sqrt(np.sum(np.abs(D) ** 2)))
+
+
 # ----------------------------------------------------------- driver
 
 class CInfo:
@@ -427,7 +446,7 @@ def schur_complex_plane(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=N
                 r2.halfplanes.append((-w, -t))
                 kids = []
                 for Ab, rr in ((A11, r1), (A22, r2)):
-                    cg, Rg = gershgorin_disk(Ab)
+                    cg, Rg = frobenius_disk(Ab)
                     ce, Re = enclosing_circle(rr)
                     kids.append(Region(cg, Rg) if Rg <= Re else Region(ce, Re))
                 info.splits += 1

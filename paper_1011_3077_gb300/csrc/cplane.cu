@@ -22,7 +22,8 @@
 // the splitter agree with any other implementation of the same definition.
 //
 // Recursion (Sec. 3.3): the disk |z - c| <= R of a node (root: Gershgorin
-// about c = tr(A)/n), a random angle theta = 2 pi u2 and offset
+// about c = tr(A)/n; after a split the smaller of ||A_ii - cI||_F about the
+// block's mean eigenvalue and the enclosing circle of its side), a random angle theta = 2 pi u2 and offset
 // a = R (u1 - 1/2) from Philox purpose 8; a step that finds one side empty
 // chops it off; the region (disk cut by the chopped half-planes) moves to its
 // enclosing circle at once when that shrinks the radius to sin(5 pi/12) R or
@@ -266,6 +267,27 @@ __global__ void zcolabs_kernel(int rows, int cols, const zt* __restrict__ A, int
     zt v = A[i + (size_t)j * lda];
     if (i == j) v = zsub(v, c);
     acc += zabs(v);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    colsum[j] = t;
+  }
+}
+
+// colsum[j] = sum_i |A_ij - [i == j] c|^2; one CTA per column, fixed order.
+__global__ void zcolsq_kernel(int rows, const zt* __restrict__ A, int lda, zt c,
+                              double* __restrict__ colsum) {
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < rows; i += 256) {
+    zt v = A[i + (size_t)j * lda];
+    if (i == j) v = zsub(v, c);
+    acc += v.x * v.x + v.y * v.y;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -899,6 +921,30 @@ Region gershgorin_disk(CDriver& D, StepBufs& b, int m, const zt* A, int lda) {
   return g;
 }
 
+// Disk |z - c| <= ||A - c I||_F about c = tr(A)/m: unlike a Gershgorin radius it
+// does not change with the basis of the block's invariant subspace, which for
+// the trailing block of a split is fixed by rounding.
+Region frobenius_disk(CDriver& D, StepBufs& b, int m, const zt* A, int lda) {
+  note_launches(1);
+  ztrace_kernel<<<1, 256, 0, D.s>>>(m, A, lda, reinterpret_cast<zt*>(b.col2));
+  double tr[2];
+  D.check(cudaMemcpyAsync(tr, b.col2, sizeof(double) * 2, cudaMemcpyDeviceToHost, D.s), "trace copy");
+  D.sync();
+  const zt c = zmk(tr[0] / m, tr[1] / m);
+  note_launches(1);
+  zcolsq_kernel<<<m, 256, 0, D.s>>>(m, A, lda, c, b.col1);
+  std::vector<double> h(m);
+  D.check(cudaMemcpyAsync(h.data(), b.col1, sizeof(double) * m, cudaMemcpyDeviceToHost, D.s), "norm copy");
+  D.sync();
+  double ss = 0.0;
+  for (int i = 0; i < m; ++i) ss += h[i];
+  Region g;
+  g.cr = c.x;
+  g.ci = c.y;
+  g.R = std::sqrt(ss);
+  return g;
+}
+
 struct CIrs {
   int iters;
   bool converged;
@@ -1121,8 +1167,8 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
           D.check(zcopy(s, k, k, b.Ahat, m, A11, k), "block copy");
           D.check(zcopy(s, m - k, m - k, b.Ahat + k + (size_t)k * m, m, A22, m - k), "block copy");
           Region g0, g1, kid0, kid1;
-          if (k > leaf) g0 = gershgorin_disk(D, b, k, A11, k);
-          if (m - k > leaf) g1 = gershgorin_disk(D, b, m - k, A22, m - k);
+          if (k > leaf) g0 = frobenius_disk(D, b, k, A11, k);
+          if (m - k > leaf) g1 = frobenius_disk(D, b, m - k, A22, m - k);
           child_regions(plan.reg, L, k > leaf ? &g0 : nullptr, m - k > leaf ? &g1 : nullptr, &kid0,
                         &kid1);
           inf.splits += 1;

@@ -198,7 +198,8 @@ struct NodePlan {
 };
 
 // Regions of the two blocks after a split on L: each side's enclosing circle,
-// or the block's own Gershgorin disk when that is not larger.
+// or the block's own disk (about its mean eigenvalue, radius ||A_ii - cI||_F)
+// when that is not larger.
 inline void child_regions(const Region& reg, const HalfPlane& L, const Region* gersh0,
                           const Region* gersh1, Region* kid0, Region* kid1) {
   Region sides[2] = {reg, reg};

@@ -14,6 +14,7 @@ from oracle.complex_qr import chouse, cqr_explicit, crq_explicit, chaar
 from oracle.complex_leaf import complex_schur, chessenberg, wilkinson_shift
 from oracle.cplane import (cirs, cirs_step, line_map, line_step, Region, enclosing_circle,
                            gershgorin_disk, schur_complex_plane, SHRINK)
+from oracle import cplane
 from oracle.irs import irs
 from oracle.solve import STATUS_OK, STATUS_NO_SPLIT
 from paper_1011_3077_gb300 import workloads
@@ -300,6 +301,21 @@ def test_gershgorin_disk_holds_the_spectrum():
         c, R = gershgorin_disk(A)
         assert abs(c - np.mean(lam)) < 1e-12 * n
         assert np.all(np.abs(lam - c) <= R * (1 + 1e-12))
+
+
+def test_frobenius_disk_holds_the_spectrum_and_ignores_the_basis():
+    rng = np.random.default_rng(64)
+    for n in (2, 9, 30):
+        lam = _crandn(rng, n)
+        A, _ = _prescribed(lam, rng, coupling=0.6)
+        c, R = cplane.frobenius_disk(A)
+        assert abs(c - np.mean(lam)) < 1e-12 * n
+        assert np.all(np.abs(lam - c) <= R * (1 + 1e-12))
+        W = cqr_explicit(_crandn(rng, n, n))[0]
+        c2, R2 = cplane.frobenius_disk(W.conj().T @ A @ W)
+        assert abs(c2 - c) < 1e-12 * n and abs(R2 - R) < 1e-12 * R
+        cg, Rg = gershgorin_disk(W.conj().T @ A @ W)
+        assert abs(Rg - gershgorin_disk(A)[1]) > 1e-6      # the Gershgorin radius does move
 
 
 # ------------------------------------------------------------ driver
