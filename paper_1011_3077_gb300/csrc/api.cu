@@ -224,6 +224,7 @@ static size_t qr_part_doubles(int m, int cols) { return (size_t)33 * JB_LD * std
 // Blocked right-looking Householder QR of the m x n matrix in q.W.
 static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
   cudaStream_t s = h->stream;
+  NvtxRange nvtx_("eig.qr");
   const int jbmax = panel_max_width(m);
   if (jbmax <= 0) {
     h->err = "matrix too tall for the on-chip panel factorisation";
@@ -375,6 +376,7 @@ static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int ld
                       int ldb, const eig_region_t& rg, double tau, int maxit,
                       bool stagnate = false, bool use_graphs = false) {
   cudaStream_t s = h->stream;
+  NvtxRange nvtx_("eig.irs");
   const size_t nn = (size_t)n * n;
   QRBufs& q = w.qr.q;
   q.ldw = 2 * n;   // the stacked matrix of this (node) size, packed
@@ -689,6 +691,7 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
                           uint64_t stream_id, int attempt, const eig_params_t& p,
                           bool irs_converged, std::vector<double>& hscores) {
   cudaStream_t s = h->stream;
+  NvtxRange nvtx_("eig.split");
   const double normA = device_norm1(h, n, n, A, lda, w.nbits);
   const int gsplit = gemm_choose_splits(n, n, n);
   SplitOut out{0, INFINITY, 0, 0, false};
@@ -728,6 +731,7 @@ static SplitOut run_split_pencil(eig_handle_t h, SplitWork& w, int n, const doub
                                  uint64_t stream_id, int attempt, const eig_params_t& p,
                                  bool conv_right, bool conv_left, std::vector<double>& hscores) {
   cudaStream_t s = h->stream;
+  NvtxRange nvtx_("eig.split_pencil");
   const double normA = device_norm1(h, n, n, A, lda, w.nbits);
   const double normB = device_norm1(h, n, n, B, ldb, w.nbits);
   const int gsplit = gemm_choose_splits(n, n, n);
@@ -1071,6 +1075,7 @@ struct SolveShared {
 // `base` points at scratch of carve_node(n, m) bytes.
 static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   cudaStream_t s = hw->stream;
+  NvtxRange nvtx_("eig.node");
   const int n = S.n, m = nd.m;
   const eig_params_t& p = S.p;
   double* An = S.Acur + nd.off + (size_t)nd.off * n;
@@ -1206,6 +1211,7 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
 // node's blocks of (A, B).
 static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   cudaStream_t s = hw->stream;
+  NvtxRange nvtx_("eig.pencil_node");
   const int n = S.n, m = nd.m;
   const eig_params_t& p = S.p;
   double* An = S.Acur + nd.off + (size_t)nd.off * n;
@@ -1425,6 +1431,7 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
                       double* dwi, double* dU, int ldu, const eig_params_t& p,
                       eig_solve_info_t* info) {
   cudaStream_t s = h->stream;
+  NvtxRange nvtx_("eig.solve");
   const bool sym = (kind == EIG_KIND_SYM);
   const bool refine = sym && split_mode(p.prec);
   const int nworkers = std::max(1, std::min(p.workers, 32));
@@ -1493,6 +1500,7 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
   if (status == EIG_OK) {
     std::vector<LeafDesc>& leaves = S.leaves;
     inf.leaves = (int)leaves.size();
+    NvtxRange nvtx_leaves("eig.leaves");
     CK(cudaMemcpyAsync(w.ddesc, leaves.data(), sizeof(LeafDesc) * leaves.size(),
                        cudaMemcpyHostToDevice, s));
     if (sym) {
@@ -1560,6 +1568,7 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
                        double* dQL, int ldql, double* dQR, int ldqr, double* dar, double* dai,
                        double* dbe, const eig_params_t& p, eig_solve_info_t* info) {
   cudaStream_t s = h->stream;
+  NvtxRange nvtx_("eig.pencil_solve");
   const int nworkers = std::max(1, std::min(p.workers, 32));
   const char* venv = std::getenv("EIGDC_VERBOSE");
   Arena meas(nullptr);
@@ -1626,6 +1635,7 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
     std::vector<LeafDesc>& leaves = S.leaves;
     const int nl = (int)leaves.size();
     inf.leaves = nl;
+    NvtxRange nvtx_leaves("eig.pencil_leaves");
     double* wr = w.wtmp;
     double* wi = w.wtmp + n;
     double* M = w.Tbuf;   // leaves' M = A B^{-1} in the diagonal blocks
@@ -2350,6 +2360,7 @@ static void server_worker(eig_server_s* S, eig_handle_s* hw) {
     eig_solve_info_t inf;
     std::memset(&inf, 0, sizeof(inf));
     try {
+      NvtxRange nvtx_("eig.request");
       hw->err.clear();
       if (r->kind == EIG_KIND_PENCIL)
         rc = pencil_impl(hw, r->n, r->dA, r->lda, r->dB, r->ldb, r->dU, r->ldu, r->dQR, r->ldqr,

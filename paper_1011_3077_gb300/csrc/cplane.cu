@@ -1011,6 +1011,7 @@ struct CStepOut {
 CStepOut line_step(CDriver& D, StepBufs& b, int m, const zt* A, const HalfPlane& L, double sc,
                    uint64_t seed, uint64_t node, int attempt, double tau, int maxit,
                    double split_tol, int v_draws) {
+  NvtxRange nvtx_("eig.cplane.step");
   const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
   const size_t mm = (size_t)m * m;
   CStepOut out;
@@ -1104,6 +1105,7 @@ struct CLeaf {
 int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_, int ldt,
                  double* dU_, int ldu, double* dw_, const eig_params_t& p, bool enclose,
                  std::vector<CplaneCluster>* clusters, eig_solve_info_t* info, std::string* err) {
+  NvtxRange nvtx_("eig.cplane.solve");
   const zt* dA = reinterpret_cast<const zt*>(dA_);
   zt* dT = reinterpret_cast<zt*>(dT_);
   zt* dU = reinterpret_cast<zt*>(dU_);

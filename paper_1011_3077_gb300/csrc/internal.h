@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/eigdc.h"
 
 namespace eigdc {
@@ -15,6 +17,15 @@ namespace eigdc {
 // Running count of kernel launches made by this library (all launchers add
 // to it); read through eig_kernel_launches().
 void note_launches(unsigned long long k);
+
+// NVTX range for the lifetime of a scope (a no-op unless a profiler is attached):
+// "eig.solve", "eig.node", "eig.irs", "eig.qr", "eig.split", "eig.leaves", ...
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------- api.cu host helpers
 // (u1, u2) of Philox pair 0 of (purpose, stream, attempt): u1 in (0, 1), u2 in [0, 1).

@@ -227,6 +227,7 @@ __global__ void diag_kernel(int n, const zt* __restrict__ T, int ldt, zt* __rest
 
 int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, int ldq,
           const double* dwi, double* dV_, int ldv, double* dlam_, std::string* err) {
+  NvtxRange nvtx_("eig.trevc");
   zt* dV = reinterpret_cast<zt*>(dV_);
   zt* dlam = reinterpret_cast<zt*>(dlam_);
   std::vector<void*> owned;
