@@ -45,6 +45,7 @@ typedef struct eig_handle_s* eig_handle_t;
 #define EIG_NEAR_SINGULAR_PENCIL 3 /* a pencil leaf's factorised matrix is near singular (Sec. 3.5) */
 #define EIG_NONFINITE 4       /* NaN/Inf met in an input or an iterate */
 #define EIG_TIMEOUT 5         /* eig_server_wait: the request did not finish in time */
+#define EIG_CANCELLED 6       /* a server request removed from the queue by eig_server_cancel */
 
 /* arithmetic of the contractions */
 #define EIG_FP64 0
@@ -129,6 +130,13 @@ typedef struct {
   int leaves;
   double flops;         /* algorithmic flops executed (formula counts, see bench) */
 } eig_solve_info_t;
+
+/* Host-side fault injection: the next `count` workspace allocations of any
+ * handle fail as if cudaMalloc had, so the call returns EIG_ERR_NOMEM (a
+ * server request then completes with that status).  0 switches it off.
+ * Returns the previous pending count, or EIG_ERR_ARG for count < 0.  No GPU
+ * work is involved; for tests of the failure paths. */
+int eig_debug_fail_allocations(int count);
 
 /* Defaults: tau = max(1e-14, 4 sqrt(n) 2^-53) at call time, maxit = 60,
  * split_tol = 0 (automatic), leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
@@ -290,6 +298,11 @@ int eig_server_poll(eig_server_t srv, uint64_t ticket, int* done, int* status, d
                     eig_solve_info_t* info);
 /* Block until the request is done (EIG_TIMEOUT after timeout_s seconds). */
 int eig_server_wait(eig_server_t srv, uint64_t ticket, double timeout_s, int* status);
+/* Cancel a request that is still queued: it is removed, reported done with
+ * status EIG_CANCELLED, and its buffers are not touched.  Returns 1 if it was
+ * cancelled, 0 if it had already been admitted (a running solve is not
+ * interrupted) or had finished, EIG_ERR_ARG for an unknown ticket. */
+int eig_server_cancel(eig_server_t srv, uint64_t ticket);
 int eig_server_stats(eig_server_t srv, unsigned long long* completed, unsigned long long* pending,
                      double* reserved_gb, double* peak_reserved_gb);
 /* Stop the workers (a running request finishes first, queued ones are

@@ -121,6 +121,17 @@ struct Arena {
   }
 };
 
+// Host-side fault injection: the next g_fail_allocs workspace allocations fail
+// as if cudaMalloc had (eig_debug_fail_allocations).
+static std::atomic<int> g_fail_allocs{0};
+
+static bool injected_alloc_failure() {
+  int v = g_fail_allocs.load();
+  while (v > 0)
+    if (g_fail_allocs.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+
 static void ensure_ws(eig_handle_t h, size_t bytes) {
   if (bytes <= h->ws_bytes) return;
   CK(cudaStreamSynchronize(h->stream));
@@ -128,7 +139,7 @@ static void ensure_ws(eig_handle_t h, size_t bytes) {
   if (h->ws) cudaFree(h->ws);
   h->ws = nullptr;
   h->ws_bytes = 0;
-  if (cudaMalloc(&h->ws, bytes) != cudaSuccess) {
+  if (injected_alloc_failure() || cudaMalloc(&h->ws, bytes) != cudaSuccess) {
     cudaGetLastError();
     h->ws = nullptr;
     h->err = "workspace allocation of " + std::to_string(bytes) + " bytes failed";
@@ -1713,6 +1724,11 @@ int eigdc::choose_k_host(const double* e, int n) { return choose_k(e, n); }
 // =================================================================== C-ABI
 extern "C" {
 
+int eig_debug_fail_allocations(int count) {
+  if (count < 0) return EIG_ERR_ARG;
+  return g_fail_allocs.exchange(count);
+}
+
 void eig_default_params(eig_params_t* p) {
   if (!p) return;
   p->tau = 0.0;
@@ -2530,6 +2546,24 @@ int eig_server_poll(eig_server_t S, uint64_t ticket, int* done, int* status, dou
     if (info) *info = r->info;
   }
   return EIG_OK;
+}
+
+int eig_server_cancel(eig_server_t S, uint64_t ticket) {
+  if (!S) return EIG_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    Request* r = find_request(S, ticket);
+    if (!r) return EIG_ERR_ARG;
+    auto it = std::find(S->queue.begin(), S->queue.end(), r);
+    if (it == S->queue.end()) return 0;   // started or finished: left to run
+    S->queue.erase(it);
+    r->status = EIG_CANCELLED;
+    r->t_start = r->t_end = now_s();
+    r->done = true;
+  }
+  S->cv_done.notify_all();
+  S->cv_work.notify_all();   // the new head of the queue may fit the budget
+  return 1;
 }
 
 int eig_server_wait(eig_server_t S, uint64_t ticket, double timeout_s, int* status) {

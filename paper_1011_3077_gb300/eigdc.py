@@ -28,6 +28,7 @@ EIG_NO_SPLIT = 2
 EIG_NEAR_SINGULAR_PENCIL = 3
 EIG_NONFINITE = 4
 EIG_TIMEOUT = 5
+EIG_CANCELLED = 6
 
 EIG_REGION_UNIT_CIRCLE = 0
 EIG_REGION_CIRCLE = 1
@@ -131,6 +132,8 @@ _SIGNATURES = {
                               ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(_D),
                               ctypes.POINTER(_D)]),
     "eig_server_destroy": (_I, [_P]),
+    "eig_server_cancel": (_I, [_P, _U64]),
+    "eig_debug_fail_allocations": (_I, [_I]),
     "eig_qr": (_I, [_P, _I, _I, _P, _I, _P, _I, _P, _I]),
     "eig_gaussian": (_I, [_P, _I, _I, _U64, _I, _U64, _I, _P, _I]),
     "eig_haar": (_I, [_P, _I, _U64, _I, _U64, _I, _P, _I]),
@@ -378,6 +381,11 @@ class Server:
         rc = lib().eig_server_wait(self._s, ticket, timeout_s, ctypes.byref(st))
         return rc, st.value
 
+    def cancel(self, ticket):
+        """1 if the queued request was removed (status EIG_CANCELLED), 0 if it
+        had already started or finished."""
+        return lib().eig_server_cancel(self._s, ticket)
+
     def stats(self):
         c = ctypes.c_ulonglong()
         q = ctypes.c_ulonglong()
@@ -589,3 +597,9 @@ def cplane_draw_line(seed, node, attempt, c, R, perpendicular_to=None):
     if rc != EIG_OK:
         raise EigError(rc, "eig_cplane_draw_line: invalid argument")
     return complex(wr.value, wi.value), t.value
+
+
+def eig_debug_fail_allocations(count):
+    """Host-side fault injection: the next `count` workspace allocations fail
+    (EIG_ERR_NOMEM).  Returns the previous pending count."""
+    return int(lib().eig_debug_fail_allocations(int(count)))

@@ -74,3 +74,13 @@ def test_struct_layout_matches_c_compiler(built, tmp_path):
             eigdc.SolveInfo.flops.offset, ctypes.sizeof(eigdc.Enclosure),
             eigdc.Enclosure.nhp.offset, eigdc.Enclosure.t.offset]
     assert got == want
+
+
+def test_fail_allocation_switch(built):
+    """The host-side fault-injection switch (no GPU work)."""
+    from paper_1011_3077_gb300 import eigdc
+    assert eigdc.eig_debug_fail_allocations(0) >= 0
+    assert eigdc.eig_debug_fail_allocations(2) == 0
+    assert eigdc.eig_debug_fail_allocations(0) == 2
+    assert eigdc.eig_debug_fail_allocations(-1) == eigdc.EIG_ERR_ARG
+    assert eigdc.eig_debug_fail_allocations(0) == 0
