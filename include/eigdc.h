@@ -435,7 +435,11 @@ typedef struct {
  *   - dA (lda >= n), dT (ldt >= n), dU (ldu >= n): device, complex; dw: device,
  *     n complex.  dA is not modified.
  *   - params: tau, maxit, split_tol (0: max(1e-12, 16 n 2^-53)), leaf_size,
- *     seed, max_fail, v_draws are used; every contraction runs in FP64.
+ *     seed, max_fail, v_draws and prec are used.  EIG_FP64: every contraction
+ *     on the FP64 pipe; EIG_FP64_TC: products with every dimension >= 128 (and
+ *     m n k >= 2^25) run as four FP64-accurate tensor-core products of the
+ *     real and imaginary planes (as eig_gemm_fp64tc); EIG_SPLIT_BF16X3 runs
+ *     as EIG_FP64.
  *   - enclose = 1: a node that fails max_fail times is returned as a cluster:
  *     its block is put in Schur form by the leaf solver and its region is
  *     written to enc[i] (up to enc_cap entries; *n_enc = number of clusters).

@@ -798,6 +798,77 @@ HalfPlane draw_line(const Region& g, uint64_t seed, uint64_t node, int attempt, 
   return make_line(g, u1, u2, has_perp, pr, pi_);
 }
 
+// ------------------------------------------------------------------ tensor-core route
+// EIG_FP64_TC: a large complex product as four FP64-accurate tensor-core
+// products of the real and imaginary planes (tcx_gemm, the error-free
+// nine-digit split), op(A) = op(Ar) + i sa op(Ai) with sa = -1 for A^H:
+//   op(A) op(B) = op(Ar)op(Br) - sa sb op(Ai)op(Bi) + i (sb op(Ar)op(Bi) + sa op(Ai)op(Br)).
+struct ZTc {
+  bool on = false;
+  double* planes = nullptr;   // Ar Ai Br Bi P1 P2 P3 P4, `plane` doubles each
+  size_t plane = 0;
+  void* ws = nullptr;
+  int* err = nullptr;         // bounded-wait error word of the tensor-core kernel
+};
+
+__global__ void zsplit_kernel(int rows, int cols, const zt* __restrict__ A, int lda,
+                              double* __restrict__ re, double* __restrict__ im) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int i = (int)(e % rows), j = (int)(e / rows);
+  const zt v = A[i + (size_t)j * lda];
+  re[e] = v.x;
+  im[e] = v.y;
+}
+
+// C = alpha (P1 - ss P2 + i (sb P3 + sa P4)) + beta C, alpha and beta real
+__global__ void zcombine_kernel(int m, int n, double ss, double sa, double sb, double alpha,
+                                double beta, const double* __restrict__ P1,
+                                const double* __restrict__ P2, const double* __restrict__ P3,
+                                const double* __restrict__ P4, zt* __restrict__ C, int ldc) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * n) return;
+  const int i = (int)(e % m), j = (int)(e / m);
+  zt v = zmk(alpha * (P1[e] - ss * P2[e]), alpha * (sb * P3[e] + sa * P4[e]));
+  if (beta != 0.0) v = zadd(v, zscale(beta, C[i + (size_t)j * ldc]));
+  C[i + (size_t)j * ldc] = v;
+}
+
+bool ztc_worth(const ZTc& tc, int m, int n, int k, zt alpha, zt beta) {
+  return tc.on && m >= 128 && n >= 128 && k >= 128 && (double)m * n * k >= 33554432.0 &&
+         alpha.y == 0.0 && beta.y == 0.0 && (size_t)m * k <= tc.plane &&
+         (size_t)k * n <= tc.plane && (size_t)m * n <= tc.plane;
+}
+
+// zgemm, or the tensor-core route for large products when it is on
+cudaError_t zmm(cudaStream_t s, const ZTc& tc, bool ta, bool tb, int m, int n, int k, zt alpha,
+                const zt* A, int lda, const zt* B, int ldb, zt beta, zt* C, int ldc) {
+  if (!ztc_worth(tc, m, n, k, alpha, beta))
+    return zgemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  const int ra = ta ? k : m, ca = ta ? m : k, rb = tb ? n : k, cb = tb ? k : n;
+  double* Ar = tc.planes;
+  double* Ai = Ar + tc.plane;
+  double* Br = Ai + tc.plane;
+  double* Bi = Br + tc.plane;
+  double* P1 = Bi + tc.plane;
+  double* P2 = P1 + tc.plane;
+  double* P3 = P2 + tc.plane;
+  double* P4 = P3 + tc.plane;
+  note_launches(2);
+  zsplit_kernel<<<nblocks((long long)ra * ca, 256), 256, 0, s>>>(ra, ca, A, lda, Ar, Ai);
+  zsplit_kernel<<<nblocks((long long)rb * cb, 256), 256, 0, s>>>(rb, cb, B, ldb, Br, Bi);
+  cudaError_t e;
+  if ((e = tcx_gemm(s, ta, tb, m, n, k, 1.0, Ar, ra, Br, rb, 0.0, P1, m, tc.ws, tc.err)) != cudaSuccess) return e;
+  if ((e = tcx_gemm(s, ta, tb, m, n, k, 1.0, Ai, ra, Bi, rb, 0.0, P2, m, tc.ws, tc.err)) != cudaSuccess) return e;
+  if ((e = tcx_gemm(s, ta, tb, m, n, k, 1.0, Ar, ra, Bi, rb, 0.0, P3, m, tc.ws, tc.err)) != cudaSuccess) return e;
+  if ((e = tcx_gemm(s, ta, tb, m, n, k, 1.0, Ai, ra, Br, rb, 0.0, P4, m, tc.ws, tc.err)) != cudaSuccess) return e;
+  const double sa = ta ? -1.0 : 1.0, sb = tb ? -1.0 : 1.0;
+  note_launches(1);
+  zcombine_kernel<<<nblocks((long long)m * n, 256), 256, 0, s>>>(m, n, sa * sb, sa, sb, alpha.x, beta.x,
+                                                               P1, P2, P3, P4, C, ldc);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ driver (host)
 struct ZFail {
   int code;
@@ -848,9 +919,10 @@ struct StepBufs {
   zt *Vh, *X, *U, *Ur, *S, *Z, *Q, *AQ, *Ahat, *R1, *R2, *tmp;
   double *Gre, *Gim, *absA, *colpart, *scores, *col1, *col2;
   ZQR q;   // V (2 cap x cap), T, tau, phases, W1, W2, gram
+  ZTc tc;  // tensor-core route of the large products (EIG_FP64_TC)
 };
 
-void make_bufs(CDriver& D, StepBufs& b, int cap) {
+void make_bufs(CDriver& D, StepBufs& b, int cap, bool tensor_cores) {
   const size_t c2 = (size_t)cap * cap;
   b.cap = cap;
   b.A0 = D.alloc<zt>(c2); b.B0 = D.alloc<zt>(c2); b.A1 = D.alloc<zt>(c2); b.B1 = D.alloc<zt>(c2);
@@ -873,6 +945,26 @@ void make_bufs(CDriver& D, StepBufs& b, int cap) {
   b.q.W1 = D.alloc<zt>((size_t)ZNB * cap);
   b.q.W2 = D.alloc<zt>((size_t)ZNB * cap);
   b.q.gram = D.alloc<zt>((size_t)nblocks(2 * cap, 64) * 1024);
+  if (tensor_cores && cap >= 128) {
+    b.tc.on = true;
+    b.tc.plane = c2;
+    b.tc.planes = D.alloc<double>(8 * c2);
+    b.tc.ws = D.alloc<char>(tcx_gemm_workspace_bytes(cap, cap, cap));
+    b.tc.err = D.alloc<int>(1);
+    D.check(cudaMemsetAsync(b.tc.err, 0, sizeof(int), D.s), "tensor-core error word");
+  }
+}
+
+// The tensor-core kernel's bounded waits report through b.tc.err.
+void check_tc(CDriver& D, StepBufs& b) {
+  if (!b.tc.on) return;
+  int e = 0;
+  D.check(cudaMemcpyAsync(&e, b.tc.err, sizeof(int), cudaMemcpyDeviceToHost, D.s), "tensor-core error copy");
+  D.sync();
+  if (e != 0) {
+    *D.err = "tensor-core GEMM: a bounded wait timed out";
+    throw ZFail{EIG_ERR_CUDA};
+  }
 }
 
 ZQR qr_view(const StepBufs& b, int m, int n) {
@@ -967,8 +1059,8 @@ CIrs cirs(CDriver& D, StepBufs& b, int m, double tau, int maxit) {
     D.check(zgeqrf(D.s, 2 * m, m, b.W, 2 * m, q, Rc, m), "IRS QR");
     D.check(zident(D.s, 2 * m, m, m, b.E), "IRS complement");
     D.check(zapply_q(D.s, q, b.E, m, false), "IRS complement");
-    D.check(zgemm(D.s, true, false, m, m, m, one, b.E, 2 * m, Aj, m, zero, An, m), "IRS A");
-    D.check(zgemm(D.s, true, false, m, m, m, one, b.E + m, 2 * m, Bj, m, zero, Bn, m), "IRS B");
+    D.check(zmm(D.s, b.tc, true, false, m, m, m, one, b.E, 2 * m, Aj, m, zero, An, m), "IRS A");
+    D.check(zmm(D.s, b.tc, true, false, m, m, m, one, b.E + m, 2 * m, Bj, m, zero, Bn, m), "IRS B");
     if (have_prev) {
       note_launches(2);
       zcoldiff_kernel<<<m, 256, 0, D.s>>>(m, Rc, Rp, b.col1);
@@ -1037,21 +1129,21 @@ CStepOut line_step(CDriver& D, StepBufs& b, int m, const zt* A, const HalfPlane&
     D.check(zgeqrf(D.s, m, m, b.X, m, q, nullptr, m), "Haar QR");
     explicit_q(D, q, b.Vh);
     // RURV(A_p): A_p V^H = U R2
-    D.check(zgemm(D.s, false, true, m, m, m, one, irs.Ap, m, b.Vh, m, zero, b.X, m), "A_p V^H");
+    D.check(zmm(D.s, b.tc, false, true, m, m, m, one, irs.Ap, m, b.Vh, m, zero, b.X, m), "A_p V^H");
     D.check(zgeqrf(D.s, m, m, b.X, m, q, b.R2, m), "RURV QR");
     explicit_q(D, q, b.U);
     // RQ of U^H (A_p + B_p) through the QR of (A_p + B_p)^H U J
     note_launches(2);
     zadd_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>((long long)mm, irs.Ap, irs.Bp, b.S);
     zrevcols_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>(m, m, b.U, b.Ur);
-    D.check(zgemm(D.s, true, false, m, m, m, one, b.S, m, b.Ur, m, zero, b.Z, m), "(A_p+B_p)^H U J");
+    D.check(zmm(D.s, b.tc, true, false, m, m, m, one, b.S, m, b.Ur, m, zero, b.Z, m), "(A_p+B_p)^H U J");
     D.check(zgeqrf(D.s, m, m, b.Z, m, q, b.R1, m), "RQ via QR");
     explicit_q(D, q, b.Ur);
     note_launches(1);
     zrevcols_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>(m, m, b.Ur, b.Q);
     // similarity and split test
-    D.check(zgemm(D.s, false, false, m, m, m, one, A, m, b.Q, m, zero, b.AQ, m), "A Q");
-    D.check(zgemm(D.s, true, false, m, m, m, one, b.Q, m, b.AQ, m, zero, b.Ahat, m), "Q^H A Q");
+    D.check(zmm(D.s, b.tc, false, false, m, m, m, one, A, m, b.Q, m, zero, b.AQ, m), "A Q");
+    D.check(zmm(D.s, b.tc, true, false, m, m, m, one, b.Q, m, b.AQ, m, zero, b.Ahat, m), "Q^H A Q");
     note_launches(1);
     zabs_kernel<<<nblocks((long long)mm, 256), 256, 0, D.s>>>((long long)mm, b.Ahat, b.absA);
     if (m >= 2)
@@ -1118,7 +1210,7 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
     CDriver D{s, err, {}};
     const int leaf = std::max(1, std::min(p.leaf_size > 0 ? p.leaf_size : 64, ZLEAF_MAX));
     StepBufs b;
-    if (n > leaf) make_bufs(D, b, n);
+    if (n > leaf) make_bufs(D, b, n, p.prec == EIG_FP64_TC);
     zt* tmpU = D.alloc<zt>((size_t)n * n);
     note_launches(1);
     zident_ld_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, n, dU, ldu);
@@ -1158,11 +1250,12 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
                                       plan.pi_);
         const CStepOut st = line_step(D, b, m, nd.A, L, plan.reg.R, p.seed, nd.id, plan.attempt, tau,
                                       maxit, stol, p.v_draws);
+        check_tc(D, b);
         inf.total_iters += st.iters;
         if (st.accepted) {
           const int k = st.k;
-          D.check(zgemm(s, false, false, n, m, m, one, dU + (size_t)nd.off * ldu, ldu, b.Q, m, zero,
-                        tmpU, n), "U update");
+          D.check(zmm(s, b.tc, false, false, n, m, m, one, dU + (size_t)nd.off * ldu, ldu, b.Q, m,
+                      zero, tmpU, n), "U update");
           D.check(zcopy(s, n, m, tmpU, n, dU + (size_t)nd.off * ldu, ldu), "U update");
           zt* A11 = D.alloc<zt>((size_t)k * k);
           zt* A22 = D.alloc<zt>((size_t)(m - k) * (m - k));
@@ -1231,12 +1324,13 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
         D.check(cudaMemcpyAsync(hst.data(), dstat, sizeof(int) * nl, cudaMemcpyDeviceToHost, s), "leaf status");
       // T = triu(U^H A U), w = diag(T)
       zt* AU = D.alloc<zt>((size_t)n * n);
-      D.check(zgemm(s, false, false, n, n, n, one, dA, lda, dU, ldu, zero, AU, n), "A U");
-      D.check(zgemm(s, true, false, n, n, n, one, dU, ldu, AU, n, zero, tmpU, n), "U^H A U");
+      D.check(zmm(s, b.tc, false, false, n, n, n, one, dA, lda, dU, ldu, zero, AU, n), "A U");
+      D.check(zmm(s, b.tc, true, false, n, n, n, one, dU, ldu, AU, n, zero, tmpU, n), "U^H A U");
       note_launches(1);
       ztriu_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, tmpU, n, dT, ldt, dw);
       D.check(cudaGetLastError(), "triangle");
       D.sync();
+      check_tc(D, b);
       for (int i = 0; i < nl; ++i)
         if (hst[i] != 0) status = EIG_NO_CONVERGENCE;
     }

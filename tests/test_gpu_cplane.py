@@ -138,3 +138,22 @@ def test_argument_errors(E):
     assert rc == eigdc.EIG_ERR_ARG
     rc, info, enc = eigdc.eig_schur_complex(h, 4, dA, 3, dA, 4, dA, 4, dA, eigdc.default_params())
     assert rc == eigdc.EIG_ERR_ARG
+
+
+def test_tensor_core_route_matches_fp64(E):
+    """EIG_FP64_TC: the large complex products run as four FP64-accurate
+    tensor-core products each; same recursion and FP64 targets as EIG_FP64."""
+    eigdc, h, torch = E
+    rng = np.random.default_rng(401)
+    n = 400
+    lam = _crandn(rng, n)
+    A = _prescribed(lam, rng)
+    res = {}
+    for prec in (eigdc.EIG_FP64, eigdc.EIG_FP64_TC):
+        p = eigdc.default_params(seed=5, leaf_size=64, prec=prec)
+        rc, T, U, w, info, _ = eigdc.schur_complex(h, A, p)
+        assert rc == eigdc.EIG_OK
+        _check(A, T, U)
+        assert _match(w, lam) <= 1e-10
+        res[prec] = info
+    assert res[eigdc.EIG_FP64].splits == res[eigdc.EIG_FP64_TC].splits
