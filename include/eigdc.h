@@ -450,6 +450,34 @@ int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* 
                       double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,
                       eig_enclosure_t* enc, int enc_cap, int* n_enc, eig_solve_info_t* info);
 
+/* The single steps of the complex path (interleaved complex, column-major,
+ * device pointers; calls synchronize the handle's stream):
+ *   eig_zgemm: C = alpha op(A) op(B) + beta C, op = X (0) or X^H (1), DFMA.
+ *   eig_zqr: X = Q R for m >= n: Q (m x n, orthonormal columns), R (n x n,
+ *     upper triangular with a real non-negative diagonal: the unique QR of a
+ *     full-rank X); dR may be NULL.
+ *   eig_zhaar: the Haar unitary of (seed, stream, attempt): the Q factor of
+ *     G = X + i Y, X and Y the Philox N(0,1) draws of purposes 4 and 7.
+ *   eig_zline_step: one step on the line Re(conj(w) z) = t with scale s
+ *     (|w| = 1, s > 0): the rotated Moebius map, IRS, the splitter
+ *     Q = GRURV(2, A_p + B_p, A_p, -1, +1) with the Haar draws of (seed,
+ *     stream, attempt), A^ = Q^H A Q and the split test; dQ and dAhat (either
+ *     may be NULL) receive Q and A^, info the iteration count, k, e(k), rank
+ *     and draw.  Returns EIG_OK for an accepted split, EIG_NO_SPLIT when IRS
+ *     converged without one, EIG_NO_CONVERGENCE when it hit maxit.  Only the
+ *     leading k columns of Q are unique (the rest are a basis of the
+ *     complementary invariant subspace that rounding picks). */
+int eig_zgemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha_re,
+              double alpha_im, const double* dA, int lda, const double* dB, int ldb,
+              double beta_re, double beta_im, double* dC, int ldc);
+int eig_zqr(eig_handle_t h, int m, int n, const double* dX, int ldx, double* dQ, int ldq,
+            double* dR, int ldr);
+int eig_zhaar(eig_handle_t h, int n, uint64_t seed, uint64_t stream, int attempt, double* dV,
+              int ldv);
+int eig_zline_step(eig_handle_t h, int n, const double* dA, int lda, double w_re, double w_im,
+                   double t, double s, uint64_t stream, int attempt, const eig_params_t* params,
+                   double* dQ, int ldq, double* dAhat, int ldah, eig_step_info_t* info);
+
 /* Host-only helpers of the Sec. 3.3 strategy (no GPU or handle needed).
  * eig_cplane_enclosing_circle: a circle (m, r) holding the region
  * {|z - c| <= R} cut by the nhp half-planes Re(conj(w_i) z) >= t_i: the

@@ -2030,6 +2030,61 @@ int eig_eigenvectors(eig_handle_t h, int n, const double* dT, int ldt, const dou
   API_END
 }
 
+int eig_zgemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha_re,
+              double alpha_im, const double* dA, int lda, const double* dB, int ldb,
+              double beta_re, double beta_im, double* dC, int ldc) {
+  API_BEGIN
+  REQUIRE(m >= 0 && n >= 0 && k >= 0, "negative size");
+  REQUIRE(dA && dB && dC, "NULL matrix");
+  REQUIRE(lda >= std::max(1, ta ? k : m) && ldb >= std::max(1, tb ? n : k) && ldc >= std::max(1, m),
+          "leading dimension too small");
+  CK(cplane_zgemm(h->stream, ta != 0, tb != 0, m, n, k, alpha_re, alpha_im, dA, lda, dB, ldb,
+                  beta_re, beta_im, dC, ldc));
+  CK(cudaStreamSynchronize(h->stream));
+  return EIG_OK;
+  API_END
+}
+
+int eig_zqr(eig_handle_t h, int m, int n, const double* dX, int ldx, double* dQ, int ldq,
+            double* dR, int ldr) {
+  API_BEGIN
+  REQUIRE(m >= 1 && n >= 1 && m >= n, "need m >= n >= 1");
+  REQUIRE(dX && ldx >= m && dQ && ldq >= m && (!dR || ldr >= n), "matrix / leading dimension invalid");
+  std::string err;
+  const int rc = cplane_qr(h->stream, m, n, dX, ldx, dQ, ldq, dR, ldr, &err);
+  if (rc < 0) h->err = err;
+  return rc;
+  API_END
+}
+
+int eig_zhaar(eig_handle_t h, int n, uint64_t seed, uint64_t stream, int attempt, double* dV,
+              int ldv) {
+  API_BEGIN
+  REQUIRE(n >= 1 && dV && ldv >= n, "dV / ldv invalid");
+  std::string err;
+  const int rc = cplane_haar(h->stream, n, seed, stream, attempt, dV, ldv, &err);
+  if (rc < 0) h->err = err;
+  return rc;
+  API_END
+}
+
+int eig_zline_step(eig_handle_t h, int n, const double* dA, int lda, double w_re, double w_im,
+                   double t, double s, uint64_t stream, int attempt, const eig_params_t* params,
+                   double* dQ, int ldq, double* dAhat, int ldah, eig_step_info_t* info) {
+  API_BEGIN
+  REQUIRE(n >= 2, "n must be >= 2");
+  REQUIRE(dA && lda >= n && (!dQ || ldq >= n) && (!dAhat || ldah >= n), "matrix / leading dimension invalid");
+  REQUIRE(s > 0.0 && std::fabs(std::hypot(w_re, w_im) - 1.0) <= 1e-12, "need s > 0 and |w| = 1");
+  const eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  std::string err;
+  const int rc = cplane_step(h->stream, n, dA, lda, w_re, w_im, t, s, p, stream, attempt, dQ, ldq,
+                             dAhat, ldah, info, &err);
+  if (rc < 0) h->err = err;
+  return rc;
+  API_END
+}
+
 int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* dT, int ldt,
                       double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,
                       eig_enclosure_t* enc, int enc_cap, int* n_enc, eig_solve_info_t* info) {

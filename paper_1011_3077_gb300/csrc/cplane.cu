@@ -1342,6 +1342,113 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
   if (info) *info = inf;
   return status;
 }
+
+// ------------------------------------------------------------------ building blocks
+// The single steps of the complex path, for tests and callers that compose
+// their own recursion (the complex counterparts of eig_qr, eig_haar and
+// eig_divide_step + eig_split).
+
+int cplane_qr(cudaStream_t s, int m, int n, const double* dX_, int ldx, double* dQ_, int ldq,
+              double* dR_, int ldr, std::string* err) {
+  int status = EIG_OK;
+  try {
+    CDriver D{s, err, {}};
+    StepBufs b;
+    const int cap = std::max(m, n);
+    // the QR buffers of a node of size cap hold an m x n factorisation with m <= 2 cap
+    b.q.V = D.alloc<zt>((size_t)m * n);
+    b.q.T = D.alloc<zt>((size_t)ZNB * (nblocks(n, ZNB) * ZNB));
+    b.q.tau = D.alloc<double>(n);
+    b.q.phases = D.alloc<zt>(n);
+    b.q.W1 = D.alloc<zt>((size_t)ZNB * cap);
+    b.q.W2 = D.alloc<zt>((size_t)ZNB * cap);
+    b.q.gram = D.alloc<zt>((size_t)nblocks(m, 64) * 1024);
+    zt* P = D.alloc<zt>((size_t)m * n);
+    D.check(zcopy(s, m, n, reinterpret_cast<const zt*>(dX_), ldx, P, m), "input copy");
+    ZQR q = b.q;
+    q.m = m;
+    q.n = n;
+    zt* R = D.alloc<zt>((size_t)n * n);
+    D.check(zgeqrf(s, m, n, P, m, q, R, n), "QR");
+    zt* Qp = D.alloc<zt>((size_t)m * n);
+    D.check(zident(s, m, n, 0, Qp), "explicit Q");
+    D.check(zapply_q(s, q, Qp, n, true), "explicit Q");
+    D.check(zcopy(s, m, n, Qp, m, reinterpret_cast<zt*>(dQ_), ldq), "Q copy");
+    if (dR_) D.check(zcopy(s, n, n, R, n, reinterpret_cast<zt*>(dR_), ldr), "R copy");
+    D.sync();
+  } catch (ZFail f) {
+    status = f.code;
+  }
+  return status;
+}
+
+int cplane_haar(cudaStream_t s, int n, uint64_t seed, uint64_t node, int attempt, double* dV_,
+                int ldv, std::string* err) {
+  int status = EIG_OK;
+  try {
+    CDriver D{s, err, {}};
+    double* Gre = D.alloc<double>((size_t)n * n);
+    double* Gim = D.alloc<double>((size_t)n * n);
+    zt* G = D.alloc<zt>((size_t)n * n);
+    D.check(gaussian(s, n, n, seed, PURPOSE_HAAR_RE, node, attempt, Gre, n), "Haar draw");
+    D.check(gaussian(s, n, n, seed, PURPOSE_HAAR_IM, node, attempt, Gim, n), "Haar draw");
+    note_launches(1);
+    zinterleave_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>((long long)n * n, Gre, Gim, G);
+    D.check(cudaGetLastError(), "Haar interleave");
+    // the Haar unitary is the Q factor of G with a non-negative real diagonal of R
+    const int rc = cplane_qr(s, n, n, reinterpret_cast<const double*>(G), n, dV_, ldv, nullptr, 0, err);
+    if (rc != EIG_OK) throw ZFail{rc};
+  } catch (ZFail f) {
+    status = f.code;
+  }
+  return status;
+}
+
+int cplane_step(cudaStream_t s, int n, const double* dA_, int lda, double w_re, double w_im,
+                double t, double sc, const eig_params_t& p, uint64_t node, int attempt,
+                double* dQ_, int ldq, double* dAhat_, int ldah, eig_step_info_t* info,
+                std::string* err) {
+  int status = EIG_OK;
+  try {
+    CDriver D{s, err, {}};
+    StepBufs b;
+    make_bufs(D, b, n, p.prec == EIG_FP64_TC);
+    zt* A = D.alloc<zt>((size_t)n * n);
+    D.check(zcopy(s, n, n, reinterpret_cast<const zt*>(dA_), lda, A, n), "input copy");
+    const double tau = p.tau > 0.0 ? p.tau : std::max(1e-14, 4.0 * std::sqrt((double)n) * 0x1p-53);
+    const double stol = p.split_tol > 0.0 ? p.split_tol : std::max(1e-12, 16.0 * n * 0x1p-53);
+    HalfPlane L;
+    L.wr = w_re;
+    L.wi = w_im;
+    L.t = t;
+    const CStepOut st = line_step(D, b, n, A, L, sc, p.seed, node, attempt, tau, p.maxit, stol,
+                                  p.v_draws);
+    check_tc(D, b);
+    if (dQ_) D.check(zcopy(s, n, n, b.Q, n, reinterpret_cast<zt*>(dQ_), ldq), "Q copy");
+    if (dAhat_) D.check(zcopy(s, n, n, b.Ahat, n, reinterpret_cast<zt*>(dAhat_), ldah), "A^ copy");
+    D.sync();
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->iters = st.iters;
+      info->converged = st.converged ? 1 : 0;
+      info->k = st.k;
+      info->split_residual = st.e;
+      info->rank = st.rank;
+      info->draw = st.draw;
+    }
+    status = st.accepted ? EIG_OK : (st.converged ? EIG_NO_SPLIT : EIG_NO_CONVERGENCE);
+  } catch (ZFail f) {
+    status = f.code;
+  }
+  return status;
+}
+
+cudaError_t cplane_zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double ar,
+                         double ai, const double* A, int lda, const double* B, int ldb, double br,
+                         double bi, double* C, int ldc) {
+  return zgemm(s, ta, tb, m, n, k, zmk(ar, ai), reinterpret_cast<const zt*>(A), lda,
+               reinterpret_cast<const zt*>(B), ldb, zmk(br, bi), reinterpret_cast<zt*>(C), ldc);
+}
 }  // namespace eigdc
 
 // ------------------------------------------------------------------ host-only C-ABI helpers

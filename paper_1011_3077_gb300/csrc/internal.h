@@ -191,6 +191,22 @@ struct CplaneCluster {
   double cr, ci, R;                    // disk
   std::vector<CplaneHalfPlane> hp;     // half-planes cutting it
 };
+// Building blocks of the complex path (interleaved complex, column-major):
+// QR with explicit Q (m x n) and R (n x n, real non-negative diagonal); the
+// Haar unitary of Philox purposes 4 (real) and 7 (imaginary); one step on the
+// line Re(conj(w) z) = t with scale sc (EIG_OK: accepted split, EIG_NO_SPLIT:
+// converged without one, EIG_NO_CONVERGENCE: IRS hit maxit).
+int cplane_qr(cudaStream_t s, int m, int n, const double* dX, int ldx, double* dQ, int ldq,
+              double* dR, int ldr, std::string* err);
+int cplane_haar(cudaStream_t s, int n, uint64_t seed, uint64_t node, int attempt, double* dV,
+                int ldv, std::string* err);
+int cplane_step(cudaStream_t s, int n, const double* dA, int lda, double w_re, double w_im,
+                double t, double sc, const eig_params_t& p, uint64_t node, int attempt,
+                double* dQ, int ldq, double* dAhat, int ldah, eig_step_info_t* info,
+                std::string* err);
+cudaError_t cplane_zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double ar,
+                         double ai, const double* A, int lda, const double* B, int ldb, double br,
+                         double bi, double* C, int ldc);
 // C = alpha op(A) op(B) + beta C over C (op = X or X^H), DFMA, 64 x 64 tiles.
 cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double2 alpha,
                   const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C,

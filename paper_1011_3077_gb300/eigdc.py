@@ -144,6 +144,11 @@ _SIGNATURES = {
     "eig_gemm_fp64tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_eigenvectors": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, _P]),
+    "eig_zgemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _D, _P, _I, _P, _I, _D, _D, _P, _I]),
+    "eig_zqr": (_I, [_P, _I, _I, _P, _I, _P, _I, _P, _I]),
+    "eig_zhaar": (_I, [_P, _I, _U64, _U64, _I, _P, _I]),
+    "eig_zline_step": (_I, [_P, _I, _P, _I, _D, _D, _D, _D, _U64, _I, ctypes.POINTER(Params),
+                            _P, _I, _P, _I, ctypes.POINTER(StepInfo)]),
     "eig_schur_complex": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(Params), _I,
                                ctypes.POINTER(Enclosure), _I, ctypes.POINTER(_I),
                                ctypes.POINTER(SolveInfo)]),
@@ -554,6 +559,31 @@ def eig_schur_complex(h, n, dA, lda, dT, ldt, dU, ldu, dw, params, enclose=False
                                  ctypes.byref(params), 1 if enclose else 0, enc, enc_cap,
                                  ctypes.byref(n_enc), ctypes.byref(info))
     return rc, info, [enc[i] for i in range(min(n_enc.value, enc_cap))]
+
+
+def eig_zgemm(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
+    alpha, beta = complex(alpha), complex(beta)
+    return lib().eig_zgemm(h.ptr, int(ta), int(tb), m, n, k, alpha.real, alpha.imag, _ptr(dA), lda,
+                           _ptr(dB), ldb, beta.real, beta.imag, _ptr(dC), ldc)
+
+
+def eig_zqr(h, m, n, dX, ldx, dQ, ldq, dR=None, ldr=0):
+    return lib().eig_zqr(h.ptr, m, n, _ptr(dX), ldx, _ptr(dQ), ldq, _ptr(dR), ldr)
+
+
+def eig_zhaar(h, n, seed, stream, attempt, dV, ldv):
+    return lib().eig_zhaar(h.ptr, n, int(seed), int(stream), int(attempt), _ptr(dV), ldv)
+
+
+def eig_zline_step(h, n, dA, lda, w, t, s, stream, attempt, params, dQ=None, ldq=0, dAhat=None,
+                   ldah=0):
+    """One complex-plane step; returns (rc, StepInfo)."""
+    info = StepInfo()
+    w = complex(w)
+    rc = lib().eig_zline_step(h.ptr, n, _ptr(dA), lda, w.real, w.imag, float(t), float(s),
+                              int(stream), int(attempt), ctypes.byref(params), _ptr(dQ), ldq,
+                              _ptr(dAhat), ldah, ctypes.byref(info))
+    return rc, info
 
 
 def schur_complex(h, A, params=None, enclose=False):

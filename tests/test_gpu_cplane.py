@@ -157,3 +157,86 @@ def test_tensor_core_route_matches_fp64(E):
         assert _match(w, lam) <= 1e-10
         res[prec] = info
     assert res[eigdc.EIG_FP64].splits == res[eigdc.EIG_FP64_TC].splits
+
+
+# ------------------------------------------------------------ building blocks
+
+def _dev(torch, A, ld=None):
+    """complex numpy (rows x cols) -> device column-major with leading dimension ld."""
+    rows, cols = A.shape
+    ld = ld or rows
+    buf = np.zeros((cols, ld), dtype=np.complex128)
+    buf[:, :rows] = A.T
+    return torch.from_numpy(buf).to("cuda")
+
+
+def _host(t, rows):
+    return t.cpu().numpy().T[:rows].copy()
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_zgemm_against_numpy(E, ta, tb):
+    eigdc, h, torch = E
+    rng = np.random.default_rng(500 + 2 * ta + tb)
+    m, n, k = 70, 37, 19
+    A = _crandn(rng, k, m) if ta else _crandn(rng, m, k)
+    B = _crandn(rng, n, k) if tb else _crandn(rng, k, n)
+    C = _crandn(rng, m, n)
+    alpha, beta = 0.5 - 1j, 0.25 + 0.5j
+    dA, dB, dC = _dev(torch, A, A.shape[0] + 3), _dev(torch, B, B.shape[0] + 2), _dev(torch, C, m + 1)
+    rc = eigdc.eig_zgemm(h, ta, tb, m, n, k, alpha, dA, A.shape[0] + 3, dB, B.shape[0] + 2, beta,
+                         dC, m + 1)
+    assert rc == eigdc.EIG_OK
+    want = alpha * (A.conj().T if ta else A) @ (B.conj().T if tb else B) + beta * C
+    assert np.abs(_host(dC, m) - want).max() <= 1e-13 * np.abs(want).max() * k
+
+
+@pytest.mark.parametrize("m,n", [(100, 70), (64, 64), (300, 33), (9, 1)])
+def test_zqr_is_the_unique_factor(E, m, n):
+    eigdc, h, torch = E
+    from oracle.complex_qr import cqr_explicit
+    rng = np.random.default_rng(600 + m + n)
+    X = _crandn(rng, m, n)
+    dX = _dev(torch, X)
+    dQ = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    dR = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    assert eigdc.eig_zqr(h, m, n, dX, m, dQ, m, dR, n) == eigdc.EIG_OK
+    Qo, Ro = cqr_explicit(X)
+    assert np.abs(_host(dQ, m) - Qo).max() <= 1e-12
+    assert np.abs(_host(dR, n) - Ro).max() <= 1e-12 * np.abs(Ro).max()
+
+
+def test_zhaar_matches_the_oracle(E):
+    eigdc, h, torch = E
+    from oracle.complex_qr import chaar
+    from oracle.philox import attempt_code
+    n = 40
+    dV = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    code = attempt_code(3, 1)
+    assert eigdc.eig_zhaar(h, n, 11, 12345, code, dV, n) == eigdc.EIG_OK
+    assert np.abs(_host(dV, n) - chaar(n, 11, 12345, code)).max() <= 1e-11
+
+
+def test_zline_step_matches_the_oracle(E):
+    eigdc, h, torch = E
+    from oracle.cplane import line_step
+    rng = np.random.default_rng(41)
+    w, t, n = np.exp(0.7j), 0.2, 70
+    along = rng.uniform(-1.5, 1.5, n)
+    along[np.abs(along - t) < 0.2] += 0.5
+    lam = w * (along + 1j * rng.uniform(-1, 1, n))
+    A = _prescribed(lam, rng)
+    p = eigdc.default_params(seed=5)
+    dA = _dev(torch, A)
+    dQ = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    dAh = torch.zeros((n, n), dtype=torch.complex128, device="cuda")
+    rc, info = eigdc.eig_zline_step(h, n, dA, n, w, t, 2.0, 1, 0, p, dQ, n, dAh, n)
+    st = line_step(A, w, t, 2.0, seed=5, stream=1, attempt=0)
+    assert rc == eigdc.EIG_OK and st.accepted
+    assert (info.k, info.rank, info.iters, info.draw) == (st.k, st.rank, st.irs.iters, st.draw)
+    k = st.k
+    Ah = _host(dAh, n)
+    # the leading k columns of the splitter (and so A^11) are unique
+    assert np.abs(Ah[:k, :k] - st.Ahat[:k, :k]).max() <= 1e-10 * np.abs(A).max()
+    assert np.abs(_host(dQ, n)[:, :k] - st.Q[:, :k]).max() <= 1e-10
+    assert info.split_residual <= 1e-12 and st.e <= 1e-12
