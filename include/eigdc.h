@@ -398,6 +398,11 @@ int eig_gemm_noalloc(void* stream, int ta, int tb, int m, int n, int k, double a
  *     differences); equal ones give non-finite vectors. */
 int eig_eigenvectors(eig_handle_t h, int n, const double* dT, int ldt, const double* dQ, int ldq,
                      const double* dwi, double* dV, int ldv, double* dlam);
+/* The same from a complex Schur form A = U T U^H (interleaved complex, T upper
+ * triangular, as eig_schur_complex returns it): dV receives unit eigenvectors
+ * U X, dlam the diagonal of T. */
+int eig_eigenvectors_complex(eig_handle_t h, int n, const double* dT, int ldt, const double* dU,
+                             int ldu, double* dV, int ldv, double* dlam);
 
 /* ------------------------------------------------------ complex-plane strategy
  * Sec. 3.3: splitting lines at random angles.  The line {z : Re(conj(w) z) = t}

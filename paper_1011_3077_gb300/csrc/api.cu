@@ -2030,6 +2030,19 @@ int eig_eigenvectors(eig_handle_t h, int n, const double* dT, int ldt, const dou
   API_END
 }
 
+int eig_eigenvectors_complex(eig_handle_t h, int n, const double* dT, int ldt, const double* dU,
+                             int ldu, double* dV, int ldv, double* dlam) {
+  API_BEGIN
+  REQUIRE(n >= 1, "n must be >= 1");
+  REQUIRE(dT && ldt >= n && dU && ldu >= n, "dT / dU invalid");
+  REQUIRE(dV && ldv >= n && dlam, "dV / dlam invalid");
+  std::string err;
+  const int rc = trevc(h->stream, n, dT, ldt, dU, ldu, nullptr, dV, ldv, dlam, &err, true);
+  if (rc < 0) h->err = err;
+  return rc;
+  API_END
+}
+
 int eig_zgemm(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha_re,
               double alpha_im, const double* dA, int lda, const double* dB, int ldb,
               double beta_re, double beta_im, double* dC, int ldc) {

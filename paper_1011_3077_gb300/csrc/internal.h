@@ -221,7 +221,10 @@ int cplane_schur(cudaStream_t s, int n, const double* dA, int lda, double* dT, i
 // Eigenvectors of A = Q T Q^T from the real Schur form (T quasi-triangular in
 // standard form, wi the imaginary parts): V (n x n complex, unit columns) and
 // lam (n complex).  Returns an EIG_* status.
+// With complex_in, dT and dQ are a complex Schur form (interleaved complex,
+// T upper triangular) and dwi is not read.
 int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, int ldq,
-          const double* dwi, double* dV, int ldv, double* dlam, std::string* err);
+          const double* dwi, double* dV, int ldv, double* dlam, std::string* err,
+          bool complex_in = false);
 
 }  // namespace eigdc

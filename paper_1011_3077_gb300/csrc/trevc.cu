@@ -2,7 +2,8 @@
 // its blocked TREVC algorithm) on sm_103a.
 //
 // Input: the real Schur form A = Q T Q^T with T quasi-upper-triangular in
-// standard form (2 x 2 blocks for complex pairs) and wi the imaginary parts.
+// standard form (2 x 2 blocks for complex pairs) and wi the imaginary parts,
+// or a complex Schur form A = U T U^H (T upper triangular; step 1 is skipped).
 //   1. Each 2 x 2 block is made triangular in complex arithmetic by the
 //      unitary G whose first column is the block's eigenvector
 //      (mu - d, c) / ||.|| for the eigenvalue mu with positive imaginary part:
@@ -58,6 +59,15 @@ __global__ void r2c_kernel(int rows, int cols, const double* __restrict__ A, int
   if (e >= (long long)rows * cols) return;
   const int i = (int)(e % rows), j = (int)(e / rows);
   B[i + (size_t)j * ldb] = tz(A[i + (size_t)j * lda], 0.0);
+}
+
+// B (rows x cols complex, ld ldb) = A (complex, ld lda)
+__global__ void c2c_kernel(int rows, int cols, const zt* __restrict__ A, int lda,
+                           zt* __restrict__ B, int ldb) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int i = (int)(e % rows), j = (int)(e / rows);
+  B[i + (size_t)j * ldb] = A[i + (size_t)j * lda];
 }
 
 // G of each 2 x 2 block at rows/cols (i, i+1): [[v0, -conj v1], [v1, conj v0]],
@@ -226,7 +236,8 @@ __global__ void diag_kernel(int n, const zt* __restrict__ T, int ldt, zt* __rest
 }  // namespace
 
 int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, int ldq,
-          const double* dwi, double* dV_, int ldv, double* dlam_, std::string* err) {
+          const double* dwi, double* dV_, int ldv, double* dlam_, std::string* err,
+          bool complex_in) {
   NvtxRange nvtx_("eig.trevc");
   zt* dV = reinterpret_cast<zt*>(dV_);
   zt* dlam = reinterpret_cast<zt*>(dlam_);
@@ -260,21 +271,30 @@ int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, in
     cleanup();
     return EIG_ERR_NOMEM;
   }
-  // complex pairs from wi (host): a pair starts where wi > 0 and wi[i+1] = -wi[i]
-  std::vector<double> hwi(n);
-  cudaError_t e = cudaMemcpyAsync(hwi.data(), dwi, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(e, "wi copy");
+  cudaError_t e = cudaSuccess;
   std::vector<int> hidx;
-  for (int i = 0; i + 1 < n; ++i)
-    if (hwi[i] > 0.0 && hwi[i + 1] == -hwi[i]) {
-      hidx.push_back(i);
-      ++i;
-    }
+  if (!complex_in) {
+    // complex pairs from wi (host): a pair starts where wi > 0 and wi[i+1] = -wi[i]
+    std::vector<double> hwi(n);
+    e = cudaMemcpyAsync(hwi.data(), dwi, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e, "wi copy");
+    for (int i = 0; i + 1 < n; ++i)
+      if (hwi[i] > 0.0 && hwi[i + 1] == -hwi[i]) {
+        hidx.push_back(i);
+        ++i;
+      }
+  }
   const int nblk = (int)hidx.size();
-  note_launches(3);
-  r2c_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, n, dT, ldt, Tc, n);
-  r2c_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, n, dQ, ldq, Qc, n);
+  note_launches(2);
+  if (complex_in) {
+    // a complex Schur form: already triangular
+    c2c_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, n, reinterpret_cast<const zt*>(dT), ldt, Tc, n);
+    c2c_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, n, reinterpret_cast<const zt*>(dQ), ldq, Qc, n);
+  } else {
+    r2c_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, n, dT, ldt, Tc, n);
+    r2c_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, n, dQ, ldq, Qc, n);
+  }
   cudaMemsetAsync(X, 0, nn * sizeof(zt), s);
   if (nblk > 0) {
     int* didx = static_cast<int*>(alloc(sizeof(int) * nblk));

@@ -144,6 +144,7 @@ _SIGNATURES = {
     "eig_gemm_fp64tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_eigenvectors": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, _P]),
+    "eig_eigenvectors_complex": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P]),
     "eig_zgemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _D, _P, _I, _P, _I, _D, _D, _P, _I]),
     "eig_zqr": (_I, [_P, _I, _I, _P, _I, _P, _I, _P, _I]),
     "eig_zhaar": (_I, [_P, _I, _U64, _U64, _I, _P, _I]),
@@ -539,6 +540,18 @@ def eigenvectors(h, T, Q, wi):
     dV = torch.zeros((n, n), dtype=torch.complex128, device=dT.device)
     dlam = torch.zeros(n, dtype=torch.complex128, device=dT.device)
     rc = eig_eigenvectors(h, n, dT, n, dQ, n, dwi, dV, n, dlam)
+    return rc, dlam.cpu().numpy(), dV.cpu().numpy().T.copy()
+
+
+def eigenvectors_complex(h, T, U):
+    """(rc, lam, V) for a complex Schur form (T, U) as schur_complex returns it."""
+    import torch
+    n = T.shape[0]
+    dT, dU = to_device_complex(T), to_device_complex(U)
+    dV = torch.zeros((n, n), dtype=torch.complex128, device=dT.device)
+    dlam = torch.zeros(n, dtype=torch.complex128, device=dT.device)
+    rc = lib().eig_eigenvectors_complex(h.ptr, n, _ptr(dT), n, _ptr(dU), n, _ptr(dV), n,
+                                        _ptr(dlam))
     return rc, dlam.cpu().numpy(), dV.cpu().numpy().T.copy()
 
 

@@ -66,3 +66,26 @@ def test_argument_errors(E):
     z = torch.zeros((4, 4), dtype=torch.complex128, device="cuda")
     rc = eigdc.eig_eigenvectors(h, 4, d, 3, d, 4, d, z, 4, z)
     assert rc == eigdc.EIG_ERR_ARG
+
+
+def test_eigenvectors_of_a_complex_schur_form(E):
+    """eig_eigenvectors_complex on eig_schur_complex's output against the
+    oracle's triangular recurrence on the same (T, U)."""
+    eigdc, h, torch = E
+    rng = np.random.default_rng(77)
+    n = 90
+    lam0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    S = np.eye(n) + 0.25 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2 * n)
+    A = S @ np.diag(lam0) @ np.linalg.inv(S)
+    rc, T, U, w, info, _ = eigdc.schur_complex(h, A, eigdc.default_params(seed=2, leaf_size=16))
+    assert rc == eigdc.EIG_OK
+    rc, lam, V = eigdc.eigenvectors_complex(h, T, U)
+    assert rc == eigdc.EIG_OK
+    X = otrevc.triangular_eigenvectors(T)
+    Vo = U @ X
+    Vo = Vo / np.linalg.norm(Vo, axis=0)
+    assert np.abs(lam - np.diag(T)).max() == 0.0
+    ph = np.sum(V.conj() * Vo, axis=0)
+    ph = ph / np.abs(ph)
+    assert np.abs(V * ph - Vo).max() <= 1e-10
+    assert np.linalg.norm(A @ V - V * lam) <= 1e-12 * np.linalg.norm(A) * np.sqrt(n)
