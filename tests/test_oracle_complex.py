@@ -399,3 +399,42 @@ def test_driver_two_step_rule_on_a_loose_disk():
                 and lines[i - 1][5] == c and lines[i - 1][6] == R
             if not prev_perp:
                 assert abs(wn - 1j * wl) < 1e-15
+
+
+def test_rotating_the_plane_leaves_the_step_unchanged():
+    # (e^{i phi} A, line e^{i phi} w) maps to e^{i phi} times the same pencil:
+    # the R_j of IRS (non-negative diagonal) and the step's decisions agree
+    rng = np.random.default_rng(91)
+    n = 30
+    lam = 1.5 * _crandn(rng, n)
+    A, _ = _prescribed(lam, rng)
+    w, t, s = np.exp(0.3j), 0.1, 3.0
+    phi = np.exp(1.1j)
+    r0 = cirs(*line_map(A, w, t, s), record_R=True)
+    r1 = cirs(*line_map(phi * A, phi * w, t, s), record_R=True)
+    assert r0.iters == r1.iters and r0.converged and r1.converged
+    for R0, R1 in zip(r0.Rs, r1.Rs):
+        assert np.abs(R0 - R1).max() <= 1e-12 * np.abs(R0).max()
+    s0 = line_step(A, w, t, s, seed=4, stream=9, attempt=0)
+    s1 = line_step(phi * A, phi * w, t, s, seed=4, stream=9, attempt=0)
+    assert (s0.k, s0.rank, s0.accepted) == (s1.k, s1.rank, s1.accepted)
+
+
+def test_squarings_follow_the_distance_to_a_rotated_line():
+    # Sec. 3.3.1, Fig. 1 with the line at an angle: normal matrices whose
+    # nearest eigenvalue sits 4e-3 from the line take the same number of
+    # squarings at n = 60 and n = 200
+    w, t = np.exp(0.8j), 0.05
+    counts = []
+    for n, seed in ((60, 1), (200, 2)):
+        rng = np.random.default_rng(seed)
+        along = rng.uniform(-1.5, 1.5, n)
+        along = np.where(np.abs(along - t) < 4e-3, t + 4e-3 * np.sign(along - t + 1e-300), along)
+        along[np.argmin(np.abs(along - t))] = t + 4e-3
+        lam = w * (along + 1j * rng.uniform(-1.5, 1.5, n))
+        W = cqr_explicit(_crandn(rng, n, n))[0]
+        A = W @ np.diag(lam) @ W.conj().T
+        res = cirs(*line_map(A, w, t, 3.0))
+        assert res.converged
+        counts.append(res.iters)
+    assert abs(counts[0] - counts[1]) <= 1
