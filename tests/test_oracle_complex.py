@@ -438,3 +438,44 @@ def test_squarings_follow_the_distance_to_a_rotated_line():
         assert res.converged
         counts.append(res.iters)
     assert abs(counts[0] - counts[1]) <= 1
+
+
+@pytest.mark.parametrize("field", ["real", "complex"])
+def test_rurv_is_rank_revealing(field):
+    # Theorem 2.1 (RURV is a strong rank-revealing factorisation w.h.p.):
+    # sigma_max(R22) >= sigma_{r+1} always (interlacing); with high probability
+    # sigma_min(R11) is within sqrt(r (n-r)) of sigma_r, ||R11^-1 R12|| = O(sqrt(r (n-r)))
+    # and sigma_max(R22) is a small multiple of sigma_{r+1}.  The constants are
+    # not stated; loose ones are checked on the median of 40 Haar draws.
+    from oracle.rurv import haar, rurv
+    from oracle.householder import qr_explicit
+    rng = np.random.default_rng(93)
+    n, r = 40, 10
+    sig = np.concatenate([rng.uniform(1.0, 2.0, r), 1e-8 * rng.uniform(0.5, 1.0, n - r)])
+    sig = -np.sort(-sig)
+    if field == "real":
+        P = qr_explicit(rng.standard_normal((n, n)))[0]
+        Q = qr_explicit(rng.standard_normal((n, n)))[0]
+    else:
+        P = cqr_explicit(_crandn(rng, n, n))[0]
+        Q = cqr_explicit(_crandn(rng, n, n))[0]
+    A = (P * sig) @ Q.conj().T
+    lo, hi, cross = [], [], []
+    for d in range(40):
+        if field == "real":
+            V = haar(n, 5, 100 + d)
+            _, R = rurv(A, V)
+        else:
+            V = chaar(n, 5, 100 + d)
+            _, R = cqr_explicit(A @ V.conj().T)
+        R11, R12, R22 = R[:r, :r], R[:r, r:], R[r:, r:]
+        s11 = np.linalg.svd(R11, compute_uv=False)
+        s22 = np.linalg.svd(R22, compute_uv=False)
+        assert s22[0] >= sig[r] * (1 - 1e-6)
+        assert s11[-1] <= np.sqrt(2) * sig[r - 1] * (1 + 1e-12)
+        lo.append(s11[-1] * np.sqrt(r * (n - r)) / sig[r - 1])
+        hi.append(s22[0] / sig[r])
+        cross.append(np.linalg.norm(np.linalg.solve(R11, R12), 2) / np.sqrt(r * (n - r)))
+    assert np.median(lo) >= 0.05
+    assert np.median(hi) <= 1e3
+    assert np.median(cross) <= 10.0
