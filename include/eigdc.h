@@ -440,7 +440,9 @@ typedef struct {
  *   - dA (lda >= n), dT (ldt >= n), dU (ldu >= n): device, complex; dw: device,
  *     n complex.  dA is not modified.
  *   - params: tau, maxit, split_tol (0: max(1e-12, 16 n 2^-53)), leaf_size,
- *     seed, max_fail, v_draws and prec are used.  EIG_FP64: every contraction
+ *     seed, max_fail, v_draws, workers and prec are used.  Independent nodes
+ *     run on `workers` host threads with their own streams; the result does
+ *     not depend on the schedule.  EIG_FP64: every contraction
  *     on the FP64 pipe; EIG_FP64_TC: products with every dimension >= 128 (and
  *     m n k >= 2^25) run as four FP64-accurate tensor-core products of the
  *     real and imaginary planes (as eig_gemm_fp64tc); EIG_SPLIT_BF16X3 runs

@@ -37,8 +37,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/eigdc.h"
@@ -1191,9 +1195,168 @@ struct CLeaf {
   zt* A;
 };
 
+// State shared by the node workers of one solve.
+struct CShared {
+  int n = 0, ldu = 0, leaf = 64, device = 0;
+  zt* dU = nullptr;
+  const eig_params_t* p = nullptr;
+  bool enclose = false;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<CNode> queue;
+  int outstanding = 0;
+  std::vector<CLeaf> leaves;
+  std::vector<CplaneCluster>* clusters = nullptr;
+  eig_solve_info_t inf;
+  int status = EIG_OK;
+  std::string err;
+  std::vector<void*> node_mem;   // node matrices, freed after the leaves
+
+  // a node matrix (m x m) that outlives the worker that made it
+  zt* alloc_node(cudaStream_t s, size_t count, std::string* e) {
+    void* q = nullptr;
+    if (cudaMallocAsync(&q, std::max<size_t>(count * sizeof(zt), 256), s) != cudaSuccess) {
+      cudaGetLastError();
+      *e = "complex-plane node allocation failed";
+      throw ZFail{EIG_ERR_NOMEM};
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    node_mem.push_back(q);
+    return static_cast<zt*>(q);
+  }
+};
+
+// One node of the recursion on stream s: steps until a split (children pushed
+// on the shared queue), a cluster (enclose) or NO_SPLIT.  Scratch is per node.
+void process_cnode(CShared& S, cudaStream_t s, CNode nd) {
+  NvtxRange nvtx_("eig.cplane.node");
+  const eig_params_t& p = *S.p;
+  const int n = S.n, m = nd.m, leaf = S.leaf;
+  const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
+  std::string err;
+  try {
+    CDriver D{s, &err, {}};
+    StepBufs b;
+    make_bufs(D, b, m, p.prec == EIG_FP64_TC);
+    zt* tmpU = D.alloc<zt>((size_t)n * m);
+    const double tau = p.tau > 0.0 ? p.tau : std::max(1e-14, 4.0 * std::sqrt((double)m) * 0x1p-53);
+    const double stol = p.split_tol > 0.0 ? p.split_tol : std::max(1e-12, 16.0 * m * 0x1p-53);
+    NodePlan plan;
+    plan.reg = nd.reg;
+    plan.max_fail = p.max_fail;
+    int iters = 0, fails = 0;
+    while (true) {
+      if (!(plan.reg.R > 0.0)) break;   // A = cI: already triangular
+      const HalfPlane L = draw_line(plan.reg, p.seed, nd.id, plan.attempt, plan.has_perp, plan.pr,
+                                    plan.pi_);
+      const CStepOut st = line_step(D, b, m, nd.A, L, plan.reg.R, p.seed, nd.id, plan.attempt, tau,
+                                    p.maxit, stol, p.v_draws);
+      check_tc(D, b);
+      iters += st.iters;
+      if (st.accepted) {
+        const int k = st.k;
+        // this node's columns of U only: disjoint from every other node's
+        D.check(zmm(s, b.tc, false, false, n, m, m, one, S.dU + (size_t)nd.off * S.ldu, S.ldu, b.Q,
+                    m, zero, tmpU, n), "U update");
+        D.check(zcopy(s, n, m, tmpU, n, S.dU + (size_t)nd.off * S.ldu, S.ldu), "U update");
+        zt* A11 = S.alloc_node(s, (size_t)k * k, &err);
+        zt* A22 = S.alloc_node(s, (size_t)(m - k) * (m - k), &err);
+        D.check(zcopy(s, k, k, b.Ahat, m, A11, k), "block copy");
+        D.check(zcopy(s, m - k, m - k, b.Ahat + k + (size_t)k * m, m, A22, m - k), "block copy");
+        Region g0, g1, kid0, kid1;
+        if (k > leaf) g0 = frobenius_disk(D, b, k, A11, k);
+        if (m - k > leaf) g1 = frobenius_disk(D, b, m - k, A22, m - k);
+        child_regions(plan.reg, L, k > leaf ? &g0 : nullptr, m - k > leaf ? &g1 : nullptr, &kid0,
+                      &kid1);
+        D.sync();   // the children's matrices and U are complete before another stream reads them
+        std::lock_guard<std::mutex> lock(S.mu);
+        S.inf.splits += 1;
+        S.inf.total_iters += iters;
+        S.inf.failed_attempts += fails;
+        S.queue.push_back({nd.off + k, m - k, A22, kid1, child_node_id(nd.id, 1), nd.depth + 1});
+        S.queue.push_back({nd.off, k, A11, kid0, child_node_id(nd.id, 0), nd.depth + 1});
+        S.outstanding += 2;
+        S.cv.notify_all();
+        return;
+      }
+      fails += 1;
+      if (plan.after_nonsplit(L, st.converged, st.rank, m)) {
+        std::lock_guard<std::mutex> lock(S.mu);
+        S.inf.total_iters += iters;
+        S.inf.failed_attempts += fails;
+        if (S.enclose) {
+          if (S.clusters) {
+            S.clusters->push_back({nd.off, m, plan.reg.cr, plan.reg.ci, plan.reg.R, {}});
+            for (const HalfPlane& h : plan.reg.hp) S.clusters->back().hp.push_back({h.wr, h.wi, h.t});
+          }
+          if (m <= ZLEAF_MAX) {
+            S.leaves.push_back({nd.off, m, nd.A});
+            return;
+          }
+          // the leaf kernel cannot take the cluster: reported, not triangularised
+        }
+        if (S.status == EIG_OK) {
+          S.status = EIG_NO_SPLIT;
+          S.err = "no split found for a node of size " + std::to_string(m);
+        }
+        return;
+      }
+    }
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.inf.total_iters += iters;
+    S.inf.failed_attempts += fails;
+  } catch (ZFail f) {
+    std::lock_guard<std::mutex> lock(S.mu);
+    if (S.status == EIG_OK) {
+      S.status = f.code;
+      S.err = err;
+    }
+  }
+}
+
+void cnode_worker(CShared& S) {
+  cudaStream_t s = nullptr;
+  if (cudaSetDevice(S.device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lock(S.mu);
+    if (S.status == EIG_OK) {
+      S.status = EIG_ERR_CUDA;
+      S.err = "worker stream creation failed";
+    }
+    S.cv.notify_all();
+    return;
+  }
+  while (true) {
+    CNode nd;
+    {
+      std::unique_lock<std::mutex> lock(S.mu);
+      S.cv.wait(lock, [&] { return !S.queue.empty() || S.outstanding == 0 || S.status != EIG_OK; });
+      if (S.status != EIG_OK || S.queue.empty()) break;
+      nd = S.queue.back();   // depth first, like the sequential order
+      S.queue.pop_back();
+      S.inf.nodes += 1;
+      S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
+      if (nd.m <= S.leaf) {
+        S.leaves.push_back({nd.off, nd.m, nd.A});
+        S.outstanding--;
+        S.cv.notify_all();
+        continue;
+      }
+    }
+    process_cnode(S, s, nd);
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.outstanding--;
+    S.cv.notify_all();
+  }
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+}
+
 }  // namespace
 
-// Complex Schur form A = U T U^H by the complex-plane recursion (Sec. 3.3).
+// Complex Schur form A = U T U^H by the complex-plane recursion (Sec. 3.3);
+// independent nodes run on p.workers host workers with their own streams.
 int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_, int ldt,
                  double* dU_, int ldu, double* dw_, const eig_params_t& p, bool enclose,
                  std::vector<CplaneCluster>* clusters, eig_solve_info_t* info, std::string* err) {
@@ -1203,97 +1366,49 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
   zt* dU = reinterpret_cast<zt*>(dU_);
   zt* dw = reinterpret_cast<zt*>(dw_);
   const zt one = zmk(1.0, 0.0), zero = zmk(0.0, 0.0);
-  eig_solve_info_t inf;
-  std::memset(&inf, 0, sizeof(inf));
+  CShared S;
+  std::memset(&S.inf, 0, sizeof(S.inf));
+  S.n = n;
+  S.ldu = ldu;
+  S.leaf = std::max(1, std::min(p.leaf_size > 0 ? p.leaf_size : 64, ZLEAF_MAX));
+  S.dU = dU;
+  S.p = &p;
+  S.enclose = enclose;
+  S.clusters = clusters;
+  cudaGetDevice(&S.device);
   int status = EIG_OK;
   try {
     CDriver D{s, err, {}};
-    const int leaf = std::max(1, std::min(p.leaf_size > 0 ? p.leaf_size : 64, ZLEAF_MAX));
-    StepBufs b;
-    if (n > leaf) make_bufs(D, b, n, p.prec == EIG_FP64_TC);
-    zt* tmpU = D.alloc<zt>((size_t)n * n);
     note_launches(1);
     zident_ld_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, n, dU, ldu);
-    zt* root = D.alloc<zt>((size_t)n * n);
+    zt* root = S.alloc_node(s, (size_t)n * n, err);
     D.check(zcopy(s, n, n, dA, lda, root, n), "input copy");
-    std::vector<CNode> work;
-    std::vector<CLeaf> leaves;
-    {
-      CNode r{0, n, root, Region(), 1ull, 0};
-      if (n > leaf) r.reg = gershgorin_disk(D, b, n, root, n);
-      work.push_back(r);
+    Region r0;
+    if (n > S.leaf) {
+      StepBufs g;
+      g.col1 = D.alloc<double>(n + 1);
+      g.col2 = D.alloc<double>(n + 1);
+      r0 = gershgorin_disk(D, g, n, root, n);
     }
-    while (!work.empty() && status == EIG_OK) {
-      CNode nd = work.back();
-      work.pop_back();
-      inf.nodes += 1;
-      inf.max_depth = std::max(inf.max_depth, nd.depth);
-      if (nd.m <= leaf) {
-        leaves.push_back({nd.off, nd.m, nd.A});
-        continue;
-      }
-      const int m = nd.m;
-      const double tau = p.tau > 0.0 ? p.tau : std::max(1e-14, 4.0 * std::sqrt((double)m) * 0x1p-53);
-      const double stol = p.split_tol > 0.0 ? p.split_tol : std::max(1e-12, 16.0 * m * 0x1p-53);
-      const int maxit = p.maxit;
-      NodePlan plan;
-      plan.reg = nd.reg;
-      plan.max_fail = p.max_fail;
-      while (true) {
-        if (!(plan.reg.R > 0.0)) {
-          // every row and column sum of |A - cI| is zero: A = cI is already
-          // triangular (U stays, T = U^H A U below)
-          D.release(nd.A);
-          break;
-        }
-        const HalfPlane L = draw_line(plan.reg, p.seed, nd.id, plan.attempt, plan.has_perp, plan.pr,
-                                      plan.pi_);
-        const CStepOut st = line_step(D, b, m, nd.A, L, plan.reg.R, p.seed, nd.id, plan.attempt, tau,
-                                      maxit, stol, p.v_draws);
-        check_tc(D, b);
-        inf.total_iters += st.iters;
-        if (st.accepted) {
-          const int k = st.k;
-          D.check(zmm(s, b.tc, false, false, n, m, m, one, dU + (size_t)nd.off * ldu, ldu, b.Q, m,
-                      zero, tmpU, n), "U update");
-          D.check(zcopy(s, n, m, tmpU, n, dU + (size_t)nd.off * ldu, ldu), "U update");
-          zt* A11 = D.alloc<zt>((size_t)k * k);
-          zt* A22 = D.alloc<zt>((size_t)(m - k) * (m - k));
-          D.check(zcopy(s, k, k, b.Ahat, m, A11, k), "block copy");
-          D.check(zcopy(s, m - k, m - k, b.Ahat + k + (size_t)k * m, m, A22, m - k), "block copy");
-          Region g0, g1, kid0, kid1;
-          if (k > leaf) g0 = frobenius_disk(D, b, k, A11, k);
-          if (m - k > leaf) g1 = frobenius_disk(D, b, m - k, A22, m - k);
-          child_regions(plan.reg, L, k > leaf ? &g0 : nullptr, m - k > leaf ? &g1 : nullptr, &kid0,
-                        &kid1);
-          inf.splits += 1;
-          work.push_back({nd.off + k, m - k, A22, kid1, child_node_id(nd.id, 1), nd.depth + 1});
-          work.push_back({nd.off, k, A11, kid0, child_node_id(nd.id, 0), nd.depth + 1});
-          D.release(nd.A);
-          break;
-        }
-        inf.failed_attempts += 1;
-        if (plan.after_nonsplit(L, st.converged, st.rank, m)) {
-          if (enclose) {
-            if (clusters) {
-              clusters->push_back({nd.off, m, plan.reg.cr, plan.reg.ci, plan.reg.R, {}});
-              for (const HalfPlane& h : plan.reg.hp) clusters->back().hp.push_back({h.wr, h.wi, h.t});
-            }
-            if (m <= ZLEAF_MAX) {
-              leaves.push_back({nd.off, m, nd.A});
-              break;
-            }
-            // the leaf kernel cannot take the cluster: reported, not triangularised
-          }
-          status = EIG_NO_SPLIT;
-          break;
-        }
-      }
-    }
+    D.sync();   // the workers' streams read the root and U
+    S.queue.push_back({0, n, root, r0, 1ull, 0});
+    S.outstanding = 1;
+    const int nw = n > S.leaf ? std::max(1, std::min(p.workers, 32)) : 1;
+    std::vector<std::thread> th;
+    for (int i = 0; i < nw; ++i) th.emplace_back(cnode_worker, std::ref(S));
+    for (auto& t : th) t.join();
+    if (clusters)   // offset order, whatever order the workers finished in
+      std::sort(clusters->begin(), clusters->end(),
+                [](const CplaneCluster& a, const CplaneCluster& b) { return a.off < b.off; });
+    status = S.status;
+    if (status < 0) *err = S.err;
     if (status == EIG_OK) {
-      // leaves: complex Schur per CTA, then U[:, off:off+m] <- U[:, off:off+m] Z_leaf
+      NvtxRange nvtx_leaves("eig.cplane.leaves");
+      // leaves in offset order (the schedule does not change the result)
+      std::vector<CLeaf>& leaves = S.leaves;
+      std::sort(leaves.begin(), leaves.end(), [](const CLeaf& a, const CLeaf& b) { return a.off < b.off; });
       const int nl = (int)leaves.size();
-      inf.leaves = nl;
+      S.inf.leaves = nl;
       std::vector<ZLeafDesc> hd(nl);
       std::vector<zt*> Zs(nl);
       int* dstat = D.alloc<int>(std::max(nl, 1));
@@ -1304,7 +1419,8 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
         hd[i] = {m, leaves[i].A, m, TZ, Zs[i], dstat + i};
       }
       ZLeafDesc* dd = D.alloc<ZLeafDesc>(std::max(nl, 1));
-      D.check(cudaMemcpyAsync(dd, hd.data(), sizeof(ZLeafDesc) * nl, cudaMemcpyHostToDevice, s), "leaf descriptors");
+      D.check(cudaMemcpyAsync(dd, hd.data(), sizeof(ZLeafDesc) * nl, cudaMemcpyHostToDevice, s),
+              "leaf descriptors");
       const int smem = 2 * ZLEAF_MAX * (ZLEAF_MAX + 1) * (int)sizeof(zt);
       D.check(cudaFuncSetAttribute(zschur_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
               "leaf attribute");
@@ -1313,6 +1429,7 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
         zschur_leaf_kernel<<<nl, 256, smem, s>>>(dd);
         D.check(cudaGetLastError(), "leaf launch");
       }
+      zt* tmpU = D.alloc<zt>((size_t)n * n);
       for (int i = 0; i < nl; ++i) {
         const int off = leaves[i].off, m = leaves[i].m;
         D.check(zgemm(s, false, false, n, m, m, one, dU + (size_t)off * ldu, ldu, Zs[i], m, zero, tmpU, n),
@@ -1323,14 +1440,23 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
       if (nl > 0)
         D.check(cudaMemcpyAsync(hst.data(), dstat, sizeof(int) * nl, cudaMemcpyDeviceToHost, s), "leaf status");
       // T = triu(U^H A U), w = diag(T)
+      StepBufs fb;
+      if (p.prec == EIG_FP64_TC && n >= 128) {
+        fb.tc.on = true;
+        fb.tc.plane = (size_t)n * n;
+        fb.tc.planes = D.alloc<double>(8 * fb.tc.plane);
+        fb.tc.ws = D.alloc<char>(tcx_gemm_workspace_bytes(n, n, n));
+        fb.tc.err = D.alloc<int>(1);
+        D.check(cudaMemsetAsync(fb.tc.err, 0, sizeof(int), s), "tensor-core error word");
+      }
       zt* AU = D.alloc<zt>((size_t)n * n);
-      D.check(zmm(s, b.tc, false, false, n, n, n, one, dA, lda, dU, ldu, zero, AU, n), "A U");
-      D.check(zmm(s, b.tc, true, false, n, n, n, one, dU, ldu, AU, n, zero, tmpU, n), "U^H A U");
+      D.check(zmm(s, fb.tc, false, false, n, n, n, one, dA, lda, dU, ldu, zero, AU, n), "A U");
+      D.check(zmm(s, fb.tc, true, false, n, n, n, one, dU, ldu, AU, n, zero, tmpU, n), "U^H A U");
       note_launches(1);
       ztriu_kernel<<<nblocks((long long)n * n, 256), 256, 0, s>>>(n, tmpU, n, dT, ldt, dw);
       D.check(cudaGetLastError(), "triangle");
       D.sync();
-      check_tc(D, b);
+      check_tc(D, fb);
       for (int i = 0; i < nl; ++i)
         if (hst[i] != 0) status = EIG_NO_CONVERGENCE;
     }
@@ -1338,8 +1464,11 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
   } catch (ZFail f) {
     status = f.code;
   }
-  inf.status = status;
-  if (info) *info = inf;
+  cudaStreamSynchronize(s);
+  for (void* q : S.node_mem) cudaFreeAsync(q, s);
+  cudaStreamSynchronize(s);
+  S.inf.status = status;
+  if (info) *info = S.inf;
   return status;
 }
 

@@ -103,7 +103,7 @@ def test_jordan_cluster_enclosure(E):
     _check(A, T, U, 1e-12)
     To, Uo, wo, io = schur_complex_plane(A, seed=1, leaf_size=4, enclose=True)
     assert len(enc) == len(io.clusters)
-    for e, (off, m, reg) in zip(enc, io.clusters):
+    for e, (off, m, reg) in zip(enc, sorted(io.clusters, key=lambda c: c[0])):
         assert (e.offset, e.size) == (off, m)
         c, R, hps = e.region()
         assert abs(c - reg.c) <= 1e-8 * (1 + abs(reg.c)) and abs(R - reg.R) <= 1e-8 * reg.R
@@ -157,6 +157,23 @@ def test_tensor_core_route_matches_fp64(E):
         assert _match(w, lam) <= 1e-10
         res[prec] = info
     assert res[eigdc.EIG_FP64].splits == res[eigdc.EIG_FP64_TC].splits
+
+
+def test_workers_do_not_change_the_result(E):
+    """Nodes on 1 or 8 host workers (own streams): bit-identical T, U, w."""
+    eigdc, h, torch = E
+    rng = np.random.default_rng(211)
+    n = 260
+    A = _prescribed(_crandn(rng, n), rng)
+    out = []
+    for workers in (1, 8):
+        p = eigdc.default_params(seed=6, leaf_size=32, workers=workers)
+        rc, T, U, w, info, _ = eigdc.schur_complex(h, A, p)
+        assert rc == eigdc.EIG_OK
+        out.append((T, U, w, info.splits, info.nodes))
+    (T1, U1, w1, s1, n1), (T8, U8, w8, s8, n8) = out
+    assert (s1, n1) == (s8, n8)
+    assert np.array_equal(T1, T8) and np.array_equal(U1, U8) and np.array_equal(w1, w8)
 
 
 # ------------------------------------------------------------ building blocks
