@@ -900,14 +900,6 @@ struct CDriver {
     owned.push_back(p);
     return static_cast<T*>(p);
   }
-  void release(void* p) {
-    for (size_t i = 0; i < owned.size(); ++i)
-      if (owned[i] == p) {
-        cudaFreeAsync(p, s);
-        owned.erase(owned.begin() + (long)i);
-        return;
-      }
-  }
   ~CDriver() {
     cudaStreamSynchronize(s);
     for (void* p : owned) cudaFreeAsync(p, s);

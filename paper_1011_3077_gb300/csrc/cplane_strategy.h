@@ -111,8 +111,8 @@ inline void enclosing_circle(const Region& g, double* mr, double* mi, double* ra
       if (line_line(g.hp[i], g.hp[j], &p) && g.contains(p.x, p.y)) corners.push_back(p);
     }
   }
-  Pt m;
-  double r;
+  Pt m{0.0, 0.0};
+  double r = 0.0;
   if (!min_circle(corners, &m, &r)) return;
   if (r >= g.R || (m.x == g.cr && m.y == g.ci)) return;
   const double dx = m.x - g.cr, dy = m.y - g.ci, dn = std::hypot(dx, dy);
