@@ -79,6 +79,7 @@ typedef struct eig_handle_s* eig_handle_t;
 #define EIG_KIND_SYM 0        /* RSEP recursion (Algorithm 6, Sec. 3.4) */
 #define EIG_KIND_NONSYM 1     /* RNEP recursion (Algorithm 5, Sec. 3.3) */
 #define EIG_KIND_PENCIL 2     /* RGNEP recursion (Algorithm 4, Sec. 3.5): eig_pencil_schur */
+#define EIG_KIND_CPLANE 3     /* complex-plane recursion (Sec. 3.3): eig_schur_complex */
 
 typedef struct {
   int kind;
@@ -159,7 +160,10 @@ unsigned long long eig_kernel_launches(void);
  * launches and return the summed launch durations (ms), the launch count and
  * the summed algorithmic flops 2mnk (the outputs may be NULL). */
 int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, double* flops);
-/* Device workspace (bytes) the handle needs for calls on size n. */
+/* Device workspace (bytes) the handle needs for calls on size n.  For
+ * EIG_KIND_CPLANE: the peak of the stream-ordered allocations of a
+ * complex-plane solve with one worker (each further worker adds the scratch
+ * of the node it holds). */
 int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes);
 
 /* --------------------------------------------------------------- the path */
@@ -292,6 +296,12 @@ int eig_server_submit_pencil(eig_server_t srv, int n, double* dA, int lda, doubl
                              double* dQL, int ldql, double* dQR, int ldqr, double* dalphar,
                              double* dalphai, double* dbeta, const eig_params_t* params,
                              uint64_t* ticket);
+/* Complex-plane request (eig_schur_complex semantics and outputs, interleaved
+ * complex buffers, no enclosure output; runs on one worker stream).  Admission
+ * and buffers as for eig_server_submit. */
+int eig_server_submit_complex(eig_server_t srv, int n, const double* dA, int lda, double* dT,
+                              int ldt, double* dU, int ldu, double* dw, const eig_params_t* params,
+                              int enclose, uint64_t* ticket);
 /* *done = 1 once finished; then *status, times[0..2] = queue wait, service,
  * latency (seconds, host steady clock) and *info are filled (each may be NULL). */
 int eig_server_poll(eig_server_t srv, uint64_t ticket, int* done, int* status, double* times,

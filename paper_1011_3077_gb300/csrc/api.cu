@@ -1798,6 +1798,10 @@ int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, 
 
 int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
   if (!h || !bytes || n < 0) return EIG_ERR_ARG;
+  if (kind == EIG_KIND_CPLANE) {   // stream-ordered allocations of one worker, not the handle's
+    *bytes = cplane_footprint(n, EIG_FP64_TC);
+    return EIG_OK;
+  }
   Arena a(nullptr);
   SolveMain w;
   NodeWork nw;
@@ -2382,6 +2386,7 @@ struct Request {
   double *dA, *dwr, *dwi, *dU;
   int ldb = 0, ldqr = 0;                                      // pencils
   double *dB = nullptr, *dQR = nullptr, *dbeta = nullptr;     // pencils
+  int enclose = 0;                                            // complex plane: dQR holds T
   eig_params_t p;
   size_t footprint;
   double t_submit = 0, t_start = 0, t_end = 0;
@@ -2395,6 +2400,7 @@ double now_s() {
 }
 
 size_t solve_footprint(int n, int kind, int prec) {
+  if (kind == EIG_KIND_CPLANE) return cplane_footprint(n, prec);
   Arena a(nullptr);
   SolveMain w;
   NodeWork nw;
@@ -2446,10 +2452,15 @@ static void server_worker(eig_server_s* S, eig_handle_s* hw) {
     try {
       NvtxRange nvtx_("eig.request");
       hw->err.clear();
-      if (r->kind == EIG_KIND_PENCIL)
+      if (r->kind == EIG_KIND_PENCIL) {
         rc = pencil_impl(hw, r->n, r->dA, r->lda, r->dB, r->ldb, r->dU, r->ldu, r->dQR, r->ldqr,
                          r->dwr, r->dwi, r->dbeta, r->p, &inf);
-      else
+      } else if (r->kind == EIG_KIND_CPLANE) {
+        std::string err;
+        rc = cplane_schur(hw->stream, r->n, r->dA, r->lda, r->dQR, r->ldqr, r->dU, r->ldu, r->dwr,
+                          r->p, r->enclose != 0, nullptr, &inf, &err);
+        if (rc < 0) hw->err = err;
+      } else
         rc = solve_impl(hw, r->kind, r->n, r->dA, r->lda, r->dwr, r->dwi, r->dU, r->ldu, r->p,
                         &inf);
     } catch (Fail f) {
@@ -2585,6 +2596,36 @@ int eig_server_submit_pencil(eig_server_t S, int n, double* dA, int lda, double*
   r->p.graphs = 0;
   if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
       (r->p.prec != EIG_FP64 && r->p.prec != EIG_FP64_TC)) {
+    delete r;
+    return EIG_ERR_ARG;
+  }
+  enqueue(S, r, ticket);
+  return EIG_OK;
+}
+
+int eig_server_submit_complex(eig_server_t S, int n, const double* dA, int lda, double* dT,
+                              int ldt, double* dU, int ldu, double* dw, const eig_params_t* params,
+                              int enclose, uint64_t* ticket) {
+  if (!S || !ticket) return EIG_ERR_ARG;
+  if (n < 1 || !dA || lda < n || !dT || ldt < n || !dU || ldu < n || !dw) return EIG_ERR_ARG;
+  Request* r = new Request();
+  r->kind = EIG_KIND_CPLANE;
+  r->n = n;
+  r->dA = const_cast<double*>(dA);   // read only
+  r->lda = lda;
+  r->dQR = dT;
+  r->ldqr = ldt;
+  r->dU = dU;
+  r->ldu = ldu;
+  r->dwr = dw;
+  r->enclose = enclose;
+  eig_default_params(&r->p);
+  if (params) r->p = *params;
+  r->p.workers = 1;
+  r->p.graphs = 0;
+  if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.leaf_size > 64 || r->p.v_draws < 1 ||
+      r->p.max_fail < 0 || r->p.split_tol < 0 ||
+      (r->p.prec != EIG_FP64 && r->p.prec != EIG_FP64_TC && r->p.prec != EIG_SPLIT_BF16X3)) {
     delete r;
     return EIG_ERR_ARG;
   }

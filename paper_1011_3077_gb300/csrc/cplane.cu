@@ -1464,6 +1464,19 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
   return status;
 }
 
+size_t cplane_footprint(int n, int prec) {
+  const size_t c2 = (size_t)n * n, z = sizeof(zt);
+  // make_bufs at the root: 24 n^2 complex (IRS, splitter, similarity, QR
+  // reflectors) + 3 n^2 doubles + panel / Gram / score vectors; the node's
+  // U update scratch n^2 complex; node matrices up to 2 n^2 complex; the
+  // final A U and U^H A U 2 n^2 complex
+  size_t bytes = 24 * c2 * z + 3 * c2 * sizeof(double) + c2 * z + 2 * c2 * z + 2 * c2 * z;
+  bytes += (size_t)(4 * ZNB + 8) * n * z + (size_t)(nblocks(2 * n, 64) * 1024) * z +
+           (size_t)((n + 31) / 32 + 8) * n * sizeof(double);
+  if (prec == EIG_FP64_TC && n >= 128) bytes += 8 * c2 * sizeof(double) + tcx_gemm_workspace_bytes(n, n, n);
+  return bytes + ((size_t)64 << 20);   // allocator granularity and leaf buffers
+}
+
 // ------------------------------------------------------------------ building blocks
 // The single steps of the complex path, for tests and callers that compose
 // their own recursion (the complex counterparts of eig_qr, eig_haar and

@@ -207,6 +207,9 @@ int cplane_step(cudaStream_t s, int n, const double* dA, int lda, double w_re, d
 cudaError_t cplane_zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double ar,
                          double ai, const double* A, int lda, const double* B, int ldb, double br,
                          double bi, double* C, int ldc);
+// Device bytes a complex-plane solve of order n holds at its peak with one
+// worker (per-node scratch of the root, node matrices, final products).
+size_t cplane_footprint(int n, int prec);
 // C = alpha op(A) op(B) + beta C over C (op = X or X^H), DFMA, 64 x 64 tiles.
 cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double2 alpha,
                   const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C,

@@ -39,6 +39,7 @@ EIG_FP64_TC = 2
 EIG_KIND_SYM = 0
 EIG_KIND_NONSYM = 1
 EIG_KIND_PENCIL = 2
+EIG_KIND_CPLANE = 3
 PURPOSE_HAAR = 4
 PURPOSE_SHIFT = 5
 PURPOSE_HAAR_LEFT = 6
@@ -125,6 +126,8 @@ _SIGNATURES = {
                                ctypes.POINTER(_U64)]),
     "eig_server_submit_pencil": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P, _P, _P,
                                       ctypes.POINTER(Params), ctypes.POINTER(_U64)]),
+    "eig_server_submit_complex": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P, ctypes.POINTER(Params),
+                                       _I, ctypes.POINTER(_U64)]),
     "eig_server_poll": (_I, [_P, _U64, ctypes.POINTER(_I), ctypes.POINTER(_I),
                              ctypes.POINTER(_D), ctypes.POINTER(SolveInfo)]),
     "eig_server_wait": (_I, [_P, _U64, _D, ctypes.POINTER(_I)]),
@@ -386,6 +389,19 @@ class Server:
         st = ctypes.c_int()
         rc = lib().eig_server_wait(self._s, ticket, timeout_s, ctypes.byref(st))
         return rc, st.value
+
+    def submit_complex(self, dA, dT, dU, dw, params=None, enclose=False):
+        """Complex-plane request on complex128 device tensors (column-major)."""
+        n = int(dA.shape[0])
+        t = ctypes.c_uint64()
+        p = params or default_params()
+        rc = lib().eig_server_submit_complex(self._s, n, _ptr(dA), n, _ptr(dT), n, _ptr(dU), n,
+                                             _ptr(dw), ctypes.byref(p), 1 if enclose else 0,
+                                             ctypes.byref(t))
+        if rc != EIG_OK:
+            raise EigError(rc, "eig_server_submit_complex failed")
+        self._keep[t.value] = (dA, dT, dU, dw)
+        return t.value
 
     def cancel(self, ticket):
         """1 if the queued request was removed (status EIG_CANCELLED), 0 if it

@@ -257,3 +257,29 @@ def test_zline_step_matches_the_oracle(E):
     assert np.abs(Ah[:k, :k] - st.Ahat[:k, :k]).max() <= 1e-10 * np.abs(A).max()
     assert np.abs(_host(dQ, n)[:, :k] - st.Q[:, :k]).max() <= 1e-10
     assert info.split_residual <= 1e-12 and st.e <= 1e-12
+
+
+def test_server_takes_complex_plane_requests(E):
+    """Complex-plane requests in the request server, mixed with symmetric ones:
+    each result is bit-identical to eig_schur_complex with one worker."""
+    eigdc, h, torch = E
+    rng = np.random.default_rng(301)
+    srv = eigdc.Server(0, 3, 40.0)
+    p = eigdc.default_params(seed=4, leaf_size=32)
+    reqs = []
+    for i in range(4):
+        n = 80 + 30 * i
+        A = _prescribed(_crandn(rng, n), rng)
+        dA = eigdc.to_device_complex(A)
+        z = lambda *s: torch.zeros(s, dtype=torch.complex128, device="cuda")
+        dT, dU, dw = z(n, n), z(n, n), z(n)
+        torch.cuda.synchronize()
+        reqs.append((A, dT, dU, dw, srv.submit_complex(dA, dT, dU, dw, p)))
+    for A, dT, dU, dw, t in reqs:
+        rc, st = srv.wait(t, 600.0)
+        assert rc == 0 and st == eigdc.EIG_OK
+        p1 = eigdc.default_params(seed=4, leaf_size=32, workers=1)
+        rc, T, U, w, info, _ = eigdc.schur_complex(h, A, p1)
+        assert rc == eigdc.EIG_OK
+        assert np.array_equal(dT.cpu().numpy().T, T) and np.array_equal(dU.cpu().numpy().T, U)
+    srv.close()
