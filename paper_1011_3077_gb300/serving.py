@@ -1,7 +1,8 @@
 """Serving loop: Poisson arrivals of mixed eigenproblems on one GPU.
 
 Requests (symmetric eigendecomposition, nonsymmetric real Schur form,
-generalized real Schur form of a regular pencil) of log-uniform size arrive
+generalized real Schur form of a regular pencil, and with a fourth --mix share
+the complex Schur form by lines at random angles) of log-uniform size arrive
 as a Poisson stream and are submitted to the native request server
 (include/eigdc.h, eig_server_*), which admits them under an HBM budget as
 workers free up and overlaps their work on the device.  The loop reports
@@ -38,9 +39,35 @@ def _orthogonal(n, gen, device):
     return Q * s
 
 
+def synthesize_complex(n, seed, device="cuda"):
+    """Complex-plane request: A = Q T Q^H with Q unitary (library QR of a complex
+    Gaussian) and T upper triangular, diagonal uniform in the disk of radius
+    1.5, strict upper part N(0, (0.1/sqrt(n))^2); returns (dA column-major
+    complex128, the prescribed eigenvalues)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    G = torch.complex(torch.randn((n, n), generator=gen, dtype=torch.float64, device=device),
+                      torch.randn((n, n), generator=gen, dtype=torch.float64, device=device))
+    Q, R = torch.linalg.qr(G)
+    ph = torch.diagonal(R) / torch.abs(torch.diagonal(R))
+    Q = Q * ph
+    rad = 1.5 * torch.sqrt(torch.rand(n, generator=gen, dtype=torch.float64, device=device))
+    ang = 2.0 * math.pi * torch.rand(n, generator=gen, dtype=torch.float64, device=device)
+    d = torch.polar(rad, ang)
+    N = torch.complex(torch.randn((n, n), generator=gen, dtype=torch.float64, device=device),
+                      torch.randn((n, n), generator=gen, dtype=torch.float64, device=device))
+    T = torch.triu(N * (0.1 / math.sqrt(2.0 * n)), 1) + torch.diag(d)
+    A = Q @ T @ Q.conj().T
+    return A.T.contiguous(), d
+
+
 def synthesize(kind, n, seed, device="cuda"):
     """(dA column-major, dB column-major or None, reference spectrum) for one request."""
     import torch
+    if kind == eigdc.EIG_KIND_CPLANE:
+        dA, d = synthesize_complex(n, seed, device)
+        return dA, None, d
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
     Q = _orthogonal(n, gen, device)
@@ -75,6 +102,10 @@ def backward_error(kind, dA, o):
     Tensors hold column-major matrices, i.e. the row-major transposes."""
     import torch
     A0 = o["A0"]
+    if kind == eigdc.EIG_KIND_CPLANE:
+        Ut, Tt = o["dU"], o["dT"]   # transposes of U and T
+        rec = (Ut.T @ Tt.T @ Ut.T.conj().T).T
+        return float(torch.linalg.norm(A0 - rec) / torch.linalg.norm(A0))
     if kind == eigdc.EIG_KIND_SYM:
         Ut = o["dU"]
         rec = Ut.T @ torch.diag(o["dwr"]) @ Ut
@@ -95,7 +126,8 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, count)
     arrivals = np.cumsum(gaps) - gaps[0]
-    kinds = rng.choice([eigdc.EIG_KIND_SYM, eigdc.EIG_KIND_NONSYM, eigdc.EIG_KIND_PENCIL][:len(mix)],
+    kinds = rng.choice([eigdc.EIG_KIND_SYM, eigdc.EIG_KIND_NONSYM, eigdc.EIG_KIND_PENCIL,
+                        eigdc.EIG_KIND_CPLANE][:len(mix)],
                        size=count, p=np.asarray(mix) / np.sum(mix))
     sizes = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(int)
     reqs = []
@@ -104,6 +136,11 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
         kind = int(kinds[i])
         dA, dB, ref = synthesize(kind, n, seed * 1000003 + i, device)
         z = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=device)
+        zc = lambda *shape: torch.zeros(shape, dtype=torch.complex128, device=device)
+        if kind == eigdc.EIG_KIND_CPLANE:
+            out = dict(dw=zc(n), dU=zc(n, n), dT=zc(n, n), A0=dA.clone())
+            reqs.append((kind, n, dA, out, ref))
+            continue
         out = dict(dwr=z(n), dwi=z(n), dU=z(n, n), A0=dA.clone())
         if kind == eigdc.EIG_KIND_PENCIL:
             out.update(dB=dB, dQR=z(n, n), dbe=z(n), B0=dB.clone())
@@ -122,6 +159,8 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
         if kind == eigdc.EIG_KIND_PENCIL:
             tickets.append(srv.submit_pencil(dA, o["dB"], o["dU"], o["dQR"], o["dwr"], o["dwi"],
                                              o["dbe"], params64))
+        elif kind == eigdc.EIG_KIND_CPLANE:
+            tickets.append(srv.submit_complex(dA, o["dT"], o["dU"], o["dw"], params64))
         else:
             tickets.append(srv.submit(kind, dA, o["dwr"], o["dwi"], o["dU"], params))
     statuses, lat, wait, service = [], [], [], []
@@ -138,7 +177,13 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
     errs, bwds, records = [], [], []
     for i, ((kind, n, dA, o, ref), st) in enumerate(zip(reqs, statuses)):
         err = bwd = None
-        if st == 0:
+        if st == 0 and kind == eigdc.EIG_KIND_CPLANE:
+            # distance of each prescribed eigenvalue to the nearest computed one
+            err = float(torch.max(torch.min(torch.abs(ref[:, None] - o["dw"][None, :]), dim=1).values))
+            errs.append(err)
+            bwd = backward_error(kind, dA, o)
+            bwds.append(bwd)
+        elif st == 0:
             w = o["dwr"] / o["dbe"] if kind == eigdc.EIG_KIND_PENCIL else o["dwr"]
             err = float(torch.max(torch.abs(torch.sort(w).values - ref)))
             errs.append(err)
@@ -163,7 +208,8 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
                       eigdc.EIG_FP64_TC: "fp64 (tensor-core error-free split)"}[prec],
         "mix": {"sym": int(np.sum(kinds == eigdc.EIG_KIND_SYM)),
                 "nonsym": int(np.sum(kinds == eigdc.EIG_KIND_NONSYM)),
-                "pencil": int(np.sum(kinds == eigdc.EIG_KIND_PENCIL))},
+                "pencil": int(np.sum(kinds == eigdc.EIG_KIND_PENCIL)),
+                "complex_plane": int(np.sum(kinds == eigdc.EIG_KIND_CPLANE))},
     }
     if verbose:
         print(json.dumps(out))
@@ -182,11 +228,15 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--prec", type=int, default=2)
     ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--mix", default="0.5,0.3,0.2",
+                    help="shares of symmetric, nonsymmetric, pencil and (optional fourth) "
+                         "complex-plane requests")
     a = ap.parse_args()
     from . import build
     build.build()
-    run(a.rate, a.count, a.nmin, a.nmax, workers=a.workers, budget_gb=a.budget_gb, prec=a.prec,
-        seed=a.seed, verbose=True)
+    mix = tuple(float(x) for x in a.mix.split(","))
+    run(a.rate, a.count, a.nmin, a.nmax, mix=mix, workers=a.workers, budget_gb=a.budget_gb,
+        prec=a.prec, seed=a.seed, verbose=True)
 
 
 if __name__ == "__main__":
