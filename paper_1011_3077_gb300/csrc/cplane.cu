@@ -85,27 +85,33 @@ int nblocks(long long count, int per) { return (int)((count + per - 1) / per); }
 // 256 threads, 4 x 4 complex outputs per thread, K slabs of 8 in shared memory.
 constexpr int ZBM = 64, ZBN = 64, ZBK = 8;
 
+// With gridDim.z > 1 (split-K), CTA z takes K in [z kchunk, (z+1) kchunk) and
+// writes its partial alpha op(A) op(B) to C + z pstride (beta is then 0).
 template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) zgemm_kernel(int m, int n, int k, zt alpha,
                                                     const zt* __restrict__ A, int lda,
                                                     const zt* __restrict__ B, int ldb, zt beta,
-                                                    zt* __restrict__ C, int ldc) {
+                                                    zt* __restrict__ C, int ldc, int kchunk,
+                                                    size_t pstride) {
   __shared__ zt As[ZBK][ZBM + 1];
   __shared__ zt Bs[ZBK][ZBN + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int row0 = blockIdx.x * ZBM, col0 = blockIdx.y * ZBN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(k, kbeg + kchunk);
+  C += blockIdx.z * pstride;
   zt acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = zmk(0.0, 0.0);
-  for (int k0 = 0; k0 < k; k0 += ZBK) {
+  for (int k0 = kbeg; k0 < kend; k0 += ZBK) {
     for (int e = tid; e < ZBK * ZBM; e += 256) {
       int r, kk;
       if (!TA) { r = e % ZBM; kk = e / ZBM; } else { kk = e % ZBK; r = e / ZBK; }
       const int gr = row0 + r, gk = k0 + kk;
       zt v = zmk(0.0, 0.0);
-      if (gr < m && gk < k) v = TA ? zconj(A[gk + (size_t)gr * lda]) : A[gr + (size_t)gk * lda];
+      if (gr < m && gk < kend) v = TA ? zconj(A[gk + (size_t)gr * lda]) : A[gr + (size_t)gk * lda];
       As[kk][r] = v;
     }
     for (int e = tid; e < ZBK * ZBN; e += 256) {
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int m, int n, int k, zt alph
       if (!TB) { kk = e % ZBK; c = e / ZBK; } else { c = e % ZBN; kk = e / ZBN; }
       const int gc = col0 + c, gk = k0 + kk;
       zt v = zmk(0.0, 0.0);
-      if (gc < n && gk < k) v = TB ? zconj(B[gc + (size_t)gk * ldb]) : B[gk + (size_t)gc * ldb];
+      if (gc < n && gk < kend) v = TB ? zconj(B[gc + (size_t)gk * ldb]) : B[gk + (size_t)gc * ldb];
       Bs[kk][c] = v;
     }
     __syncthreads();
@@ -147,22 +153,71 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int m, int n, int k, zt alph
   }
 }
 
+// C = sum_z P[z] (in z order) + beta C; P[z] is m x n with leading dimension m
+__global__ void zreduce_kernel(int m, int n, int splits, const zt* __restrict__ P, size_t pstride,
+                               zt beta, zt* __restrict__ C, int ldc) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * n) return;
+  const int i = (int)(e % m), j = (int)(e / m);
+  zt v = P[e];
+  for (int z = 1; z < splits; ++z) v = zadd(v, P[e + z * pstride]);
+  if (beta.x != 0.0 || beta.y != 0.0) v = zfma(beta, C[i + (size_t)j * ldc], v);
+  C[i + (size_t)j * ldc] = v;
+}
+
+void zgemm_launch(cudaStream_t s, bool ta, bool tb, dim3 g, int m, int n, int k, zt alpha,
+                  const zt* A, int lda, const zt* B, int ldb, zt beta, zt* C, int ldc, int kchunk,
+                  size_t pstride) {
+  note_launches(1);
+  if (!ta && !tb)
+    zgemm_kernel<false, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pstride);
+  else if (ta && !tb)
+    zgemm_kernel<true, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pstride);
+  else if (!ta && tb)
+    zgemm_kernel<false, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pstride);
+  else
+    zgemm_kernel<true, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, kchunk, pstride);
+}
+
 }  // namespace
 
 cudaError_t zgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double2 alpha,
                   const double2* A, int lda, const double2* B, int ldb, double2 beta, double2* C,
                   int ldc) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  dim3 g(nblocks(m, ZBM), nblocks(n, ZBN));
-  note_launches(1);
-  if (!ta && !tb) zgemm_kernel<false, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (ta && !tb) zgemm_kernel<true, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (!ta && tb) zgemm_kernel<false, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
-  else zgemm_kernel<true, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  dim3 g(nblocks(m, ZBM), nblocks(n, ZBN), 1);
+  zgemm_launch(s, ta, tb, g, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, std::max(k, 1), 0);
   return cudaGetLastError();
 }
 
 namespace {
+
+// Splits of K for a product whose tile grid is small: about two CTAs per SM
+// (152 SMs) without chunks shorter than 256.
+int zsplits(int m, int n, int k) {
+  const long long tiles = (long long)nblocks(m, ZBM) * nblocks(n, ZBN);
+  int sp = (int)std::min<long long>(16, std::max<long long>(1, 304 / std::max<long long>(tiles, 1)));
+  sp = std::min(sp, std::max(1, k / 256));
+  return sp;
+}
+
+// zgemm with split-K partials in `partial` (capacity `cap` complex entries);
+// falls back to one pass when the partials do not fit.
+cudaError_t zgemm_sk(cudaStream_t s, bool ta, bool tb, int m, int n, int k, zt alpha, const zt* A,
+                     int lda, const zt* B, int ldb, zt beta, zt* C, int ldc, zt* partial, size_t cap) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  int sp = zsplits(m, n, k);
+  const size_t pstride = (size_t)m * n;
+  if (!partial || (size_t)sp * pstride > cap) sp = 1;
+  if (sp == 1) return zgemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+  const int kchunk = ((k + sp - 1) / sp + ZBK - 1) / ZBK * ZBK;
+  sp = (k + kchunk - 1) / kchunk;
+  dim3 g(nblocks(m, ZBM), nblocks(n, ZBN), sp);
+  zgemm_launch(s, ta, tb, g, m, n, k, alpha, A, lda, B, ldb, zmk(0.0, 0.0), partial, m, kchunk, pstride);
+  note_launches(1);
+  zreduce_kernel<<<nblocks((long long)m * n, 256), 256, 0, s>>>(m, n, sp, partial, pstride, beta, C, ldc);
+  return cudaGetLastError();
+}
 
 // ------------------------------------------------------------------ elementwise
 // B = A (rows x cols)
@@ -515,6 +570,8 @@ struct ZQR {
   zt* W1;       // ZNB x n
   zt* W2;       // ZNB x n
   zt* gram;     // ceil(m / 64) x 1024
+  zt* part = nullptr;   // split-K partials of the V^H C products
+  size_t part_cap = 0;  // complex entries
   int m, n;
 };
 
@@ -540,7 +597,8 @@ cudaError_t zgeqrf(cudaStream_t s, int m, int n, zt* P, int ldp, const ZQR& q, z
     if (nc > 0) {
       zt* C = P + j0 + (size_t)(j0 + jb) * ldp;
       cudaError_t e;
-      if ((e = zgemm(s, true, false, jb, nc, mm, one, Vp, m, C, ldp, zero, q.W1, ZNB)) != cudaSuccess) return e;
+      if ((e = zgemm_sk(s, true, false, jb, nc, mm, one, Vp, m, C, ldp, zero, q.W1, ZNB, q.part,
+                        q.part_cap)) != cudaSuccess) return e;
       if ((e = zgemm(s, true, false, jb, nc, jb, one, Tp, ZNB, q.W1, ZNB, zero, q.W2, ZNB)) != cudaSuccess) return e;
       if ((e = zgemm(s, false, false, mm, nc, jb, mone, Vp, m, q.W2, ZNB, one, C, ldp)) != cudaSuccess) return e;
     }
@@ -566,7 +624,8 @@ cudaError_t zapply_q(cudaStream_t s, const ZQR& q, zt* E, int c, bool phase_fix)
     const zt* Tp = q.T + (size_t)j0 * ZNB;
     zt* Ep = E + j0;
     cudaError_t e;
-    if ((e = zgemm(s, true, false, jb, c, mm, one, Vp, m, Ep, m, zero, q.W1, ZNB)) != cudaSuccess) return e;
+    if ((e = zgemm_sk(s, true, false, jb, c, mm, one, Vp, m, Ep, m, zero, q.W1, ZNB, q.part,
+                      q.part_cap)) != cudaSuccess) return e;
     if ((e = zgemm(s, false, false, jb, c, jb, one, Tp, ZNB, q.W1, ZNB, zero, q.W2, ZNB)) != cudaSuccess) return e;
     if ((e = zgemm(s, false, false, mm, c, jb, mone, Vp, m, q.W2, ZNB, one, Ep, m)) != cudaSuccess) return e;
   }
@@ -941,6 +1000,8 @@ void make_bufs(CDriver& D, StepBufs& b, int cap, bool tensor_cores) {
   b.q.W1 = D.alloc<zt>((size_t)ZNB * cap);
   b.q.W2 = D.alloc<zt>((size_t)ZNB * cap);
   b.q.gram = D.alloc<zt>((size_t)nblocks(2 * cap, 64) * 1024);
+  b.q.part_cap = (size_t)16 * ZNB * cap;
+  b.q.part = D.alloc<zt>(b.q.part_cap);
   if (tensor_cores && cap >= 128) {
     b.tc.on = true;
     b.tc.plane = c2;
@@ -1471,7 +1532,7 @@ size_t cplane_footprint(int n, int prec) {
   // U update scratch n^2 complex; node matrices up to 2 n^2 complex; the
   // final A U and U^H A U 2 n^2 complex
   size_t bytes = 24 * c2 * z + 3 * c2 * sizeof(double) + c2 * z + 2 * c2 * z + 2 * c2 * z;
-  bytes += (size_t)(4 * ZNB + 8) * n * z + (size_t)(nblocks(2 * n, 64) * 1024) * z +
+  bytes += (size_t)(20 * ZNB + 8) * n * z + (size_t)(nblocks(2 * n, 64) * 1024) * z +
            (size_t)((n + 31) / 32 + 8) * n * sizeof(double);
   if (prec == EIG_FP64_TC && n >= 128) bytes += 8 * c2 * sizeof(double) + tcx_gemm_workspace_bytes(n, n, n);
   return bytes + ((size_t)64 << 20);   // allocator granularity and leaf buffers
