@@ -410,6 +410,20 @@ def cplane_arm(args, torch, eigdc, h, dev, stream, world):
     bwd = float(torch.linalg.norm(Ac - U @ T @ U.conj().t()) / torch.linalg.norm(Ac))
     I = torch.eye(n, dtype=torch.complex128, device=dev)
     orth = float(torch.linalg.norm(U.conj().t() @ U - I))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle's complex-plane driver on the same construction at n = 128,
+        # scaled by (n/128)^3 (the step cost is cubic)
+        from oracle.cplane import schur_complex_plane
+        ns = min(n, 128)
+        As, _ = workloads.normal_complex(ns, seed=30)
+        t0 = time.perf_counter()
+        schur_complex_plane(As, seed=0, leaf_size=64)
+        ts = time.perf_counter() - t0
+        cpu = {"kind": "oracle", "value": 1.0 / (ts * (n / ns) ** 3), "unit": "solves/s",
+               "cores": os.cpu_count(),
+               "sample": "oracle complex-plane solve of the same construction at n=%d (%.1f s), "
+                         "scaled by (n/%d)^3" % (ns, ts, ns)}
     line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
             "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -421,7 +435,7 @@ def cplane_arm(args, torch, eigdc, h, dev, stream, world):
             "splits": info.splits, "nodes": info.nodes, "squarings": info.total_iters,
             "backward_error": bwd, "orthogonality_frobenius": orth,
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
-            "e2e": None, "cpu_baseline": None}
+            "e2e": None, "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
