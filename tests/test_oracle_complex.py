@@ -479,3 +479,42 @@ def test_rurv_is_rank_revealing(field):
     assert np.median(lo) >= 0.05
     assert np.median(hi) <= 1e3
     assert np.median(cross) <= 10.0
+
+
+def test_squaring_count_follows_the_papers_distance_formula():
+    # Sec. 3.3 (eqs. p-eq and d1): with d_L(A, I) the distance to the line,
+    #   d_L = 2 min_theta sigma_min(sin(theta)(A - aI) + i cos(theta) I),
+    # and n_a = ||(A - aI + I, A - aI - I)||, about log2(n_a/d_L - 1) +
+    # log2 log2(1/eps) squarings reach relative error eps.  For a normal A,
+    # d_L = 2 min_lambda |delta| / sqrt(1 + gamma^2) (delta + i gamma = lambda - a);
+    # that closed form is checked against a grid over theta, then the squaring
+    # counts of the rotated, scaled problem against the bound.
+    rng = np.random.default_rng(5)
+    for trial in range(6):
+        n = 40
+        w = np.exp(2j * np.pi * rng.uniform())
+        t = rng.uniform(-0.3, 0.3)
+        s = 3.0
+        lam = 1.5 * _crandn(rng, n)
+        dist = 10.0 ** rng.uniform(-6, -1)
+        lam[0] = w * (t + dist + 1j * rng.uniform(-1, 1))
+        W = cqr_explicit(_crandn(rng, n, n))[0]
+        A = W @ np.diag(lam) @ W.conj().T
+        res = cirs(*line_map(A, w, t, s))
+        assert res.converged
+        zp = (np.conj(w) * lam - t) / s                  # the line becomes Re z = 0
+        dL = 2.0 * np.min(np.abs(zp.real) / np.sqrt(1.0 + zp.imag ** 2))
+        Ap = (np.conj(w) * A - t * np.eye(n)) / s
+        if trial == 0:
+            smin = lambda th: np.linalg.svd(np.sin(th) * Ap + 1j * np.cos(th) * np.eye(n),
+                                            compute_uv=False)[-1]
+            # the minimiser: sin(theta) gamma + cos(theta) = 0 for the nearest eigenvalue
+            i = int(np.argmin(np.abs(zp.real) / np.sqrt(1.0 + zp.imag ** 2)))
+            th_star = np.arctan2(1.0, -zp.imag[i])
+            assert abs(2.0 * smin(th_star) - dL) <= 1e-8 * dL
+            grid = min(smin(th) for th in np.linspace(0.0, np.pi, 4001))
+            assert 2.0 * grid >= dL * (1.0 - 1e-9)            # nothing smaller elsewhere
+        na = np.linalg.norm(np.vstack([Ap + np.eye(n), Ap - np.eye(n)]), 2)
+        eps = 4.0 * np.sqrt(n) * 2.0 ** -53              # the stopping tolerance tau
+        bound = np.log2(na / dL - 1.0) + np.log2(np.log2(1.0 / eps))
+        assert bound - 2.0 <= res.iters <= bound + 1.0
