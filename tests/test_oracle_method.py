@@ -640,3 +640,33 @@ def test_trevc_eigenvectors_of_schur_form(kind):
         k = int(np.argmin(np.abs(w_ref - lam[j])))
         cosang = abs(np.vdot(V_ref[:, k], V[:, j])) / np.linalg.norm(V_ref[:, k])
         assert cosang >= 1.0 - 1e-8
+
+
+def test_real_line_squarings_follow_the_papers_distance_formula():
+    # Sec. 3.3 (eqs. p-eq and d1) on the real path: a real normal matrix with
+    # pairs a +- ib, the line Re z = sigma with scale s.  In the scaled frame
+    # z' = (z - sigma)/s, d_L = 2 min |Re z'| / sqrt(1 + (Im z')^2) and about
+    # log2(n_a/d_L - 1) + log2 log2(1/eps) squarings reach relative error eps.
+    rng = np.random.default_rng(17)
+    for trial in range(5):
+        n = 40
+        npair = n // 2
+        re = rng.uniform(-1.5, 1.5, npair)
+        im = rng.uniform(-1.5, 1.5, npair)
+        sigma, s = rng.uniform(-0.3, 0.3), 3.0
+        re[0] = sigma + 10.0 ** rng.uniform(-6, -1)
+        D = np.zeros((n, n))
+        for i in range(npair):
+            D[2 * i:2 * i + 2, 2 * i:2 * i + 2] = [[re[i], im[i]], [-im[i], re[i]]]
+        Q = workloads.random_orthogonal(n, rng)
+        A = Q @ D @ Q.T
+        res = irs(*region_map(A, None, REGION_LINE, sigma, s))
+        assert res.converged
+        lam = np.concatenate([re + 1j * im, re - 1j * im])
+        zp = (lam - sigma) / s
+        dL = 2.0 * np.min(np.abs(zp.real) / np.sqrt(1.0 + zp.imag ** 2))
+        Ap = (A - sigma * np.eye(n)) / s
+        na = np.linalg.norm(np.vstack([Ap + np.eye(n), Ap - np.eye(n)]), 2)
+        eps = 4.0 * np.sqrt(n) * 2.0 ** -53
+        bound = np.log2(na / dL - 1.0) + np.log2(np.log2(1.0 / eps))
+        assert bound - 2.0 <= res.iters <= bound + 1.0
