@@ -404,8 +404,9 @@ int eig_gemm_noalloc(void* stream, int ta, int tb, int m, int n, int k, double a
  *   - dT (ldt >= n), dQ (ldq >= n), dwi (n): device, real, not modified.
  *   - dV (ldv >= n): device, complex (interleaved), receives unit 2-norm
  *     eigenvectors, A V = V diag(lam); dlam: device, n complex eigenvalues.
- *   - The eigenvalues must be distinct (the recurrence divides by their
- *     differences); equal ones give non-finite vectors. */
+ *   - The recurrence divides by eigenvalue differences; one of modulus below
+ *     2^-53 max |T_ii| is replaced by that value, so equal eigenvalues give
+ *     large but finite vectors. */
 int eig_eigenvectors(eig_handle_t h, int n, const double* dT, int ldt, const double* dQ, int ldq,
                      const double* dwi, double* dV, int ldv, double* dlam);
 /* The same from a complex Schur form A = U T U^H (interleaved complex, T upper

@@ -49,16 +49,33 @@ def real_to_complex_schur(T, Q, wi):
     return Tc, Qc
 
 
+def small_pivot(T):
+    """smin = u max_i |T_ii| (u = 2^-53; 2^-1022 if T's diagonal is zero)."""
+    d = np.abs(np.diag(np.asarray(T)))
+    top = float(np.max(d)) if d.size else 0.0
+    return max(2.0 ** -53 * top, 2.0 ** -1022)
+
+
 def triangular_eigenvectors(T):
-    """Upper triangular X with T X = X diag(T), X_jj = 1 (distinct eigenvalues)."""
+    """Upper triangular X with T X = X diag(T), X_jj = 1.
+
+    A denominator T_jj - T_ii of modulus below small_pivot(T) is replaced by
+    small_pivot(T) (reading: the paper divides by it directly; an exact double
+    eigenvalue would give an infinite vector, and the standard triangular
+    eigenvector solvers perturb such pivots to the rounding level instead).
+    Distinct eigenvalues separated by more than that are unaffected."""
     T = np.asarray(T)
     n = T.shape[0]
+    smin = small_pivot(T)
     X = np.zeros((n, n), dtype=np.result_type(T.dtype, np.float64))
     for j in range(n):
         X[j, j] = 1.0
         for i in range(j - 1, -1, -1):
             s = T[i, j] * X[j, j] + T[i, i + 1:j] @ X[i + 1:j, j]
-            X[i, j] = s / (T[j, j] - T[i, i])
+            den = T[j, j] - T[i, i]
+            if abs(den) < smin:
+                den = smin
+            X[i, j] = s / den
     return X
 
 

@@ -16,7 +16,8 @@
 //      GEMM and (T_II - lambda_j I) X(I, j) = rhs_j is a back substitution
 //      per column.  The GEMMs carry the O(n^3) work (the blocked form's point).
 //   3. V = Qc X with unit 2-norm columns.
-// Distinct eigenvalues are assumed (the recurrence divides by T_jj - T_ii).
+// A pivot T_jj - T_ii below u max |T_ii| is replaced by that value (equal
+// eigenvalues give large, finite vectors instead of a division by zero).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -140,8 +141,14 @@ __global__ void lower_zero_kernel(int n, zt* __restrict__ T, int ldt) {
 
 // Diagonal blocks of X (one CTA per block of TB): X_jj = 1 and the recurrence
 // X_ij = (T_ij + sum_{k=i+1}^{j-1} T_ik X_kj) / (T_jj - T_ii); one thread per column.
+// A denominator of modulus below smin (u max |T_ii|) is replaced by smin, so
+// an exact double eigenvalue gives a large, finite vector.
+__device__ __forceinline__ zt guard_pivot(zt d, double smin) {
+  return (d.x * d.x + d.y * d.y < smin * smin) ? tz(smin, 0.0) : d;
+}
+
 __global__ void __launch_bounds__(TB) trevc_diag_kernel(int n, const zt* __restrict__ T, int ldt,
-                                                        zt* __restrict__ X, int ldx) {
+                                                        zt* __restrict__ X, int ldx, double smin) {
   __shared__ zt Ts[TB][TB + 1];
   __shared__ zt Xs[TB][TB + 1];
   const int J0 = blockIdx.x * TB;
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(TB) trevc_diag_kernel(int n, const zt* __restr
     for (int i = j - 1; i >= 0; --i) {
       zt s = Ts[i][j];
       for (int k = i + 1; k < j; ++k) s = tadd(s, tmul(Ts[i][k], Xs[k][j]));
-      Xs[i][j] = tdiv(s, tsub(lam, Ts[i][i]));
+      Xs[i][j] = tdiv(s, guard_pivot(tsub(lam, Ts[i][i]), smin));
     }
   }
   __syncthreads();
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(TB) trevc_diag_kernel(int n, const zt* __restr
 __global__ void __launch_bounds__(128) trevc_row_kernel(int n, int I0, int bi, int c0,
                                                         const zt* __restrict__ T, int ldt,
                                                         const zt* __restrict__ rhs, int ldr,
-                                                        zt* __restrict__ X, int ldx) {
+                                                        zt* __restrict__ X, int ldx, double smin) {
   __shared__ zt Ts[TB][TB + 1];
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
     const int i = e % TB, j = e / TB;
@@ -194,7 +201,9 @@ __global__ void __launch_bounds__(128) trevc_row_kernel(int n, int I0, int bi, i
 #pragma unroll
       for (int q = r + 1; q < TB; ++q)
         if (q < bi) s = tsub(s, tmul(Ts[r][q], x[q]));
-      x[r] = tdiv(s, tsub(Ts[r][r], lam));
+      // (T_rr - lambda_j) x_r = s: the guarded pivot is -(lambda_j - T_rr)
+      const zt g = guard_pivot(tsub(lam, Ts[r][r]), smin);
+      x[r] = tdiv(s, tz(-g.x, -g.y));
     }
   }
 #pragma unroll
@@ -311,10 +320,20 @@ int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, in
     rot_cols_kernel<<<tblocks((long long)n * nblk, 256), 256, 0, s>>>(n, nblk, didx, G, Tc, n, Qc, n);
     rot_rows_kernel<<<tblocks((long long)n * nblk, 256), 256, 0, s>>>(n, nblk, didx, G, Tc, n);
   }
-  note_launches(2);
+  note_launches(1);
   lower_zero_kernel<<<tblocks((long long)nn, 256), 256, 0, s>>>(n, Tc, n);
+  // smin = u max |T_ii| from the diagonal of Tc
+  std::vector<double> hd(2 * (size_t)n);
+  e = cudaMemcpy2DAsync(hd.data(), 2 * sizeof(double), Tc, (n + 1) * sizeof(zt), 2 * sizeof(double), n,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(e, "diagonal copy");
+  double top = 0.0;
+  for (int i = 0; i < n; ++i) top = std::max(top, std::hypot(hd[2 * i], hd[2 * i + 1]));
+  const double smin = std::max(0x1p-53 * top, 0x1p-1022);
   const int nb = (n + TB - 1) / TB;
-  trevc_diag_kernel<<<nb, TB, 0, s>>>(n, Tc, n, X, n);
+  note_launches(1);
+  trevc_diag_kernel<<<nb, TB, 0, s>>>(n, Tc, n, X, n, smin);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "diagonal blocks");
   const zt one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0), mone = make_double2(-1.0, 0.0);
   for (int I = nb - 2; I >= 0; --I) {
@@ -324,7 +343,7 @@ int trevc(cudaStream_t s, int n, const double* dT, int ldt, const double* dQ, in
                    n, zero, rhs, TB)) != cudaSuccess)
       return fail(e, "block row GEMM");
     note_launches(1);
-    trevc_row_kernel<<<tblocks(nc, 128), 128, 0, s>>>(n, I0, bi, c0, Tc, n, rhs, TB, X, n);
+    trevc_row_kernel<<<tblocks(nc, 128), 128, 0, s>>>(n, I0, bi, c0, Tc, n, rhs, TB, X, n, smin);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "block row solve");
   }
   if ((e = zgemm(s, false, false, n, n, n, one, Qc, n, X, n, zero, dV, ldv)) != cudaSuccess)

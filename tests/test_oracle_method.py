@@ -670,3 +670,17 @@ def test_real_line_squarings_follow_the_papers_distance_formula():
         eps = 4.0 * np.sqrt(n) * 2.0 ** -53
         bound = np.log2(na / dL - 1.0) + np.log2(np.log2(1.0 / eps))
         assert bound - 2.0 <= res.iters <= bound + 1.0
+
+
+def test_trevc_small_pivot_keeps_vectors_finite():
+    from oracle.trevc import triangular_eigenvectors, small_pivot
+    # an exact double eigenvalue: the plain recurrence divides by zero
+    T = np.array([[1.0, 2.0, 0.5], [0.0, 1.0, 0.3], [0.0, 0.0, -0.5]])
+    X = triangular_eigenvectors(T)
+    assert np.all(np.isfinite(X))
+    assert X[0, 1] == 2.0 / small_pivot(T)
+    # distinct eigenvalues: the same as the plain recurrence
+    rng = np.random.default_rng(4)
+    T2 = np.triu(rng.standard_normal((6, 6)))
+    X2 = triangular_eigenvectors(T2)
+    assert np.abs(T2 @ X2 - X2 * np.diag(T2)).max() <= 1e-12 * np.abs(X2).max()
