@@ -387,6 +387,7 @@ class CInfo:
         self.recenters = []        # (node, old radius, new radius, "one chop" | "two chops")
         self.lines = []            # (node, attempt, w, t, outcome, disk centre, disk radius, rank)
         self.clusters = []         # (offset, size, Region)
+        self.split_regions = []    # (node, Region, (w, t), [own disks], [child Regions])
 
 
 def draw_line(region, seed, node, attempt, perpendicular_to=None):
@@ -444,11 +445,13 @@ def schur_complex_plane(A, seed=0, leaf_size=64, tau=None, maxit=60, split_tol=N
                 r1.halfplanes.append((w, t))
                 r2 = region.copy()
                 r2.halfplanes.append((-w, -t))
-                kids = []
+                kids, own = [], []
                 for Ab, rr in ((A11, r1), (A22, r2)):
                     cg, Rg = frobenius_disk(Ab)
+                    own.append((cg, Rg))
                     ce, Re = enclosing_circle(rr)
                     kids.append(Region(cg, Rg) if Rg <= Re else Region(ce, Re))
+                info.split_regions.append((node, region.copy(), (w, t), own, kids))
                 info.splits += 1
                 info.lines.append((node, attempt, w, t, "split", region.c, region.R, st.rank))
                 work.append((off + k, m - k, A22, kids[1], child_node(node, 1), depth + 1))

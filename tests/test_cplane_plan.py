@@ -106,3 +106,34 @@ def test_node_plan_replays_the_oracle(harness, name, make, kw):
                        and int(end[5]) == len(reg.halfplanes) for reg in clusters)
         checked += 1
     assert checked >= 1
+
+
+@pytest.fixture(scope="module")
+def children_harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = tmp_path_factory.mktemp("kids") / "cplane_children"
+    subprocess.check_call([cxx, "-std=c++17", "-O2", "-I", CSRC,
+                           os.path.join(HERE, "harness", "cplane_children.cpp"), "-o", str(exe)])
+    return str(exe)
+
+
+@pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
+def test_child_regions_replay_the_oracle(children_harness, name, make, kw):
+    """After every split of the oracle's solves, the library's child_regions
+    gives the children the same disks (each side's enclosing circle, or the
+    block's own disk when that is not larger)."""
+    A = make()
+    T, U, w, info = cplane.schur_complex_plane(A, **kw)
+    for node, reg, (wl, t), own, kids in info.split_regions:
+        rows = ["%.17g %.17g %.17g %d" % (reg.c.real, reg.c.imag, reg.R, len(reg.halfplanes))]
+        rows += ["%.17g %.17g %.17g" % (hw.real, hw.imag, ht) for hw, ht in reg.halfplanes]
+        rows.append("%.17g %.17g %.17g" % (wl.real, wl.imag, t))
+        rows += ["%.17g %.17g %.17g" % (c.real, c.imag, R) for c, R in own]
+        out = subprocess.run([children_harness], input="\n".join(rows) + "\n", capture_output=True,
+                             text=True, check=True).stdout.split("\n")
+        for line, kid in zip(out[:2], kids):
+            _, cr, ci, R = line.split()
+            assert abs(complex(float(cr), float(ci)) - kid.c) <= 1e-13 * (1 + abs(kid.c))
+            assert abs(float(R) - kid.R) <= 1e-13 * kid.R
