@@ -461,8 +461,8 @@ typedef struct {
  *   - enclose = 1: a node that fails max_fail times is returned as a cluster:
  *     its block is put in Schur form by the leaf solver and its region is
  *     written to enc[i] (up to enc_cap entries; *n_enc = number of clusters).
- *     enclose = 0: such a node stops the solve with EIG_NO_SPLIT, and so
- *     does a cluster larger than 64 (it is still written to enc).
+ *     enclose = 0: such a node stops the solve with EIG_NO_SPLIT.  Clusters
+ *     larger than 64 use a global-memory form of the leaf solver.
  *   - Returns EIG_NO_CONVERGENCE if a leaf's QR iteration ran out of steps. */
 int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* dT, int ldt,
                       double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,

@@ -640,6 +640,7 @@ struct ZLeafDesc {
   zt* T;         // m x m, ld m
   zt* Z;         // m x m, ld m
   int* status;   // 0 ok, 1 iteration budget spent
+  zt* work;      // zschur_leaf_global_kernel only: 2 m^2 + 2 m complex
 };
 
 __device__ void zleaf_givens(zt a, zt b, zt* G) {
@@ -656,55 +657,67 @@ __device__ void zleaf_givens(zt a, zt b, zt* G) {
 }
 
 // H <- G_k H G_k^H on indices (k, k+1), Z <- Z G_k^H (all threads take part).
-__device__ void zleaf_rotate(int m, zt (*H)[ZLEAF_MAX + 1], zt (*Z)[ZLEAF_MAX + 1], int k,
-                             const zt* G) {
+// Storage of a leaf's H and Z: shared memory (m <= ZLEAF_MAX) or global scratch.
+struct SharedMat {
+  zt (*p)[ZLEAF_MAX + 1];
+  __device__ zt& operator()(int i, int j) const { return p[i][j]; }
+};
+struct GlobalMat {
+  zt* p;
+  int ld;
+  __device__ zt& operator()(int i, int j) const { return p[i + (size_t)j * ld]; }
+};
+
+// block-wide scalars of the leaf solver (shared memory)
+struct LeafShared {
+  zt G[4];
+  double tau;
+  int lo, hi, act;
+};
+
+template <class Mat>
+__device__ void zleaf_rotate(int m, Mat H, Mat Z, int k, const zt* G) {
   for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    const zt h0 = H[k][c], h1 = H[k + 1][c];
-    H[k][c] = zfma(G[0], h0, zmul(G[1], h1));
-    H[k + 1][c] = zfma(G[2], h0, zmul(G[3], h1));
+    const zt h0 = H(k, c), h1 = H(k + 1, c);
+    H(k, c) = zfma(G[0], h0, zmul(G[1], h1));
+    H(k + 1, c) = zfma(G[2], h0, zmul(G[3], h1));
   }
   __syncthreads();
   // right multiplication by G^H: [x0, x1] G^H = [x0 conj(G0) + x1 conj(G1), x0 conj(G2) + x1 conj(G3)]
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
-    const zt h0 = H[r][k], h1 = H[r][k + 1];
-    H[r][k] = zadd(zmul(h0, zconj(G[0])), zmul(h1, zconj(G[1])));
-    H[r][k + 1] = zadd(zmul(h0, zconj(G[2])), zmul(h1, zconj(G[3])));
-    const zt z0 = Z[r][k], z1 = Z[r][k + 1];
-    Z[r][k] = zadd(zmul(z0, zconj(G[0])), zmul(z1, zconj(G[1])));
-    Z[r][k + 1] = zadd(zmul(z0, zconj(G[2])), zmul(z1, zconj(G[3])));
+    const zt h0 = H(r, k), h1 = H(r, k + 1);
+    H(r, k) = zadd(zmul(h0, zconj(G[0])), zmul(h1, zconj(G[1])));
+    H(r, k + 1) = zadd(zmul(h0, zconj(G[2])), zmul(h1, zconj(G[3])));
+    const zt z0 = Z(r, k), z1 = Z(r, k + 1);
+    Z(r, k) = zadd(zmul(z0, zconj(G[0])), zmul(z1, zconj(G[1])));
+    Z(r, k + 1) = zadd(zmul(z0, zconj(G[2])), zmul(z1, zconj(G[3])));
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __restrict__ desc) {
-  extern __shared__ zt zsm[];
-  zt (*H)[ZLEAF_MAX + 1] = reinterpret_cast<zt (*)[ZLEAF_MAX + 1]>(zsm);
-  zt (*Z)[ZLEAF_MAX + 1] = reinterpret_cast<zt (*)[ZLEAF_MAX + 1]>(zsm + ZLEAF_MAX * (ZLEAF_MAX + 1));
-  __shared__ zt u[ZLEAF_MAX];
-  __shared__ zt dots[ZLEAF_MAX];
-  __shared__ zt G[4];
-  __shared__ double s_tau;
-  __shared__ int s_lo, s_hi, s_act;
-  const ZLeafDesc d = desc[blockIdx.x];
-  const int m = d.m;
+// The leaf solver on H, Z (m x m) with the work vectors u, dots (m each).
+template <class Mat>
+__device__ void zleaf_solve(const ZLeafDesc& d, int m, Mat H, Mat Z, zt* u, zt* dots,
+                            LeafShared& sh) {
+  zt* G = sh.G;
+  double& s_tau = sh.tau;
+  int& s_lo = sh.lo;
+  int& s_hi = sh.hi;
+  int& s_act = sh.act;
   const int tid = threadIdx.x;
-  if (m < 1 || m > ZLEAF_MAX) {   // the shared arrays hold at most ZLEAF_MAX rows
-    if (tid == 0) *d.status = 1;
-    return;
-  }
   for (int e = tid; e < m * m; e += blockDim.x) {
     const int i = e % m, j = e / m;
-    H[i][j] = d.A[i + (size_t)j * d.lda];
-    Z[i][j] = zmk(i == j ? 1.0 : 0.0, 0.0);
+    H(i, j) = d.A[i + (size_t)j * d.lda];
+    Z(i, j) = zmk(i == j ? 1.0 : 0.0, 0.0);
   }
   __syncthreads();
   // Householder reduction to Hessenberg form (the reflector convention of the QR)
   for (int k = 0; k + 2 < m; ++k) {
     if (tid == 0) {
       double ss = 0.0;
-      for (int r = k + 1; r < m; ++r) ss += H[r][k].x * H[r][k].x + H[r][k].y * H[r][k].y;
+      for (int r = k + 1; r < m; ++r) ss += H(r, k).x * H(r, k).x + H(r, k).y * H(r, k).y;
       const double nrm = sqrt(ss);
-      const zt x0 = H[k + 1][k];
+      const zt x0 = H(k + 1, k);
       const double a0 = zabs(x0);
       if (nrm == 0.0) {
         s_tau = 0.0;
@@ -714,7 +727,7 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
         const zt iv = zmk(ph.x / mag, -ph.y / mag);
         s_tau = mag / nrm;
         u[k + 1] = zmk(1.0, 0.0);
-        for (int r = k + 2; r < m; ++r) u[r] = zmul(H[r][k], iv);
+        for (int r = k + 2; r < m; ++r) u[r] = zmul(H(r, k), iv);
       }
     }
     __syncthreads();
@@ -723,31 +736,31 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
     // left: H(k+1:, :) -= tau u (u^H H(k+1:, :))
     for (int c = tid; c < m; c += blockDim.x) {
       zt acc = zmk(0.0, 0.0);
-      for (int r = k + 1; r < m; ++r) acc = zcfma(u[r], H[r][c], acc);
+      for (int r = k + 1; r < m; ++r) acc = zcfma(u[r], H(r, c), acc);
       dots[c] = zscale(tk, acc);
     }
     __syncthreads();
     for (int e = tid; e < (m - k - 1) * m; e += blockDim.x) {
       const int r = k + 1 + e % (m - k - 1), c = e / (m - k - 1);
-      H[r][c] = zsub(H[r][c], zmul(u[r], dots[c]));
+      H(r, c) = zsub(H(r, c), zmul(u[r], dots[c]));
     }
     __syncthreads();
     // right: H(:, k+1:) -= tau (H(:, k+1:) u) u^H, same for Z
     for (int r = tid; r < m; r += blockDim.x) {
       zt ah = zmk(0.0, 0.0), az = zmk(0.0, 0.0);
       for (int c = k + 1; c < m; ++c) {
-        ah = zfma(H[r][c], u[c], ah);
-        az = zfma(Z[r][c], u[c], az);
+        ah = zfma(H(r, c), u[c], ah);
+        az = zfma(Z(r, c), u[c], az);
       }
       ah = zscale(tk, ah);
       az = zscale(tk, az);
       for (int c = k + 1; c < m; ++c) {
-        H[r][c] = zsub(H[r][c], zmul(ah, zconj(u[c])));
-        Z[r][c] = zsub(Z[r][c], zmul(az, zconj(u[c])));
+        H(r, c) = zsub(H(r, c), zmul(ah, zconj(u[c])));
+        Z(r, c) = zsub(Z(r, c), zmul(az, zconj(u[c])));
       }
     }
     __syncthreads();
-    for (int r = k + 2 + tid; r < m; r += blockDim.x) H[r][k] = zmk(0.0, 0.0);
+    for (int r = k + 2 + tid; r < m; r += blockDim.x) H(r, k) = zmk(0.0, 0.0);
     __syncthreads();
   }
   // single-shift QR with deflation, Wilkinson and exceptional shifts
@@ -757,14 +770,14 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
     if (tid == 0) {
       int lo = hi;
       while (lo > 0) {
-        double scale = zabs(H[lo - 1][lo - 1]) + zabs(H[lo][lo]);
+        double scale = zabs(H(lo - 1, lo - 1)) + zabs(H(lo, lo));
         if (scale == 0.0) {
           scale = 0.0;
           for (int a = lo - 1; a <= hi; ++a)
-            for (int b = lo - 1; b <= hi; ++b) scale += zabs(H[a][b]);
+            for (int b = lo - 1; b <= hi; ++b) scale += zabs(H(a, b));
         }
-        if (zabs(H[lo][lo - 1]) <= 0x1p-53 * scale) {
-          H[lo][lo - 1] = zmk(0.0, 0.0);
+        if (zabs(H(lo, lo - 1)) <= 0x1p-53 * scale) {
+          H(lo, lo - 1) = zmk(0.0, 0.0);
           break;
         }
         --lo;
@@ -780,9 +793,9 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
         --budget;
         zt mu;
         if (its % 10 == 0) {
-          mu = zadd(H[hi][hi], zmk(0.75 * zabs(H[hi][hi - 1]), 0.0));
+          mu = zadd(H(hi, hi), zmk(0.75 * zabs(H(hi, hi - 1)), 0.0));
         } else {
-          const zt a = H[hi - 1][hi - 1], b = H[hi - 1][hi], c = H[hi][hi - 1], dd = H[hi][hi];
+          const zt a = H(hi - 1, hi - 1), b = H(hi - 1, hi), c = H(hi, hi - 1), dd = H(hi, hi);
           const zt tr2 = zscale(0.5, zadd(a, dd));
           const zt hd = zscale(0.5, zsub(a, dd));
           const zt disc2 = zadd(zmul(hd, hd), zmul(b, c));
@@ -795,7 +808,7 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
           const zt l1 = zadd(tr2, disc), l2 = zsub(tr2, disc);
           mu = zabs(zsub(l1, dd)) <= zabs(zsub(l2, dd)) ? l1 : l2;
         }
-        zleaf_givens(zsub(H[lo][lo], mu), H[lo + 1][lo], G);
+        zleaf_givens(zsub(H(lo, lo), mu), H(lo + 1, lo), G);
       }
       if (budget < 0) s_act = 2;
     }
@@ -813,19 +826,51 @@ __global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __res
     }
     zleaf_rotate(m, H, Z, lo, G);
     for (int k = lo + 1; k < hi; ++k) {
-      if (tid == 0) zleaf_givens(H[k][k - 1], H[k + 1][k - 1], G);
+      if (tid == 0) zleaf_givens(H(k, k - 1), H(k + 1, k - 1), G);
       __syncthreads();
       zleaf_rotate(m, H, Z, k, G);
-      if (tid == 0) H[k + 1][k - 1] = zmk(0.0, 0.0);
+      if (tid == 0) H(k + 1, k - 1) = zmk(0.0, 0.0);
       __syncthreads();
     }
   }
   for (int e = tid; e < m * m; e += blockDim.x) {
     const int i = e % m, j = e / m;
-    d.T[i + (size_t)j * m] = i <= j ? H[i][j] : zmk(0.0, 0.0);
-    d.Z[i + (size_t)j * m] = Z[i][j];
+    d.T[i + (size_t)j * m] = i <= j ? H(i, j) : zmk(0.0, 0.0);
+    d.Z[i + (size_t)j * m] = Z(i, j);
   }
   if (tid == 0) *d.status = ok ? 0 : 1;
+}
+
+// Leaves of at most ZLEAF_MAX rows: H and Z in shared memory, one CTA each.
+__global__ void __launch_bounds__(256) zschur_leaf_kernel(const ZLeafDesc* __restrict__ desc) {
+  extern __shared__ zt zsm[];
+  __shared__ zt u[ZLEAF_MAX];
+  __shared__ zt dots[ZLEAF_MAX];
+  __shared__ LeafShared sh;
+  const ZLeafDesc d = desc[blockIdx.x];
+  const int m = d.m;
+  if (m < 1 || m > ZLEAF_MAX) {   // the shared arrays hold at most ZLEAF_MAX rows
+    if (threadIdx.x == 0) *d.status = 1;
+    return;
+  }
+  SharedMat H{reinterpret_cast<zt (*)[ZLEAF_MAX + 1]>(zsm)};
+  SharedMat Z{reinterpret_cast<zt (*)[ZLEAF_MAX + 1]>(zsm + ZLEAF_MAX * (ZLEAF_MAX + 1))};
+  zleaf_solve(d, m, H, Z, u, dots, sh);
+}
+
+// Larger leaves (clusters reported with an enclosure): the same solver with H,
+// Z, u and dots in the global scratch d.work (2 m^2 + 2 m complex), one CTA each.
+__global__ void __launch_bounds__(256) zschur_leaf_global_kernel(const ZLeafDesc* __restrict__ desc) {
+  __shared__ LeafShared sh;
+  const ZLeafDesc d = desc[blockIdx.x];
+  const int m = d.m;
+  if (m < 1 || d.work == nullptr) {
+    if (threadIdx.x == 0) *d.status = 1;
+    return;
+  }
+  const size_t mm = (size_t)m * m;
+  zleaf_solve(d, m, GlobalMat{d.work, m}, GlobalMat{d.work + mm, m}, d.work + 2 * mm,
+              d.work + 2 * mm + m, sh);
 }
 
 // trace of A (n x n): one CTA, fixed summation order
@@ -1342,11 +1387,8 @@ void process_cnode(CShared& S, cudaStream_t s, CNode nd) {
             S.clusters->push_back({nd.off, m, plan.reg.cr, plan.reg.ci, plan.reg.R, {}});
             for (const HalfPlane& h : plan.reg.hp) S.clusters->back().hp.push_back({h.wr, h.wi, h.t});
           }
-          if (m <= ZLEAF_MAX) {
-            S.leaves.push_back({nd.off, m, nd.A});
-            return;
-          }
-          // the leaf kernel cannot take the cluster: reported, not triangularised
+          S.leaves.push_back({nd.off, m, nd.A});   // larger than a leaf: the global-memory solver
+          return;
         }
         if (S.status == EIG_OK) {
           S.status = EIG_NO_SPLIT;
@@ -1462,25 +1504,42 @@ int cplane_schur(cudaStream_t s, int n, const double* dA_, int lda, double* dT_,
       std::sort(leaves.begin(), leaves.end(), [](const CLeaf& a, const CLeaf& b) { return a.off < b.off; });
       const int nl = (int)leaves.size();
       S.inf.leaves = nl;
-      std::vector<ZLeafDesc> hd(nl);
+      // small leaves in shared memory, clusters above ZLEAF_MAX rows in global scratch
+      std::vector<ZLeafDesc> hsmall, hbig;
       std::vector<zt*> Zs(nl);
       int* dstat = D.alloc<int>(std::max(nl, 1));
       for (int i = 0; i < nl; ++i) {
         const int m = leaves[i].m;
         zt* TZ = D.alloc<zt>(2 * (size_t)m * m);
         Zs[i] = TZ + (size_t)m * m;
-        hd[i] = {m, leaves[i].A, m, TZ, Zs[i], dstat + i};
+        ZLeafDesc dsc{m, leaves[i].A, m, TZ, Zs[i], dstat + i, nullptr};
+        if (m <= ZLEAF_MAX) {
+          hsmall.push_back(dsc);
+        } else {
+          dsc.work = D.alloc<zt>(2 * (size_t)m * m + 2 * (size_t)m);
+          hbig.push_back(dsc);
+        }
       }
+      const int ns = (int)hsmall.size(), nbig = (int)hbig.size();
       ZLeafDesc* dd = D.alloc<ZLeafDesc>(std::max(nl, 1));
-      D.check(cudaMemcpyAsync(dd, hd.data(), sizeof(ZLeafDesc) * nl, cudaMemcpyHostToDevice, s),
-              "leaf descriptors");
+      if (ns > 0)
+        D.check(cudaMemcpyAsync(dd, hsmall.data(), sizeof(ZLeafDesc) * ns, cudaMemcpyHostToDevice, s),
+                "leaf descriptors");
+      if (nbig > 0)
+        D.check(cudaMemcpyAsync(dd + ns, hbig.data(), sizeof(ZLeafDesc) * nbig, cudaMemcpyHostToDevice, s),
+                "leaf descriptors");
       const int smem = 2 * ZLEAF_MAX * (ZLEAF_MAX + 1) * (int)sizeof(zt);
       D.check(cudaFuncSetAttribute(zschur_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
               "leaf attribute");
-      if (nl > 0) {
+      if (ns > 0) {
         note_launches(1);
-        zschur_leaf_kernel<<<nl, 256, smem, s>>>(dd);
+        zschur_leaf_kernel<<<ns, 256, smem, s>>>(dd);
         D.check(cudaGetLastError(), "leaf launch");
+      }
+      if (nbig > 0) {
+        note_launches(1);
+        zschur_leaf_global_kernel<<<nbig, 256, 0, s>>>(dd + ns);
+        D.check(cudaGetLastError(), "large leaf launch");
       }
       zt* tmpU = D.alloc<zt>((size_t)n * n);
       for (int i = 0; i < nl; ++i) {

@@ -283,3 +283,30 @@ def test_server_takes_complex_plane_requests(E):
         assert rc == eigdc.EIG_OK
         assert np.array_equal(dT.cpu().numpy().T, T) and np.array_equal(dU.cpu().numpy().T, U)
     srv.close()
+
+
+def test_large_cluster_uses_the_global_memory_leaf(E):
+    """A 70 x 70 Jordan block (a cluster above the 64-row shared-memory leaf)
+    is reported with its enclosure and triangularised by the global-memory
+    form of the leaf solver."""
+    eigdc, h, torch = E
+    rng = np.random.default_rng(88)
+    n, nj = 100, 70
+    D = np.zeros((n, n))
+    D[:n - nj, :n - nj] = np.diag(-rng.uniform(0.5, 1.5, n - nj))
+    D[n - nj:, n - nj:] = 0.1 * np.eye(nj) + np.diag(np.ones(nj - 1), 1)
+    Q = workloads.random_orthogonal(n, rng)
+    A = Q @ D @ Q.T
+    p = eigdc.default_params(seed=1, leaf_size=8)
+    rc, T, U, w, info, enc = eigdc.schur_complex(h, A, p, enclose=True)
+    assert rc == eigdc.EIG_OK
+    _check(A, T, U, 1e-12)
+    big = [e for e in enc if e.size > 64]
+    assert len(big) == 1
+    c, R, hps = big[0].region()
+    assert abs(0.1 - c) <= R and all((np.conj(hw) * 0.1).real >= ht - 1e-12 for hw, ht in hps)
+    # the oracle reports one cluster of that kind as well (86 rows at offset 2
+    # on this input; the exact size follows rounding-sensitive decisions in
+    # the pseudospectrum, so only its existence is compared)
+    To, Uo, wo, io = schur_complex_plane(A, seed=1, leaf_size=8, enclose=True)
+    assert sum(1 for _, m, _ in io.clusters if m > 64) == 1
