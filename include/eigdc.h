@@ -385,7 +385,10 @@ int eig_gemm_split(eig_handle_t h, int ta, int tb, int m, int n, int k, double a
  *     split (large m * n, or small k) never use the array.
  *   - The array's device address is looked up on the first call on each
  *     device (with that device current); make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: a
+ *     device reset (cudaDeviceReset, or the primary context destroyed and
+ *     made again) invalidates it, and the entry point must not be called on
+ *     that device afterwards.
  *   - All calls share the array; calls that overlap on the GPU race on it.
  */
 int eig_gemm_noalloc(void* stream, int ta, int tb, int m, int n, int k, double alpha,
@@ -462,7 +465,9 @@ typedef struct {
  *     its block is put in Schur form by the leaf solver and its region is
  *     written to enc[i] (up to enc_cap entries; *n_enc = number of clusters).
  *     enclose = 0: such a node stops the solve with EIG_NO_SPLIT.  Clusters
- *     larger than 64 use a global-memory form of the leaf solver.
+ *     of 65..512 rows use a global-memory form of the leaf solver (one CTA);
+ *     a cluster above 512 rows is still written to enc, and the solve
+ *     returns EIG_NO_SPLIT.
  *   - Returns EIG_NO_CONVERGENCE if a leaf's QR iteration ran out of steps. */
 int eig_schur_complex(eig_handle_t h, int n, const double* dA, int lda, double* dT, int ldt,
                       double* dU, int ldu, double* dw, const eig_params_t* params, int enclose,

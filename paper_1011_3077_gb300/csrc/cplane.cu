@@ -59,6 +59,10 @@ constexpr int PURPOSE_HAAR_IM = 7;
 constexpr int PURPOSE_LINE = 8;
 constexpr int ZNB = 32;           // panel width of the complex QR (T leading dimension)
 constexpr int ZLEAF_MAX = 64;     // largest leaf of the complex Schur kernel
+// Largest cluster put in Schur form by the global-memory leaf solver (one CTA,
+// O(m^3) serial-ish work: m = 512 is about 0.2 s).  A larger cluster is still
+// reported with its enclosure, and the solve returns EIG_NO_SPLIT.
+constexpr int ZLEAF_GLOBAL_MAX = 512;
 
 __host__ __device__ __forceinline__ zt zmk(double r, double i) { return make_double2(r, i); }
 __device__ __forceinline__ zt zadd(zt a, zt b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -864,7 +868,7 @@ __global__ void __launch_bounds__(256) zschur_leaf_global_kernel(const ZLeafDesc
   __shared__ LeafShared sh;
   const ZLeafDesc d = desc[blockIdx.x];
   const int m = d.m;
-  if (m < 1 || d.work == nullptr) {
+  if (m < 1 || m > ZLEAF_GLOBAL_MAX || d.work == nullptr) {
     if (threadIdx.x == 0) *d.status = 1;
     return;
   }
@@ -1387,7 +1391,16 @@ void process_cnode(CShared& S, cudaStream_t s, CNode nd) {
             S.clusters->push_back({nd.off, m, plan.reg.cr, plan.reg.ci, plan.reg.R, {}});
             for (const HalfPlane& h : plan.reg.hp) S.clusters->back().hp.push_back({h.wr, h.wi, h.t});
           }
-          S.leaves.push_back({nd.off, m, nd.A});   // larger than a leaf: the global-memory solver
+          if (m > ZLEAF_GLOBAL_MAX) {   // too large for the one-CTA leaf solver
+            if (S.status == EIG_OK) {
+              S.status = EIG_NO_SPLIT;
+              S.err = "cluster of " + std::to_string(m) + " rows (enclosure reported) exceeds the " +
+                      std::to_string(ZLEAF_GLOBAL_MAX) + "-row leaf solver";
+            }
+            return;
+          }
+          // the leaf phase picks shared-memory or global-memory storage by m
+          S.leaves.push_back({nd.off, m, nd.A});
           return;
         }
         if (S.status == EIG_OK) {
@@ -1594,7 +1607,12 @@ size_t cplane_footprint(int n, int prec) {
   bytes += (size_t)(20 * ZNB + 8) * n * z + (size_t)(nblocks(2 * n, 64) * 1024) * z +
            (size_t)((n + 31) / 32 + 8) * n * sizeof(double);
   if (prec == EIG_FP64_TC && n >= 128) bytes += 8 * c2 * sizeof(double) + tcx_gemm_workspace_bytes(n, n, n);
-  return bytes + ((size_t)64 << 20);   // allocator granularity and leaf buffers
+  // leaf buffers, held beside the root's: T and Z (2 m^2 complex) per leaf and
+  // the global solver's scratch (2 m^2 + 2 m) per cluster; with every leaf or
+  // cluster at most ZLEAF_GLOBAL_MAX rows, sum m_i^2 <= ZLEAF_GLOBAL_MAX n
+  const size_t lm = (size_t)std::min(n, ZLEAF_GLOBAL_MAX);
+  bytes += (4 * lm + 2) * (size_t)n * z;
+  return bytes + ((size_t)64 << 20);   // allocator granularity
 }
 
 // ------------------------------------------------------------------ building blocks

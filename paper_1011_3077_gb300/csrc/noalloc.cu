@@ -13,7 +13,9 @@
 // In host code g_gemm_scratch names a host-side stand-in, not a device
 // address, so the kernels are given the address cudaGetSymbolAddress returns
 // for the current device; it is looked up once per device, on that device's
-// first call, which therefore should come before any stream capture.
+// first call, which therefore should come before any stream capture.  The
+// cached address outlives nothing but the device's primary context: after a
+// device reset the entry point must not be called on that device again.
 //
 // Every call shares the array and it keeps the contents of the last call.
 // Nothing in it needs to start at zero: each K-chunk partial a call reads is

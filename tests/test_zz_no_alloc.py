@@ -28,6 +28,29 @@ def env():
     h.close()
 
 
+def _splits(m, n, k):
+    """K-chunk count the library's split-K chooser picks for an m x n x k
+    product: whole waves of two CTAs per SM on 152 SMs, chunks of at least
+    128, at most 32 (restated here so each case can assert which path, the
+    static scratch or none, it exercises)."""
+    bm, bn = (32, 128) if m <= 32 else (64, 64)
+    tiles = -(-m // bm) * -(-n // bn)
+    wave = 2 * 152
+    if tiles >= wave:
+        return 1
+    best, best_eff = 1, 0.0
+    for s in range(1, max(1, min(32, k // 128)) + 1):
+        ctas = tiles * s
+        waves = -(-ctas // wave)
+        eff = ctas / (waves * wave) - 0.002 * s
+        if eff > best_eff:
+            best, best_eff = s, eff
+    return best
+
+
+SCRATCH = 1 << 20   # doubles in the library's static split-K array
+
+
 def _case(rng, m, n, k, ta, tb):
     A = rng.standard_normal((k, m) if ta else (m, k))
     B = rng.standard_normal((n, k) if tb else (k, n))
@@ -35,13 +58,18 @@ def _case(rng, m, n, k, ta, tb):
     return A, B, C
 
 
-@pytest.mark.parametrize("m,n,k,ta,tb", [
-    (64, 64, 4096, 1, 0),     # 16 K-chunks: uses the static scratch
-    (130, 70, 1300, 0, 1),    # a few K-chunks, ragged tiles
-    (300, 257, 5, 0, 0),      # no split: the scratch is not touched
+@pytest.mark.parametrize("m,n,k,ta,tb,split", [
+    (64, 64, 4096, 1, 0, True),     # many K-chunks in the static scratch
+    (130, 70, 1300, 0, 1, True),    # a few K-chunks, ragged tiles
+    (256, 256, 2048, 0, 0, True),   # splits * m * n exactly fills the scratch
+    (300, 257, 5, 0, 0, False),     # no split: the scratch is not touched
 ])
-def test_noalloc_matches_eig_gemm_twice(env, m, n, k, ta, tb):
+def test_noalloc_matches_eig_gemm_twice(env, m, n, k, ta, tb, split):
     eigdc, h, torch = env
+    s = _splits(m, n, k)
+    assert (s > 1) == split and s * m * n <= SCRATCH
+    if (m, n, k) == (256, 256, 2048):
+        assert s * m * n == SCRATCH
     rng = np.random.default_rng(m * 31 + k)
     stream = torch.cuda.current_stream()
     for call in range(2):
@@ -62,11 +90,14 @@ def test_noalloc_matches_eig_gemm_twice(env, m, n, k, ta, tb):
         assert np.max(np.abs(got - exact)) <= tol
 
 
-def test_noalloc_rejects_oversized_scratch(env):
+@pytest.mark.parametrize("m,n,k", [
+    (512, 512, 8192),    # splits * m * n far above 2^20 doubles
+    (256, 256, 2176),    # one K-chunk more than the exact fit above
+])
+def test_noalloc_rejects_oversized_scratch(env, m, n, k):
     eigdc, h, torch = env
-    m = n = 512
-    k = 8192              # 5 K-chunks of 512 x 512 > 2^20 doubles
-    dA = torch.zeros((m, k), dtype=torch.float64, device="cuda")
+    assert _splits(m, n, k) * m * n > SCRATCH
+    dA = torch.zeros((k, m), dtype=torch.float64, device="cuda")
     dB = torch.zeros((n, k), dtype=torch.float64, device="cuda")
     dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
     rc = eigdc.eig_gemm_noalloc(torch.cuda.current_stream(), 0, 0, m, n, k, 1.0, dA, m, dB, k,
