@@ -50,7 +50,7 @@ def parse():
                     help="strict-upper scale of T in units of 1/sqrt(n) (1.0 = the exact "
                          "construction, whose eigenvalues are too ill-conditioned to split "
                          "in FP64 at n=2048; 0.1 = the documented reduced-coupling variant)")
-    ap.add_argument("--prec", type=int, default=2, choices=[0, 2],
+    ap.add_argument("--prec", type=int, default=2, choices=[0, 1, 2],
                     help="2: FP64-accurate contractions on the tensor cores (error-free "
                          "nine-digit BF16 split) for the large products; 0: every contraction "
                          "on the FP64 DFMA pipe")
@@ -61,13 +61,15 @@ def parse():
                          "device-wide synchronisation while a solve runs)")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
-    ap.add_argument("--workload", default="schur", choices=["schur", "batched", "svd", "cplane"],
+    ap.add_argument("--workload", default="schur",
+                    choices=["schur", "batched", "svd", "cplane", "sym"],
                     help="schur: one nonsymmetric n x n solve per step (default); batched: "
                          "--count independent symmetric problems, n log-uniform in [32, 512], "
                          "solved by eig_solve_batched per step; svd: singular values and "
                          "vectors of one n x n matrix per step (eig_svd); cplane: the complex "
                          "Schur form of one n x n matrix per step by lines at random angles "
-                         "(eig_schur_complex)")
+                         "(eig_schur_complex); sym: the full eigendecomposition of one "
+                         "symmetric n x n matrix with a semicircle spectrum per step")
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -440,6 +442,95 @@ def cplane_arm(args, torch, eigdc, h, dev, stream, world):
         print(json.dumps(line), flush=True)
 
 
+def orth_2norm(U, torch, iters=40):
+    """||U^T U - I||_2 by power iteration on the symmetric residual."""
+    n = U.shape[0]
+    E = U.t() @ U - torch.eye(n, dtype=U.dtype, device=U.device)
+    v = torch.ones(n, dtype=U.dtype, device=U.device) / np.sqrt(n)
+    est = 0.0
+    for _ in range(iters):
+        wv = E @ v
+        est = float(torch.linalg.norm(wv))
+        if est == 0.0:
+            break
+        v = wv / est
+    return est
+
+
+def sym_arm(args, torch, eigdc, h, dev, stream, world):
+    """Full symmetric eigendecomposition of A = Q diag(lambda) Q^T per step,
+    lambda from the Wigner semicircle on [-1, 1] (lambda = sqrt(u1) cos(2 pi
+    u2)), Q Haar, median-shift recursion to 64 x 64 leaves.  Reports the
+    error of each result against the prescribed spectrum, ||U^T U - I||_2 and
+    the backward error ||A - U L U^T||_F / ||A||_F."""
+    from paper_1011_3077_gb300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    n = args.n
+    A, lam = workloads.symmetric_semicircle(n, seed=3 + rank)
+    dA0 = eigdc.to_device(A, dev)
+    dA = torch.empty_like(dA0)
+    dw = torch.zeros(n, dtype=torch.float64, device=dev)
+    dU = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec,
+                                  graphs=args.graphs)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        dA.copy_(dA0)
+        rc, info = eigdc.eig_solve(h, eigdc.EIG_KIND_SYM, n, dA, n, dw, None, dU, n, params)
+        if rc != eigdc.EIG_OK:
+            raise RuntimeError("eig_solve failed: %d %s" % (rc, h.last_error()))
+        return info
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    l0 = eigdc.eig_kernel_launches()
+    ms, infos = [], []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos.append(step())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    launches = eigdc.eig_kernel_launches() - l0
+    total_ms = max_over_ranks(sum(ms), dev, world)
+    # accuracy of the last result (column-major U: the tensor holds U^T)
+    U = dU.t()
+    lam_t = torch.from_numpy(lam.copy()).to(dev)
+    nA = float(np.max(np.abs(lam)))
+    eig_err = float(torch.max(torch.abs(dw - lam_t)))
+    R = dA0 - (U * dw) @ U.t()
+    bwd = float(torch.linalg.norm(R) / torch.linalg.norm(dA0))
+    orth = orth_2norm(U, torch)
+    info = infos[-1]
+    names = {0: "fp64", 1: "split bf16x3 (FP32-level tensor-core products, FP64 panels, "
+                       "split tests and refinement)", 2: "fp64 (tensor-core error-free split)"}
+    line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
+            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "symmetric eigendecomposition, A = Q diag(lambda) Q^T, n=%d, "
+                                   "lambda semicircle on [-1, 1], Q Haar, median-shift recursion "
+                                   "to 64x64 leaves" % n,
+                       "n": n, "precision": names[args.prec], "workers": args.workers,
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "gflops": float(np.mean([i.flops for i in infos])) * args.steps * world /
+                      (total_ms / 1e3) / 1e9,
+            "eigenvalue_error_rel": eig_err / nA, "backward_error": bwd, "orthogonality_2": orth,
+            "solve_info": {"nodes": info.nodes, "splits": info.splits,
+                           "total_iters": info.total_iters, "failed_attempts": info.failed_attempts,
+                           "leaves": info.leaves, "max_depth": info.max_depth},
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
+            "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     args = parse()
@@ -463,8 +554,9 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream(dev)
     h = eigdc.Handle(local, stream)
-    if args.workload in ("batched", "svd", "cplane"):
-        arm = {"batched": batched_arm, "svd": svd_arm, "cplane": cplane_arm}[args.workload]
+    if args.workload in ("batched", "svd", "cplane", "sym"):
+        arm = {"batched": batched_arm, "svd": svd_arm, "cplane": cplane_arm,
+               "sym": sym_arm}[args.workload]
         arm(args, torch, eigdc, h, dev, stream, world)
         h.close()
         if world > 1:
