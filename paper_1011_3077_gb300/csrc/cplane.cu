@@ -805,7 +805,9 @@ __device__ void zleaf_solve(const ZLeafDesc& d, int m, Mat H, Mat Z, zt* u, zt* 
           const zt disc2 = zadd(zmul(hd, hd), zmul(b, c));
           // principal complex square root
           const double r = zabs(disc2);
-          double sr = sqrt(0.5 * (r + disc2.x));
+          // hypot may round r a little below |disc2.x| when disc2 is nearly a
+          // negative real (a conjugate pair of a real block): clamp both radicands
+          double sr = sqrt(0.5 * fmax(r + disc2.x, 0.0));
           double si = sqrt(0.5 * fmax(r - disc2.x, 0.0));
           if (disc2.y < 0.0) si = -si;
           const zt disc = zmk(sr, si);
