@@ -69,3 +69,46 @@ def test_symmetric_semicircle_n1024_matches_oracle(E, prec):
     assert np.max(np.abs(w - lam)) <= 1e-10 * nA
     assert _orth2(Uv) <= 1e-12
     assert np.linalg.norm(A - (Uv * w) @ Uv.T) <= 1e-12 * np.linalg.norm(A)
+
+
+def _eig_condition(T):
+    """kappa_i = ||y_i|| ||x_i|| / |y_i^T x_i| of the triangular T from the
+    oracle's eigenvector recurrence (right vectors of T, left vectors as the
+    right vectors of the reversed transpose, which is again upper triangular)."""
+    n = T.shape[0]
+    X = otrevc.triangular_eigenvectors(T)
+    J = np.arange(n)[::-1]
+    Yr = otrevc.triangular_eigenvectors(T.T[J][:, J])
+    Y = Yr[J][:, J]
+    num = np.linalg.norm(X, axis=0) * np.linalg.norm(Y, axis=0)
+    return num / np.abs(np.sum(Y * X, axis=0))
+
+
+def _nonsym_case():
+    if "nonsym" not in _cache:
+        # strict-upper scale 0.1/sqrt(n): at 1/sqrt(n) the oracle itself stops
+        # with NO_SPLIT at n = 1024 (13 splits, then a node whose
+        # pseudospectrum reaches every line tried)
+        A, d, T0 = workloads.nonsymmetric_schur(N, seed=2, offdiag_scale=0.1 / np.sqrt(N))
+        To, Qo, wro, wio, io = oschur(A, seed=2)
+        assert io.status == 0
+        _cache["nonsym"] = (A, d, T0, wro, io, _eig_condition(T0))
+    return _cache["nonsym"]
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_nonsymmetric_n1024_matches_oracle(E, prec):
+    eigdc, h, torch = E
+    A, d, T0, wro, io, kappa = _nonsym_case()
+    rc, T, Us, wr, wi, info = eigdc.schur_nonsymmetric(h, A, eigdc.default_params(seed=2, prec=prec))
+    assert rc == eigdc.EIG_OK, h.last_error()
+    assert (info.splits, info.nodes, info.failed_attempts) == (io.splits, io.nodes,
+                                                               io.failed_attempts)
+    assert np.all(wi == 0.0)
+    nA = np.linalg.norm(A, 2)
+    order = np.argsort(d)
+    tol = 1e-13 * N * kappa[order] * nA + 1e-12
+    assert np.all(np.abs(np.sort(wr) - d[order]) <= tol)
+    assert np.all(np.abs(np.sort(wr) - np.sort(wro)) <= 2 * tol)
+    assert _orth2(Us) <= 1e-12
+    assert np.linalg.norm(A - Us @ T @ Us.T) <= 1e-12 * np.linalg.norm(A)
