@@ -71,6 +71,10 @@ def parse():
                          "(eig_schur_complex); sym: the full eigendecomposition of one "
                          "symmetric n x n matrix with a semicircle spectrum per step")
     ap.add_argument("--count", type=int, default=2000)
+    ap.add_argument("--fused", type=int, default=1, choices=[0, 1],
+                    help="batched workload: 1 = one persistent fused launch per step "
+                         "(eig_solve_batched_fused, launch shape from eig_fused_autotune); "
+                         "0 = the host-driven executor (eig_solve_batched)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -245,14 +249,26 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
     params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec,
                                   graphs=args.graphs)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tuning = None
+    if args.fused:
+        # launch shape of the persistent kernel from the autotuner (untimed)
+        rc, best, cands = eigdc.eig_fused_autotune(h, 160, 32, 512, seed=11)
+        if rc != eigdc.EIG_OK:
+            raise RuntimeError("eig_fused_autotune failed: %d %s" % (rc, h.last_error()))
+        tuning = {"best": {"nb": best[0], "ctas_per_sm": best[1], "ms": best[2]},
+                  "candidates": [{"nb": c[0], "ctas_per_sm": c[1], "ms": c[2]} for c in cands],
+                  "sample": "160 problems, n log-uniform in [32, 512], A = (G + G^T)/2"}
 
     def step():
         for a, b in zip(work, A0):
             a.copy_(b)
-        rc, st, infos = eigdc.eig_solve_batched(h, eigdc.EIG_KIND_SYM, ns, work, ns, wr, None, Us,
-                                                ns, params)
+        if args.fused:
+            rc, st, infos = eigdc.eig_solve_batched_fused(h, ns, work, ns, wr, Us, ns, params)
+        else:
+            rc, st, infos = eigdc.eig_solve_batched(h, eigdc.EIG_KIND_SYM, ns, work, ns, wr, None,
+                                                    Us, ns, params)
         if rc != eigdc.EIG_OK or any(x != 0 for x in st):
-            raise RuntimeError("eig_solve_batched failed: %d %s" % (rc, h.last_error()))
+            raise RuntimeError("batched solve failed: %d %s" % (rc, h.last_error()))
         return infos
 
     for _ in range(max(args.warmup, 0)):
@@ -295,9 +311,12 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
                        "count": args.count, "n_min": int(sizes.min()), "n_max": int(sizes.max()),
                        "sum_n2": int(np.sum(sizes.astype(np.int64) ** 2)),
                        "workers": args.workers,
-                       "precision": "fp64" if args.prec == 0 else
+                       "form": "one persistent fused launch per step (a CTA per problem)"
+                               if args.fused else "host-driven executor",
+                       "precision": "fp64" if (args.prec == 0 or args.fused) else
                                     "fp64 (tensor-core error-free split)",
                        "l2": "flushed between timed steps (512 MiB write)"},
+            "autotune": tuning,
             "gflops": flops * world / (total_ms / 1e3) / 1e9,
             "max_eigenvalue_error": eig_err, "backward_error_sample25": bwd,
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,

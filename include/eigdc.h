@@ -68,6 +68,18 @@ typedef struct eig_handle_s* eig_handle_t;
  * kernel, and every other setting (tau, split_tol, no refinement) is that of
  * EIG_FP64. */
 #define EIG_FP64_TC 2
+/* split precision with unbiased FP32-level products: the error-free split of
+ * EIG_FP64_TC cut to four 6-bit digits (24 bits of each row / column maximum)
+ * and weight levels 0..3 (10 digit pairs), each level accumulated exactly in
+ * FP32 over 960-wide K chunks and drained into FP64 (eig_gemm_fp32tc).  BF16
+ * x 3 accumulates every plane product of the whole K range in one FP32
+ * accumulator whose additions truncate, a bias that grows with K; here every
+ * product of the path (trailing updates and reflector products of the panels
+ * included) carries an error of about 2^-24 max|row| max|column| per term
+ * with no drift.  Panels, norms, the R-test, the split test and the rank
+ * decision stay FP64; the other settings (tau, split_tol, refinement of
+ * symmetric solves) are those of EIG_SPLIT_BF16X3. */
+#define EIG_SPLIT_FP32 3
 
 /* regions (Sec. 3.1 unit circle; Sec. 3.3 line via the Moebius map
  * f(z) = (z - sigma + s)/(z - sigma - s); Sec. 3.5 circles |z - c| = r) */
@@ -272,6 +284,46 @@ int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double*
                       const int* ldu, const eig_params_t* params, int* status,
                       eig_solve_info_t* infos);
 
+/* Fused batched symmetric solves: every problem's whole recursion (the
+ * inverse-free iteration of Algorithm 3, the GRURV splitter of Algorithms 1-2,
+ * the similarity and split test of Algorithm 6, the median-shift strategy of
+ * Sec. 3.4 and Jacobi leaves) runs inside one CTA, and one persistent launch
+ * covers the batch: CTAs take the problems largest first from an atomic
+ * counter (the independence of Sec. 4.3).  Every product runs on the FP64
+ * pipe (params->prec is not used) with the same Philox draws, node ids and
+ * decisions as eig_solve, so each problem takes eig_solve's recursion tree.
+ *   - Arrays are HOST arrays of length count; n[i] in [1, 512]; dA[i] (lda[i]
+ *     >= n[i]) symmetric, overwritten as by eig_solve (EIG_KIND_SYM);
+ *     dw[i] <- eigenvalues ascending; dU[i] (ldu[i] >= n[i]) <- eigenvectors.
+ *   - status[i] and infos[i] (if infos != NULL) as for eig_solve_batched;
+ *     returns a negative code only for argument or system errors.
+ *   - The panel width and CTAs per SM are those chosen by the last
+ *     eig_fused_autotune on the handle (default: 32-column panels, two CTAs
+ *     per SM).  Workspace: about 25 max(n)^2 doubles per CTA, on the handle.
+ *   - Synchronizes the handle's stream before returning. */
+int eig_solve_batched_fused(eig_handle_t h, int count, const int* n, double* const* dA,
+                            const int* lda, double* const* dw, double* const* dU, const int* ldu,
+                            const eig_params_t* params, int* status, eig_solve_info_t* infos);
+
+/* One candidate launch shape of the fused batched solver and its time. */
+typedef struct {
+  int nb;            /* panel width of the blocked QR (16 or 32) */
+  int ctas_per_sm;   /* resident CTAs per SM of the persistent launch */
+  double ms;         /* CUDA-event time of the launch on the tuning batch */
+} eig_fused_config_t;
+
+/* Autotuner of the fused batched solver: draws `samples` symmetric problems
+ * (n log-uniform in [nmin, nmax] from `seed`, A = (G + G^T)/2 with Philox
+ * Gaussians), times one fused launch over them for each panel width in
+ * {16, 32} and each CTAs-per-SM count from 1 to min(3, resident limit), and
+ * keeps the fastest on the handle for later eig_solve_batched_fused calls.
+ * table (table_cap entries) receives the candidates and *n_table their
+ * number; *best the winner.  Allocates (and frees) the sample matrices with
+ * cudaMalloc. */
+int eig_fused_autotune(eig_handle_t h, int samples, int nmin, int nmax, uint64_t seed,
+                       eig_fused_config_t* table, int table_cap, int* n_table,
+                       eig_fused_config_t* best);
+
 /* ------------------------------------------------------------- serving
  * A request server: `workers` host threads, each with its own CUDA stream
  * and workspace, take submitted requests in arrival order as soon as a worker
@@ -367,6 +419,14 @@ int eig_gemm_fp64tc(eig_handle_t h, int ta, int tb, int m, int n, int k, double 
 int eig_gemm_split(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
                    const double* dA, int lda, const double* dB, int ldb, double beta,
                    double* dC, int ldc);
+
+/* C = alpha op(A) op(B) + beta C with the four-digit error-free split of
+ * EIG_SPLIT_FP32 on the tcgen05 tensor cores: FP32-level accuracy (error
+ * about K 2^-24 max|row of op(A)| max|column of op(B)| in the worst case),
+ * exact chunked accumulation, no K-dependent bias. */
+int eig_gemm_fp32tc(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+                    const double* dA, int lda, const double* dB, int ldb, double beta,
+                    double* dC, int ldc);
 
 /* ------------------------------------------------------ no-allocation GEMM
  * The paper has no counterpart: this entry point serves callers that cannot

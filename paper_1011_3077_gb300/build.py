@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeigdc.so")
 SOURCES = ["linalg.cu", "misc.cu", "leaves.cu", "tc_gemm.cu", "tcx_gemm.cu", "api.cu", "noalloc.cu",
-           "cplane.cu", "trevc.cu"]
+           "cplane.cu", "trevc.cu", "fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -38,7 +38,8 @@ def _stale(obj, src):
         return True
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "tc_ptx.cuh"),
-            os.path.join(CSRC, "cplane_strategy.h"),
+            os.path.join(CSRC, "cplane_strategy.h"), os.path.join(CSRC, "jacobi_leaf.cuh"),
+            os.path.join(CSRC, "fused_dev.cuh"),
             os.path.join(os.path.dirname(HERE), "include", "eigdc.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

@@ -71,6 +71,10 @@ struct eig_handle_s {
   };
   std::vector<IrsGraph> graphs;
   bool graphs_off = false;
+  // fused batched solver: panel width and CTAs per SM (0: automatic), set by
+  // eig_fused_autotune
+  int fused_nb = 32;
+  int fused_cps = 0;
 };
 
 static void clear_graphs(eig_handle_s* h) {
@@ -189,14 +193,30 @@ struct QRBufs {
   int* tcerr = nullptr;    // device flag of the tensor-core kernel
 };
 
-static bool split_mode(int prec) { return prec == EIG_SPLIT_BF16X3; }
-// contractions on the tensor cores: BF16 x 3 (FP32-level) or the FP64-accurate split
-static bool tc_path(int prec) { return prec == EIG_SPLIT_BF16X3 || prec == EIG_FP64_TC; }
+// split precision: FP32-level products on the tensor cores, FP64 panels,
+// tests and refinement (BF16 x 3, or the unbiased four-digit split)
+static bool split_mode(int prec) { return prec == EIG_SPLIT_BF16X3 || prec == EIG_SPLIT_FP32; }
+// contractions on the tensor cores: the split-precision forms or the FP64-accurate split
+static bool tc_path(int prec) { return split_mode(prec) || prec == EIG_FP64_TC; }
+static bool valid_prec(int prec) {
+  return prec == EIG_FP64 || prec == EIG_SPLIT_BF16X3 || prec == EIG_FP64_TC ||
+         prec == EIG_SPLIT_FP32;
+}
 
 static size_t tc_ws_bytes(int prec, int m, int n, int k) {
   if (prec == EIG_SPLIT_BF16X3) return tc_gemm_workspace_bytes(m, n, k);
+  if (prec == EIG_SPLIT_FP32) return tcx32_gemm_workspace_bytes(m, n, k);
   if (prec == EIG_FP64_TC) return tcx_gemm_workspace_bytes(m, n, k);
   return 0;
+}
+
+// FP32-level tensor-core product of the split-precision form `prec`
+static cudaError_t split_gemm(cudaStream_t s, int prec, bool ta, bool tb, int m, int n, int k,
+                              double alpha, const double* A, int lda, const double* B, int ldb,
+                              double beta, double* C, int ldc, void* ws, int* err) {
+  if (prec == EIG_SPLIT_FP32)
+    return tcx32_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
+  return tc_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
 }
 
 // Products that stay on the FP64 DFMA kernel in EIG_FP64_TC mode: the digit
@@ -215,7 +235,8 @@ static void mm(eig_handle_t h, int prec, void* tcw, int* tcerr, bool ta, bool tb
                int k, double alpha, const double* A, int lda, const double* B, int ldb,
                double beta, double* C, int ldc, int splits, double* part) {
   if (split_mode(prec))
-    CK(tc_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
+    CK(split_gemm(h->stream, prec, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw,
+                  tcerr));
   else if (prec == EIG_FP64_TC && tcx_worth(m, n, k))
     CK(tcx_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, tcw, tcerr));
   else
@@ -252,11 +273,11 @@ static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
       double* C = q.W + j0 + (size_t)(j0 + jb) * q.ldw;
       if (split_mode(q.prec)) {
         // (V^T C)^T = C^T V on the tensor cores (M = nc rows, N = jb)
-        CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
-                   q.tcerr));
+        CK(split_gemm(s, q.prec, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part,
+                      nc, q.tcw, q.tcerr));
         CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk, true));
-        CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw, q.tcw,
-                   q.tcerr));
+        CK(split_gemm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C,
+                      q.ldw, q.tcw, q.tcerr));
       } else {
         int sp = gemm_choose_splits(jb, nc, mb);
         sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
@@ -286,11 +307,11 @@ static void apply_q(eig_handle_t h, int m, int nref, int jbmax, QRBufs& q, doubl
     double* Yb = Y + j0 + (size_t)c0 * ldy;
     const double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
     if (split_mode(q.prec)) {
-      CK(tc_gemm(s, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc, q.tcw,
-                 q.tcerr));
+      CK(split_gemm(s, q.prec, true, false, nc, jb, mb, 1.0, Yb, ldy, Vb, q.ldv, 0.0, q.part, nc,
+                    q.tcw, q.tcerr));
       CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, false, q.Wk, true));
-      CK(tc_gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy, q.tcw,
-                 q.tcerr));
+      CK(split_gemm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, Yb, ldy,
+                    q.tcw, q.tcerr));
       continue;
     }
     int sp = gemm_choose_splits(jb, nc, mb);
@@ -1691,7 +1712,7 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
 
 static void check_params(eig_handle_t h, const eig_params_t& p) {
   if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0 ||
-      (p.prec != EIG_FP64 && p.prec != EIG_SPLIT_BF16X3 && p.prec != EIG_FP64_TC)) {
+      !valid_prec(p.prec)) {
     h->err = "invalid eig_params_t";
     throw Fail{EIG_ERR_ARG};
   }
@@ -1808,11 +1829,12 @@ int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {
   const bool pencil = (kind == EIG_KIND_PENCIL);
   carve_main(a, n, true, w, pencil);
   // the largest node scratch over the precision modes
-  Arena b1(nullptr), b2(nullptr);
-  NodeWork nw2;
+  Arena b1(nullptr), b2(nullptr), b3(nullptr);
+  NodeWork nw2, nw3;
   carve_node(b1, n, n, EIG_SPLIT_BF16X3, nw, pencil);
   carve_node(b2, n, n, EIG_FP64_TC, nw2, pencil);
-  a.used += std::max(b1.used, b2.used);
+  carve_node(b3, n, n, EIG_SPLIT_FP32, nw3, pencil);
+  a.used += std::max(std::max(b1.used, b2.used), b3.used);
   *bytes = a.used;
   return EIG_OK;
 }
@@ -2237,6 +2259,195 @@ int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double*
   API_END
 }
 
+}  // extern "C"
+
+namespace {
+
+// One persistent launch of the fused batched solver over the problems
+// (largest first); fills status / infos; *ms (if non-null) gets the kernel's
+// CUDA-event time on the handle's stream.
+void fused_run(eig_handle_t h, int count, const int* n, double* const* dA, const int* lda,
+               double* const* dw, double* const* dU, const int* ldu, const eig_params_t& p,
+               int nb, int cps, int* status, eig_solve_info_t* infos, float* ms) {
+  cudaStream_t s = h->stream;
+  int mx = 1;
+  for (int i = 0; i < count; ++i) mx = std::max(mx, n[i]);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  const int maxc = fused_max_ctas_per_sm();
+  const int c = cps > 0 ? std::min(cps, maxc) : std::min(2, maxc);
+  const int ctas = std::max(1, std::min(count, sms * c));
+  const size_t pb = round_up(sizeof(FusedProblem) * count);
+  const size_t ob = round_up(sizeof(int) * count);
+  const size_t rb = round_up(sizeof(FusedResult) * count);
+  const size_t total = pb + ob + rb + 256 + fused_workspace_bytes(mx, ctas);
+  ensure_ws(h, total);
+  char* base = h->ws;
+  FusedProblem* dprobs = reinterpret_cast<FusedProblem*>(base);
+  int* dorder = reinterpret_cast<int*>(base + pb);
+  FusedResult* dres = reinterpret_cast<FusedResult*>(base + pb + ob);
+  int* dcounter = reinterpret_cast<int*>(base + pb + ob + rb);
+  void* dws = base + pb + ob + rb + 256;
+  char* pin = static_cast<char*>(pinned(h, std::max(pb + ob, rb) + 64));
+  FusedProblem* hp = reinterpret_cast<FusedProblem*>(pin);
+  int* ho = reinterpret_cast<int*>(pin + pb);
+  for (int i = 0; i < count; ++i) hp[i] = FusedProblem{n[i], lda[i], ldu[i], 0, dA[i], dw[i], dU[i]};
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::memcpy(ho, order.data(), sizeof(int) * count);
+  CK(cudaMemcpyAsync(dprobs, hp, pb + ob, cudaMemcpyHostToDevice, s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+  }
+  CK(fused_batched(s, count, dprobs, dorder, dres, dcounter, p, nb, ctas, mx, dws));
+  if (ms) CK(cudaEventRecord(e1, s));
+  // the staging area is reused for the results once the inputs are copied
+  CK(cudaStreamSynchronize(s));
+  FusedResult* hr = reinterpret_cast<FusedResult*>(pin);
+  CK(cudaMemcpyAsync(hr, dres, sizeof(FusedResult) * count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ms) {
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  for (int i = 0; i < count; ++i) {
+    const FusedResult& r = hr[i];
+    status[i] = r.status;
+    if (infos) {
+      eig_solve_info_t inf;
+      inf.status = r.status;
+      inf.nodes = r.nodes;
+      inf.splits = r.splits;
+      inf.max_depth = r.max_depth;
+      inf.total_iters = r.total_iters;
+      inf.failed_attempts = r.failed_attempts;
+      inf.leaves = r.leaves;
+      inf.flops = r.flops;
+      infos[i] = inf;
+    }
+  }
+}
+
+// splitmix64-based uniform in [0, 1) (host-side draws of the tuner's sizes)
+double tune_uniform(uint64_t& st) {
+  st += 0x9E3779B97F4A7C15ull;
+  uint64_t z = st;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1p-53;
+}
+
+}  // namespace
+
+extern "C" {
+
+int eig_solve_batched_fused(eig_handle_t h, int count, const int* n, double* const* dA,
+                            const int* lda, double* const* dw, double* const* dU, const int* ldu,
+                            const eig_params_t* params, int* status, eig_solve_info_t* infos) {
+  API_BEGIN
+  REQUIRE(count >= 0, "count < 0");
+  REQUIRE(count == 0 || (n && dA && lda && dw && dU && ldu && status), "NULL array");
+  for (int i = 0; i < count; ++i) {
+    REQUIRE(n[i] >= 1 && n[i] <= fused_max_n(),
+            "problem " + std::to_string(i) + ": n must be in [1, " +
+                std::to_string(fused_max_n()) + "]");
+    REQUIRE(dA[i] && lda[i] >= n[i] && dw[i] && dU[i] && ldu[i] >= n[i],
+            "invalid problem " + std::to_string(i));
+  }
+  if (count == 0) return EIG_OK;
+  eig_params_t p = params_or_default(params);
+  check_params(h, p);
+  fused_run(h, count, n, dA, lda, dw, dU, ldu, p, h->fused_nb, h->fused_cps, status, infos,
+            nullptr);
+  for (int i = 0; i < count; ++i)
+    if (status[i] != EIG_OK) {
+      h->err = "problem " + std::to_string(i) + " returned " + std::to_string(status[i]);
+      break;
+    }
+  return EIG_OK;
+  API_END
+}
+
+int eig_fused_autotune(eig_handle_t h, int samples, int nmin, int nmax, uint64_t seed,
+                       eig_fused_config_t* table, int table_cap, int* n_table,
+                       eig_fused_config_t* best) {
+  API_BEGIN
+  REQUIRE(samples >= 1 && samples <= 100000, "samples must be in [1, 100000]");
+  REQUIRE(nmin >= 1 && nmax >= nmin && nmax <= fused_max_n(), "need 1 <= nmin <= nmax <= 512");
+  REQUIRE(table_cap >= 0 && (table_cap == 0 || table), "table / table_cap invalid");
+  cudaStream_t s = h->stream;
+  // sizes log-uniform in [nmin, nmax]; A = (G + G^T) / 2 from Philox Gaussians
+  std::vector<int> ns(samples), lds(samples);
+  uint64_t st = seed;
+  size_t elems = 0;
+  for (int i = 0; i < samples; ++i) {
+    const double u = tune_uniform(st);
+    ns[i] = std::max(nmin, std::min(nmax, (int)std::lround(std::exp(std::log((double)nmin) +
+                                                                     u * (std::log((double)nmax) -
+                                                                          std::log((double)nmin))))));
+    lds[i] = ns[i];
+    elems += 3 * (size_t)ns[i] * ns[i] + ns[i];
+  }
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * elems) != cudaSuccess) {
+    cudaGetLastError();
+    h->err = "autotune sample allocation failed";
+    return EIG_ERR_NOMEM;
+  }
+  std::vector<double*> A0(samples), A(samples), w(samples), U(samples);
+  size_t off = 0;
+  for (int i = 0; i < samples; ++i) {
+    const size_t nn = (size_t)ns[i] * ns[i];
+    A0[i] = buf + off; off += nn;
+    A[i] = buf + off; off += nn;
+    U[i] = buf + off; off += nn;
+    w[i] = buf + off; off += ns[i];
+  }
+  int rc = EIG_OK;
+  try {
+    for (int i = 0; i < samples; ++i) {
+      CK(gaussian(s, ns[i], ns[i], seed, 9, (uint64_t)i, 0, A0[i], ns[i]));
+      CK(symmetrize(s, ns[i], A0[i], ns[i]));
+    }
+    eig_params_t p;
+    eig_default_params(&p);
+    p.seed = seed;
+    std::vector<int> stv(samples);
+    const int maxc = fused_max_ctas_per_sm();
+    std::vector<eig_fused_config_t> tab;
+    eig_fused_config_t win{32, std::min(2, maxc), INFINITY};
+    for (int nb : {16, 32}) {
+      for (int cps = 1; cps <= std::min(3, maxc); ++cps) {
+        for (int i = 0; i < samples; ++i)
+          CK(cudaMemcpyAsync(A[i], A0[i], sizeof(double) * ns[i] * ns[i], cudaMemcpyDeviceToDevice, s));
+        float ms = 0.0f;
+        fused_run(h, samples, ns.data(), A.data(), lds.data(), w.data(), U.data(), lds.data(), p,
+                  nb, cps, stv.data(), nullptr, &ms);
+        const eig_fused_config_t c{nb, cps, (double)ms};
+        tab.push_back(c);
+        if (c.ms < win.ms) win = c;
+      }
+    }
+    h->fused_nb = win.nb;
+    h->fused_cps = win.ctas_per_sm;
+    if (best) *best = win;
+    if (n_table) *n_table = (int)tab.size();
+    for (int i = 0; i < (int)tab.size() && i < table_cap; ++i) table[i] = tab[i];
+  } catch (Fail f) {
+    rc = f.code;
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(buf);
+  return rc;
+  API_END
+}
+
 int eig_qr(eig_handle_t h, int m, int n, const double* dX, int ldx, double* dQ, int ldq,
            double* dR, int ldr) {
   API_BEGIN
@@ -2359,6 +2570,29 @@ int eig_gemm_split(eig_handle_t h, int ta, int tb, int m, int n, int k, double a
   CK(cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
   CK(tc_gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, h->ws,
              derr));
+  int* hf = static_cast<int*>(pinned(h, 64));
+  CK(cudaMemcpyAsync(hf, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (*hf) {
+    h->err = "tensor-core GEMM: a bounded wait timed out (flag " + std::to_string(*hf) + ")";
+    return EIG_ERR_CUDA;
+  }
+  return EIG_OK;
+  API_END
+}
+
+int eig_gemm_fp32tc(eig_handle_t h, int ta, int tb, int m, int n, int k, double alpha,
+                    const double* dA, int lda, const double* dB, int ldb, double beta, double* dC,
+                    int ldc) {
+  API_BEGIN
+  REQUIRE(m >= 0 && n >= 0 && k >= 0 && dC && ldc >= std::max(m, 1), "invalid arguments");
+  REQUIRE(lda >= std::max(1, ta ? k : m) && ldb >= std::max(1, tb ? n : k), "invalid ld");
+  const size_t need = tcx32_gemm_workspace_bytes(m, n, k) + 256;
+  ensure_ws(h, need);
+  int* derr = reinterpret_cast<int*>(h->ws + need - 256);
+  CK(cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
+  CK(tcx32_gemm(h->stream, ta != 0, tb != 0, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc,
+                h->ws, derr));
   int* hf = static_cast<int*>(pinned(h, 64));
   CK(cudaMemcpyAsync(hf, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -2560,7 +2794,7 @@ int eig_server_submit(eig_server_t S, int kind, int n, double* dA, int lda, doub
   r->p.workers = 1;
   r->p.graphs = 0;   // the caller keeps running CUDA work while requests are served
   if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.v_draws < 1 ||
-      (r->p.prec != EIG_FP64 && r->p.prec != EIG_SPLIT_BF16X3 && r->p.prec != EIG_FP64_TC)) {
+      !valid_prec(r->p.prec)) {
     delete r;
     return EIG_ERR_ARG;
   }
@@ -2625,7 +2859,7 @@ int eig_server_submit_complex(eig_server_t S, int n, const double* dA, int lda, 
   r->p.graphs = 0;
   if (r->p.maxit < 0 || r->p.leaf_size < 1 || r->p.leaf_size > 64 || r->p.v_draws < 1 ||
       r->p.max_fail < 0 || r->p.split_tol < 0 ||
-      (r->p.prec != EIG_FP64 && r->p.prec != EIG_FP64_TC && r->p.prec != EIG_SPLIT_BF16X3)) {
+      !valid_prec(r->p.prec)) {
     delete r;
     return EIG_ERR_ARG;
   }

@@ -78,6 +78,14 @@ size_t tcx_gemm_workspace_bytes(int m, int n, int k);
 cudaError_t tcx_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
                      int ldc, void* ws, int* err);
+// FP32-level GEMM on the tensor cores: the same error-free split with four
+// 6-bit digits (24 bits of each row / column maximum) and levels 0..3 (10
+// digit pairs), exact FP32 accumulation per 960-wide K chunk, FP64 drain: no
+// accumulation bias, error about 2^-24 max|row| max|column| per product term.
+size_t tcx32_gemm_workspace_bytes(int m, int n, int k);
+cudaError_t tcx32_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                       const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                       int ldc, void* ws, int* err);
 cudaError_t tc_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
                     const double* A, int lda, const double* B, int ldb, double beta, double* C,
                     int ldc, void* ws, int* err);
@@ -179,6 +187,30 @@ cudaError_t pencil_leaves_phase2(cudaStream_t s, int count, const LeafDesc* d_de
 cudaError_t apply_leaf_vectors(cudaStream_t s, int count, const LeafDesc* d_desc, int n,
                                const double* Uin, int ldu_in, double* Uout, int ldu_out,
                                const double* Z);
+
+// ------------------------------------------------------------- fused.cu
+// One problem of the fused batched symmetric solver (device array entry).
+struct FusedProblem {
+  int n, lda, ldu, pad;
+  double* A;   // in: symmetric A; out: the block-diagonal working matrix (as eig_solve)
+  double* w;   // out: eigenvalues ascending
+  double* U;   // out: eigenvectors
+};
+struct FusedResult {
+  int status, nodes, splits, max_depth, total_iters, failed_attempts, leaves, pad;
+  double flops;
+};
+// Device bytes of the per-CTA workspaces for problems up to mx and `ctas` CTAs.
+size_t fused_workspace_bytes(int mx, int ctas);
+size_t fused_smem_bytes();
+int fused_max_n();
+// One persistent launch over `count` problems (CTAs take them in `order`
+// from an atomic counter); nb = 16 or 32 (panel width).
+cudaError_t fused_batched(cudaStream_t s, int count, const FusedProblem* probs, const int* order,
+                          FusedResult* results, int* counter, const eig_params_t& p, int nb,
+                          int ctas, int mx, void* ws);
+// Resident CTAs per SM of the fused kernel (occupancy calculator).
+int fused_max_ctas_per_sm();
 
 // ------------------------------------------------------------- cplane.cu
 // Complex-plane recursion (Sec. 3.3).  Complex arrays are interleaved (re, im)

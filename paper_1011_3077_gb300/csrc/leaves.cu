@@ -15,6 +15,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "jacobi_leaf.cuh"
 
 namespace eigdc {
 
@@ -22,129 +23,23 @@ constexpr int LMAX = 64;
 constexpr double U_ROUND = 1.1102230246251565e-16;   // 2^-53
 
 // ---------------------------------------------------------------- Jacobi
-__device__ __forceinline__ void sym_schur2(double app, double aqq, double apq, double& c,
-                                           double& s) {
-  if (apq == 0.0) {
-    c = 1.0;
-    s = 0.0;
-    return;
-  }
-  const double tau = (aqq - app) / (2.0 * apq);
-  double t;
-  if (tau >= 0.0) t = 1.0 / (tau + sqrt(1.0 + tau * tau));
-  else t = -1.0 / (-tau + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
-  s = t * c;
-}
-
-__global__ void __launch_bounds__(256)
+// One CTA per leaf; the solver body (jacobi_leaf.cuh) is shared with the
+// fused batched solver.
+__global__ void __launch_bounds__(JL_THREADS)
 jacobi_kernel(const LeafDesc* __restrict__ desc, const double* __restrict__ A, int lda,
               double* __restrict__ w, double* __restrict__ Z, int* status) {
-  __shared__ double S[LMAX][LMAX + 1];
-  __shared__ double Vs[LMAX][LMAX + 1];
-  __shared__ int pr[LMAX / 2][2];
-  __shared__ double rot[LMAX / 2][2];
-  __shared__ double red[8];
-  __shared__ double sh_tol, sh_off;
+  __shared__ JacobiShared J;
   const LeafDesc d = desc[blockIdx.x];
-  const int m = d.m, off = d.off;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < m * m; idx += 256) {
-    const int i = idx % m, j = idx / m;
-    S[i][j] = A[(size_t)(off + i) + (size_t)(off + j) * lda];
-    Vs[i][j] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  // ||A||_F
-  double f = 0.0;
-  for (int idx = tid; idx < m * m; idx += 256) {
-    const double x = S[idx % m][idx / m];
-    f = fma(x, x, f);
-  }
-  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
-  if ((tid & 31) == 0) red[tid >> 5] = f;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += red[q];
-    sh_tol = m * U_ROUND * sqrt(t);
-  }
-  __syncthreads();
-  const int mm = m + (m & 1);
-  const int npairs = mm / 2;
-  bool converged = (m <= 1);
-  for (int sweep = 0; sweep < 40 && !converged; ++sweep) {
-    double o2 = 0.0;
-    for (int idx = tid; idx < m * m; idx += 256) {
-      const int i = idx % m, j = idx / m;
-      if (i != j) o2 = fma(S[i][j], S[i][j], o2);
-    }
-    for (int o = 16; o > 0; o >>= 1) o2 += __shfl_xor_sync(0xffffffffu, o2, o);
-    if ((tid & 31) == 0) red[tid >> 5] = o2;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int q = 0; q < 8; ++q) t += red[q];
-      sh_off = sqrt(t);
-    }
-    __syncthreads();
-    if (sh_off <= sh_tol) {
-      converged = true;
-      break;
-    }
-    for (int r = 0; r < mm - 1; ++r) {
-      if (tid < npairs) {
-        auto pos = [&](int q) { return q == 0 ? 0 : ((q - 1 + r) % (mm - 1)) + 1; };
-        int a = pos(tid), b = pos(mm - 1 - tid);
-        const int p = min(a, b), q = max(a, b);
-        double c = 1.0, s = 0.0;
-        if (q < m) sym_schur2(S[p][p], S[q][q], S[p][q], c, s);
-        pr[tid][0] = p;
-        pr[tid][1] = q;
-        rot[tid][0] = c;
-        rot[tid][1] = s;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < npairs * m; idx += 256) {
-        const int t = idx / m, j = idx % m;
-        const double s = rot[t][1];
-        if (s == 0.0) continue;
-        const double c = rot[t][0];
-        const int p = pr[t][0], q = pr[t][1];
-        const double a = S[p][j], b = S[q][j];
-        S[p][j] = c * a - s * b;
-        S[q][j] = s * a + c * b;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < npairs * m; idx += 256) {
-        const int t = idx / m, i = idx % m;
-        const double s = rot[t][1];
-        if (s == 0.0) continue;
-        const double c = rot[t][0];
-        const int p = pr[t][0], q = pr[t][1];
-        const double a = S[i][p], b = S[i][q];
-        S[i][p] = c * a - s * b;
-        S[i][q] = s * a + c * b;
-        const double va = Vs[i][p], vb = Vs[i][q];
-        Vs[i][p] = c * va - s * vb;
-        Vs[i][q] = s * va + c * vb;
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = tid; i < m; i += 256) w[off + i] = S[i][i];
-  for (int idx = tid; idx < m * m; idx += 256) {
-    const int i = idx % m, j = idx / m;
-    Z[(size_t)d.zoff + i + (size_t)j * LMAX] = Vs[i][j];
-  }
-  if (tid == 0 && !converged) atomicOr(status, 1);
+  const bool ok = jacobi_leaf(d.m, A + (size_t)d.off + (size_t)d.off * lda, lda, w + d.off,
+                              Z + d.zoff, LMAX, J);
+  if (threadIdx.x == 0 && !ok) atomicOr(status, 1);
 }
 
 cudaError_t jacobi_leaves(cudaStream_t s, int count, const LeafDesc* d_desc, const double* A,
                           int lda, double* w, double* Z, int* status) {
   if (count == 0) return cudaSuccess;
   note_launches(1);
-  jacobi_kernel<<<count, 256, 0, s>>>(d_desc, A, lda, w, Z, status);
+  jacobi_kernel<<<count, JL_THREADS, 0, s>>>(d_desc, A, lda, w, Z, status);
   return cudaGetLastError();
 }
 

@@ -43,21 +43,33 @@ namespace eigdc {
 bool make_plane_map(CUtensorMap* map, void* base, int rows, int kp, int box_rows, int planes);
 
 constexpr int TX_BM = 128, TX_BN = 48, TX_BK = 64;
-constexpr int TX_DIGITS = 9;             // 6-bit digits per operand
-constexpr int TX_LEVELS = 10;            // kept levels l = i + j <= 9
-constexpr int TX_CHUNK_TILES = 7;        // K tiles per exact chunk (448 of K)
 constexpr int TX_BSTAGES = 2, TX_ASLOTS = 4;
 constexpr int TX_THREADS = 192;
 constexpr int TX_TILE_A = TX_BM * TX_BK * 2;   // bytes of one digit plane slab of A
 constexpr int TX_TILE_B = TX_BN * TX_BK * 2;
-constexpr uint32_t TX_TMEM_COLS = 512;   // >= TX_LEVELS * TX_BN, power of two
-static_assert(TX_LEVELS * TX_BN <= (int)TX_TMEM_COLS, "levels fit in TMEM");
 static_assert(TX_TILE_A % 1024 == 0 && TX_TILE_B % 1024 == 0, "1024-byte swizzle atoms");
-// exactness: the largest level has 9 digit pairs of at most 64 * 64
-static_assert((long long)9 * TX_CHUNK_TILES * TX_BK * 64 * 64 < (1LL << 24), "exact FP32 chunk");
 
+// Digit count DIG and the levels kept:
+//   DIG = 9: levels 0..9 (53 digit pairs), FP64 accuracy;
+//   DIG = 4: levels 0..3 (10 digit pairs), FP32-level accuracy (24 bits of
+//            each row / column maximum), the split-precision form.
+// CHUNK_TILES: 64-wide K tiles per exact FP32 chunk, so that a level's
+// partial sums (pairs per level x chunk x 64^2) stay integers below 2^24.
+template <int DIG>
+struct TxCfg {
+  static constexpr int DIGITS = DIG;
+  static constexpr int LEVELS = (DIG == 9) ? 10 : DIG;
+  static constexpr int MAXPAIRS = (DIG == 9) ? 9 : DIG;   // digit pairs of the fullest level
+  static constexpr int CHUNK_TILES = (DIG == 9) ? 7 : 15;
+  static constexpr uint32_t TMEM_COLS = (DIG == 9) ? 512 : 256;   // >= LEVELS * TX_BN, power of two
+  static_assert(LEVELS * TX_BN <= (int)TMEM_COLS, "levels fit in TMEM");
+  static_assert((long long)MAXPAIRS * CHUNK_TILES * TX_BK * 64 * 64 < (1LL << 24),
+                "exact FP32 chunk");
+};
+
+template <int DIG>
 struct TxSmem {
-  uint8_t b[TX_BSTAGES][TX_DIGITS][TX_TILE_B];
+  uint8_t b[TX_BSTAGES][DIG][TX_TILE_B];
   uint8_t a[TX_ASLOTS][TX_TILE_A];
   uint64_t bfull[TX_BSTAGES], bempty[TX_BSTAGES];
   uint64_t afull[TX_ASLOTS], aempty[TX_ASLOTS];
@@ -98,7 +110,8 @@ __device__ __forceinline__ int row_exponent(unsigned long long maxbits) {
   return E == 0 ? -1022 : E - 1022;
 }
 
-// Digit planes P[p][r*kp + k] (p = 0..8) and row exponents expo[r].
+// Digit planes P[p][r*kp + k] (p = 0..DIG-1) and row exponents expo[r].
+template <int DIG>
 __global__ void __launch_bounds__(256)
 slice_kernel(int rows, int K, int kp, const double* __restrict__ X, int ldx, int kcontig,
              const unsigned long long* __restrict__ mx, __nv_bfloat16* __restrict__ P,
@@ -134,22 +147,26 @@ slice_kernel(int rows, int K, int kp, const double* __restrict__ X, int ldx, int
     const bool neg = (b >> 63) != 0;
     const size_t o = (size_t)r * kp + k;
 #pragma unroll
-    for (int p = 0; p < TX_DIGITS; ++p) {
+    for (int p = 0; p < DIG; ++p) {
       int d = (int)((F >> (56 - 6 * p)) & 63ull);
-      if (p == TX_DIGITS - 1) d += (int)((F >> 7) & 1ull);   // round the last digit
+      if (p == DIG - 1) d += (int)((F >> (55 - 6 * p)) & 1ull);   // round the last digit
       P[p * pstride + o] = __int2bfloat16_rn(neg ? -d : d);
     }
   }
 }
 
 // ------------------------------------------------------------------ GEMM
+template <int DIG>
 __global__ void __launch_bounds__(TX_THREADS, 1)
 tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 int M, int N, int kp, double alpha, double beta, double* __restrict__ C, int ldc,
                 const int* __restrict__ expA, const int* __restrict__ expB, int* err) {
   extern __shared__ uint8_t smem_raw[];
-  TxSmem& S = *reinterpret_cast<TxSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                         ~static_cast<uintptr_t>(1023));
+  using Cfg = TxCfg<DIG>;
+  constexpr int TX_DIGITS = Cfg::DIGITS, TX_LEVELS = Cfg::LEVELS, TX_CHUNK_TILES = Cfg::CHUNK_TILES;
+  constexpr uint32_t TX_TMEM_COLS = Cfg::TMEM_COLS;
+  TxSmem<DIG>& S = *reinterpret_cast<TxSmem<DIG>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                   ~static_cast<uintptr_t>(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TX_BM, n0 = blockIdx.y * TX_BN;
   const int nk = kp / TX_BK;
@@ -317,12 +334,17 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // ------------------------------------------------------------------ host side
 static size_t align1k(size_t b) { return (b + 1023) & ~(size_t)1023; }
 
-size_t tcx_gemm_workspace_bytes(int m, int n, int k) {
+template <int DIG>
+static size_t tcx_ws_bytes(int m, int n, int k) {
   const size_t kp = ((size_t)std::max(k, 1) + TX_BK - 1) / TX_BK * TX_BK;
-  auto planes = [&](int rows) { return align1k((size_t)TX_DIGITS * rows * kp * 2); };
+  auto planes = [&](int rows) { return align1k((size_t)DIG * rows * kp * 2); };
   return planes(m) + planes(n) + align1k((size_t)(m + n) * 8) + align1k((size_t)(m + n) * 4) + 256;
 }
 
+size_t tcx_gemm_workspace_bytes(int m, int n, int k) { return tcx_ws_bytes<9>(m, n, k); }
+size_t tcx32_gemm_workspace_bytes(int m, int n, int k) { return tcx_ws_bytes<4>(m, n, k); }
+
+template <int DIG>
 static cudaError_t slice_operand(cudaStream_t s, int rows, int K, int kp, const double* X, int ldx,
                                  bool kcontig, unsigned long long* mx, void* planes, int* expo) {
   if (rows <= 0) return cudaSuccess;
@@ -333,45 +355,60 @@ static cudaError_t slice_operand(cudaStream_t s, int rows, int K, int kp, const 
   rowmax_kernel<<<g1, 256, 0, s>>>(rows, K, X, ldx, kcontig ? 1 : 0, mx);
   dim3 g2((kp + 63) / 64, (rows + 31) / 32);
   note_launches(1);
-  slice_kernel<<<g2, 256, 0, s>>>(rows, K, kp, X, ldx, kcontig ? 1 : 0, mx,
-                                  static_cast<__nv_bfloat16*>(planes), (size_t)rows * kp, expo);
+  slice_kernel<DIG><<<g2, 256, 0, s>>>(rows, K, kp, X, ldx, kcontig ? 1 : 0, mx,
+                                       static_cast<__nv_bfloat16*>(planes), (size_t)rows * kp,
+                                       expo);
+  return cudaGetLastError();
+}
+
+template <int DIG>
+static cudaError_t tcx_run(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                           const double* A, int lda, const double* B, int ldb, double beta,
+                           double* C, int ldc, void* ws, int* err) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (k <= 0) return gemm(s, false, false, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, 1, nullptr);
+  const int kp = ((k + TX_BK - 1) / TX_BK) * TX_BK;
+  char* base = static_cast<char*>(ws);
+  const size_t abytes = align1k((size_t)DIG * m * kp * 2);
+  const size_t bbytes = align1k((size_t)DIG * n * kp * 2);
+  void* pa = base;
+  void* pb = base + abytes;
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(base + abytes + bbytes);
+  int* ex = reinterpret_cast<int*>(base + abytes + bbytes + align1k((size_t)(m + n) * 8));
+  // op(A) is m x k: its K-major rows are contiguous when A is stored k x m (ta)
+  cudaError_t e = slice_operand<DIG>(s, m, k, kp, A, lda, ta, mx, pa, ex);
+  if (e != cudaSuccess) return e;
+  // the MMA's B operand is op(B)^T (n x k): contiguous in k when B is k x n (!tb)
+  e = slice_operand<DIG>(s, n, k, kp, B, ldb, !tb, mx + m, pb, ex + m);
+  if (e != cudaSuccess) return e;
+  CUtensorMap ta_map, tb_map;
+  if (!make_plane_map(&ta_map, pa, m, kp, TX_BM, DIG) ||
+      !make_plane_map(&tb_map, pb, n, kp, TX_BN, DIG))
+    return cudaErrorInvalidValue;
+  const size_t smem = sizeof(TxSmem<DIG>) + 1024;
+  static const bool attr = [smem] {
+    cudaFuncSetAttribute(tcx_gemm_kernel<DIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    return true;
+  }();
+  (void)attr;
+  dim3 grid((m + TX_BM - 1) / TX_BM, (n + TX_BN - 1) / TX_BN);
+  note_launches(1);
+  tcx_gemm_kernel<DIG><<<grid, TX_THREADS, smem, s>>>(ta_map, tb_map, m, n, kp, alpha, beta, C,
+                                                      ldc, ex, ex + m, err);
   return cudaGetLastError();
 }
 
 cudaError_t tcx_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
                      int ldc, void* ws, int* err) {
-  if (m <= 0 || n <= 0) return cudaSuccess;
-  if (k <= 0) return gemm(s, false, false, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, 1, nullptr);
-  const int kp = ((k + TX_BK - 1) / TX_BK) * TX_BK;
-  char* base = static_cast<char*>(ws);
-  const size_t abytes = align1k((size_t)TX_DIGITS * m * kp * 2);
-  const size_t bbytes = align1k((size_t)TX_DIGITS * n * kp * 2);
-  void* pa = base;
-  void* pb = base + abytes;
-  unsigned long long* mx = reinterpret_cast<unsigned long long*>(base + abytes + bbytes);
-  int* ex = reinterpret_cast<int*>(base + abytes + bbytes + align1k((size_t)(m + n) * 8));
-  // op(A) is m x k: its K-major rows are contiguous when A is stored k x m (ta)
-  cudaError_t e = slice_operand(s, m, k, kp, A, lda, ta, mx, pa, ex);
-  if (e != cudaSuccess) return e;
-  // the MMA's B operand is op(B)^T (n x k): contiguous in k when B is k x n (!tb)
-  e = slice_operand(s, n, k, kp, B, ldb, !tb, mx + m, pb, ex + m);
-  if (e != cudaSuccess) return e;
-  CUtensorMap ta_map, tb_map;
-  if (!make_plane_map(&ta_map, pa, m, kp, TX_BM, TX_DIGITS) ||
-      !make_plane_map(&tb_map, pb, n, kp, TX_BN, TX_DIGITS))
-    return cudaErrorInvalidValue;
-  const size_t smem = sizeof(TxSmem) + 1024;
-  static const bool attr = [smem] {
-    cudaFuncSetAttribute(tcx_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return true;
-  }();
-  (void)attr;
-  dim3 grid((m + TX_BM - 1) / TX_BM, (n + TX_BN - 1) / TX_BN);
-  note_launches(1);
-  tcx_gemm_kernel<<<grid, TX_THREADS, smem, s>>>(ta_map, tb_map, m, n, kp, alpha, beta, C, ldc, ex,
-                                                 ex + m, err);
-  return cudaGetLastError();
+  return tcx_run<9>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
+}
+
+cudaError_t tcx32_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                       const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                       int ldc, void* ws, int* err) {
+  return tcx_run<4>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
 }
 
 }  // namespace eigdc

@@ -36,6 +36,7 @@ EIG_REGION_LINE = 2
 EIG_FP64 = 0
 EIG_SPLIT_BF16X3 = 1
 EIG_FP64_TC = 2
+EIG_SPLIT_FP32 = 3
 EIG_KIND_SYM = 0
 EIG_KIND_NONSYM = 1
 EIG_KIND_PENCIL = 2
@@ -91,6 +92,10 @@ class Enclosure(ctypes.Structure):
         return complex(self.c_re, self.c_im), self.R, hps
 
 
+class FusedConfig(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -121,6 +126,10 @@ _SIGNATURES = {
                      ctypes.POINTER(SolveInfo)]),
     "eig_solve_batched": (_I, [_P, _I, _I, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Params),
                                _P, _P]),
+    "eig_solve_batched_fused": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Params),
+                                     _P, _P]),
+    "eig_fused_autotune": (_I, [_P, _I, _I, _I, _U64, ctypes.POINTER(FusedConfig), _I,
+                                ctypes.POINTER(_I), ctypes.POINTER(FusedConfig)]),
     "eig_server_create": (_I, [ctypes.POINTER(_P), _I, _I, _D]),
     "eig_server_submit": (_I, [_P, _I, _I, _P, _I, _P, _P, _P, _I, ctypes.POINTER(Params),
                                ctypes.POINTER(_U64)]),
@@ -145,6 +154,7 @@ _SIGNATURES = {
     "eig_gemm": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_split": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_fp64tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
+    "eig_gemm_fp32tc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_gemm_noalloc": (_I, [_P, _I, _I, _I, _I, _I, _D, _P, _I, _P, _I, _D, _P, _I]),
     "eig_eigenvectors": (_I, [_P, _I, _P, _I, _P, _I, _P, _P, _I, _P]),
     "eig_eigenvectors_complex": (_I, [_P, _I, _P, _I, _P, _I, _P, _I, _P]),
@@ -341,6 +351,39 @@ def eig_solve_batched(h, kind, ns, dAs, ldas, dwrs, dwis, dUs, ldus, params):
     return rc, [st[i] for i in range(count)], [infos[i] for i in range(count)]
 
 
+def eig_solve_batched_fused(h, ns, dAs, ldas, dws, dUs, ldus, params):
+    """One persistent fused launch over symmetric problems (n <= 512); returns
+    (rc, status list, infos)."""
+    count = len(ns)
+    I = ctypes.c_int * max(count, 1)
+    Pp = ctypes.c_void_p * max(count, 1)
+    n_a, lda_a, ldu_a = I(*ns), I(*ldas), I(*ldus)
+    A_a = Pp(*[t.data_ptr() for t in dAs])
+    w_a = Pp(*[t.data_ptr() for t in dws])
+    U_a = Pp(*[t.data_ptr() for t in dUs])
+    st = I()
+    infos = (SolveInfo * max(count, 1))()
+    rc = lib().eig_solve_batched_fused(h.ptr, count, ctypes.cast(n_a, _P), ctypes.cast(A_a, _P),
+                                       ctypes.cast(lda_a, _P), ctypes.cast(w_a, _P),
+                                       ctypes.cast(U_a, _P), ctypes.cast(ldu_a, _P),
+                                       ctypes.byref(params), ctypes.cast(st, _P),
+                                       ctypes.cast(infos, _P))
+    return rc, [st[i] for i in range(count)], [infos[i] for i in range(count)]
+
+
+def eig_fused_autotune(h, samples, nmin, nmax, seed=0):
+    """Times the fused solver's launch shapes on a synthetic batch and keeps the
+    fastest on the handle; returns (rc, best, [candidates])."""
+    cap = 16
+    table = (FusedConfig * cap)()
+    nt = ctypes.c_int(0)
+    best = FusedConfig()
+    rc = lib().eig_fused_autotune(h.ptr, samples, nmin, nmax, int(seed), table, cap,
+                                  ctypes.byref(nt), ctypes.byref(best))
+    cands = [(table[i].nb, table[i].ctas_per_sm, table[i].ms) for i in range(min(nt.value, cap))]
+    return rc, (best.nb, best.ctas_per_sm, best.ms), cands
+
+
 class Server:
     """eig_server_* wrapper: submit device buffers, poll or wait for completion."""
 
@@ -466,6 +509,11 @@ def eig_gemm_split(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
 
 def eig_gemm_fp64tc(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
     return h.check(lib().eig_gemm_fp64tc(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
+                                        _ptr(dB), ldb, beta, _ptr(dC), ldc))
+
+
+def eig_gemm_fp32tc(h, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc):
+    return h.check(lib().eig_gemm_fp32tc(h.ptr, int(ta), int(tb), m, n, k, alpha, _ptr(dA), lda,
                                         _ptr(dB), ldb, beta, _ptr(dC), ldc))
 
 

@@ -6,13 +6,7 @@ agree to the oracle's own accuracy, and the GPU result meets the targets of
 the oracle pins -- T upper triangular, ||U^H U - I|| <= 1e-12,
 ||A - U T U^H||_F / ||A||_F <= 1e-13 -- and reports the same cluster
 enclosures for the Jordan example.
-
-These tests have not yet run on a GB300: the module is skipped until the
-first hardware run of the complex path
-(EIGDC_RUN_PENDING=1 runs them before that).
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -20,10 +14,7 @@ from oracle.cplane import schur_complex_plane
 from oracle.solve import STATUS_OK, STATUS_NO_SPLIT
 from paper_1011_3077_gb300 import workloads
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("EIGDC_RUN_PENDING") != "1",
-                                 reason="complex path: first hardware run pending "
-                                        "(EIGDC_RUN_PENDING=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")

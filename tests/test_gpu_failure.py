@@ -2,22 +2,13 @@
 EIG_ERR_NOMEM (solve and server request) and leaves the handle usable, and a
 queued server request can be cancelled (status EIG_CANCELLED) while a running
 one is left to finish.
-
-These tests have not yet run on a GB300: the module is skipped until the
-first hardware run of the injection and cancel paths
-(EIGDC_RUN_PENDING=1 runs them before that).
 """
-import os
-
 import numpy as np
 import pytest
 
 from paper_1011_3077_gb300 import workloads
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("EIGDC_RUN_PENDING") != "1",
-                                 reason="failure paths: first hardware run pending "
-                                        "(EIGDC_RUN_PENDING=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")

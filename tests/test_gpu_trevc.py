@@ -5,23 +5,14 @@ oracle (oracle/trevc.py) takes the same (T, Q, wi).  Eigenvalues agree to
 1e-13 |A|, each eigenvector agrees with the oracle's up to a unit scalar to
 1e-10 kappa (the recurrence divides by eigenvalue differences), and
 ||A V - V diag(lam)||_F <= 1e-12 ||A||_F ||V||_F.
-
-These tests have not yet run on a GB300: the module is skipped until the
-first hardware run of the eigenvector kernels
-(EIGDC_RUN_PENDING=1 runs them before that).
 """
-import os
-
 import numpy as np
 import pytest
 
 from oracle import trevc as otrevc
 from paper_1011_3077_gb300 import workloads
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("EIGDC_RUN_PENDING") != "1",
-                                 reason="eigenvector kernels: first hardware run pending "
-                                        "(EIGDC_RUN_PENDING=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
