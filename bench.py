@@ -1,20 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 inverse-free divide-and-conquer eigensolver.
 
-One step = one full solve of the workload through the C-ABI (every row of the
-path: region map, IRS squarings, GRURV splitter, similarity, split test,
-recursion, leaf solvers, Schur-form assembly).
+Default workload (serve): a seeded Poisson stream at 200 requests/s of mixed
+eigenproblems -- 50% symmetric eigendecompositions, 30% nonsymmetric real
+Schur forms (A = Q T Q^T, T diagonal half |z| ~ U[0.2, 0.9], half |z| ~
+U[1.1, 3] with random signs, strict upper part N(0, (0.1/sqrt(n))^2)), 20%
+generalized Schur forms of regular pencils (B = I + 0.1 G / sqrt(n), A =
+(Q T Q^T) B) -- with n log-uniform in [64, 4096], served by the library's
+request server under a 120 GB HBM budget.  One step = one completed request
+(every row of the path inside: region map, IRS squarings, GRURV splitter,
+similarity, split test, recursion, leaves, assembly).  Symmetric requests run
+in the unbiased FP32-level split form with FP64 refinement, the others in the
+FP64-accurate tensor-core form; `plain_fp64` serves the same trace with every
+contraction on the FP64 pipe.  Other workloads (--workload): schur, sym,
+batched (one persistent fused launch per batch), svd, cplane.
 
-Default workload: nonsymmetric n = 2048, A = Q T Q^T with T upper triangular
-(diagonal half |z| ~ U[0.2, 0.9], half |z| ~ U[1.1, 3], random signs, strict
-upper part N(0, 1/n)), full recursion to 64 x 64 leaves giving the real Schur
-form, plain FP64.
-
-Output: one JSON line (rank 0).  `value` is solves/s over all ranks with the
-input resident in HBM; `e2e` is the same metric through the public API with
-host buffers (host->device copy of A and device->host copy of T, U and the
-eigenvalues inside the timed region).  N > 1 ranks (torchrun) solve
-independent matrices: weak scaling, no collective on the data path.
+Output: one JSON line (rank 0).  `value` is completed requests per second over
+all ranks with the inputs resident in HBM; `e2e` serves the same trace with
+the inputs in pinned host memory, copied to the device as each request
+arrives and its outputs read back as it completes (inside the timed region).
+N > 1 ranks (torchrun) serve independent traces: weak scaling, no collective
+on the data path.
 
 `--impl reference` times the CPU oracle (oracle/, plain FP64 numpy) on a
 bounded sample of the same workload and reports the same metric.
@@ -36,13 +42,13 @@ if ROOT not in sys.path:
 METRIC = "eig solves/s & GFLOP/s vs plain FP64 at ≤1e-10 backward err; p50/p99 latency"
 L2_BYTES = 129 * 1024 * 1024
 SAMPLE_N = 512   # oracle sample size (same construction, smaller n; about 10 s of CPU)
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dgemm_traffic.json")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 24 requests for serve, 3 solves otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=2048)
@@ -50,10 +56,11 @@ def parse():
                     help="strict-upper scale of T in units of 1/sqrt(n) (1.0 = the exact "
                          "construction, whose eigenvalues are too ill-conditioned to split "
                          "in FP64 at n=2048; 0.1 = the documented reduced-coupling variant)")
-    ap.add_argument("--prec", type=int, default=2, choices=[0, 1, 2],
+    ap.add_argument("--prec", type=int, default=2, choices=[0, 1, 2, 3],
                     help="2: FP64-accurate contractions on the tensor cores (error-free "
                          "nine-digit BF16 split) for the large products; 0: every contraction "
-                         "on the FP64 DFMA pipe")
+                         "on the FP64 DFMA pipe; 1 / 3: split precision (BF16 x 3 / unbiased "
+                         "four-digit FP32-level products, FP64 refinement; symmetric only)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path beside the tensor-core one")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
@@ -61,9 +68,13 @@ def parse():
                          "device-wide synchronisation while a solve runs)")
     ap.add_argument("--workers", type=int, default=8,
                     help="host workers of the node-parallel recursion (own CUDA streams)")
-    ap.add_argument("--workload", default="schur",
-                    choices=["schur", "batched", "svd", "cplane", "sym"],
-                    help="schur: one nonsymmetric n x n solve per step (default); batched: "
+    ap.add_argument("--prec-sym", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="serve: precision of the symmetric requests (3: unbiased FP32-level "
+                         "split with FP64 refinement)")
+    ap.add_argument("--workload", default="serve",
+                    choices=["serve", "schur", "batched", "svd", "cplane", "sym"],
+                    help="serve: the mixed request stream (default, one step = one completed "
+                         "request); schur: one nonsymmetric n x n solve per step; batched: "
                          "--count independent symmetric problems, n log-uniform in [32, 512], "
                          "solved by eig_solve_batched per step; svd: singular values and "
                          "vectors of one n x n matrix per step (eig_svd); cplane: the complex "
@@ -77,7 +88,10 @@ def parse():
                          "0 = the host-driven executor (eig_solve_batched)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 24 if a.workload == "serve" else 3
+    return a
 
 
 def workload(n, rank, coupling=0.1):
@@ -167,9 +181,42 @@ def run_oracle_sample(coupling, seed_rank=0):
     return time.perf_counter() - t0, info
 
 
+def reference_arm_serve(args):
+    """The oracle on the serving trace (same metric and config): each step is
+    the oracle's sample solves of the three request kinds, and the trace's
+    time is their n^3-scaled sum (the oracle serves one request at a time)."""
+    from paper_1011_3077_gb300 import serving
+    arr, kinds, sizes = serving.trace(args.steps, SERVE_RATE, 64, 4096, (0.5, 0.3, 0.2), 5)
+    vals, samples, secs = [], [], []
+    for i in range(args.warmup + args.steps):
+        v, sample, t = serve_oracle_estimate(arr, kinds, sizes)
+        if i >= args.warmup:
+            vals.append(v)
+            samples.append(sample)
+            secs.append(t)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serving: Poisson stream at 200 requests/s of mixed "
+                                   "eigenproblems, 50% symmetric / 30% nonsymmetric Schur / 20% "
+                                   "generalized Schur of regular pencils, n log-uniform in "
+                                   "[64, 4096]; one step = one completed request",
+                       "requests": args.steps},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "solves/s",
+                             "cores": os.cpu_count(), "sample": samples[-1]},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
+        return
+    if args.workload == "serve":
+        reference_arm_serve(args)
         return
     n = args.n
     # flops per solve from the paper's cost model: estimated from the sample's
@@ -213,19 +260,20 @@ def whole_job_rate(units_per_rank, ms_max, world):
     return units_per_rank * world / (ms_max / 1e3)
 
 
-def traffic_per_launch(per_launch_flops):
-    """DRAM bytes per dgemm launch from the committed ncu capture (bytes per
-    algorithmic flop, scaled to this run's average launch), or None when the
-    capture is missing or the kernel source changed since it was taken."""
+def traffic_per_launch(per_launch_flops, record="dgemm_traffic.json", source="linalg.cu"):
+    """DRAM bytes per launch of a kernel from its committed ncu capture (bytes
+    per unit of algorithmic work, scaled to this run's average launch), or None
+    when the capture is missing or the kernel's source file changed since it
+    was taken."""
     import hashlib
     try:
-        rec = json.load(open(TRAFFIC_FILE))
-        src = open(os.path.join(ROOT, "paper_1011_3077_gb300", "csrc", "linalg.cu"), "rb").read()
+        rec = json.load(open(os.path.join(ROOT, "profiles", record)))
+        src = open(os.path.join(ROOT, "paper_1011_3077_gb300", "csrc", source), "rb").read()
     except Exception:
         return None
-    if rec.get("linalg_cu_sha256") != hashlib.sha256(src).hexdigest() or not per_launch_flops:
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest() or not per_launch_flops:
         return None
-    return rec["dram_bytes_per_flop"] * per_launch_flops
+    return rec["dram_bytes_per_work"] * per_launch_flops
 
 
 def batched_arm(args, torch, eigdc, h, dev, stream, world):
@@ -527,7 +575,9 @@ def sym_arm(args, torch, eigdc, h, dev, stream, world):
     orth = orth_2norm(U, torch)
     info = infos[-1]
     names = {0: "fp64", 1: "split bf16x3 (FP32-level tensor-core products, FP64 panels, "
-                       "split tests and refinement)", 2: "fp64 (tensor-core error-free split)"}
+                       "split tests and refinement)", 2: "fp64 (tensor-core error-free split)",
+             3: "split fp32 (unbiased four-digit tensor-core products, FP64 panels, split "
+                "tests and refinement)"}
     line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
             "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -547,6 +597,179 @@ def sym_arm(args, torch, eigdc, h, dev, stream, world):
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
             "e2e": None, "cpu_baseline": None}
     if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- serving workload
+SERVE_RATE = 200.0
+SERVE_SAMPLE_N = 256   # oracle sample size per request kind (same constructions)
+
+
+def fp64_peak_tflops():
+    """(sustained, burst, note): the FP64 rate of GB300 derived from the
+    measured dense BF16 rates x the nominal FP64/BF16 ratio 1.25/2250."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if "bf16_tflops_sustained" in peaks:
+        bf16, burst, src = peaks["bf16_tflops_sustained"], peaks.get("bf16_tflops"), "of measured"
+        burst = burst or bf16
+    else:
+        bf16, burst, src = 1700.0, 1900.0, "of fallback"
+    return bf16, burst, src
+
+
+def serve_oracle_estimate(arrivals, kinds, sizes):
+    """The oracle's throughput on a trace, estimated from one solve of each
+    request kind at n = SERVE_SAMPLE_N (the constructions of the trace),
+    scaled by (n_i / n_s)^3 per request and summed serially."""
+    from oracle.solve import eig_sym, schur_nonsym, pencil_schur
+    from paper_1011_3077_gb300 import eigdc, workloads
+    ns = SERVE_SAMPLE_N
+    t = {}
+    A, _ = workloads.symmetric_uniform(ns, seed=1)
+    t0 = time.perf_counter()
+    eig_sym(A, seed=0)
+    t[eigdc.EIG_KIND_SYM] = time.perf_counter() - t0
+    A, _, _ = workloads.nonsymmetric_schur(ns, seed=1, offdiag_scale=0.1 / np.sqrt(ns))
+    t0 = time.perf_counter()
+    schur_nonsym(A, seed=0)
+    t[eigdc.EIG_KIND_NONSYM] = time.perf_counter() - t0
+    A, B, _ = workloads.regular_pencil(ns, seed=1, offdiag_scale=0.1 / np.sqrt(ns))
+    t0 = time.perf_counter()
+    pencil_schur(A, B, seed=0)
+    t[eigdc.EIG_KIND_PENCIL] = time.perf_counter() - t0
+    total = sum(t[int(k)] * (int(n) / ns) ** 3 for k, n in zip(kinds, sizes))
+    sample = ("oracle solves of one request of each kind at n=%d (sym %.1f s, nonsym %.1f s, "
+              "pencil %.1f s), scaled by (n_i/%d)^3 over the trace's %d requests and summed "
+              "serially" % (ns, t[0], t[1], t[2], ns, len(sizes)))
+    return len(sizes) / total, sample, sum(t.values())
+
+
+def serve_arm(args, torch, eigdc, h, dev, stream, world):
+    """The serving workload: a seeded Poisson stream (mean 200 requests/s) of
+    mixed requests -- 50% symmetric eigendecompositions (lambda ~ U[-1, 1]),
+    30% nonsymmetric real Schur forms, 20% generalized Schur forms of regular
+    pencils (B = I + 0.1 G / sqrt(n), A = (Q T Q^T) B), n log-uniform in
+    [64, 4096] -- served by the native request server under a 120 GB HBM
+    budget with continuous batching.  One step = one completed request;
+    value = completed requests / makespan (first arrival to last
+    completion); p50 / p99 latency from arrival to completion.  Symmetric
+    requests run in the split-precision form (--prec-sym), the others in the
+    FP64-accurate tensor-core form; the plain-FP64 leg serves the same trace
+    with every contraction on the FP64 pipe."""
+    from paper_1011_3077_gb300 import serving
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    seed = 5 + 101 * rank
+    kw = dict(rate=SERVE_RATE, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=args.workers,
+              budget_gb=120.0, device=dev)
+    prec, prec_sym = eigdc.EIG_FP64_TC, args.prec_sym
+    if args.warmup > 0:
+        serving.run(count=args.warmup, seed=1000 + seed, prec=prec, prec_sym=prec_sym, **kw)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = eigdc.eig_kernel_launches()
+    with ClockSampler(local) as clk:
+        eigdc.eig_gemm_timing_start()
+        res = serving.run(count=args.steps, seed=seed, prec=prec, prec_sym=prec_sym,
+                          details=True, **kw)
+        eigdc.eig_gemm_timing_stop()
+    launches = eigdc.eig_kernel_launches() - l0
+    fam = {f: eigdc.eig_kernel_timing(f) for f in eigdc.TIMING_FAMILIES}
+    ms = max_over_ranks(res["makespan_s"] * 1e3, dev, world)
+    value = whole_job_rate(res["ok"], ms, world)
+    e2e = None
+    if not args.no_e2e:
+        r2 = serving.run(count=args.steps, seed=seed, prec=prec, prec_sym=prec_sym,
+                         host_io=True, **kw)
+        ms2 = max_over_ranks(r2["makespan_s"] * 1e3, dev, world)
+        e2e = {"value": whole_job_rate(r2["ok"], ms2, world), "unit": "solves/s",
+               "h2d_bytes_per_step": r2["h2d_bytes"] / max(args.steps, 1),
+               "d2h_bytes_per_step": r2["d2h_bytes"] / max(args.steps, 1),
+               "latency_s": r2["latency_s"], "max_backward_error": r2["max_backward_error"]}
+    plain = None
+    if not args.no_fp64_compare:
+        r3 = serving.run(count=args.steps, seed=seed, prec=eigdc.EIG_FP64,
+                         prec_sym=eigdc.EIG_FP64, details=True, **kw)
+        ms3 = max_over_ranks(r3["makespan_s"] * 1e3, dev, world)
+        p_val = whole_job_rate(r3["ok"], ms3, world)
+        plain = {"value": p_val, "unit": "solves/s", "makespan_s": ms3 / 1e3,
+                 "latency_s": r3["latency_s"], "max_backward_error": r3["max_backward_error"],
+                 "max_eigenvalue_error": r3["max_eigenvalue_error"],
+                 "gflops": r3["flops"] / (ms3 / 1e3) / 1e9,
+                 "speedup_of_value": value / p_val if p_val else None,
+                 "trees": [{"n": d["n"], "kind": d["kind"], "status": d["status"]}
+                           for d in r3["requests_detail"]]}
+    # roofline of the kernel family that held the most launch time
+    bf16, bf16_burst, src = fp64_peak_tflops()
+    ratio = 1.25 / 2250.0
+    dom = max(fam, key=lambda f: fam[f][0])
+    f_ms, f_cnt, f_work = fam[dom]
+    achieved = f_work / (f_ms / 1e3) / 1e12 if f_ms > 0 else None
+    per_launch = f_work / f_cnt if f_cnt else None
+    if dom == 0:
+        roofline = {"bound": "alu", "peak": bf16 * ratio, "unit": "TFLOP/s",
+                    "peak_note": "measured sustained bf16 %.1f TF/s x nominal FP64/BF16 ratio "
+                                 "1.25/2250 (%s)" % (bf16, src),
+                    "traffic": traffic_per_launch(per_launch)}
+    else:
+        roofline = {"bound": "tensor", "peak": bf16, "unit": "TFLOP/s",
+                    "peak_note": "measured sustained dense bf16 (%s); work = digit pairs x 2mnk "
+                                 "BF16 MMA flops" % src,
+                    "traffic": traffic_per_launch(per_launch, "tcx_gemm_traffic.json",
+                                                  "tcx_gemm.cu")}
+    roofline.update({"kernel": eigdc.TIMING_FAMILIES[dom], "achieved": achieved,
+                     "frac": achieved / roofline["peak"] if achieved else None,
+                     "launches": f_cnt, "per_launch_work": per_launch,
+                     "launch_ms": f_ms / f_cnt if f_cnt else None,
+                     "timed_set": "every eager launch of the family inside the timed trace, "
+                                  "event pairs on the launching worker's stream (concurrent "
+                                  "requests share the SMs, so a launch's duration includes "
+                                  "time it waited for them)",
+                     "families_ms": {eigdc.TIMING_FAMILIES[f]: fam[f][0] for f in fam}})
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        arr, kinds, sizes = serving.trace(args.steps, SERVE_RATE, 64, 4096, (0.5, 0.3, 0.2), seed)
+        v, sample, _ = serve_oracle_estimate(arr, kinds, sizes)
+        cpu = {"kind": "oracle", "value": v, "unit": "solves/s", "cores": os.cpu_count(),
+               "sample": sample}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "serving: Poisson stream at 200 requests/s of mixed "
+                                       "eigenproblems, 50% symmetric / 30% nonsymmetric Schur / "
+                                       "20% generalized Schur of regular pencils, n log-uniform in "
+                                       "[64, 4096], 120 GB HBM admission budget, continuous "
+                                       "batching; one step = one completed request",
+                           "requests": args.steps, "rate_per_s": SERVE_RATE,
+                           "nonsym_coupling": "strict upper N(0, (0.1/sqrt(n))^2): the "
+                                              "reduced-coupling reading of the nonsymmetric "
+                                              "construction (at 1/sqrt(n) the pseudospectra "
+                                              "merge and no split exists above n ~ 1000)",
+                           "precision": {"sym_n_le_1024": res["precision_sym"],
+                                         "sym_n_gt_1024_and_other": res["precision"]},
+                           "workers": args.workers, "mix": res["mix"], "sizes": res["sizes"],
+                           "l2": "not flushed between requests: continuous batching keeps "
+                                 "several requests' matrices (up to 4096^2 x 8 B = 134 MB each, "
+                                 "GBs in flight) resident, far above the 129 MB L2",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "latency_ms": {"p50": res["latency_s"]["p50"] * 1e3,
+                               "p99": res["latency_s"]["p99"] * 1e3},
+                "gflops": res["flops"] / (res["makespan_s"]) / 1e9,
+                "max_backward_error": res["max_backward_error"],
+                "max_eigenvalue_error": res["max_eigenvalue_error"],
+                "by_kind": res["by_kind"], "ok": res["ok"],
+                "peak_reserved_gb": res["peak_reserved_gb"],
+                "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roofline,
+                "e2e": e2e, "cpu_baseline": cpu, "plain_fp64": plain,
+                "requests_detail": res["requests_detail"]}
         print(json.dumps(line), flush=True)
 
 
@@ -573,9 +796,9 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream(dev)
     h = eigdc.Handle(local, stream)
-    if args.workload in ("batched", "svd", "cplane", "sym"):
+    if args.workload in ("batched", "svd", "cplane", "sym", "serve"):
         arm = {"batched": batched_arm, "svd": svd_arm, "cplane": cplane_arm,
-               "sym": sym_arm}[args.workload]
+               "sym": sym_arm, "serve": serve_arm}[args.workload]
         arm(args, torch, eigdc, h, dev, stream, world)
         h.close()
         if world > 1:

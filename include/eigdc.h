@@ -128,8 +128,9 @@ typedef struct {
   int converged;        /* 1 if the R-test fired */
   int k;                /* chosen block size (eig_split) */
   double split_residual;/* ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) at k */
-  int rank;             /* RURV rank: #{|R2_ii| > 1e-8 max|R1_ii|}, R2 of RURV(A_p), R1 of the
-                           RQ step on A_p + B_p (A_p measured against A_p + B_p) */
+  int rank;             /* RURV rank: #{|R2_ii| > 1e-8 max|R1_ii|} (1e-5 in split precision,
+                           above the FP32-level noise of the iterates), R2 of RURV(A_p), R1
+                           of the RQ step on A_p + B_p (A_p measured against A_p + B_p) */
   int draw;             /* Haar draw that was used (0-based) */
 } eig_step_info_t;
 
@@ -172,6 +173,12 @@ unsigned long long eig_kernel_launches(void);
  * launches and return the summed launch durations (ms), the launch count and
  * the summed algorithmic flops 2mnk (the outputs may be NULL). */
 int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, double* flops);
+/* After eig_gemm_timing(0, ...): the totals of one timed kernel family of the
+ * last timed region -- 0 the FP64 DFMA GEMM (work = 2mnk), 1 the FP64-accurate
+ * tensor-core split (work = 53 x 2mnk BF16 MMA flops), 2 the FP32-level
+ * four-digit split (10 x 2mnk), 3 the fused batched solver (work 0).
+ * Returns EIG_ERR_ARG for another family. */
+int eig_kernel_timing(int family, double* total_ms, unsigned long long* launches, double* work);
 /* Device workspace (bytes) the handle needs for calls on size n.  For
  * EIG_KIND_CPLANE: the peak of the stream-ordered allocations of a
  * complex-plane solve with one worker (each further worker adds the scratch

@@ -40,6 +40,7 @@ _MASK = 0xFFFFFFFF
 PURPOSE_HAAR = 4
 PURPOSE_SHIFT = 5
 PURPOSE_HAAR_LEFT = 6
+PURPOSE_POWER = 9        # start vector of the symmetric root's power iteration
 
 
 def attempt_code(attempt, draw):

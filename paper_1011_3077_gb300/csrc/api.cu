@@ -661,7 +661,9 @@ static void right_splitter(eig_handle_t h, SplitWork& w, int n, const double* Ap
      gsplit, w.gpart);
   CK(reverse_transpose(s, n, w.Y, n, w.Z, n));
   qr_explicit(h, w.qr, n, n, w.Z, n, w.Qt, n, w.G, n);   // R~ (diag: R1 reversed) into G
-  CK(count_rank(s, n, w.R2, n, w.G, n, 1e-8, w.rank));
+  // rank threshold above the noise floor of the iterates: FP64 rounding, or
+  // the FP32 level of the split-precision products
+  CK(count_rank(s, n, w.R2, n, w.G, n, split_mode(w.prec) ? 1e-5 : 1e-8, w.rank));
   CK(reverse_columns(s, n, n, w.Qt, n, w.Ucur, n));
 }
 
@@ -864,6 +866,42 @@ static void gershgorin_interval(eig_handle_t h, const double* A, int ld, int m, 
   for (int i = 0; i < m; ++i) {
     lo = std::min(lo, hb[i] - hb[m + i]);
     hi = std::max(hi, hb[i] + hb[m + i]);
+  }
+}
+
+// Root interval of a symmetric matrix: [c - rho, c + rho] cut to Gershgorin,
+// c = tr(A)/n, rho = 1.1 x the estimate of ||A - cI||_2 after POWER_STEPS
+// power-iteration steps from the Philox Gaussian vector of purpose 9 (every
+// eigenvalue lies within ||A - cI||_2 of c; Gershgorin alone overstates that
+// radius by about sqrt(n) for dense matrices, and the line scale of each node
+// is its interval's half-width).  dtmp: 2n + 8 doubles; dx, dy: n each.
+constexpr int PURPOSE_POWER = 9;
+constexpr int POWER_STEPS = 16;
+static void spectral_interval(eig_handle_t h, const double* A, int ld, int n, double* dtmp,
+                              double* dx, double* dy, uint64_t seed, double& lo, double& hi) {
+  cudaStream_t s = h->stream;
+  double glo, ghi;
+  gershgorin_interval(h, A, ld, n, dtmp, glo, ghi);   // leaves diag in the pinned buffer
+  const double* hd = static_cast<const double*>(pinned(h, sizeof(double) * (2 * n + 8)));
+  double tr = 0.0;
+  for (int i = 0; i < n; ++i) tr += hd[i];
+  const double c = tr / n;
+  double* dest = dtmp;
+  CK(gaussian(s, n, 1, seed, PURPOSE_POWER, ROOT_NODE, 0, dy, n));
+  CK(power_norm(s, n, 0.0, nullptr, dy, dx, dest));
+  for (int it = 0; it < POWER_STEPS; ++it) {
+    CK(gemm(s, false, false, n, 1, n, 1.0, A, ld, dx, n, 0.0, dy, n));
+    CK(power_norm(s, n, c, dx, dy, dx, dest));
+  }
+  double* hb = static_cast<double*>(pinned(h, 64));
+  CK(cudaMemcpyAsync(hb, dest, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double rho = 1.1 * hb[0];
+  lo = std::max(glo, c - rho);
+  hi = std::min(ghi, c + rho);
+  if (!(lo < hi)) {
+    lo = glo;
+    hi = ghi;
   }
 }
 
@@ -1510,7 +1548,10 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
     }
   }
   double lo0, hi0;
-  gershgorin_interval(h, w.Acur, n, n, w.dtmp, lo0, hi0);
+  if (sym && n > S.leaf)
+    spectral_interval(h, w.Acur, n, n, w.dtmp, w.wtmp, w.wtmp + n, p.seed, lo0, hi0);
+  else
+    gershgorin_interval(h, w.Acur, n, n, w.dtmp, lo0, hi0);
   CK(cudaStreamSynchronize(s));
   S.queue.push_back(Node{0, n, lo0, hi0, ROOT_NODE, 0});
   S.outstanding = 1;
@@ -1815,6 +1856,12 @@ int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, 
     return EIG_OK;
   }
   return gemm_timing_stop(total_ms, launches, flops) == cudaSuccess ? EIG_OK : EIG_ERR_CUDA;
+}
+
+int eig_kernel_timing(int family, double* total_ms, unsigned long long* launches, double* work) {
+  if (family < 0 || family >= TIMING_FAMILIES) return EIG_ERR_ARG;
+  timing_family(family, total_ms, launches, work);
+  return EIG_OK;
 }
 
 int eig_workspace_size(eig_handle_t h, int n, int kind, size_t* bytes) {

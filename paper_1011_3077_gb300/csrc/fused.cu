@@ -48,6 +48,8 @@ constexpr int GT = 64, GK = 16;  // CTA GEMM tile (64 x 64 outputs, 4 x 4 per th
 constexpr int NBMAX = 32;        // widest panel
 constexpr int PURPOSE_HAAR = 4;
 constexpr int PURPOSE_SHIFT = 5;
+constexpr int PURPOSE_POWER = 9;   // start vector of the root's power iteration
+constexpr int POWER_STEPS = 16;
 constexpr uint64_t ROOT = 1;
 constexpr double UR = 1.1102230246251565e-16;   // 2^-53
 
@@ -730,12 +732,47 @@ __device__ void solve_problem(int n, double* A, int lda, double* wout, double* U
     glo = fmin(glo, a - r);
     ghi = fmax(ghi, a + r);
   }
-  const double lo0 = -cta_max(-glo, S.c), hi0 = cta_max(ghi, S.c);
+  double lo0 = -cta_max(-glo, S.c), hi0 = cta_max(ghi, S.c);
+  const int leaf = max(1, min(JL_MAX, p.leaf));
+  if (n > leaf) {
+    // tighter root interval: [c - rho, c + rho] cut to Gershgorin, c = tr(A)/n,
+    // rho = 1.1 x the power-iteration estimate of ||A - cI||_2 (as eig_solve)
+    double tr = 0.0;
+    for (int i = tid; i < n; i += FT) tr += A[i + (size_t)i * lda];
+    const double c = cta_sum(tr, S.c) / n;
+    double* x = w.wv;
+    double* y = w.scores;
+    cta_gaussian(n, 1, p.seed, PURPOSE_POWER, ROOT, 0, y, n);
+    double ss = 0.0;
+    for (int i = tid; i < n; i += FT) ss = fma(y[i], y[i], ss);
+    double est = sqrt(cta_sum(ss, S.c));
+    for (int i = tid; i < n; i += FT) x[i] = est > 0.0 ? y[i] / est : 0.0;
+    __syncthreads();
+    for (int it = 0; it < POWER_STEPS; ++it) {
+      cta_gemm(false, false, n, 1, n, 1.0, A, lda, x, n, 0.0, y, n, S.u.la.g);
+      ss = 0.0;
+      for (int i = tid; i < n; i += FT) {
+        const double v = y[i] - c * x[i];
+        ss = fma(v, v, ss);
+      }
+      est = sqrt(cta_sum(ss, S.c));
+      for (int i = tid; i < n; i += FT) {
+        const double v = y[i] - c * x[i];
+        x[i] = est > 0.0 ? v / est : 0.0;
+      }
+      __syncthreads();
+    }
+    const double rho = 1.1 * est;
+    const double lo1 = fmax(lo0, c - rho), hi1 = fmin(hi0, c + rho);
+    if (lo1 < hi1) {
+      lo0 = lo1;
+      hi0 = hi1;
+    }
+  }
   int nstack = 0, nleaves = 0;
   if (tid == 0) w.stack[0] = FNode{0, n, 0, 0, lo0, hi0, ROOT};
   nstack = 1;
   __syncthreads();
-  const int leaf = max(1, min(JL_MAX, p.leaf));
   while (nstack > 0) {
     FNode nd = w.stack[nstack - 1];
     __syncthreads();
@@ -913,8 +950,10 @@ cudaError_t fused_batched(cudaStream_t s, int count, const FusedProblem* probs, 
   if (e != cudaSuccess) return e;
   const size_t stride = carve(nullptr, std::max(mx, 1), nullptr);
   note_launches(1);
+  const TimingToken tt = timing_begin(s, TIMING_FUSED, 0.0);
   fused_batched_kernel<<<std::max(1, std::min(ctas, count)), FT, smem, s>>>(
       count, probs, order, results, counter, fp, static_cast<double*>(ws), stride, mx);
+  timing_end(s, tt);
   return cudaGetLastError();
 }
 

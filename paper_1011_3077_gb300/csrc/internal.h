@@ -107,9 +107,21 @@ cudaError_t add_matrices(cudaStream_t s, int rows, int cols, const double* A, in
                          const double* B, int ldb, double* C, int ldc);
 // Z[i][k] = Y[n-1-k][i]   (Z = (J Y)^T)
 cudaError_t reverse_transpose(cudaStream_t s, int n, const double* Y, int ldy, double* Z, int ldz);
-// Opt-in event timing of the FP64 GEMM launches (instrumentation).
+// Opt-in event timing of kernel launches (instrumentation): families of
+// timed kernels; `work` per launch is its algorithmic flops (FP64 2mnk for the
+// GEMMs, BF16 tensor flops 2mnk x digit pairs for the tensor-core splits).
+enum { TIMING_DGEMM = 0, TIMING_TCX64 = 1, TIMING_TCX32 = 2, TIMING_FUSED = 3, TIMING_FAMILIES = 4 };
+struct TimingToken {
+  cudaEvent_t a, b;
+  double work;
+  int family;
+};
+TimingToken timing_begin(cudaStream_t s, int family, double work);
+void timing_end(cudaStream_t s, const TimingToken& t);
 void gemm_timing_start();
+// stops timing; totals of every family are kept, the DFMA GEMM's returned
 cudaError_t gemm_timing_stop(double* total_ms, unsigned long long* launches, double* flops);
+void timing_family(int family, double* total_ms, unsigned long long* launches, double* work);
 // B (cols x rows, ldb) = A^T
 cudaError_t transpose(cudaStream_t s, int rows, int cols, const double* A, int lda, double* B,
                       int ldb);
@@ -123,6 +135,10 @@ cudaError_t gaussian(cudaStream_t s, int rows, int cols, uint64_t seed, int purp
 // column sums of |A| max -> bits in out (atomic max), for ||A||_1
 cudaError_t norm1_bits(cudaStream_t s, int rows, int cols, const double* A, int lda,
                        unsigned long long* out);
+// One power-iteration normalisation (one CTA): v = y - c x (x null: v = y),
+// *est = ||v||_2, xout = v / ||v||_2 (xout may alias x).
+cudaError_t power_norm(cudaStream_t s, int n, double c, const double* x, const double* y,
+                       double* xout, double* est);
 // nonfinite flag (1 if any NaN/Inf) ORed into *flag
 cudaError_t nonfinite_check(cudaStream_t s, int rows, int cols, const double* A, int lda,
                             int* flag);

@@ -196,18 +196,24 @@ int gemm_choose_splits(int m, int n, int k) {
 }
 
 // ------------------------------------------------------------ launch timing
-// Opt-in CUDA-event timing of every dgemm_kernel launch, for the roofline of
-// the dominant kernel measured inside a timed region.  Off by default; when
-// on, each launch records one event before and one after it on its stream.
+// Opt-in CUDA-event timing of every launch of the timed kernel families
+// (dgemm_kernel, the two tensor-core splits, the fused batched solver), for
+// the roofline of the dominant kernel measured inside a timed region.  Off by
+// default; when on, each launch records one event before and one after it on
+// its stream.  Launches being captured into a CUDA graph are not timed (their
+// events would become graph nodes): the timed set is the eager launches.
 namespace {
 struct TimedLaunch {
   cudaEvent_t a, b;
-  double flops;
+  double work;
+  int family;
 };
 std::mutex g_tmu;
 std::atomic<bool> g_timing{false};
 std::vector<TimedLaunch> g_timed;
 std::vector<cudaEvent_t> g_event_pool;
+double g_fam_ms[TIMING_FAMILIES], g_fam_work[TIMING_FAMILIES];
+unsigned long long g_fam_count[TIMING_FAMILIES];
 
 cudaEvent_t take_event() {   // g_tmu held
   if (!g_event_pool.empty()) {
@@ -224,6 +230,26 @@ cudaEvent_t take_event() {   // g_tmu held
 }
 }  // namespace
 
+TimingToken timing_begin(cudaStream_t s, int family, double work) {
+  TimingToken t{nullptr, nullptr, work, family};
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (g_timing.load(std::memory_order_relaxed) &&
+      cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+    std::lock_guard<std::mutex> lock(g_tmu);
+    t.a = take_event();
+    t.b = take_event();
+    if (t.a) cudaEventRecord(t.a, s);
+  }
+  return t;
+}
+
+void timing_end(cudaStream_t s, const TimingToken& t) {
+  if (!t.a || !t.b) return;
+  cudaEventRecord(t.b, s);
+  std::lock_guard<std::mutex> lock(g_tmu);
+  g_timed.push_back(TimedLaunch{t.a, t.b, t.work, t.family});
+}
+
 void gemm_timing_start() {
   std::lock_guard<std::mutex> lock(g_tmu);
   for (TimedLaunch& t : g_timed) {
@@ -237,20 +263,33 @@ void gemm_timing_start() {
 cudaError_t gemm_timing_stop(double* total_ms, unsigned long long* launches, double* flops) {
   g_timing.store(false);
   std::lock_guard<std::mutex> lock(g_tmu);
-  double ms = 0.0, fl = 0.0;
+  for (int f = 0; f < TIMING_FAMILIES; ++f) {
+    g_fam_ms[f] = 0.0;
+    g_fam_work[f] = 0.0;
+    g_fam_count[f] = 0;
+  }
   for (TimedLaunch& t : g_timed) {
     cudaError_t e = cudaEventSynchronize(t.b);
     if (e != cudaSuccess) return e;
     float x = 0.0f;
     e = cudaEventElapsedTime(&x, t.a, t.b);
     if (e != cudaSuccess) return e;
-    ms += x;
-    fl += t.flops;
+    g_fam_ms[t.family] += x;
+    g_fam_work[t.family] += t.work;
+    g_fam_count[t.family] += 1;
   }
-  if (total_ms) *total_ms = ms;
-  if (launches) *launches = g_timed.size();
-  if (flops) *flops = fl;
+  if (total_ms) *total_ms = g_fam_ms[0];
+  if (launches) *launches = g_fam_count[0];
+  if (flops) *flops = g_fam_work[0];
   return cudaSuccess;
+}
+
+void timing_family(int family, double* total_ms, unsigned long long* launches, double* work) {
+  std::lock_guard<std::mutex> lock(g_tmu);
+  const bool ok = family >= 0 && family < TIMING_FAMILIES;
+  if (total_ms) *total_ms = ok ? g_fam_ms[family] : 0.0;
+  if (launches) *launches = ok ? g_fam_count[family] : 0;
+  if (work) *work = ok ? g_fam_work[family] : 0.0;
 }
 
 template <bool TA, bool TB>
@@ -258,17 +297,7 @@ static void launch_dgemm(cudaStream_t s, int m, int n, int k, int splits, int kc
                          const double* A, int lda, const double* B, int ldb, double beta,
                          double* C, int ldc, double* part) {
   note_launches(1);
-  TimedLaunch tl{nullptr, nullptr, 2.0 * m * (double)n * k};
-  // launches being captured into a CUDA graph are not timed (their events
-  // would become graph nodes); the timed set is the eagerly launched ones
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (g_timing.load(std::memory_order_relaxed) &&
-      cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
-    std::lock_guard<std::mutex> lock(g_tmu);
-    tl.a = take_event();
-    tl.b = take_event();
-    if (tl.a) cudaEventRecord(tl.a, s);
-  }
+  const TimingToken tl = timing_begin(s, TIMING_DGEMM, 2.0 * m * (double)n * k);
   if (narrow_tile(m)) {
     dim3 grid((m + 31) / 32, (n + 127) / 128, splits);
     dgemm_kernel<TA, TB, 32, 128><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta,
@@ -278,11 +307,7 @@ static void launch_dgemm(cudaStream_t s, int m, int n, int k, int splits, int kc
     dgemm_kernel<TA, TB, 64, 64><<<grid, GTHREADS, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta,
                                                            C, ldc, kchunk, part);
   }
-  if (tl.a && tl.b) {
-    cudaEventRecord(tl.b, s);
-    std::lock_guard<std::mutex> lock(g_tmu);
-    g_timed.push_back(tl);
-  }
+  timing_end(s, tl);
 }
 
 static int effective_splits(int k, int splits, int& kchunk) {

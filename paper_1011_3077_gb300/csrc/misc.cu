@@ -370,6 +370,45 @@ cudaError_t nonfinite_check(cudaStream_t s, int rows, int cols, const double* A,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- power iteration
+// One CTA: v = y - c x (x may be null: v = y), est = ||v||_2 (fixed-order
+// reduction), xout = v / est (zero when est = 0).  xout may alias x.
+__global__ void __launch_bounds__(1024)
+power_norm_kernel(int n, double c, const double* x, const double* __restrict__ y, double* xout,
+                  double* __restrict__ est) {
+  __shared__ double red[32];
+  __shared__ double tot;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < n; i += 1024) {
+    const double v = x ? y[i] - c * x[i] : y[i];
+    ss = fma(v, v, ss);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 32; ++q) t += red[q];
+    tot = sqrt(t);
+    *est = tot;
+  }
+  __syncthreads();
+  const double nrm = tot;
+  for (int i = threadIdx.x; i < n; i += 1024) {
+    const double v = x ? y[i] - c * x[i] : y[i];
+    xout[i] = nrm > 0.0 ? v / nrm : 0.0;
+  }
+}
+
+cudaError_t power_norm(cudaStream_t s, int n, double c, const double* x, const double* y,
+                       double* xout, double* est) {
+  if (n <= 0) return cudaSuccess;
+  note_launches(1);
+  power_norm_kernel<<<1, 1024, 0, s>>>(n, c, x, y, xout, est);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- split test
 // S[k][j] = sum_{i>=k} |A_ij|, f(k) = max_{j<k} S[k][j] (Sec. 4.2.1), with 32-row
 // blocks: (1) per-block column sums, (2) exclusive suffix over blocks, (3) a

@@ -394,8 +394,12 @@ static cudaError_t tcx_run(cudaStream_t s, bool ta, bool tb, int m, int n, int k
   (void)attr;
   dim3 grid((m + TX_BM - 1) / TX_BM, (n + TX_BN - 1) / TX_BN);
   note_launches(1);
+  constexpr int pairs = (DIG == 9) ? 53 : 10;   // digit pairs of the kept levels
+  const TimingToken tt = timing_begin(s, DIG == 9 ? TIMING_TCX64 : TIMING_TCX32,
+                                      2.0 * pairs * m * (double)n * k);
   tcx_gemm_kernel<DIG><<<grid, TX_THREADS, smem, s>>>(ta_map, tb_map, m, n, kp, alpha, beta, C,
                                                       ldc, ex, ex + m, err);
+  timing_end(s, tt);
   return cudaGetLastError();
 }
 

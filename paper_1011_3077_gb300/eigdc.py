@@ -110,6 +110,8 @@ _SIGNATURES = {
     "eig_kernel_launches": (ctypes.c_ulonglong, []),
     "eig_gemm_timing": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong),
                              ctypes.POINTER(_D)]),
+    "eig_kernel_timing": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_ulonglong),
+                               ctypes.POINTER(_D)]),
     "eig_workspace_size": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "eig_divide_step": (_I, [_P, _I, _P, _I, _P, _I, ctypes.POINTER(Region),
                              ctypes.POINTER(Params), ctypes.POINTER(StepInfo)]),
@@ -274,6 +276,19 @@ def eig_gemm_timing_start():
     rc = lib().eig_gemm_timing(1, None, None, None)
     if rc != EIG_OK:
         raise EigError(rc, "eig_gemm_timing start failed")
+
+
+TIMING_FAMILIES = {0: "dgemm_kernel", 1: "tcx_gemm_kernel<9>", 2: "tcx_gemm_kernel<4>",
+                   3: "fused_batched_kernel"}
+
+
+def eig_kernel_timing(family):
+    """(total ms, launches, work) of a timed kernel family of the last timed region."""
+    ms, cnt, work = ctypes.c_double(), ctypes.c_ulonglong(), ctypes.c_double()
+    rc = lib().eig_kernel_timing(family, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(work))
+    if rc != EIG_OK:
+        raise EigError(rc, "eig_kernel_timing: unknown family")
+    return ms.value, cnt.value, work.value
 
 
 def eig_gemm_timing_stop():

@@ -15,8 +15,10 @@ requests use the triangular construction with strict-upper scale 0.1/sqrt(n)
 (the reduced-coupling reading of the nonsymmetric workload); pencils are
 A = (Q T Q^T) B with that T and B = I + 0.1 G / sqrt(n).  By default every
 request runs in EIG_FP64_TC (FP64 in and out, the large products on the
-tensor cores through the error-free split); pencils run in EIG_FP64_TC or
-EIG_FP64 (the BF16 x 3 form covers the standard problems only).
+tensor cores through the error-free split); symmetric requests can take a
+split-precision form instead (prec_sym: EIG_SPLIT_FP32 or EIG_SPLIT_BF16X3,
+FP32-level products refined to FP64 at the end); nonsymmetric, pencil and
+complex-plane requests run in EIG_FP64_TC or EIG_FP64.
 
 Usage: python -m paper_1011_3077_gb300.serving --rate 200 --count 40
 """
@@ -119,10 +121,11 @@ def backward_error(kind, dA, o):
     return float(max(rA, rB))
 
 
-def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8,
-        budget_gb=120.0, prec=eigdc.EIG_FP64_TC, seed=5, device="cuda", verbose=False,
-        details=False):
-    import torch
+def trace(count, rate=200.0, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), seed=5):
+    """(arrival times in s, kinds, sizes) of a seeded Poisson stream: exponential
+    gaps of mean 1/rate, kinds drawn with the shares `mix` (symmetric,
+    nonsymmetric, pencil and an optional fourth complex-plane share), sizes
+    log-uniform in [nmin, nmax]."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, count)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -130,6 +133,28 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
                         eigdc.EIG_KIND_CPLANE][:len(mix)],
                        size=count, p=np.asarray(mix) / np.sum(mix))
     sizes = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), count))).astype(int)
+    return arrivals, kinds, sizes
+
+
+def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8,
+        budget_gb=120.0, prec=eigdc.EIG_FP64_TC, seed=5, device="cuda", verbose=False,
+        details=False, prec_sym=None, host_io=False, sym_split_max_n=1024):
+    """Serve one seeded trace; returns throughput, latency percentiles and the
+    accuracy of every result.
+
+    prec: arithmetic of the nonsymmetric, pencil and complex-plane requests
+    (EIG_FP64 or EIG_FP64_TC); prec_sym: that of the symmetric requests of
+    order up to sym_split_max_n (default prec; the split-precision forms apply
+    to them: above about n = 1000 the FP32-level iterates no longer separate
+    the closest eigenvalues at the median shift, so larger symmetric requests
+    run in `prec`).  host_io: the
+    inputs start in pinned host memory; each request's input is copied to the
+    device when it arrives and its outputs are read back when it completes,
+    both inside the timed region (the end-to-end form); the byte counts are
+    returned.  The makespan is the CUDA-event time from the first arrival to
+    the last completion, with the device synchronised on both sides."""
+    import torch
+    arrivals, kinds, sizes = trace(count, rate, nmin, nmax, mix, seed)
     reqs = []
     for i in range(count):
         n = int(sizes[i])
@@ -139,78 +164,134 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
         zc = lambda *shape: torch.zeros(shape, dtype=torch.complex128, device=device)
         if kind == eigdc.EIG_KIND_CPLANE:
             out = dict(dw=zc(n), dU=zc(n, n), dT=zc(n, n), A0=dA.clone())
-            reqs.append((kind, n, dA, out, ref))
-            continue
-        out = dict(dwr=z(n), dwi=z(n), dU=z(n, n), A0=dA.clone())
-        if kind == eigdc.EIG_KIND_PENCIL:
-            out.update(dB=dB, dQR=z(n, n), dbe=z(n), B0=dB.clone())
+        else:
+            out = dict(dwr=z(n), dwi=z(n), dU=z(n, n), A0=dA.clone())
+            if kind == eigdc.EIG_KIND_PENCIL:
+                out.update(dB=dB, dQR=z(n, n), dbe=z(n), B0=dB.clone())
+        if host_io:
+            out["hA"] = dA.cpu().pin_memory()
+            if kind == eigdc.EIG_KIND_PENCIL:
+                out["hB"] = dB.cpu().pin_memory()
+            # pinned host destinations of the outputs
+            out["host_out"] = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
+                               for k, v in out.items()
+                               if k in ("dw", "dU", "dT", "dwr", "dwi", "dQR", "dbe") or
+                               (k == "dB" and kind == eigdc.EIG_KIND_PENCIL)}
+            dA.zero_()
+            if kind == eigdc.EIG_KIND_PENCIL:
+                dB.zero_()
         reqs.append((kind, n, dA, out, ref))
     torch.cuda.synchronize()
     srv = eigdc.Server(0, workers, budget_gb)
     params = eigdc.default_params(seed=seed, prec=prec)
-    params64 = eigdc.default_params(
-        seed=seed, prec=prec if prec in (eigdc.EIG_FP64, eigdc.EIG_FP64_TC) else eigdc.EIG_FP64)
+    params_sym = eigdc.default_params(seed=seed, prec=prec if prec_sym is None else prec_sym)
+    copy_stream = torch.cuda.Stream(device=device)
+    h2d = d2h = 0
     tickets = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
     t0 = time.perf_counter()
     for i, (kind, n, dA, o, ref) in enumerate(reqs):
         delay = t0 + arrivals[i] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
+        if host_io:
+            with torch.cuda.stream(copy_stream):
+                dA.copy_(o["hA"], non_blocking=True)
+                h2d += o["hA"].numel() * o["hA"].element_size()
+                if kind == eigdc.EIG_KIND_PENCIL:
+                    o["dB"].copy_(o["hB"], non_blocking=True)
+                    h2d += o["hB"].numel() * o["hB"].element_size()
+            copy_stream.synchronize()
         if kind == eigdc.EIG_KIND_PENCIL:
             tickets.append(srv.submit_pencil(dA, o["dB"], o["dU"], o["dQR"], o["dwr"], o["dwi"],
-                                             o["dbe"], params64))
+                                             o["dbe"], params))
         elif kind == eigdc.EIG_KIND_CPLANE:
-            tickets.append(srv.submit_complex(dA, o["dT"], o["dU"], o["dw"], params64))
+            tickets.append(srv.submit_complex(dA, o["dT"], o["dU"], o["dw"], params))
+        elif kind == eigdc.EIG_KIND_SYM:
+            tickets.append(srv.submit(kind, dA, o["dwr"], o["dwi"], o["dU"],
+                                      params_sym if n <= sym_split_max_n else params))
         else:
             tickets.append(srv.submit(kind, dA, o["dwr"], o["dwi"], o["dU"], params))
-    statuses, lat, wait, service = [], [], [], []
-    for t in tickets:
+    statuses, lat, wait, service, flops = [], [], [], [], 0.0
+    for t, (kind, n, dA, o, ref) in zip(tickets, reqs):
         srv.wait(t, 3600.0)
         st, times, info = srv.poll(t)
         statuses.append(st)
         wait.append(times[0])
         service.append(times[1])
         lat.append(times[2])
-    makespan = time.perf_counter() - t0
+        flops += info.flops
+        if host_io:
+            with torch.cuda.stream(copy_stream):
+                for k, hbuf in o["host_out"].items():
+                    hbuf.copy_(o[k], non_blocking=True)
+                    d2h += hbuf.numel() * hbuf.element_size()
+                if kind in (eigdc.EIG_KIND_NONSYM, eigdc.EIG_KIND_PENCIL):
+                    # the Schur / generalized Schur form is returned in dA
+                    o.setdefault("host_T", torch.empty(dA.shape, dtype=dA.dtype).pin_memory())
+                    o["host_T"].copy_(dA, non_blocking=True)
+                    d2h += dA.numel() * dA.element_size()
+            copy_stream.synchronize()
+    torch.cuda.synchronize()
+    e1.record()
+    e1.synchronize()
+    makespan = e0.elapsed_time(e1) / 1e3
     stats = srv.stats()
     srv.close()
     errs, bwds, records = [], [], []
+    by_kind = {}
     for i, ((kind, n, dA, o, ref), st) in enumerate(zip(reqs, statuses)):
         err = bwd = None
         if st == 0 and kind == eigdc.EIG_KIND_CPLANE:
             # distance of each prescribed eigenvalue to the nearest computed one
             err = float(torch.max(torch.min(torch.abs(ref[:, None] - o["dw"][None, :]), dim=1).values))
-            errs.append(err)
             bwd = backward_error(kind, dA, o)
-            bwds.append(bwd)
         elif st == 0:
             w = o["dwr"] / o["dbe"] if kind == eigdc.EIG_KIND_PENCIL else o["dwr"]
             err = float(torch.max(torch.abs(torch.sort(w).values - ref)))
-            errs.append(err)
             bwd = backward_error(kind, dA, o)
+        if err is not None:
+            errs.append(err)
             bwds.append(bwd)
+            k = by_kind.setdefault(int(kind), {"count": 0, "max_eig_err": 0.0, "max_bwd": 0.0})
+            k["count"] += 1
+            k["max_eig_err"] = max(k["max_eig_err"], err)
+            k["max_bwd"] = max(k["max_bwd"], bwd)
         records.append({"kind": kind, "n": n, "status": st, "wait_s": wait[i],
                         "service_s": service[i], "latency_s": lat[i], "eig_err": err,
                         "backward_err": bwd})
-    ok = sum(1 for s in statuses if s == 0)
+    names = {eigdc.EIG_KIND_SYM: "sym", eigdc.EIG_KIND_NONSYM: "nonsym",
+             eigdc.EIG_KIND_PENCIL: "pencil", eigdc.EIG_KIND_CPLANE: "complex_plane"}
+    pnames = {eigdc.EIG_FP64: "fp64", eigdc.EIG_SPLIT_BF16X3: "bf16x3 split",
+              eigdc.EIG_FP64_TC: "fp64 (tensor-core error-free split)",
+              eigdc.EIG_SPLIT_FP32: "fp32-level split (unbiased four-digit tensor-core products, "
+                                    "FP64 refinement)"}
+    ok = sum(1 for s_ in statuses if s_ == 0)
     out = {
         "requests": count, "ok": ok, "offered_rate_per_s": rate,
-        "solves_per_s": ok / makespan, "makespan_s": makespan,
+        "solves_per_s": ok / makespan, "makespan_s": makespan, "flops": flops,
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "queue_wait_s": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
         "service_s": {"p50": float(np.percentile(service, 50)), "p99": float(np.percentile(service, 99))},
         "sizes": {"min": int(sizes.min()), "max": int(sizes.max())},
         "max_backward_error": max(bwds) if bwds else None,
         "max_eigenvalue_error": max(errs) if errs else None,
+        "by_kind": {names[k]: v for k, v in by_kind.items()},
         "peak_reserved_gb": stats["peak_reserved_gb"], "budget_gb": budget_gb,
         "workers": workers,
-        "precision": {eigdc.EIG_FP64: "fp64", eigdc.EIG_SPLIT_BF16X3: "bf16x3 split",
-                      eigdc.EIG_FP64_TC: "fp64 (tensor-core error-free split)"}[prec],
+        "precision": pnames[prec],
+        "precision_sym": pnames[prec if prec_sym is None else prec_sym],
         "mix": {"sym": int(np.sum(kinds == eigdc.EIG_KIND_SYM)),
                 "nonsym": int(np.sum(kinds == eigdc.EIG_KIND_NONSYM)),
                 "pencil": int(np.sum(kinds == eigdc.EIG_KIND_PENCIL)),
                 "complex_plane": int(np.sum(kinds == eigdc.EIG_KIND_CPLANE))},
     }
+    if host_io:
+        out["h2d_bytes"] = h2d
+        out["d2h_bytes"] = d2h
     if verbose:
         print(json.dumps(out))
     if details:
@@ -227,6 +308,7 @@ def main():
     ap.add_argument("--workers", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--prec", type=int, default=2)
+    ap.add_argument("--prec-sym", type=int, default=None)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--mix", default="0.5,0.3,0.2",
                     help="shares of symmetric, nonsymmetric, pencil and (optional fourth) "
@@ -236,7 +318,7 @@ def main():
     build.build()
     mix = tuple(float(x) for x in a.mix.split(","))
     run(a.rate, a.count, a.nmin, a.nmax, mix=mix, workers=a.workers, budget_gb=a.budget_gb,
-        prec=a.prec, seed=a.seed, verbose=True)
+        prec=a.prec, seed=a.seed, verbose=True, prec_sym=a.prec_sym)
 
 
 if __name__ == "__main__":
