@@ -13,7 +13,9 @@ similarity, split test, recursion, leaves, assembly).  Symmetric requests run
 in the unbiased FP32-level split form with FP64 refinement, the others in the
 FP64-accurate tensor-core form; `plain_fp64` serves the same trace with every
 contraction on the FP64 pipe.  Other workloads (--workload): schur, sym,
-batched (one persistent fused launch per batch), svd, cplane.
+batched (one persistent fused launch per batch), svd, cplane, step (one
+divide step at the root of the symmetric semicircle matrix), gemm (isolated
+products of each contraction form).
 
 Output: one JSON line (rank 0).  `value` is completed requests per second over
 all ranks with the inputs resident in HBM; `e2e` serves the same trace with
@@ -72,7 +74,7 @@ def parse():
                     help="serve: precision of the symmetric requests (3: unbiased FP32-level "
                          "split with FP64 refinement)")
     ap.add_argument("--workload", default="serve",
-                    choices=["serve", "schur", "batched", "svd", "cplane", "sym"],
+                    choices=["serve", "schur", "batched", "svd", "cplane", "sym", "step", "gemm"],
                     help="serve: the mixed request stream (default, one step = one completed "
                          "request); schur: one nonsymmetric n x n solve per step; batched: "
                          "--count independent symmetric problems, n log-uniform in [32, 512], "
@@ -82,6 +84,8 @@ def parse():
                          "(eig_schur_complex); sym: the full eigendecomposition of one "
                          "symmetric n x n matrix with a semicircle spectrum per step")
     ap.add_argument("--count", type=int, default=2000)
+    ap.add_argument("--nmin", type=int, default=32, help="batched: smallest problem")
+    ap.add_argument("--nmax", type=int, default=512, help="batched: largest problem")
     ap.add_argument("--fused", type=int, default=1, choices=[0, 1],
                     help="batched workload: 1 = one persistent fused launch per step "
                          "(eig_solve_batched_fused, launch shape from eig_fused_autotune); "
@@ -284,7 +288,8 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
     the handle's stream around it bracket the whole batch."""
     from paper_1011_3077_gb300 import serving
     rng = np.random.default_rng(0xE16D0004 + int(os.environ.get("RANK", "0")))
-    sizes = np.rint(np.exp(rng.uniform(np.log(32), np.log(512), args.count))).astype(int)
+    sizes = np.rint(np.exp(rng.uniform(np.log(args.nmin), np.log(args.nmax),
+                                       args.count))).astype(int)
     A0, refs = [], []
     for i, n in enumerate(sizes):
         dA, _, ref = serving.synthesize(eigdc.EIG_KIND_SYM, int(n), 7919 * i + 11, dev)
@@ -354,8 +359,8 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batched symmetric eigendecompositions, %d independent "
-                                   "problems, n log-uniform in [32, 512], lambda ~ U[-1, 1]"
-                                   % args.count,
+                                   "problems, n log-uniform in [%d, %d], lambda ~ U[-1, 1]"
+                                   % (args.count, args.nmin, args.nmax),
                        "count": args.count, "n_min": int(sizes.min()), "n_max": int(sizes.max()),
                        "sum_n2": int(np.sum(sizes.astype(np.int64) ** 2)),
                        "workers": args.workers,
@@ -600,6 +605,125 @@ def sym_arm(args, torch, eigdc, h, dev, stream, world):
         print(json.dumps(line), flush=True)
 
 
+def gemm_arm(args, torch, eigdc, h, dev, stream, world):
+    """Isolated n x n x n products (A^T B) of each contraction form: the FP64
+    DFMA kernel, the FP64-accurate nine-digit tensor-core split, the five- and
+    four-digit split tiers (through eig_gemm_fp32tc for four digits) and BF16 x 3;
+    CUDA-event time per call with the operand splits included."""
+    n = args.n
+    X = torch.randn((n, n), dtype=torch.float64, device=dev)
+    Y = torch.randn((n, n), dtype=torch.float64, device=dev)
+    Z = torch.empty((n, n), dtype=torch.float64, device=dev)
+    forms = [("fp64 dfma", eigdc.eig_gemm, 1), ("fp64 tensor-core split (9 digits)",
+                                                 eigdc.eig_gemm_fp64tc, 53),
+             ("fp32-level tensor-core split (4 digits)", eigdc.eig_gemm_fp32tc, 10),
+             ("bf16x3", eigdc.eig_gemm_split, 6)]
+    out = {}
+    for name, f, products in forms:
+        for _ in range(max(args.warmup, 1)):
+            f(h, 1, 0, n, n, n, 1.0, X, n, Y, n, 0.0, Z, n)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            f(h, 1, 0, n, n, n, 1.0, X, n, Y, n, 0.0, Z, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms": ms, "tflops_equivalent": 2.0 * n ** 3 / ms / 1e9,
+                     "tensor_tflops": products * 2.0 * n ** 3 / ms / 1e9 if products > 1 else None}
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps({"metric": "contraction rate", "unit": "TFLOP/s", "n": n,
+                          "shape": "A^T B, %d^3" % n, "forms": out}), flush=True)
+
+
+def step_arm(args, torch, eigdc, h, dev, stream, world):
+    """One spectral divide step per step at the root of the symmetric
+    semicircle matrix (the full-recursion workload's first node): IRS on the
+    line Re z = sigma (sigma the median of the diagonal, scale 1.1 max|lambda|)
+    until the R-test, then the GRURV splitter, the similarity and the split
+    test (eig_divide_step + eig_split).  Reports the model flops of the step
+    (7.33 p + 16) n^3 against the FP64 rate, and the live timing of the
+    dominant kernel family."""
+    from paper_1011_3077_gb300 import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    n = args.n
+    A, lam = workloads.symmetric_semicircle(n, seed=3 + rank)
+    sigma = float(np.median(np.diag(A)))
+    scale = 1.1 * float(np.max(np.abs(lam)))
+    dA0 = eigdc.to_device(A, dev)
+    # the pencil of the line: (A - (sigma - s) I, A - (sigma + s) I), solved on
+    # the unit circle (the Moebius map of Sec. 3.3)
+    eye = torch.eye(n, dtype=torch.float64, device=dev)
+    dAm0 = dA0 - (sigma - scale) * eye
+    dBm0 = dA0 - (sigma + scale) * eye
+    del eye
+    dAp, dBp = torch.empty_like(dA0), torch.empty_like(dA0)
+    dAh = torch.empty_like(dA0)
+    dQ = torch.empty_like(dA0)
+    reg = eigdc.Region(eigdc.EIG_REGION_UNIT_CIRCLE, 0.0, 1.0)
+    params = eigdc.default_params(seed=0, prec=args.prec, graphs=args.graphs)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        dAp.copy_(dAm0)
+        dBp.copy_(dBm0)
+        rc, si = eigdc.eig_divide_step(h, n, dAp, n, dBp, n, reg, params)
+        if rc != eigdc.EIG_OK:
+            raise RuntimeError("eig_divide_step failed: %d %s" % (rc, h.last_error()))
+        dAh.copy_(dA0)
+        rc, sp = eigdc.eig_split(h, n, dAp, dBp, n, dAh, n, dQ, n, 1, 1, 0, params)
+        if rc not in (eigdc.EIG_OK, eigdc.EIG_NO_SPLIT):
+            raise RuntimeError("eig_split failed: %d %s" % (rc, h.last_error()))
+        return si, sp
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    ms, res = [], []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        eigdc.eig_gemm_timing_start()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res.append(step())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        eigdc.eig_gemm_timing_stop()
+    fam = {f: eigdc.eig_kernel_timing(f) for f in eigdc.TIMING_FAMILIES}
+    total_ms = max_over_ranks(sum(ms), dev, world)
+    si, sp = res[-1]
+    model = ((22.0 / 3.0) * si.iters + 16.0 * (sp.draw + 1)) * float(n) ** 3
+    bf16, burst, src = fp64_peak_tflops()
+    fp64_peak = bf16 * 1.25 / 2250.0
+    achieved = model / (total_ms / args.steps / 1e3) / 1e12
+    line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
+            "unit": "divide steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "one spectral divide step at the root of the symmetric "
+                                   "semicircle matrix, n=%d (IRS to the R-test, GRURV, "
+                                   "similarity, split test)" % n,
+                       "n": n, "precision": {0: "fp64", 1: "bf16x3 split",
+                                             2: "fp64 (tensor-core error-free split)",
+                                             3: "fp32-level split"}[args.prec],
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "squarings": si.iters, "k": sp.k, "rank": sp.rank,
+            "split_residual": sp.split_residual,
+            "model_flops": model, "model_tflops": achieved,
+            "model_frac_of_fp64_peak": achieved / fp64_peak,
+            "fp64_peak_note": "measured sustained bf16 %.1f TF/s x nominal FP64/BF16 ratio "
+                              "1.25/2250 (%s)" % (bf16, src),
+            "families": {eigdc.TIMING_FAMILIES[f]: {"ms": fam[f][0], "launches": fam[f][1],
+                                                    "work": fam[f][2]} for f in fam},
+            "clocks": clk.summary(), "roofline": None, "e2e": None, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------- serving workload
 SERVE_RATE = 200.0
 SERVE_SAMPLE_N = 256   # oracle sample size per request kind (same constructions)
@@ -703,7 +827,8 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
                  "max_eigenvalue_error": r3["max_eigenvalue_error"],
                  "gflops": r3["flops"] / (ms3 / 1e3) / 1e9,
                  "speedup_of_value": value / p_val if p_val else None,
-                 "trees": [{"n": d["n"], "kind": d["kind"], "status": d["status"]}
+                 "trees": [{k: d[k] for k in ("n", "kind", "status", "splits", "nodes",
+                                              "failed_attempts", "squarings", "service_s")}
                            for d in r3["requests_detail"]]}
     # roofline of the kernel family that held the most launch time
     bf16, bf16_burst, src = fp64_peak_tflops()
@@ -796,9 +921,9 @@ def main():
         dist.barrier()
     stream = torch.cuda.current_stream(dev)
     h = eigdc.Handle(local, stream)
-    if args.workload in ("batched", "svd", "cplane", "sym", "serve"):
-        arm = {"batched": batched_arm, "svd": svd_arm, "cplane": cplane_arm,
-               "sym": sym_arm, "serve": serve_arm}[args.workload]
+    if args.workload in ("batched", "svd", "cplane", "sym", "serve", "step", "gemm"):
+        arm = {"batched": batched_arm, "svd": svd_arm, "cplane": cplane_arm, "sym": sym_arm,
+               "serve": serve_arm, "step": step_arm, "gemm": gemm_arm}[args.workload]
         arm(args, torch, eigdc, h, dev, stream, world)
         h.close()
         if world > 1:

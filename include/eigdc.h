@@ -106,7 +106,8 @@ typedef struct {
                         <= 0: max(1e-12, 16 n 2^-53) for a node of size n (the FP64 rounding
                         floor of that ratio grows like n u), pencils max(1e-10, 16 n 2^-53)
                         (two independently computed subspaces; the finished solve's backward
-                        error stays 10-50x below the score); split precision: >= 1e-3 */
+                        error stays 10-50x below the score); BF16 x 3: >= 1e-3;
+                        EIG_SPLIT_FP32: >= 1e-6 at the RURV rank */
   int leaf_size;     /* nodes of at most this size go to the leaf solver (<= 64) */
   int prec;          /* EIG_FP64 or EIG_SPLIT_BF16X3 */
   uint64_t seed;     /* Philox key of every draw of the method */

@@ -191,11 +191,30 @@ struct QRBufs {
   int prec = EIG_FP64;     // arithmetic of the reflector products
   void* tcw = nullptr;     // BF16 planes (split precision)
   int* tcerr = nullptr;    // device flag of the tensor-core kernel
+  // two-level form (tensor-core modes): outer blocks of NB2 columns whose
+  // aggregated reflector updates the trailing matrix in one tensor-core
+  // product pair; TB holds each outer block's NB2 x NB2 T (ld NB2), WB / WB2
+  // its NB2 x cols products; cap2 = columns the buffers were carved for
+  double* TB = nullptr;
+  double* WB = nullptr;
+  double* WB2 = nullptr;
+  int cap2 = 0;
+  bool two_level = false;   // set by geqrf: the last factorisation used it
 };
 
+constexpr int NB2 = 256;   // outer block width of the two-level QR
+
+// Internal tier of EIG_SPLIT_FP32 (never passed in by a caller): the
+// error-free split with five digits (30 bits), taken by a node whose attempt
+// found a true split (0 < rank < n) that the four-digit products could not
+// resolve below the split tolerance; the next tier is EIG_FP64_TC.
+constexpr int PREC_SPLIT30 = 13;
+
 // split precision: FP32-level products on the tensor cores, FP64 panels,
-// tests and refinement (BF16 x 3, or the unbiased four-digit split)
-static bool split_mode(int prec) { return prec == EIG_SPLIT_BF16X3 || prec == EIG_SPLIT_FP32; }
+// tests and refinement (BF16 x 3, or the unbiased four- / five-digit split)
+static bool split_mode(int prec) {
+  return prec == EIG_SPLIT_BF16X3 || prec == EIG_SPLIT_FP32 || prec == PREC_SPLIT30;
+}
 // contractions on the tensor cores: the split-precision forms or the FP64-accurate split
 static bool tc_path(int prec) { return split_mode(prec) || prec == EIG_FP64_TC; }
 static bool valid_prec(int prec) {
@@ -203,9 +222,15 @@ static bool valid_prec(int prec) {
          prec == EIG_SPLIT_FP32;
 }
 
+// Plane workspace of a product in `prec`; EIG_SPLIT_FP32 reserves the largest
+// of its tiers (four, five and nine digits).
 static size_t tc_ws_bytes(int prec, int m, int n, int k) {
   if (prec == EIG_SPLIT_BF16X3) return tc_gemm_workspace_bytes(m, n, k);
-  if (prec == EIG_SPLIT_FP32) return tcx32_gemm_workspace_bytes(m, n, k);
+  if (prec == EIG_SPLIT_FP32)
+    return std::max(std::max(tcx32_gemm_workspace_bytes(m, n, k),
+                             tcx30_gemm_workspace_bytes(m, n, k)),
+                    tcx_gemm_workspace_bytes(m, n, k));
+  if (prec == PREC_SPLIT30) return tcx30_gemm_workspace_bytes(m, n, k);
   if (prec == EIG_FP64_TC) return tcx_gemm_workspace_bytes(m, n, k);
   return 0;
 }
@@ -216,6 +241,8 @@ static cudaError_t split_gemm(cudaStream_t s, int prec, bool ta, bool tb, int m,
                               double beta, double* C, int ldc, void* ws, int* err) {
   if (prec == EIG_SPLIT_FP32)
     return tcx32_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
+  if (prec == PREC_SPLIT30)
+    return tcx30_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
   return tc_gemm(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
 }
 
@@ -248,12 +275,88 @@ static size_t tcw_qr_bytes(int prec, int m, int n) {
   return std::max(tc_ws_bytes(prec, n, JB_LD_C, m), tc_ws_bytes(prec, m, n, JB_LD_C));
 }
 
+// The two-level QR runs in the modes whose tensor-core product is the
+// error-free digit split (FP64-accurate or the split-precision tiers), on
+// factorisations tall and wide enough for NB2-wide outer updates to fill it.
+static bool tcx_family(int prec) {
+  return prec == EIG_FP64_TC || prec == EIG_SPLIT_FP32 || prec == PREC_SPLIT30;
+}
+static bool two_level_fits(int m, int n) { return m >= 512 && n >= 2 * NB2; }
+// plane scratch of the outer products (NB2 x n x m and m x n x NB2, T products)
+static size_t tcw_qr2_bytes(int prec, int m, int n) {
+  if (!tcx_family(prec) || !two_level_fits(m, n)) return 0;
+  return std::max(std::max(tc_ws_bytes(prec, NB2, n, m), tc_ws_bytes(prec, m, n, NB2)),
+                  tc_ws_bytes(prec, NB2, n, NB2));
+}
+
 constexpr int JB_LD = 32;
 
 // split-K partials of the jb x cols reflector products (at most 32 K-chunks)
 static size_t qr_part_doubles(int m, int cols) { return (size_t)33 * JB_LD * std::max(cols, 1) + 0 * m; }
 
-// Blocked right-looking Householder QR of the m x n matrix in q.W.
+// Product of an outer block reflector (two-level QR) in the mode's
+// tensor-core arithmetic: the split tiers, or the FP64-accurate split where it
+// pays (tcx_worth), else the FP64 DFMA kernel.
+static void outer_mm(eig_handle_t h, const QRBufs& q, bool ta, bool tb, int m, int n, int k,
+                     double alpha, const double* A, int lda, const double* B, int ldb,
+                     double beta, double* C, int ldc) {
+  if (split_mode(q.prec))
+    CK(split_gemm(h->stream, q.prec, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, q.tcw,
+                  q.tcerr));
+  else if (tcx_worth(m, n, k))
+    CK(tcx_gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, q.tcw, q.tcerr));
+  else
+    CK(gemm(h->stream, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc));
+}
+
+// C <- (I - V T V^T)^T C for the reflectors of one panel (rows j0.., jb
+// columns) on the nc columns of C (mb rows, ldw).
+static void panel_update(eig_handle_t h, QRBufs& q, int j0, int jb, int mb, double* C, int nc) {
+  cudaStream_t s = h->stream;
+  double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
+  if (split_mode(q.prec)) {
+    // (V^T C)^T = C^T V on the tensor cores (M = nc rows, N = jb)
+    CK(split_gemm(s, q.prec, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part,
+                  nc, q.tcw, q.tcerr));
+    CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk, true));
+    CK(split_gemm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C,
+                  q.ldw, q.tcw, q.tcerr));
+  } else {
+    int sp = gemm_choose_splits(jb, nc, mb);
+    sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
+    if (sp < 0) CK(cudaGetLastError());
+    CK(reduce_trmm(s, jb, nc, q.part, sp, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk));
+    CK(gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw));
+  }
+}
+
+// T of the outer block J0..J0+JB (aggregated from its panels' T factors by
+// T_{1:c+jb} = [[T_{1:c}, -T_{1:c} (V_{1:c}^T V_b) T_b], [0, T_b]]) into TB.
+static void outer_T(eig_handle_t h, QRBufs& q, int m, int J0, int JB, int jbmax) {
+  cudaStream_t s = h->stream;
+  double* TBb = q.TB + (size_t)(J0 / NB2) * NB2 * NB2;
+  CK(cudaMemsetAsync(TBb, 0, sizeof(double) * NB2 * NB2, s));
+  const int mb = m - J0;
+  const double* Vo = q.V + J0 + (size_t)J0 * q.ldv;
+  for (int c0 = 0; c0 < JB; c0 += jbmax) {
+    const int jb = std::min(jbmax, JB - c0);
+    const double* Tin = q.T + (size_t)(J0 + c0) * q.ldt;
+    CK(copy_matrix(s, jb, jb, Tin, q.ldt, TBb + c0 + (size_t)c0 * NB2, NB2));
+    if (c0 == 0) continue;
+    // G = V_{1:c}^T V_b (c0 x jb, deterministic split-K over the mb rows)
+    CK(gemm(s, true, false, c0, jb, mb, 1.0, Vo, q.ldv, Vo + (size_t)c0 * q.ldv, q.ldv, 0.0, q.WB,
+            NB2, gemm_choose_splits(c0, jb, mb), q.part));
+    CK(gemm(s, false, false, c0, jb, c0, 1.0, TBb, NB2, q.WB, NB2, 0.0, q.WB2, NB2));
+    CK(gemm(s, false, false, c0, jb, jb, -1.0, q.WB2, NB2, Tin, q.ldt, 0.0,
+            TBb + (size_t)c0 * NB2, NB2));
+  }
+}
+
+// Blocked right-looking Householder QR of the m x n matrix in q.W.  In the
+// tensor-core modes (two_level_fits), panels of jbmax columns update only
+// their NB2-column outer block on the FP64 pipe, and each outer block's
+// aggregated reflector then updates the trailing matrix in one tensor-core
+// product pair (the rank-NB2 compact-WY update).
 static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
   cudaStream_t s = h->stream;
   NvtxRange nvtx_("eig.qr");
@@ -262,28 +365,33 @@ static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
     h->err = "matrix too tall for the on-chip panel factorisation";
     throw Fail{EIG_ERR_ARG};
   }
-  for (int j0 = 0; j0 < n; j0 += jbmax) {
-    const int jb = std::min(jbmax, n - j0);
-    double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
-    CK(panel_qr(s, m - j0, jb, q.W + j0 + (size_t)j0 * q.ldw, q.ldw, Vb, q.ldv, q.tau + j0,
-                q.T + (size_t)j0 * q.ldt, q.ldt));
-    const int nc = n - j0 - jb;
-    if (nc > 0) {
-      const int mb = m - j0;
-      double* C = q.W + j0 + (size_t)(j0 + jb) * q.ldw;
-      if (split_mode(q.prec)) {
-        // (V^T C)^T = C^T V on the tensor cores (M = nc rows, N = jb)
-        CK(split_gemm(s, q.prec, true, false, nc, jb, mb, 1.0, C, q.ldw, Vb, q.ldv, 0.0, q.part,
-                      nc, q.tcw, q.tcerr));
-        CK(reduce_trmm(s, jb, nc, q.part, 1, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk, true));
-        CK(split_gemm(s, q.prec, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C,
-                      q.ldw, q.tcw, q.tcerr));
-      } else {
-        int sp = gemm_choose_splits(jb, nc, mb);
-        sp = gemm_partials(s, true, jb, nc, mb, Vb, q.ldv, C, q.ldw, sp, q.part);
-        if (sp < 0) CK(cudaGetLastError());
-        CK(reduce_trmm(s, jb, nc, q.part, sp, q.T + (size_t)j0 * q.ldt, q.ldt, true, q.Wk));
-        CK(gemm(s, false, false, mb, nc, jb, -1.0, Vb, q.ldv, q.Wk, jb, 1.0, C, q.ldw));
+  q.two_level = q.TB != nullptr && tcx_family(q.prec) && two_level_fits(m, n) && n <= q.cap2 &&
+                NB2 % jbmax == 0;
+  const int outer = q.two_level ? NB2 : n;
+  for (int J0 = 0; J0 < n; J0 += outer) {
+    const int JB = std::min(outer, n - J0);
+    const int jend = J0 + JB;
+    if (q.two_level)   // rows J0.. of the block's reflectors above each panel are zero
+      CK(cudaMemset2DAsync(q.V + J0 + (size_t)J0 * q.ldv, sizeof(double) * q.ldv, 0,
+                           sizeof(double) * JB, JB, s));
+    for (int j0 = J0; j0 < jend; j0 += jbmax) {
+      const int jb = std::min(jbmax, jend - j0);
+      double* Vb = q.V + j0 + (size_t)j0 * q.ldv;
+      CK(panel_qr(s, m - j0, jb, q.W + j0 + (size_t)j0 * q.ldw, q.ldw, Vb, q.ldv, q.tau + j0,
+                  q.T + (size_t)j0 * q.ldt, q.ldt));
+      const int nc = jend - j0 - jb;
+      if (nc > 0) panel_update(h, q, j0, jb, m - j0, q.W + j0 + (size_t)(j0 + jb) * q.ldw, nc);
+    }
+    if (q.two_level) {
+      outer_T(h, q, m, J0, JB, jbmax);
+      const int NC = n - jend, mb = m - J0;
+      if (NC > 0) {
+        const double* Vo = q.V + J0 + (size_t)J0 * q.ldv;
+        const double* TBb = q.TB + (size_t)(J0 / NB2) * NB2 * NB2;
+        double* C = q.W + J0 + (size_t)jend * q.ldw;
+        outer_mm(h, q, true, false, JB, NC, mb, 1.0, Vo, q.ldv, C, q.ldw, 0.0, q.WB, NB2);
+        outer_mm(h, q, true, false, JB, NC, JB, 1.0, TBb, NB2, q.WB, NB2, 0.0, q.WB2, NB2);
+        outer_mm(h, q, false, false, mb, NC, JB, -1.0, Vo, q.ldv, q.WB2, NB2, 1.0, C, q.ldw);
       }
     }
   }
@@ -292,10 +400,30 @@ static int geqrf(eig_handle_t h, int m, int n, QRBufs& q) {
 
 // Y <- Q Y for the reflectors of an m x nref factorisation (applied last
 // block first).  skip_identity: Y started as [I; 0], so columns left of a
-// block's first row are still unit vectors it does not touch.
+// block's first row are still unit vectors it does not touch.  After a
+// two-level factorisation the outer blocks' aggregated reflectors are applied
+// with tensor-core products.
 static void apply_q(eig_handle_t h, int m, int nref, int jbmax, QRBufs& q, double* Y, int ldy,
                     int ncols, bool skip_identity) {
   cudaStream_t s = h->stream;
+  if (q.two_level) {
+    const int nout = (nref + NB2 - 1) / NB2;
+    for (int b = nout - 1; b >= 0; --b) {
+      const int J0 = b * NB2;
+      const int JB = std::min(NB2, nref - J0);
+      const int mb = m - J0;
+      const int c0 = skip_identity ? J0 : 0;
+      const int nc = ncols - c0;
+      if (nc <= 0) continue;
+      double* Yb = Y + J0 + (size_t)c0 * ldy;
+      const double* Vo = q.V + J0 + (size_t)J0 * q.ldv;
+      const double* TBb = q.TB + (size_t)b * NB2 * NB2;
+      outer_mm(h, q, true, false, JB, nc, mb, 1.0, Vo, q.ldv, Yb, ldy, 0.0, q.WB, NB2);
+      outer_mm(h, q, false, false, JB, nc, JB, 1.0, TBb, NB2, q.WB, NB2, 0.0, q.WB2, NB2);
+      outer_mm(h, q, false, false, mb, nc, JB, -1.0, Vo, q.ldv, q.WB2, NB2, 1.0, Yb, ldy);
+    }
+    return;
+  }
   const int nblocks = (nref + jbmax - 1) / jbmax;
   for (int b = nblocks - 1; b >= 0; --b) {
     const int j0 = b * jbmax;
@@ -326,8 +454,15 @@ struct QRWork {
   QRBufs q;
 };
 
-static size_t carve_qr(Arena& a, int m, int n, QRWork& w, int prec = EIG_FP64) {
+static size_t carve_qr(Arena& a, int m, int n, QRWork& w, int prec = EIG_FP64,
+                       int outer_prec = EIG_FP64) {
   const size_t start = a.used;
+  if (tcx_family(outer_prec) && two_level_fits(m, n)) {
+    w.q.TB = a.take<double>((size_t)((n + NB2 - 1) / NB2) * NB2 * NB2);
+    w.q.WB = a.take<double>((size_t)NB2 * n);
+    w.q.WB2 = a.take<double>((size_t)NB2 * n);
+    w.q.cap2 = n;
+  }
   w.q.W = a.take<double>((size_t)m * n);
   w.q.ldw = m;
   w.q.V = a.take<double>((size_t)m * n);
@@ -382,10 +517,12 @@ static size_t carve_irs(Arena& a, int n, IRSWork& w, int prec = EIG_FP64) {
   w.prec = prec;
   // one plane buffer serves the QR's reflector products and the complement
   // products (they run one after the other on the stream)
-  w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(tc_ws_bytes(prec, n, n, n),
-                                                       split_mode(prec) ? tcw_qr_bytes(prec, 2 * n, n) : 0))
-                           : nullptr;
-  carve_qr(a, 2 * n, n, w.qr, EIG_FP64);
+  w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(
+                              std::max(tc_ws_bytes(prec, n, n, n),
+                                       split_mode(prec) ? tcw_qr_bytes(prec, 2 * n, n) : 0),
+                              tcw_qr2_bytes(prec, 2 * n, n)))
+                        : nullptr;
+  carve_qr(a, 2 * n, n, w.qr, EIG_FP64, prec);
   w.qr.q.prec = prec;
   w.qr.q.tcw = w.tcw;
   return a.used - start;
@@ -582,10 +719,12 @@ static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64,
   w.nbits = a.take<unsigned long long>(4);
   w.rank = a.take<int>(4);
   w.prec = prec;
-  w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(tc_ws_bytes(prec, n, n, n),
-                                                       split_mode(prec) ? tcw_qr_bytes(prec, n, n) : 0))
-                           : nullptr;
-  carve_qr(a, n, n, w.qr, EIG_FP64);
+  w.tcw = tc_path(prec) ? (void*)a.take<char>(std::max(
+                              std::max(tc_ws_bytes(prec, n, n, n),
+                                       split_mode(prec) ? tcw_qr_bytes(prec, n, n) : 0),
+                              tcw_qr2_bytes(prec, n, n)))
+                        : nullptr;
+  carve_qr(a, n, n, w.qr, EIG_FP64, prec);
   w.qr.q.prec = prec;
   w.qr.q.tcw = w.tcw;
   return a.used - start;
@@ -601,7 +740,13 @@ static size_t carve_split(Arena& a, int n, SplitWork& w, int prec = EIG_FP64,
 static double effective_split_tol(const eig_params_t& p, int n, bool pencil = false) {
   double t = p.split_tol > 0 ? p.split_tol
                              : std::max(pencil ? 1e-10 : 1e-12, 16.0 * n * 0x1p-53);
-  if (split_mode(p.prec)) t = std::max(t, 1e-3);
+  // split precision: FP32-level iterates.  BF16 x 3 accepts up to 1e-3;
+  // EIG_SPLIT_FP32 holds its tiers to 1e-6, the coupling the closing FP64
+  // refinement resolves pair by pair (measured: splits accepted at 1e-3 left
+  // eigenvalue errors of 4e-5 after the refinement at n = 8192, where
+  // neighbouring eigenvalues are 2e-4 apart)
+  if (p.prec == EIG_SPLIT_BF16X3) t = std::max(t, 1e-3);
+  else if (split_mode(p.prec)) t = std::max(t, 1e-6);
   return t;
 }
 
@@ -747,6 +892,14 @@ static SplitOut run_split(eig_handle_t h, SplitWork& w, int n, const double* Ap,
     out.rank = rank;
     out.draw = draw;
     pick_k(out, hscores, n);
+    if (split_mode(p.prec) && rank > 0 && rank < n) {
+      // FP32-level scores sit near the split tolerance, where the argmin can
+      // fall on a block size far from the eigenvalue count (measured: k =
+      // n - 1 at e = 8.6e-4 for rank 2690 of 4096); the rank-revealed size
+      // is the split, and its score is the test
+      out.k = rank;
+      out.e = hscores[rank - 1];
+    }
     out.accepted = irs_converged && out.k > 0 && out.k < n && out.e <= effective_split_tol(p, n);
     if (out.accepted || !irs_converged || rank == 0 || rank == n) break;
   }
@@ -1165,7 +1318,13 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   int attempt = 0, fails = 0;
   double flops = 0.0;
   int iters = 0, failed = 0;
+  // precision tier of this node's attempts: EIG_SPLIT_FP32 starts with
+  // four-digit products and escalates (five digits, then the FP64-accurate
+  // split) when an attempt finds a true split it cannot resolve
+  int tier = p.prec;
   while (true) {
+    w.irs.prec = w.irs.qr.q.prec = tier;
+    w.split.prec = w.split.qr.q.prec = tier;
     eig_region_t rg;
     if (!S.sym && p.root_unit_circle && nd.id == ROOT_NODE && attempt == 0) {
       rg.kind = EIG_REGION_UNIT_CIRCLE;
@@ -1179,12 +1338,14 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
       rg.c_or_sigma = sigma;
       rg.r_or_s = sc;
     }
-    const double tau_m = tau > 0 ? tau : (split_mode(p.prec) ? 1e-5 : default_tau(m));
-    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(p.prec),
+    const double tau_m = tau > 0 ? tau : (split_mode(tier) ? 1e-5 : default_tau(m));
+    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(tier),
                         p.graphs != 0);
     iters += ir.iters;
     flops += ir.iters * flops_irs_iter(m);
-    SplitOut so = run_split(hw, w.split, m, ir.Ap, ir.Bp, m, An, n, S.sym, nd.id, attempt, S.pp,
+    eig_params_t pt = S.pp;
+    pt.prec = tier;
+    SplitOut so = run_split(hw, w.split, m, ir.Ap, ir.Bp, m, An, n, S.sym, nd.id, attempt, pt,
                             ir.converged, hscores);
     flops += (so.draw + 1) * (flops_grurv(m) + flops_similarity(m));
     if (S.verbose)
@@ -1243,6 +1404,15 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
       return;
     }
     failed++;
+    if (p.prec == EIG_SPLIT_FP32 && tier != EIG_FP64_TC && ir.converged && so.rank > 0 &&
+        so.rank < m) {
+      // a split exists but the tier's products left ||E21|| above the
+      // tolerance: the same attempt (shift and draws) one tier up
+      tier = (tier == EIG_SPLIT_FP32) ? PREC_SPLIT30 : EIG_FP64_TC;
+      if (S.verbose)
+        std::fprintf(stderr, "[eigdc] node off=%d m=%d: precision tier %d\n", nd.off, m, tier);
+      continue;
+    }
     if (rg.kind == EIG_REGION_LINE && ir.converged) {
       if (so.rank == 0) nd.hi = rg.c_or_sigma;
       else if (so.rank == m) nd.lo = rg.c_or_sigma;

@@ -287,12 +287,10 @@ __device__ void cta_panel(int mp, int jb, double* __restrict__ P, int ldp, Panel
       *p = (v0 != 0.0) ? *p / v0 : 0.0;
     }
     __syncthreads();
-    if (beta != 0.0 && c + 1 < jb) {
-      const int rows = mp - c, cols = jb - c - 1;
-      for (int idx = tid; idx < rows * cols; idx += FT) {
-        const int r = c + idx % rows, k = c + 1 + idx / rows;
+    if (beta != 0.0) {
+      for (int r = c + tid; r < mp; r += FT) {
         const double w = (r == c) ? 1.0 : P[r + (size_t)c * ldp];
-        P[r + (size_t)k * ldp] -= beta * ps.dk[k] * w;
+        for (int k = c + 1; k < jb; ++k) P[r + (size_t)k * ldp] -= beta * ps.dk[k] * w;
       }
     }
     if (tid < c) {

@@ -83,6 +83,11 @@ cudaError_t tcx_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, doub
 // digit pairs), exact FP32 accumulation per 960-wide K chunk, FP64 drain: no
 // accumulation bias, error about 2^-24 max|row| max|column| per product term.
 size_t tcx32_gemm_workspace_bytes(int m, int n, int k);
+// The same with five digits (30 bits, levels 0..4, 15 digit pairs).
+size_t tcx30_gemm_workspace_bytes(int m, int n, int k);
+cudaError_t tcx30_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                       const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                       int ldc, void* ws, int* err);
 cudaError_t tcx32_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
                        const double* A, int lda, const double* B, int ldb, double beta, double* C,
                        int ldc, void* ws, int* err);

@@ -51,6 +51,8 @@ static_assert(TX_TILE_A % 1024 == 0 && TX_TILE_B % 1024 == 0, "1024-byte swizzle
 
 // Digit count DIG and the levels kept:
 //   DIG = 9: levels 0..9 (53 digit pairs), FP64 accuracy;
+//   DIG = 5: levels 0..4 (15 digit pairs), 30 bits of each row / column
+//            maximum (the split-precision form's second tier);
 //   DIG = 4: levels 0..3 (10 digit pairs), FP32-level accuracy (24 bits of
 //            each row / column maximum), the split-precision form.
 // CHUNK_TILES: 64-wide K tiles per exact FP32 chunk, so that a level's
@@ -60,7 +62,7 @@ struct TxCfg {
   static constexpr int DIGITS = DIG;
   static constexpr int LEVELS = (DIG == 9) ? 10 : DIG;
   static constexpr int MAXPAIRS = (DIG == 9) ? 9 : DIG;   // digit pairs of the fullest level
-  static constexpr int CHUNK_TILES = (DIG == 9) ? 7 : 15;
+  static constexpr int CHUNK_TILES = (DIG == 9) ? 7 : (DIG == 5 ? 12 : 15);
   static constexpr uint32_t TMEM_COLS = (DIG == 9) ? 512 : 256;   // >= LEVELS * TX_BN, power of two
   static_assert(LEVELS * TX_BN <= (int)TMEM_COLS, "levels fit in TMEM");
   static_assert((long long)MAXPAIRS * CHUNK_TILES * TX_BK * 64 * 64 < (1LL << 24),
@@ -343,6 +345,7 @@ static size_t tcx_ws_bytes(int m, int n, int k) {
 
 size_t tcx_gemm_workspace_bytes(int m, int n, int k) { return tcx_ws_bytes<9>(m, n, k); }
 size_t tcx32_gemm_workspace_bytes(int m, int n, int k) { return tcx_ws_bytes<4>(m, n, k); }
+size_t tcx30_gemm_workspace_bytes(int m, int n, int k) { return tcx_ws_bytes<5>(m, n, k); }
 
 template <int DIG>
 static cudaError_t slice_operand(cudaStream_t s, int rows, int K, int kp, const double* X, int ldx,
@@ -394,7 +397,7 @@ static cudaError_t tcx_run(cudaStream_t s, bool ta, bool tb, int m, int n, int k
   (void)attr;
   dim3 grid((m + TX_BM - 1) / TX_BM, (n + TX_BN - 1) / TX_BN);
   note_launches(1);
-  constexpr int pairs = (DIG == 9) ? 53 : 10;   // digit pairs of the kept levels
+  constexpr int pairs = (DIG == 9) ? 53 : (DIG == 5 ? 15 : 10);   // digit pairs of the kept levels
   const TimingToken tt = timing_begin(s, DIG == 9 ? TIMING_TCX64 : TIMING_TCX32,
                                       2.0 * pairs * m * (double)n * k);
   tcx_gemm_kernel<DIG><<<grid, TX_THREADS, smem, s>>>(ta_map, tb_map, m, n, kp, alpha, beta, C,
@@ -407,6 +410,12 @@ cudaError_t tcx_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, doub
                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
                      int ldc, void* ws, int* err) {
   return tcx_run<9>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
+}
+
+cudaError_t tcx30_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,
+                       const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                       int ldc, void* ws, int* err) {
+  return tcx_run<5>(s, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, err);
 }
 
 cudaError_t tcx32_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,

@@ -33,12 +33,15 @@ from . import eigdc
 
 
 def _orthogonal(n, gen, device):
+    """Haar orthogonal factor (sign-fixed QR of a Gaussian; the QR runs on the
+    host, which keeps input generation off the device's linear-algebra
+    library)."""
     import torch
     G = torch.randn((n, n), generator=gen, dtype=torch.float64, device=device)
-    Q, R = torch.linalg.qr(G)
+    Q, R = torch.linalg.qr(G.cpu())
     s = torch.sign(torch.diagonal(R))
     s[s == 0] = 1.0
-    return Q * s
+    return (Q * s).to(device)
 
 
 def synthesize_complex(n, seed, device="cuda"):
@@ -51,9 +54,9 @@ def synthesize_complex(n, seed, device="cuda"):
     gen.manual_seed(int(seed))
     G = torch.complex(torch.randn((n, n), generator=gen, dtype=torch.float64, device=device),
                       torch.randn((n, n), generator=gen, dtype=torch.float64, device=device))
-    Q, R = torch.linalg.qr(G)
+    Q, R = torch.linalg.qr(G.cpu())
     ph = torch.diagonal(R) / torch.abs(torch.diagonal(R))
-    Q = Q * ph
+    Q = (Q * ph).to(device)
     rad = 1.5 * torch.sqrt(torch.rand(n, generator=gen, dtype=torch.float64, device=device))
     ang = 2.0 * math.pi * torch.rand(n, generator=gen, dtype=torch.float64, device=device)
     d = torch.polar(rad, ang)
@@ -215,11 +218,13 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
                                       params_sym if n <= sym_split_max_n else params))
         else:
             tickets.append(srv.submit(kind, dA, o["dwr"], o["dwi"], o["dU"], params))
-    statuses, lat, wait, service, flops = [], [], [], [], 0.0
+    statuses, lat, wait, service, flops, trees = [], [], [], [], 0.0, []
     for t, (kind, n, dA, o, ref) in zip(tickets, reqs):
         srv.wait(t, 3600.0)
         st, times, info = srv.poll(t)
         statuses.append(st)
+        trees.append({"splits": info.splits, "nodes": info.nodes,
+                      "failed_attempts": info.failed_attempts, "squarings": info.total_iters})
         wait.append(times[0])
         service.append(times[1])
         lat.append(times[2])
@@ -260,9 +265,11 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
             k["count"] += 1
             k["max_eig_err"] = max(k["max_eig_err"], err)
             k["max_bwd"] = max(k["max_bwd"], bwd)
-        records.append({"kind": kind, "n": n, "status": st, "wait_s": wait[i],
-                        "service_s": service[i], "latency_s": lat[i], "eig_err": err,
-                        "backward_err": bwd})
+        rec = {"kind": kind, "n": n, "status": st, "wait_s": wait[i],
+               "service_s": service[i], "latency_s": lat[i], "eig_err": err,
+               "backward_err": bwd}
+        rec.update(trees[i])
+        records.append(rec)
     names = {eigdc.EIG_KIND_SYM: "sym", eigdc.EIG_KIND_NONSYM: "nonsym",
              eigdc.EIG_KIND_PENCIL: "pencil", eigdc.EIG_KIND_CPLANE: "complex_plane"}
     pnames = {eigdc.EIG_FP64: "fp64", eigdc.EIG_SPLIT_BF16X3: "bf16x3 split",

@@ -154,3 +154,30 @@ def test_fp64tc_pencil_solve(E):
     assert np.linalg.norm(QL.T @ QL - np.eye(n), 2) <= 1e-12
     assert np.max(np.abs(np.sort(ar / be) - np.sort(d))) <= 1e-9
     assert info.splits == res[eigdc.EIG_FP64][-1].splits
+
+
+@pytest.mark.parametrize("n,sq", [(600, 2), (777, 1)])
+def test_fp64tc_two_level_irs_iterates_match_oracle(E, n, sq):
+    """At these sizes the QR of the stacked 2n x n matrix and the complement
+    Q [0; I] run in the two-level form (256-column outer blocks whose
+    aggregated reflectors update the trailing matrix on the tensor cores):
+    exactly `sq` squarings (R-test off) give the oracle's A_p, B_p and
+    R_{p-1} elementwise (tolerance of the FP64 iterate tests, the error-free
+    split keeping FP64 accuracy)."""
+    eigdc, h, torch = E
+    from oracle.irs import irs as oirs
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n))
+    B = rng.standard_normal((n, n)) + 2 * np.eye(n)
+    dA, dB = eigdc.to_device(A), eigdc.to_device(B)
+    reg = eigdc.Region(0, 0.0, 1.0)
+    p = eigdc.default_params(tau=-1.0, maxit=sq - 1, prec=eigdc.EIG_FP64_TC)
+    rc, info = eigdc.eig_divide_step(h, n, dA, n, dB, n, reg, p)
+    assert rc == eigdc.EIG_NO_CONVERGENCE and info.iters == sq
+    res = oirs(A, B, tau=-1.0, maxit=sq - 1, record_R=True)
+    scale = np.linalg.norm(np.vstack([A, B]), 2)
+    assert np.max(np.abs(eigdc.to_host(dA) - res.Ap)) <= 1e-11 * scale
+    assert np.max(np.abs(eigdc.to_host(dB) - res.Bp)) <= 1e-11 * scale
+    dR = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    eigdc.eig_last_R(h, n, dR, n)
+    assert np.max(np.abs(eigdc.to_host(dR) - res.Rs[-1])) <= 1e-11 * scale
