@@ -264,7 +264,8 @@ def whole_job_rate(units_per_rank, ms_max, world):
     return units_per_rank * world / (ms_max / 1e3)
 
 
-def traffic_per_launch(per_launch_flops, record="dgemm_traffic.json", source="linalg.cu"):
+def traffic_per_launch(per_launch_flops, record="dgemm_traffic.json", source="linalg.cu",
+                       key="dram_bytes_per_work"):
     """DRAM bytes per launch of a kernel from its committed ncu capture (bytes
     per unit of algorithmic work, scaled to this run's average launch), or None
     when the capture is missing or the kernel's source file changed since it
@@ -277,7 +278,9 @@ def traffic_per_launch(per_launch_flops, record="dgemm_traffic.json", source="li
         return None
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest() or not per_launch_flops:
         return None
-    return rec["dram_bytes_per_work"] * per_launch_flops
+    if key not in rec:
+        return None
+    return rec[key] * per_launch_flops
 
 
 def batched_arm(args, torch, eigdc, h, dev, stream, world):
@@ -847,7 +850,9 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
                     "peak_note": "measured sustained dense bf16 (%s); work = digit pairs x 2mnk "
                                  "BF16 MMA flops" % src,
                     "traffic": traffic_per_launch(per_launch, "tcx_gemm_traffic.json",
-                                                  "tcx_gemm.cu")}
+                                                  "tcx_gemm.cu",
+                                                  "dram_bytes_per_work" if dom == 1 else
+                                                  "dram_bytes_per_work_4digit")}
     roofline.update({"kernel": eigdc.TIMING_FAMILIES[dom], "achieved": achieved,
                      "frac": achieved / roofline["peak"] if achieved else None,
                      "launches": f_cnt, "per_launch_work": per_launch,
@@ -856,7 +861,8 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
                                   "event pairs on the launching worker's stream (concurrent "
                                   "requests share the SMs, so a launch's duration includes "
                                   "time it waited for them)",
-                     "families_ms": {eigdc.TIMING_FAMILIES[f]: fam[f][0] for f in fam}})
+                     "families": {eigdc.TIMING_FAMILIES[f]: {"ms": fam[f][0], "launches": fam[f][1],
+                                                             "work": fam[f][2]} for f in fam}})
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         arr, kinds, sizes = serving.trace(args.steps, SERVE_RATE, 64, 4096, (0.5, 0.3, 0.2), seed)

@@ -58,11 +58,12 @@ typedef struct eig_handle_s* eig_handle_t;
 #define EIG_SPLIT_BF16X3 1
 /* FP64-accurate contractions on the tensor cores: the large products of the
  * path (complement products of the squarings, splitter, similarity; every
- * dimension >= 128) split their FP64 operands error-free into nine 6-bit
- * digits per row / column (power-of-two scaled, stored exactly as BF16),
- * multiply the digit pairs of weight levels 0..9 with tcgen05.mma into one
- * FP32 TMEM accumulator per level, exact because each 448-wide K chunk keeps
- * every partial sum an integer below 2^24, and drain the levels into FP64
+ * dimension >= 128) split their FP64 operands error-free into nine signed
+ * 6-bit digits per row / column (balanced, |digit| <= 32; power-of-two
+ * scaled, stored exactly as BF16), multiply the digit pairs of weight levels
+ * 0..9 with tcgen05.mma into one FP32 TMEM accumulator per level, exact
+ * because each 1792-wide K chunk keeps every partial sum an integer below
+ * 2^24, and drain the levels into FP64
  * (eig_gemm_fp64tc).  Error ~ K 2^-53 of max|row| max|column|, like an FP64
  * GEMM; the rank-32 reflector products of the panels stay on the FP64 DFMA
  * kernel, and every other setting (tau, split_tol, no refinement) is that of
@@ -77,8 +78,14 @@ typedef struct eig_handle_s* eig_handle_t;
  * product of the path (trailing updates and reflector products of the panels
  * included) carries an error of about 2^-24 max|row| max|column| per term
  * with no drift.  Panels, norms, the R-test, the split test and the rank
- * decision stay FP64; the other settings (tau, split_tol, refinement of
- * symmetric solves) are those of EIG_SPLIT_BF16X3. */
+ * decision stay FP64.  Each node starts at the tier its eigenvalue interval
+ * can resolve -- four digits, five digits (30 bits) or the FP64-accurate
+ * split of EIG_FP64_TC, chosen from m max(|lo|, |hi|) / (hi - lo), an
+ * estimate of how much the split residual amplifies the tier's rounding --
+ * and escalates one tier when an attempt finds a true split (0 < rank < m)
+ * whose residual stays above split_tol (>= 1e-6).  Symmetric solves end with
+ * the FP64 refinement of EIG_SPLIT_BF16X3 when some accepted split ran at an
+ * FP32-level tier. */
 #define EIG_SPLIT_FP32 3
 
 /* regions (Sec. 3.1 unit circle; Sec. 3.3 line via the Moebius map
@@ -100,7 +107,11 @@ typedef struct {
 } eig_region_t;
 
 typedef struct {
-  double tau;        /* IRS stopping ratio ||R_j - R_{j-1}||_1 <= tau ||R_{j-1}||_1; <= 0: default */
+  double tau;        /* IRS stopping ratio ||R_j - R_{j-1}||_1 <= tau ||R_{j-1}||_1; <= 0: default.
+                        The tensor-core modes also stop once the ratio is below their rounding
+                        floor's level (split precision 1e-3, EIG_FP64_TC 1e-10) and fell by
+                        less than 4x over the last squaring (EIGDC_VERBOSE=1 prints the
+                        ratio of each squaring to stderr) */
   int maxit;         /* IRS runs j = 0..maxit (Algorithm 3, "until j > maxit") */
   double split_tol;  /* accept a split when ||E21||_1/||A||_1 (+ ||F21||_1/||B||_1) <= split_tol;
                         <= 0: max(1e-12, 16 n 2^-53) for a node of size n (the FP64 rounding
@@ -109,7 +120,7 @@ typedef struct {
                         error stays 10-50x below the score); BF16 x 3: >= 1e-3;
                         EIG_SPLIT_FP32: >= 1e-6 at the RURV rank */
   int leaf_size;     /* nodes of at most this size go to the leaf solver (<= 64) */
-  int prec;          /* EIG_FP64 or EIG_SPLIT_BF16X3 */
+  int prec;          /* EIG_FP64, EIG_SPLIT_BF16X3, EIG_FP64_TC or EIG_SPLIT_FP32 */
   uint64_t seed;     /* Philox key of every draw of the method */
   int max_fail;      /* unproductive attempts per node before EIG_NO_SPLIT */
   int nb;            /* panel width of the blocked QR (0: automatic) */
@@ -177,7 +188,8 @@ int eig_gemm_timing(int enable, double* total_ms, unsigned long long* launches, 
 /* After eig_gemm_timing(0, ...): the totals of one timed kernel family of the
  * last timed region -- 0 the FP64 DFMA GEMM (work = 2mnk), 1 the FP64-accurate
  * tensor-core split (work = 53 x 2mnk BF16 MMA flops), 2 the FP32-level
- * four-digit split (10 x 2mnk), 3 the fused batched solver (work 0).
+ * four- and five-digit splits (10 or 15 x 2mnk), 3 the fused batched solver
+ * (work 0).
  * Returns EIG_ERR_ARG for another family. */
 int eig_kernel_timing(int family, double* total_ms, unsigned long long* launches, double* work);
 /* Device workspace (bytes) the handle needs for calls on size n.  For

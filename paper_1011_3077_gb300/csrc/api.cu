@@ -210,6 +210,25 @@ constexpr int NB2 = 256;   // outer block width of the two-level QR
 // resolve below the split tolerance; the next tier is EIG_FP64_TC.
 constexpr int PREC_SPLIT30 = 13;
 
+// First tier of an EIG_SPLIT_FP32 node of size m whose eigenvalues lie in
+// [lo, hi].  A split's residual ||E21|| / ||A|| is about the tier's rounding
+// level times ||A_node|| over the eigenvalue gap at the line, and the mean gap
+// is (hi - lo) / m, so kappa = m max(|lo|, |hi|) / (hi - lo) estimates the
+// amplification.  The first tier whose level times kappa stays below the
+// 1e-6 split tolerance is taken: four digits at about 2^-20 per unit of
+// kappa, five digits at about 2^-27 (fitted to the solver's own log on the
+// semicircle at n = 8192: five-digit attempts succeeded up to m ~ 165 near
+// the centre of the spectrum, kappa ~ 80, and four-digit ones never did);
+// else the FP64-accurate split.  Starting there saves the attempts that
+// cannot succeed; a node still escalates when its attempt fails.
+static int split_start_tier(int m, double lo, double hi) {
+  const double w = hi - lo, a = std::max(std::fabs(lo), std::fabs(hi));
+  const double kappa = w > 0.0 ? m * a / w : INFINITY;
+  if (kappa * 0x1p-20 <= 1e-6) return EIG_SPLIT_FP32;
+  if (kappa * 0x1p-27 <= 1e-6) return PREC_SPLIT30;
+  return EIG_FP64_TC;
+}
+
 // split precision: FP32-level products on the tensor cores, FP64 panels,
 // tests and refinement (BF16 x 3, or the unbiased four- / five-digit split)
 static bool split_mode(int prec) {
@@ -539,11 +558,29 @@ struct IRSOut {
 
 static double default_tau(int n) { return std::max(1e-14, 4.0 * std::sqrt((double)n) * 0x1p-53); }
 
-// stagnate: also stop once the ratio is below 1e-3 and has stopped falling
-// quadratically (the FP32-level floor of the split-precision iterates).
+// Below this ratio the R-test also stops once the ratio has stopped falling
+// quadratically: the rounding floor of the iterates has been reached.  The
+// split-precision iterates sit at an FP32-level floor (1e-3); the FP64-
+// accurate tensor-core products keep an FP64-level floor that at large n can
+// lie a little above default_tau (1e-10); plain FP64 keeps the plain R-test.
+static double stall_level(int prec) {
+  if (split_mode(prec)) return 1e-3;
+  return prec == EIG_FP64_TC ? 1e-10 : 0.0;
+}
+
+static bool irs_trace() {
+  static const bool on = [] {
+    const char* v = std::getenv("EIGDC_VERBOSE");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+
+// stall_below > 0: also stop once the ratio is below stall_below and fell by
+// less than 4x over the last squaring (stall_level).
 static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int lda, const double* B,
                       int ldb, const eig_region_t& rg, double tau, int maxit,
-                      bool stagnate = false, bool use_graphs = false) {
+                      double stall_below = 0.0, bool use_graphs = false) {
   cudaStream_t s = h->stream;
   NvtxRange nvtx_("eig.irs");
   const size_t nn = (size_t)n * n;
@@ -657,7 +694,10 @@ static IRSOut run_irs(eig_handle_t h, IRSWork& w, int n, const double* A, int ld
       const double ratio = den > 0.0 ? num / den : (num == 0.0 ? 0.0 : INFINITY);
       const double prev = out.last_ratio;
       out.last_ratio = ratio;
-      const bool stalled = stagnate && j >= 2 && ratio <= 1e-3 && ratio > 0.25 * prev;
+      const bool stalled = j >= 2 && ratio <= stall_below && ratio > 0.25 * prev;
+      if (irs_trace())
+        std::fprintf(stderr, "[eigdc] irs n=%d squaring=%d ratio=%.3e tau=%.3e%s\n", n, j + 1,
+                     ratio, tau, stalled ? " (stalled)" : "");
       if (ratio <= tau || stalled) {
         out.iters = j + 1;
         out.converged = true;
@@ -1275,6 +1315,9 @@ static size_t carve_main(Arena& a, int n, bool refine, SolveMain& w, bool pencil
 struct SolveShared {
   int n = 0, ldu = 0, leaf = 64;
   bool sym = true, verbose = false;
+  // split precision: some accepted split ran at an FP32-level tier, so the
+  // eigendecomposition needs the closing FP64 refinement
+  bool low_tier = false;
   double* Acur = nullptr;
   double* dU = nullptr;        // pencils: Q_L
   bool pencil = false;
@@ -1318,10 +1361,11 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
   int attempt = 0, fails = 0;
   double flops = 0.0;
   int iters = 0, failed = 0;
-  // precision tier of this node's attempts: EIG_SPLIT_FP32 starts with
-  // four-digit products and escalates (five digits, then the FP64-accurate
-  // split) when an attempt finds a true split it cannot resolve
-  int tier = p.prec;
+  // precision tier of this node's attempts: EIG_SPLIT_FP32 starts at the
+  // tier its interval can resolve (split_start_tier) and escalates (five
+  // digits, then the FP64-accurate split) when an attempt finds a true split
+  // it cannot resolve
+  int tier = p.prec == EIG_SPLIT_FP32 ? split_start_tier(m, nd.lo, nd.hi) : p.prec;
   while (true) {
     w.irs.prec = w.irs.qr.q.prec = tier;
     w.split.prec = w.split.qr.q.prec = tier;
@@ -1339,7 +1383,7 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
       rg.r_or_s = sc;
     }
     const double tau_m = tau > 0 ? tau : (split_mode(tier) ? 1e-5 : default_tau(m));
-    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, split_mode(tier),
+    IRSOut ir = run_irs(hw, w.irs, m, An, n, nullptr, 0, rg, tau_m, p.maxit, stall_level(tier),
                         p.graphs != 0);
     iters += ir.iters;
     flops += ir.iters * flops_irs_iter(m);
@@ -1391,6 +1435,7 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
       }
       CK2(hw, cudaStreamSynchronize(s));   // children may run on other streams
       std::lock_guard<std::mutex> lock(S.mu);
+      if (split_mode(tier)) S.low_tier = true;
       S.inf.nodes++;
       S.inf.splits++;
       S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
@@ -1495,8 +1540,9 @@ static void process_pencil_node(eig_handle_t hw, SolveShared& S, Node nd, char* 
       rg.c_or_sigma = c + R * (xi - 0.5);
       rg.r_or_s = R;
     }
-    IRSOut ir = run_irs(hw, w.irs, m, P, n, Qm, n, rg, tau, p.maxit, false, p.graphs != 0);
-    IRSOut il = run_irs(hw, w.irsL, m, w.At, m, w.Bt, m, rg, tau, p.maxit, false, p.graphs != 0);
+    const double stall = p.tau > 0 ? 0.0 : stall_level(p.prec);
+    IRSOut ir = run_irs(hw, w.irs, m, P, n, Qm, n, rg, tau, p.maxit, stall, p.graphs != 0);
+    IRSOut il = run_irs(hw, w.irsL, m, w.At, m, w.Bt, m, rg, tau, p.maxit, stall, p.graphs != 0);
     iters += ir.iters;
     flops += (ir.iters + il.iters) * flops_irs_iter(m);
     SplitOut so = run_split_pencil(hw, w.split, m, ir.Ap, ir.Bp, il.Ap, il.Bp, m, P, n, Qm, n,
@@ -1759,7 +1805,7 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
       status = EIG_NO_CONVERGENCE;
       h->err = "a leaf solver did not converge";
     }
-    if (refine) {
+    if (refine && S.low_tier) {
       inf.flops += refine_symmetric(h, n, dA, lda, dU, ldu, w.wtmp, w.G, w.AU, w.S, w.E, w.bits);
     }
     if (sym) {
@@ -2095,7 +2141,7 @@ int eig_divide_step(eig_handle_t h, int n, double* dA, int lda, double* dB, int 
   const double tau = p.tau > 0 ? p.tau
                                : (p.tau < 0 ? -1.0 : (split_mode(p.prec) ? 1e-5 : default_tau(n)));
   IRSOut o = run_irs(h, w, n, dA, lda, dB, ldb, *region, tau, p.maxit,
-                     split_mode(p.prec) && p.tau >= 0);
+                     p.tau >= 0 ? stall_level(p.prec) : 0.0);
   cudaStream_t s = h->stream;
   CK(copy_matrix(s, n, n, o.Ap, n, dA, lda));
   if (dB) CK(copy_matrix(s, n, n, o.Bp, n, dB, ldb));

@@ -71,8 +71,8 @@ cudaError_t reduce_trmm(cudaStream_t s, int jb, int n, const double* partial, in
 // (the BF16 planes of both operands); *err gets a nonzero bit if a bounded
 // wait in the kernel timed out.
 size_t tc_gemm_workspace_bytes(int m, int n, int k);
-// FP64-accurate GEMM on the tensor cores (error-free 9-digit split, exact FP32
-// accumulation per 448-wide K chunk, FP64 drain); `ws` must hold
+// FP64-accurate GEMM on the tensor cores (error-free split into nine balanced
+// digits, exact FP32 accumulation per 1792-wide K chunk, FP64 drain); `ws` must hold
 // tcx_gemm_workspace_bytes(m, n, k) bytes; err as for tc_gemm.
 size_t tcx_gemm_workspace_bytes(int m, int n, int k);
 cudaError_t tcx_gemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha,

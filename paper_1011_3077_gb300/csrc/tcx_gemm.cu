@@ -4,25 +4,29 @@
 // multiplication and its applications", Numer. Algorithms 59, 2012):
 //
 //   * every row r of op(A) (and every column c of op(B)) is scaled by a power
-//     of two 2^e with max |x| < 2^e, and |x| 2^-e is cut into nine 6-bit
-//     digits: x = sign * 2^e * sum_p d_p 2^(-6(p+1)), d_p in [0, 63] (the last
-//     digit rounded, <= 64).  Each digit is an integer, stored exactly as BF16
-//     (one plane per digit);
-//   * the product of two rows is 2^(e_r + e_c - 12) sum_l L_l 2^(-6 l) with
+//     of two 2^e with max |x| < 2^e, and |x| 2^-e is cut into nine signed
+//     digits in balanced form: x = sign * 2^(e-5) * sum_p d_p 2^(-6p) with
+//     d_0 in [0, 32] and d_p in [-32, 31] below it (53 bits of 2^e, the last
+//     digit rounded; a digit of 32 or more borrows one from the digit above).
+//     Each digit is an integer, stored exactly as BF16 (one plane per digit);
+//   * the product of two rows is 2^(e_r + e_c - 10) sum_l L_l 2^(-6 l) with
 //     the level sums L_l = sum_{i+j=l} sum_k d_i(r,k) d_j(c,k).  Levels
 //     0..9 are kept (53 digit pairs); the first dropped level weighs about
-//     2^-57 K relative to 2^(e_r + e_c), below FP64 rounding of the product;
+//     2^-60 K relative to 2^(e_r + e_c), below FP64 rounding of the product;
 //   * each level is accumulated by tcgen05.mma (kind::f16, BF16 inputs, FP32
 //     accumulator) in its own TMEM columns.  Every partial sum is an integer
-//     below 9 * 448 * 64^2 < 2^24 as long as a chunk spans at most 448 of K, so
-//     the FP32 accumulation is exact; after each chunk four drain warps read
-//     the ten accumulators (tcgen05.ld) and add them, scaled by 2^(-6 l), to
-//     FP64 registers.
+//     below 9 * 1792 * 32^2 < 2^24 as long as a chunk spans at most 1792 of K,
+//     so the FP32 accumulation is exact; after each chunk four drain warps
+//     read the ten accumulators (tcgen05.ld) and add them, scaled by
+//     2^(-6 l), to FP64 registers.  (The balanced digits halve the digit
+//     bound, so a chunk is four times longer than with digits in [0, 64]:
+//     the drain's FP64 work, on a pipe about 1/1800 of the tensor rate,
+//     shrinks fourfold.)
 //
 // Kernel (one CTA per 128 x 48 tile of C, 192 threads):
 //   warp 0: TMA producer -- per 64-wide K tile the nine B digit planes
 //           (48 x 64 each, one stage of a 2-stage ring) and, one by one, the
-//           nine A digit planes (128 x 64, a 4-slot ring);
+//           nine A digit planes (128 x 64, a 7-slot ring);
 //   warp 1: TMEM allocation (512 columns) and the single MMA-issuing thread;
 //   warps 2-5: drain and epilogue (warp w reads TMEM lanes 32 (w % 4) + 0..31,
 //           i.e. rows of the tile).
@@ -43,7 +47,7 @@ namespace eigdc {
 bool make_plane_map(CUtensorMap* map, void* base, int rows, int kp, int box_rows, int planes);
 
 constexpr int TX_BM = 128, TX_BN = 48, TX_BK = 64;
-constexpr int TX_BSTAGES = 2, TX_ASLOTS = 4;
+constexpr int TX_BSTAGES = 2;
 constexpr int TX_THREADS = 192;
 constexpr int TX_TILE_A = TX_BM * TX_BK * 2;   // bytes of one digit plane slab of A
 constexpr int TX_TILE_B = TX_BN * TX_BK * 2;
@@ -55,26 +59,39 @@ static_assert(TX_TILE_A % 1024 == 0 && TX_TILE_B % 1024 == 0, "1024-byte swizzle
 //            maximum (the split-precision form's second tier);
 //   DIG = 4: levels 0..3 (10 digit pairs), FP32-level accuracy (24 bits of
 //            each row / column maximum), the split-precision form.
+// DIG = 9 uses balanced digits (|d| <= 32); the FP32-level tiers keep digits
+// in [0, 64] (24 / 30 bits of the maximum rather than 23 / 29).
 // CHUNK_TILES: 64-wide K tiles per exact FP32 chunk, so that a level's
-// partial sums (pairs per level x chunk x 64^2) stay integers below 2^24.
+// partial sums (pairs per level x chunk x DMAX^2) stay integers below 2^24.
+// TOP / SHIFT0: F = floor(|x| 2^(TOP - e)) < 2^TOP and digit p is bits
+// SHIFT0 - 6p .. SHIFT0 - 6p + 5 of F; the product of two rows carries
+// 2^(e_r + e_c - SCALE).  ASLOTS: slots of the A digit-plane ring.
 template <int DIG>
 struct TxCfg {
   static constexpr int DIGITS = DIG;
+  static constexpr bool BALANCED = (DIG == 9);
   static constexpr int LEVELS = (DIG == 9) ? 10 : DIG;
   static constexpr int MAXPAIRS = (DIG == 9) ? 9 : DIG;   // digit pairs of the fullest level
-  static constexpr int CHUNK_TILES = (DIG == 9) ? 7 : (DIG == 5 ? 12 : 15);
+  static constexpr int DMAX = BALANCED ? 32 : 64;
+  static constexpr int TOP = BALANCED ? 60 : 62;
+  static constexpr int SHIFT0 = BALANCED ? 55 : 56;
+  static constexpr int SCALE = BALANCED ? 10 : 12;
+  static constexpr int CHUNK_TILES = (DIG == 9) ? 28 : (DIG == 5 ? 12 : 15);
+  static constexpr int ASLOTS = (DIG == 9) ? 7 : 4;
   static constexpr uint32_t TMEM_COLS = (DIG == 9) ? 512 : 256;   // >= LEVELS * TX_BN, power of two
   static_assert(LEVELS * TX_BN <= (int)TMEM_COLS, "levels fit in TMEM");
-  static_assert((long long)MAXPAIRS * CHUNK_TILES * TX_BK * 64 * 64 < (1LL << 24),
+  static_assert((long long)MAXPAIRS * CHUNK_TILES * TX_BK * DMAX * DMAX < (1LL << 24),
                 "exact FP32 chunk");
+  static_assert(SHIFT0 - 6 * (DIG - 1) - 1 >= 0 && SHIFT0 + 6 == TOP + (BALANCED ? 1 : 0),
+                "digit layout");
 };
 
 template <int DIG>
 struct TxSmem {
   uint8_t b[TX_BSTAGES][DIG][TX_TILE_B];
-  uint8_t a[TX_ASLOTS][TX_TILE_A];
+  uint8_t a[TxCfg<DIG>::ASLOTS][TX_TILE_A];
   uint64_t bfull[TX_BSTAGES], bempty[TX_BSTAGES];
-  uint64_t afull[TX_ASLOTS], aempty[TX_ASLOTS];
+  uint64_t afull[TxCfg<DIG>::ASLOTS], aempty[TxCfg<DIG>::ASLOTS];
   uint64_t accfull, accempty;
   uint32_t tmem_base;
   int abort_flag;
@@ -118,6 +135,7 @@ __global__ void __launch_bounds__(256)
 slice_kernel(int rows, int K, int kp, const double* __restrict__ X, int ldx, int kcontig,
              const unsigned long long* __restrict__ mx, __nv_bfloat16* __restrict__ P,
              size_t pstride, int* __restrict__ expo) {
+  using Cfg = TxCfg<DIG>;
   __shared__ double tile[32][65];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   const int tid = threadIdx.x;
@@ -141,17 +159,24 @@ slice_kernel(int rows, int K, int kp, const double* __restrict__ X, int ldx, int
     const int E = (int)((b >> 52) & 0x7FF);
     const unsigned long long mant = b & ((1ull << 52) - 1);
     const unsigned long long M = E ? (mant | (1ull << 52)) : mant;
-    // F = floor(|x| 2^(62 - e)) = M 2^(Ee - 1075 + 62 - e) < 2^62
-    const int sh = (E ? E : 1) - 1013 - e;
+    // F = floor(|x| 2^(TOP - e)) = M 2^(Ee - 1075 + TOP - e) < 2^TOP
+    const int sh = (E ? E : 1) - 1075 + Cfg::TOP - e;
     unsigned long long F;
     if (sh >= 0) F = M << sh;
     else F = (-sh >= 64) ? 0ull : (M >> (-sh));
     const bool neg = (b >> 63) != 0;
     const size_t o = (size_t)r * kp + k;
+    // the bit below the last digit rounds it; in balanced form a digit of 32
+    // or more becomes d - 64 and carries one into the digit above
+    int carry = (int)((F >> (Cfg::SHIFT0 - 6 * (DIG - 1) - 1)) & 1ull);
 #pragma unroll
-    for (int p = 0; p < DIG; ++p) {
-      int d = (int)((F >> (56 - 6 * p)) & 63ull);
-      if (p == DIG - 1) d += (int)((F >> (55 - 6 * p)) & 1ull);   // round the last digit
+    for (int p = DIG - 1; p >= 0; --p) {
+      int d = (int)((F >> (Cfg::SHIFT0 - 6 * p)) & 63ull) + carry;
+      carry = 0;
+      if (Cfg::BALANCED && p > 0 && d >= 32) {
+        d -= 64;
+        carry = 1;
+      }
       P[p * pstride + o] = __int2bfloat16_rn(neg ? -d : d);
     }
   }
@@ -166,6 +191,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   extern __shared__ uint8_t smem_raw[];
   using Cfg = TxCfg<DIG>;
   constexpr int TX_DIGITS = Cfg::DIGITS, TX_LEVELS = Cfg::LEVELS, TX_CHUNK_TILES = Cfg::CHUNK_TILES;
+  constexpr int TX_ASLOTS = Cfg::ASLOTS;
   constexpr uint32_t TX_TMEM_COLS = Cfg::TMEM_COLS;
   TxSmem<DIG>& S = *reinterpret_cast<TxSmem<DIG>*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                    ~static_cast<uintptr_t>(1023));
@@ -312,7 +338,7 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (lane == 0) mbar_arrive(&S.accempty);
     }
     if (good && !S.abort_flag && row < M) {
-      const int er = expA[row] - 12;
+      const int er = expA[row] - Cfg::SCALE;
 #pragma unroll
       for (int j = 0; j < TX_BN; ++j) {
         const int col = n0 + j;
@@ -388,6 +414,7 @@ static cudaError_t tcx_run(cudaStream_t s, bool ta, bool tb, int m, int n, int k
   if (!make_plane_map(&ta_map, pa, m, kp, TX_BM, DIG) ||
       !make_plane_map(&tb_map, pb, n, kp, TX_BN, DIG))
     return cudaErrorInvalidValue;
+  static_assert(sizeof(TxSmem<DIG>) + 1024 <= 232448, "227 KB of dynamic shared memory");
   const size_t smem = sizeof(TxSmem<DIG>) + 1024;
   static const bool attr = [smem] {
     cudaFuncSetAttribute(tcx_gemm_kernel<DIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,

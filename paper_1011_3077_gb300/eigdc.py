@@ -278,7 +278,7 @@ def eig_gemm_timing_start():
         raise EigError(rc, "eig_gemm_timing start failed")
 
 
-TIMING_FAMILIES = {0: "dgemm_kernel", 1: "tcx_gemm_kernel<9>", 2: "tcx_gemm_kernel<4>",
+TIMING_FAMILIES = {0: "dgemm_kernel", 1: "tcx_gemm_kernel<9>", 2: "tcx_gemm_kernel<4>/<5>",
                    3: "fused_batched_kernel"}
 
 

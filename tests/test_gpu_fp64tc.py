@@ -1,13 +1,15 @@
 """FP64-accurate tensor-core contractions (EIG_FP64_TC) on the GPU.
 
 The error-free split cuts every row of op(A) and column of op(B) into nine
-6-bit digits below a power-of-two scale 2^e (the last digit rounded) and keeps
-the digit-pair levels 0..9, each accumulated exactly in FP32 over 448-wide K
-chunks.  Error model per element, with a = max |row of op(A)|, b = max |column
-of op(B)|: digit truncation <= 2 * 2^-55 a b per term, dropped levels
-<= 2^-57 a b per term, FP64 drain rounding ~ 10 u |c| per chunk.  Tests use
+signed 6-bit digits in balanced form (|digit| <= 32, 53 bits below a
+power-of-two scale 2^e, the last digit rounded) and keeps the digit-pair
+levels 0..9, each accumulated exactly in FP32 over 1792-wide K chunks.  Error
+model per element, with a = max |row of op(A)|, b = max |column of op(B)|:
+digit rounding <= 2 * 2^-53 a b per term, dropped levels <= 2^-59 a b per
+term, FP64 drain rounding ~ 10 u |c| per chunk.  Tests use
 |C - C_ref| <= 16 k u a b (u = 2^-53), which also covers the FP64 rounding of
-the reference; an inexact FP32 accumulation would break it by ~2^29.
+the reference; an inexact FP32 accumulation would break it by ~2^29.  Shapes
+with k > 1792 (up to 4100 here) span several exact chunks.
 Integer operands whose digits are exact give an exactly integer product: that
 pins the exactness of the tensor-core accumulation bit for bit.
 Whole solves in EIG_FP64_TC meet the FP64 targets (eigenvalue error
@@ -52,7 +54,8 @@ def _run(eigdc, h, torch, A, B, ta, tb, alpha=1.0, beta=0.0, C0=None):
 
 @pytest.mark.parametrize("m,n,k,ta,tb", [
     (1, 1, 1, 0, 0), (63, 65, 17, 0, 0), (130, 70, 300, 1, 0), (128, 48, 448, 0, 0),
-    (200, 100, 1000, 0, 1), (257, 129, 2048, 1, 0), (64, 130, 33, 1, 1), (700, 500, 4100, 0, 0)])
+    (200, 100, 1000, 0, 1), (257, 129, 2048, 1, 0), (64, 130, 33, 1, 1), (700, 500, 4100, 0, 0),
+    (128, 48, 1792, 0, 0), (96, 60, 3585, 1, 1)])
 def test_fp64tc_gemm_accuracy(E, m, n, k, ta, tb):
     eigdc, h, torch = E
     rng = np.random.default_rng(m * 7 + n + k)
