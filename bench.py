@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--prec-sym", type=int, default=3, choices=[0, 1, 2, 3],
                     help="serve: precision of the symmetric requests (3: unbiased FP32-level "
                          "split with FP64 refinement)")
+    ap.add_argument("--fused-tail", type=int, default=0,
+                    help="symmetric solves (sym, serve): nodes of at most this many rows finish "
+                         "in one launch of the fused batched solver (0: off)")
     ap.add_argument("--workload", default="serve",
                     choices=["serve", "schur", "batched", "svd", "cplane", "sym", "step", "gemm"],
                     help="serve: the mixed request stream (default, one step = one completed "
@@ -110,7 +113,7 @@ def config(n, args):
                         "N(0, (%g/sqrt(n))^2), full recursion to 64x64 leaves, unit-circle "
                         "root split then Moebius lines" % (n, args.coupling),
             "n": n, "coupling": args.coupling, "leaf_size": 64,
-            "precision": "fp64" if args.prec == 0 else "fp64 (tensor-core error-free split)",
+            "precision": PREC_NAMES[args.prec],
             "workers": args.workers,
             "l2": "flushed between timed steps (512 MiB write)",
             "parallelism": "replicas" if args.gpus > 1 else "single"}
@@ -264,6 +267,14 @@ def whole_job_rate(units_per_rank, ms_max, world):
     return units_per_rank * world / (ms_max / 1e3)
 
 
+PREC_NAMES = {0: "fp64", 1: "split bf16x3 (FP32-level tensor-core products, FP64 panels, "
+                           "split tests and refinement)",
+              2: "fp64 (tensor-core error-free split)",
+              3: "split fp32 (error-free split at four / five digits per node where it can "
+                 "resolve the split, else the FP64-accurate split; FP64 panels, split tests and "
+                 "refinement)"}
+
+
 def traffic_per_launch(per_launch_flops, record="dgemm_traffic.json", source="linalg.cu",
                        key="dram_bytes_per_work"):
     """DRAM bytes per launch of a kernel from its committed ncu capture (bytes
@@ -369,8 +380,7 @@ def batched_arm(args, torch, eigdc, h, dev, stream, world):
                        "workers": args.workers,
                        "form": "one persistent fused launch per step (a CTA per problem)"
                                if args.fused else "host-driven executor",
-                       "precision": "fp64" if (args.prec == 0 or args.fused) else
-                                    "fp64 (tensor-core error-free split)",
+                       "precision": "fp64" if args.fused else PREC_NAMES[args.prec],
                        "l2": "flushed between timed steps (512 MiB write)"},
             "autotune": tuning,
             "gflops": flops * world / (total_ms / 1e3) / 1e9,
@@ -433,8 +443,7 @@ def svd_arm(args, torch, eigdc, h, dev, stream, world):
             "config": {"workload": "SVD of A = U diag(s) V^T, n=%d, s ~ U[0.05, 1], through the "
                                    "symmetric embedding of order 2n" % n,
                        "n": n, "workers": args.workers,
-                       "precision": "fp64" if args.prec == 0 else
-                                    "fp64 (tensor-core error-free split)",
+                       "precision": PREC_NAMES[args.prec],
                        "l2": "flushed between timed steps (512 MiB write)"},
             "gflops": flops * world / (total_ms / 1e3) / 1e9, "singular_value_error": err,
             "backward_error": bwd, "orthogonality_frobenius": orth,
@@ -547,7 +556,7 @@ def sym_arm(args, torch, eigdc, h, dev, stream, world):
     dw = torch.zeros(n, dtype=torch.float64, device=dev)
     dU = torch.zeros((n, n), dtype=torch.float64, device=dev)
     params = eigdc.default_params(seed=0, leaf_size=64, workers=args.workers, prec=args.prec,
-                                  graphs=args.graphs)
+                                  graphs=args.graphs, fused_tail=args.fused_tail)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -582,10 +591,7 @@ def sym_arm(args, torch, eigdc, h, dev, stream, world):
     bwd = float(torch.linalg.norm(R) / torch.linalg.norm(dA0))
     orth = orth_2norm(U, torch)
     info = infos[-1]
-    names = {0: "fp64", 1: "split bf16x3 (FP32-level tensor-core products, FP64 panels, "
-                       "split tests and refinement)", 2: "fp64 (tensor-core error-free split)",
-             3: "split fp32 (unbiased four-digit tensor-core products, FP64 panels, split "
-                "tests and refinement)"}
+    names = PREC_NAMES
     line = {"metric": METRIC, "value": whole_job_rate(args.steps, total_ms, world),
             "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -594,6 +600,7 @@ def sym_arm(args, torch, eigdc, h, dev, stream, world):
                                    "lambda semicircle on [-1, 1], Q Haar, median-shift recursion "
                                    "to 64x64 leaves" % n,
                        "n": n, "precision": names[args.prec], "workers": args.workers,
+                       "fused_tail": args.fused_tail,
                        "l2": "flushed between timed steps (512 MiB write)"},
             "gflops": float(np.mean([i.flops for i in infos])) * args.steps * world /
                       (total_ms / 1e3) / 1e9,
@@ -792,7 +799,7 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     seed = 5 + 101 * rank
     kw = dict(rate=SERVE_RATE, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=args.workers,
-              budget_gb=120.0, device=dev)
+              budget_gb=120.0, device=dev, fused_tail=args.fused_tail)
     prec, prec_sym = eigdc.EIG_FP64_TC, args.prec_sym
     if args.warmup > 0:
         serving.run(count=args.warmup, seed=1000 + seed, prec=prec, prec_sym=prec_sym, **kw)
@@ -886,7 +893,8 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
                                               "merge and no split exists above n ~ 1000)",
                            "precision": {"sym_n_le_1024": res["precision_sym"],
                                          "sym_n_gt_1024_and_other": res["precision"]},
-                           "workers": args.workers, "mix": res["mix"], "sizes": res["sizes"],
+                           "workers": args.workers, "fused_tail_sym": args.fused_tail,
+                           "mix": res["mix"], "sizes": res["sizes"],
                            "l2": "not flushed between requests: continuous batching keeps "
                                  "several requests' matrices (up to 4096^2 x 8 B = 134 MB each, "
                                  "GBs in flight) resident, far above the 129 MB L2",

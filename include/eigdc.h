@@ -132,6 +132,14 @@ typedef struct {
                         graphs (per worker stream, cached on the handle) and replay them; the
                         caller must not synchronize the whole device (cudaDeviceSynchronize)
                         from another thread while the call runs.  0 (default): plain launches */
+  int fused_tail;    /* eig_solve symmetric: nodes of at most this many rows (capped at 512; 0,
+                        the default, or <= leaf_size: none) are collected and finished by one
+                        launch of the fused batched solver (eig_solve_batched_fused), each
+                        node's sub-recursion in one CTA with its own node id, interval and
+                        depth -- the same decisions as eig_solve takes, FP64 arithmetic on the
+                        DFMA pipe.  It replaces the many short launches of small nodes by one
+                        launch; a node in one CTA takes about 1e-7 m^3 seconds, so large values
+                        lengthen a single solve */
 } eig_params_t;
 
 typedef struct {
@@ -166,7 +174,7 @@ int eig_debug_fail_allocations(int count);
 
 /* Defaults: tau = max(1e-14, 4 sqrt(n) 2^-53) at call time, maxit = 60,
  * split_tol = 0 (automatic), leaf_size = 64, seed = 0, max_fail = 8, nb = 0,
- * v_draws = 4, root_unit_circle = 1, workers = 8, graphs = 0. */
+ * v_draws = 4, root_unit_circle = 1, workers = 8, graphs = 0, fused_tail = 0. */
 void eig_default_params(eig_params_t* p);
 
 /* Create a handle bound to CUDA device `device` and stream `stream`

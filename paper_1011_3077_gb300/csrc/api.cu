@@ -1139,8 +1139,17 @@ __global__ void permute_columns_kernel(int n, const double* __restrict__ U, int 
 // E are n x n scratch; lam receives the eigenvalues.  Returns flops executed.
 static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, double* U, int ldu,
                                double* lam, double* G, double* AU, double* S, double* E,
-                               unsigned long long* dbits) {
+                               unsigned long long* dbits, void* tcw, int* tcerr) {
   cudaStream_t s = h->stream;
+  // the n x n products on the tensor cores in the FP64-accurate split (error
+  // of an FP64 GEMM) where it pays, else on the DFMA kernel
+  auto rmm = [&](bool ta, bool tb, int m_, int n_, int k_, double alpha, const double* X, int ldx,
+                 const double* Y, int ldy, double beta, double* Z, int ldz) {
+    if (tcw && tcx_worth(m_, n_, k_))
+      return tcx_gemm(s, ta, tb, m_, n_, k_, alpha, X, ldx, Y, ldy, beta, Z, ldz, tcw, tcerr);
+    return gemm(s, ta, tb, m_, n_, k_, alpha, X, ldx, Y, ldy, beta, Z, ldz);
+  };
+  if (tcerr) CK(cudaMemsetAsync(tcerr, 0, sizeof(int), s));
   double flops = 0.0;
   const double u = 0x1p-53;
   // one pinned staging area: n eigenvalues, then the residual words
@@ -1148,9 +1157,9 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
   double* hl = reinterpret_cast<double*>(pin);
   unsigned long long* hb = reinterpret_cast<unsigned long long*>(pin + sizeof(double) * ((size_t)n + 8));
   for (int step = 0; step < 6; ++step) {
-    CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
-    CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
-    CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, AU, n, 0.0, S, n));
+    CK(rmm(true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
+    CK(rmm(false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
+    CK(rmm(true, false, n, n, n, 1.0, U, ldu, AU, n, 0.0, S, n));
     flops += 6.0 * (double)n * n * n;
     CK(cudaMemsetAsync(dbits, 0, 3 * sizeof(unsigned long long), s));
     CK(oa_diag(s, n, G, S, lam, &dbits[0]));
@@ -1168,7 +1177,7 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
     const double floor_ = 8.0 * std::sqrt((double)n) * u;
     if (offS <= floor_ * normA && maxR <= floor_) break;
     CK(oa_correction(s, n, G, S, lam, 64.0 * u * normA, E));
-    CK(gemm(s, false, false, n, n, n, 1.0, U, ldu, E, n, 0.0, AU, n));
+    CK(rmm(false, false, n, n, n, 1.0, U, ldu, E, n, 0.0, AU, n));
     flops += 2.0 * (double)n * n * n;
     if (ldu == n) {
       CK(add_inplace(s, (size_t)n * n, U, AU));
@@ -1194,8 +1203,8 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
     permute_columns_kernel<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(n, U, ldu, dperm, G, n);
     CK(cudaGetLastError());
     CK(copy_matrix(s, n, n, G, n, U, ldu));
-    CK(gemm(s, false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
-    CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, AU, n, 0.0, S, n));
+    CK(rmm(false, false, n, n, n, 1.0, A, lda, U, ldu, 0.0, AU, n));
+    CK(rmm(true, false, n, n, n, 1.0, U, ldu, AU, n, 0.0, S, n));
     flops += 4.0 * (double)n * n * n;
     // lam = diag(S) (the radii output is not used)
     CK(diag_gershgorin(s, n, S, n, lam, E));
@@ -1239,12 +1248,21 @@ static double refine_symmetric(eig_handle_t h, int n, const double* A, int lda, 
   }
   // final orthogonalisation without eigen-corrections (no division by gaps,
   // so no amplification of rounding): X <- X + X (I - X^T X) / 2
-  CK(gemm(s, true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
+  CK(rmm(true, false, n, n, n, 1.0, U, ldu, U, ldu, 0.0, G, n));
   CK(oa_correction(s, n, G, S, lam, INFINITY, E));   // every pair takes r_ij / 2
-  CK(gemm(s, false, false, n, n, n, 1.0, U, ldu, E, n, 0.0, AU, n));
+  CK(rmm(false, false, n, n, n, 1.0, U, ldu, E, n, 0.0, AU, n));
   if (ldu == n) CK(add_inplace(s, (size_t)n * n, U, AU));
   else CK(add_matrices(s, n, n, U, ldu, AU, n, U, ldu));
   flops += 4.0 * (double)n * n * n;
+  if (tcerr) {
+    int* hf = static_cast<int*>(pinned(h, 64));
+    CK(cudaMemcpyAsync(hf, tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (*hf) {
+      h->err = "tensor-core GEMM: a bounded wait timed out";
+      throw Fail{EIG_ERR_CUDA};
+    }
+  }
   return flops;
 }
 
@@ -1280,6 +1298,8 @@ static size_t carve_node(Arena& a, int n_total, int m, int prec, NodeWork& w,
 struct SolveMain {
   double *Acur, *wtmp, *Zleaf, *dtmp, *sortbuf, *Tbuf, *gpart;
   double *G, *AU, *S, *E;   // refinement scratch (split precision, symmetric)
+  void* rtcw = nullptr;      // refinement: digit planes of its n x n x n products
+  int* rtcerr = nullptr;
   unsigned long long* bits;
   int* status;
   LeafDesc* ddesc;
@@ -1305,6 +1325,10 @@ static size_t carve_main(Arena& a, int n, bool refine, SolveMain& w, bool pencil
   w.AU = refine ? a.take<double>(nn) : nullptr;
   w.S = refine ? a.take<double>(nn) : nullptr;
   w.E = refine ? a.take<double>(nn) : nullptr;
+  if (refine) {
+    w.rtcw = a.take<char>(tc_ws_bytes(EIG_FP64_TC, n, n, n));
+    w.rtcerr = a.take<int>(8);
+  }
   w.bits = a.take<unsigned long long>(8);
   w.status = a.take<int>(8);
   w.ddesc = a.take<LeafDesc>(std::max(1, n));
@@ -1318,6 +1342,10 @@ struct SolveShared {
   // split precision: some accepted split ran at an FP32-level tier, so the
   // eigendecomposition needs the closing FP64 refinement
   bool low_tier = false;
+  // symmetric nodes of at most fused_tail rows (0: none) are not processed
+  // here but collected for one launch of the fused batched solver
+  int fused_tail = 0;
+  std::vector<Node> deferred;
   double* Acur = nullptr;
   double* dU = nullptr;        // pencils: Q_L
   bool pencil = false;
@@ -1350,6 +1378,11 @@ static void process_node(eig_handle_t hw, SolveShared& S, Node nd, char* base) {
     S.inf.nodes++;
     S.inf.max_depth = std::max(S.inf.max_depth, nd.depth);
     S.leaves.push_back(LeafDesc{nd.off, m, (int)S.leaves.size() * 64 * 64});
+    return;
+  }
+  if (m <= S.fused_tail) {
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.deferred.push_back(nd);
     return;
   }
   Arena arena(base);
@@ -1713,6 +1746,84 @@ static void ensure_workers(eig_handle_t h, int count) {
   }
 }
 
+size_t fused_run_bytes(eig_handle_t h, int count, int mx, int cps, int* ctas_out);
+void fused_run(eig_handle_t h, int count, const int* n, double* const* dA, const int* lda,
+               double* const* dw, double* const* dU, const int* ldu, const eig_params_t& p,
+               int nb, int cps, int* status, eig_solve_info_t* infos, float* ms,
+               const FusedProblem* nodes = nullptr);
+
+// The fused tail of a symmetric solve: every deferred node (at most
+// fused_tail rows) is finished by one launch of the fused batched solver on a
+// worker handle -- each node's whole sub-recursion in one CTA, continuing the
+// node's id, interval and depth, so the tree is the one eig_solve would
+// build -- then U[:, off:off+m] <- U[:, off:off+m] Z for each node's
+// eigenvectors Z.  Eigenvalues land in wtmp[off..off+m).
+static void run_fused_tail(eig_handle_t h, SolveShared& S, double* wtmp, double* dU, int ldu,
+                           eig_solve_info_t& inf, int& status) {
+  const int cnt = (int)S.deferred.size();
+  const int n = S.n;
+  // the recursion's last launches (single-worker mode: on h's stream) must
+  // have finished before another stream reads the node blocks
+  CK(cudaStreamSynchronize(h->stream));
+  ensure_workers(h, 1);
+  eig_handle_t hw = h->workers[0];
+  CK(cudaSetDevice(hw->device));
+  std::vector<int> ns(cnt), lds(cnt, n), ldz(cnt), st(cnt);
+  std::vector<double*> A(cnt), W(cnt), Z(cnt);
+  std::vector<FusedProblem> roots(cnt);
+  std::vector<eig_solve_info_t> infos(cnt);
+  std::vector<size_t> zoff(cnt);
+  size_t zsize = 0;
+  int mmax = 1;
+  for (int i = 0; i < cnt; ++i) {
+    const Node& nd = S.deferred[i];
+    ns[i] = nd.m;
+    ldz[i] = nd.m;
+    A[i] = S.Acur + nd.off + (size_t)nd.off * n;
+    W[i] = wtmp + nd.off;
+    zoff[i] = zsize;
+    zsize += (size_t)nd.m * nd.m;
+    mmax = std::max(mmax, nd.m);
+    roots[i] = FusedProblem{};
+    roots[i].id = nd.id;
+    roots[i].lo = nd.lo;
+    roots[i].hi = nd.hi;
+    roots[i].depth = nd.depth;
+    roots[i].has_interval = 1;
+  }
+  const size_t fb = round_up(fused_run_bytes(hw, cnt, mmax, h->fused_cps, nullptr));
+  const size_t zb = round_up(sizeof(double) * zsize);
+  ensure_ws(hw, fb + zb + sizeof(double) * (size_t)n * mmax);
+  double* zbase = reinterpret_cast<double*>(hw->ws + fb);
+  double* tmp = reinterpret_cast<double*>(hw->ws + fb + zb);
+  for (int i = 0; i < cnt; ++i) Z[i] = zbase + zoff[i];
+  fused_run(hw, cnt, ns.data(), A.data(), lds.data(), W.data(), Z.data(), ldz.data(), S.p,
+            h->fused_nb, h->fused_cps, st.data(), infos.data(), nullptr, roots.data());
+  cudaStream_t s = hw->stream;
+  for (int i = 0; i < cnt; ++i) {
+    const Node& nd = S.deferred[i];
+    const int m = nd.m;
+    CK(gemm(s, false, false, n, m, m, 1.0, dU + (size_t)nd.off * ldu, ldu, Z[i], m, 0.0, tmp,
+            n));
+    CK(copy_matrix(s, n, m, tmp, n, dU + (size_t)nd.off * ldu, ldu));
+    const eig_solve_info_t& r = infos[i];
+    if (r.status != EIG_OK && status == EIG_OK) {
+      status = r.status;
+      h->err = r.status == EIG_NO_SPLIT ? "no split found for a node (fused tail)"
+                                        : "a node of the fused tail failed";
+    }
+    inf.nodes += r.nodes;
+    inf.splits += r.splits;
+    inf.max_depth = std::max(inf.max_depth, r.max_depth);
+    inf.total_iters += r.total_iters;
+    inf.failed_attempts += r.failed_attempts;
+    inf.leaves += r.leaves;
+    inf.flops += r.flops + 2.0 * n * (double)m * m;
+  }
+  CK(cudaStreamSynchronize(s));
+  CK(cudaSetDevice(h->device));
+}
+
 static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, double* dwr,
                       double* dwi, double* dU, int ldu, const eig_params_t& p,
                       eig_solve_info_t* info) {
@@ -1743,6 +1854,7 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
   S.Acur = w.Acur;
   S.dU = dU;
   S.p = p;
+  S.fused_tail = (sym && p.fused_tail > S.leaf) ? std::min(p.fused_tail, fused_max_n()) : 0;
   // split precision: FP32-level iterates, so the R-test and the split test
   // are read at that level; the FP64 refinement at the end restores accuracy
   S.pp = p;
@@ -1789,6 +1901,7 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
   if (status == EIG_OK) {
     std::vector<LeafDesc>& leaves = S.leaves;
     inf.leaves = (int)leaves.size();
+    if (!S.deferred.empty()) run_fused_tail(h, S, w.wtmp, dU, ldu, inf, status);
     NvtxRange nvtx_leaves("eig.leaves");
     CK(cudaMemcpyAsync(w.ddesc, leaves.data(), sizeof(LeafDesc) * leaves.size(),
                        cudaMemcpyHostToDevice, s));
@@ -1806,7 +1919,8 @@ static int solve_impl(eig_handle_t h, int kind, int n, double* dA, int lda, doub
       h->err = "a leaf solver did not converge";
     }
     if (refine && S.low_tier) {
-      inf.flops += refine_symmetric(h, n, dA, lda, dU, ldu, w.wtmp, w.G, w.AU, w.S, w.E, w.bits);
+      inf.flops += refine_symmetric(h, n, dA, lda, dU, ldu, w.wtmp, w.G, w.AU, w.S, w.E, w.bits,
+                                  w.rtcw, w.rtcerr);
     }
     if (sym) {
       // eigenvalues ascending with their vectors
@@ -1969,7 +2083,7 @@ static int pencil_impl(eig_handle_t h, int n, double* dA, int lda, double* dB, i
 
 static void check_params(eig_handle_t h, const eig_params_t& p) {
   if (p.maxit < 0 || p.leaf_size < 1 || p.v_draws < 1 || p.max_fail < 0 || p.split_tol < 0 ||
-      !valid_prec(p.prec)) {
+      p.fused_tail < 0 || !valid_prec(p.prec)) {
     h->err = "invalid eig_params_t";
     throw Fail{EIG_ERR_ARG};
   }
@@ -2021,6 +2135,7 @@ void eig_default_params(eig_params_t* p) {
   p->root_unit_circle = 1;
   p->workers = 8;
   p->graphs = 0;
+  p->fused_tail = 0;
 }
 
 int eig_create(eig_handle_t* out, int device, void* stream) {
@@ -2526,24 +2641,39 @@ int eig_solve_batched(eig_handle_t h, int kind, int count, const int* n, double*
 
 namespace {
 
-// One persistent launch of the fused batched solver over the problems
-// (largest first); fills status / infos; *ms (if non-null) gets the kernel's
-// CUDA-event time on the handle's stream.
-void fused_run(eig_handle_t h, int count, const int* n, double* const* dA, const int* lda,
-               double* const* dw, double* const* dU, const int* ldu, const eig_params_t& p,
-               int nb, int cps, int* status, eig_solve_info_t* infos, float* ms) {
-  cudaStream_t s = h->stream;
-  int mx = 1;
-  for (int i = 0; i < count; ++i) mx = std::max(mx, n[i]);
+// Launch shape of the fused batched solver on h's device: CTAs for `count`
+// problems (cps CTAs per SM, 0: automatic) and the workspace bytes fused_run
+// takes from the front of h's workspace for problems of at most mx rows.
+size_t fused_run_bytes(eig_handle_t h, int count, int mx, int cps, int* ctas_out) {
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
   const int maxc = fused_max_ctas_per_sm();
   const int c = cps > 0 ? std::min(cps, maxc) : std::min(2, maxc);
   const int ctas = std::max(1, std::min(count, sms * c));
+  if (ctas_out) *ctas_out = ctas;
   const size_t pb = round_up(sizeof(FusedProblem) * count);
   const size_t ob = round_up(sizeof(int) * count);
   const size_t rb = round_up(sizeof(FusedResult) * count);
-  const size_t total = pb + ob + rb + 256 + fused_workspace_bytes(mx, ctas);
+  return pb + ob + rb + 256 + fused_workspace_bytes(std::max(mx, 1), ctas);
+}
+
+// One persistent launch of the fused batched solver over the problems
+// (largest first); fills status / infos; *ms (if non-null) gets the kernel's
+// CUDA-event time on the handle's stream.  nodes (optional): per problem the
+// node id, interval and depth of the recursion it continues (id, lo, hi,
+// depth, has_interval of FusedProblem; the other fields are ignored).
+void fused_run(eig_handle_t h, int count, const int* n, double* const* dA, const int* lda,
+               double* const* dw, double* const* dU, const int* ldu, const eig_params_t& p,
+               int nb, int cps, int* status, eig_solve_info_t* infos, float* ms,
+               const FusedProblem* nodes) {
+  cudaStream_t s = h->stream;
+  int mx = 1;
+  for (int i = 0; i < count; ++i) mx = std::max(mx, n[i]);
+  int ctas = 1;
+  const size_t total = fused_run_bytes(h, count, mx, cps, &ctas);
+  const size_t pb = round_up(sizeof(FusedProblem) * count);
+  const size_t ob = round_up(sizeof(int) * count);
+  const size_t rb = round_up(sizeof(FusedResult) * count);
   ensure_ws(h, total);
   char* base = h->ws;
   FusedProblem* dprobs = reinterpret_cast<FusedProblem*>(base);
@@ -2554,7 +2684,16 @@ void fused_run(eig_handle_t h, int count, const int* n, double* const* dA, const
   char* pin = static_cast<char*>(pinned(h, std::max(pb + ob, rb) + 64));
   FusedProblem* hp = reinterpret_cast<FusedProblem*>(pin);
   int* ho = reinterpret_cast<int*>(pin + pb);
-  for (int i = 0; i < count; ++i) hp[i] = FusedProblem{n[i], lda[i], ldu[i], 0, dA[i], dw[i], dU[i]};
+  for (int i = 0; i < count; ++i) {
+    hp[i] = FusedProblem{n[i], lda[i], ldu[i], 0, dA[i], dw[i], dU[i], 1, 0.0, 0.0, 0, 0};
+    if (nodes) {
+      hp[i].id = nodes[i].id;
+      hp[i].lo = nodes[i].lo;
+      hp[i].hi = nodes[i].hi;
+      hp[i].depth = nodes[i].depth;
+      hp[i].has_interval = nodes[i].has_interval;
+    }
+  }
   std::vector<int> order(count);
   for (int i = 0; i < count; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
@@ -2896,7 +3035,7 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-size_t solve_footprint(int n, int kind, int prec) {
+size_t solve_footprint(int n, int kind, int prec, int fused_tail = 0, int leaf = 64) {
   if (kind == EIG_KIND_CPLANE) return cplane_footprint(n, prec);
   Arena a(nullptr);
   SolveMain w;
@@ -2904,7 +3043,17 @@ size_t solve_footprint(int n, int kind, int prec) {
   const bool pencil = kind == EIG_KIND_PENCIL;
   carve_main(a, n, kind == EIG_KIND_SYM && split_mode(prec), w, pencil);
   carve_node(a, n, n, prec, nw, pencil);
-  return a.used;
+  size_t bytes = a.used;
+  // fused tail (symmetric): at most n / (leaf + 1) nodes of at most T rows,
+  // one CTA each (at most 2 per SM of 152), their eigenvector blocks and the
+  // n x T product buffer
+  const int t = std::min(std::min(fused_tail, fused_max_n()), n);
+  if (kind == EIG_KIND_SYM && t > leaf) {
+    const int cnt = std::max(1, n / (std::max(leaf, 1) + 1));
+    bytes += fused_workspace_bytes(t, std::min(cnt, 2 * 152)) +
+             sizeof(double) * (2 * (size_t)n * t) + (size_t)cnt * 512 + 4096;
+  }
+  return bytes;
 }
 
 }  // namespace
@@ -3023,7 +3172,7 @@ int eig_server_create(eig_server_t* out, int device, int workers, double hbm_bud
 }
 
 static void enqueue(eig_server_s* S, Request* r, uint64_t* ticket) {
-  r->footprint = solve_footprint(r->n, r->kind, r->p.prec);
+  r->footprint = solve_footprint(r->n, r->kind, r->p.prec, r->p.fused_tail, r->p.leaf_size);
   std::memset(&r->info, 0, sizeof(r->info));
   {
     std::lock_guard<std::mutex> lock(S->mu);

@@ -703,8 +703,12 @@ __device__ SplitRes cta_split(int m, const double* Ap, const double* Bp, const d
   return out;
 }
 
-__device__ void solve_problem(int n, double* A, int lda, double* wout, double* U, int ldu,
-                              const FParams& p, Ws& w, FusedSmem& S, FusedResult& res) {
+__device__ void solve_problem(const FusedProblem& pr, const FParams& p, Ws& w, FusedSmem& S,
+                              FusedResult& res) {
+  const int n = pr.n, lda = pr.lda, ldu = pr.ldu;
+  double* A = pr.A;
+  double* wout = pr.w;
+  double* U = pr.U;
   const int tid = threadIdx.x;
   const int nb = p.nb;
   res = FusedResult{};
@@ -720,55 +724,61 @@ __device__ void solve_problem(int n, double* A, int lda, double* wout, double* U
     return;
   }
   cta_identity(n, n, 0, U, ldu);
-  // root interval: Gershgorin
-  double glo = INFINITY, ghi = -INFINITY;
-  for (int i = tid; i < n; i += FT) {
-    double r = 0.0;
-    for (int j = 0; j < n; ++j)
-      if (j != i) r += fabs(A[i + (size_t)j * lda]);
-    const double a = A[i + (size_t)i * lda];
-    glo = fmin(glo, a - r);
-    ghi = fmax(ghi, a + r);
-  }
-  double lo0 = -cta_max(-glo, S.c), hi0 = cta_max(ghi, S.c);
   const int leaf = max(1, min(JL_MAX, p.leaf));
-  if (n > leaf) {
-    // tighter root interval: [c - rho, c + rho] cut to Gershgorin, c = tr(A)/n,
-    // rho = 1.1 x the power-iteration estimate of ||A - cI||_2 (as eig_solve)
-    double tr = 0.0;
-    for (int i = tid; i < n; i += FT) tr += A[i + (size_t)i * lda];
-    const double c = cta_sum(tr, S.c) / n;
-    double* x = w.wv;
-    double* y = w.scores;
-    cta_gaussian(n, 1, p.seed, PURPOSE_POWER, ROOT, 0, y, n);
-    double ss = 0.0;
-    for (int i = tid; i < n; i += FT) ss = fma(y[i], y[i], ss);
-    double est = sqrt(cta_sum(ss, S.c));
-    for (int i = tid; i < n; i += FT) x[i] = est > 0.0 ? y[i] / est : 0.0;
-    __syncthreads();
-    for (int it = 0; it < POWER_STEPS; ++it) {
-      cta_gemm(false, false, n, 1, n, 1.0, A, lda, x, n, 0.0, y, n, S.u.la.g);
-      ss = 0.0;
-      for (int i = tid; i < n; i += FT) {
-        const double v = y[i] - c * x[i];
-        ss = fma(v, v, ss);
-      }
-      est = sqrt(cta_sum(ss, S.c));
-      for (int i = tid; i < n; i += FT) {
-        const double v = y[i] - c * x[i];
-        x[i] = est > 0.0 ? v / est : 0.0;
-      }
-      __syncthreads();
+  double lo0 = pr.lo, hi0 = pr.hi;
+  if (!pr.has_interval) {
+    // root interval: Gershgorin
+    double glo = INFINITY, ghi = -INFINITY;
+    for (int i = tid; i < n; i += FT) {
+      double r = 0.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) r += fabs(A[i + (size_t)j * lda]);
+      const double a = A[i + (size_t)i * lda];
+      glo = fmin(glo, a - r);
+      ghi = fmax(ghi, a + r);
     }
-    const double rho = 1.1 * est;
-    const double lo1 = fmax(lo0, c - rho), hi1 = fmin(hi0, c + rho);
-    if (lo1 < hi1) {
-      lo0 = lo1;
-      hi0 = hi1;
+    lo0 = -cta_max(-glo, S.c);
+    hi0 = cta_max(ghi, S.c);
+    if (n > leaf) {
+      // tighter root interval: [c - rho, c + rho] cut to Gershgorin, c = tr(A)/n,
+      // rho = 1.1 x the power-iteration estimate of ||A - cI||_2 (as eig_solve)
+      double tr = 0.0;
+      for (int i = tid; i < n; i += FT) tr += A[i + (size_t)i * lda];
+      const double c = cta_sum(tr, S.c) / n;
+      double* x = w.wv;
+      double* y = w.scores;
+      cta_gaussian(n, 1, p.seed, PURPOSE_POWER, ROOT, 0, y, n);
+      double ss = 0.0;
+      for (int i = tid; i < n; i += FT) ss = fma(y[i], y[i], ss);
+      double est = sqrt(cta_sum(ss, S.c));
+      for (int i = tid; i < n; i += FT) x[i] = est > 0.0 ? y[i] / est : 0.0;
+      __syncthreads();
+      for (int it = 0; it < POWER_STEPS; ++it) {
+        cta_gemm(false, false, n, 1, n, 1.0, A, lda, x, n, 0.0, y, n, S.u.la.g);
+        ss = 0.0;
+        for (int i = tid; i < n; i += FT) {
+          const double v = y[i] - c * x[i];
+          ss = fma(v, v, ss);
+        }
+        est = sqrt(cta_sum(ss, S.c));
+        for (int i = tid; i < n; i += FT) {
+          const double v = y[i] - c * x[i];
+          x[i] = est > 0.0 ? v / est : 0.0;
+        }
+        __syncthreads();
+      }
+      const double rho = 1.1 * est;
+      const double lo1 = fmax(lo0, c - rho), hi1 = fmin(hi0, c + rho);
+      if (lo1 < hi1) {
+        lo0 = lo1;
+        hi0 = hi1;
+      }
     }
   }
   int nstack = 0, nleaves = 0;
-  if (tid == 0) w.stack[0] = FNode{0, n, 0, 0, lo0, hi0, ROOT};
+  if (tid == 0)
+    w.stack[0] = pr.has_interval ? FNode{0, n, pr.depth, 0, lo0, hi0, pr.id}
+                                 : FNode{0, n, 0, 0, lo0, hi0, ROOT};
   nstack = 1;
   __syncthreads();
   while (nstack > 0) {
@@ -893,7 +903,7 @@ fused_batched_kernel(int count, const FusedProblem* __restrict__ probs,
     const int i = order[q];
     const FusedProblem pr = probs[i];
     FusedResult r;
-    solve_problem(pr.n, pr.A, pr.lda, pr.w, pr.U, pr.ldu, p, w, S, r);
+    solve_problem(pr, p, w, S, r);
     if (threadIdx.x == 0) results[i] = r;
     __syncthreads();
   }

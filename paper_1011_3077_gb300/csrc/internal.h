@@ -216,6 +216,13 @@ struct FusedProblem {
   double* A;   // in: symmetric A; out: the block-diagonal working matrix (as eig_solve)
   double* w;   // out: eigenvalues ascending
   double* U;   // out: eigenvectors
+  // has_interval != 0: the problem is a node of a larger recursion -- its
+  // Philox node id, eigenvalue interval [lo, hi] and depth continue that
+  // recursion; else it is a root (id 1, interval from Gershgorin and the
+  // power-iteration estimate, depth 0)
+  uint64_t id;
+  double lo, hi;
+  int depth, has_interval;
 };
 struct FusedResult {
   int status, nodes, splits, max_depth, total_iters, failed_attempts, leaves, pad;

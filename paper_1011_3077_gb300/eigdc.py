@@ -61,7 +61,8 @@ class Params(ctypes.Structure):
                 ("prec", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("max_fail", ctypes.c_int), ("nb", ctypes.c_int),
                 ("v_draws", ctypes.c_int), ("root_unit_circle", ctypes.c_int),
-                ("workers", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("workers", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("fused_tail", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):

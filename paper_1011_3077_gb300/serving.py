@@ -141,7 +141,7 @@ def trace(count, rate=200.0, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), seed=5):
 
 def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8,
         budget_gb=120.0, prec=eigdc.EIG_FP64_TC, seed=5, device="cuda", verbose=False,
-        details=False, prec_sym=None, host_io=False, sym_split_max_n=1024):
+        details=False, prec_sym=None, host_io=False, sym_split_max_n=1024, fused_tail=0):
     """Serve one seeded trace; returns throughput, latency percentiles and the
     accuracy of every result.
 
@@ -154,7 +154,9 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
     inputs start in pinned host memory; each request's input is copied to the
     device when it arrives and its outputs are read back when it completes,
     both inside the timed region (the end-to-end form); the byte counts are
-    returned.  The makespan is the CUDA-event time from the first arrival to
+    returned.  fused_tail: the symmetric requests' nodes of at most this many
+    rows finish in one launch of the fused batched solver (eig_params_t).
+    The makespan is the CUDA-event time from the first arrival to
     the last completion, with the device synchronised on both sides."""
     import torch
     arrivals, kinds, sizes = trace(count, rate, nmin, nmax, mix, seed)
@@ -186,8 +188,11 @@ def run(rate=200.0, count=40, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=8
         reqs.append((kind, n, dA, out, ref))
     torch.cuda.synchronize()
     srv = eigdc.Server(0, workers, budget_gb)
-    params = eigdc.default_params(seed=seed, prec=prec)
-    params_sym = eigdc.default_params(seed=seed, prec=prec if prec_sym is None else prec_sym)
+    # fused_tail applies to the symmetric requests only (their small nodes
+    # finish in one launch of the fused batched solver)
+    params = eigdc.default_params(seed=seed, prec=prec, fused_tail=fused_tail)
+    params_sym = eigdc.default_params(seed=seed, prec=prec if prec_sym is None else prec_sym,
+                                      fused_tail=fused_tail)
     copy_stream = torch.cuda.Stream(device=device)
     h2d = d2h = 0
     tickets = []

@@ -7,7 +7,9 @@ and meet the FP64 targets of the whole-solve parity tests: eigenvalues within
 1e-12 ||A|| of the oracle's and within 1e-10 ||A|| of the prescribed spectrum,
 ||U^T U - I||_2 <= 1e-12, ||A - U L U^T||_F / ||A||_F <= 1e-12.  Against the
 host-driven eig_solve_batched the trees are equal and the eigenvalues agree
-to 1e-12 ||A|| (the two paths block their products differently).
+to 1e-12 ||A|| (the two paths block their products differently).  The same
+kernel finishes the small nodes of eig_solve (fused_tail), continuing each
+node's id, interval and depth: the tree must not change.
 """
 import numpy as np
 import pytest
@@ -117,3 +119,41 @@ def test_fused_autotune_then_solve(E):
     assert rc == eigdc.EIG_OK and all(s == 0 for s in st)
     for A, lam, w, U in zip(mats, lams, ws, Us):
         _targets(A, w, U, lam)
+
+
+@pytest.mark.parametrize("n,tail,prec", [(300, 128, 0), (700, 200, 0), (700, 160, 2)])
+def test_fused_tail_takes_the_same_tree(E, n, tail, prec):
+    """eig_solve with fused_tail: the nodes of at most `tail` rows finish in one
+    launch of the fused solver, continuing their node ids and intervals.  The
+    recursion must be the one without the tail (and, at n = 300, the
+    oracle's): equal split, node and failed-attempt counts and depth;
+    eigenvalues within 1e-12 ||A|| of the tail-free solve; FP64 targets."""
+    eigdc, h, torch = E
+    A, lam = workloads.symmetric_semicircle(n, seed=n + tail)
+    out = {}
+    for t in (0, tail):
+        p = eigdc.default_params(seed=4, prec=prec, fused_tail=t)
+        rc, w, U, info = eigdc.solve_symmetric(h, A, p)
+        assert rc == eigdc.EIG_OK, h.last_error()
+        _targets(A, w, U, lam)
+        out[t] = (w, info)
+    (w0, i0), (w1, i1) = out[0], out[tail]
+    key = lambda i: (i.splits, i.nodes, i.failed_attempts, i.max_depth, i.leaves)
+    assert key(i1) == key(i0)
+    assert np.max(np.abs(w1 - w0)) <= 1e-12 * np.max(np.abs(lam))
+    if n <= 300:
+        wo, Uo, io = oeig_sym(A, seed=4)
+        assert (i1.splits, i1.nodes, i1.failed_attempts) == (io.splits, io.nodes,
+                                                             io.failed_attempts)
+        assert np.max(np.abs(w1 - wo)) <= 1e-12 * np.max(np.abs(lam))
+
+
+def test_fused_tail_argument_check(E):
+    eigdc, h, torch = E
+    A, lam = workloads.symmetric_uniform(100, seed=1)
+    rc, w, U, info = eigdc.solve_symmetric(h, A, eigdc.default_params(fused_tail=-1))
+    assert rc == eigdc.EIG_ERR_ARG
+    # a tail at or below the leaf size has no node to take: the plain solve
+    rc, w, U, info = eigdc.solve_symmetric(h, A, eigdc.default_params(fused_tail=64))
+    assert rc == eigdc.EIG_OK
+    _targets(A, w, U, lam)
