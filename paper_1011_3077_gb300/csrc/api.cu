@@ -268,8 +268,9 @@ static cudaError_t split_gemm(cudaStream_t s, int prec, bool ta, bool tb, int m,
 // Products that stay on the FP64 DFMA kernel in EIG_FP64_TC mode: the digit
 // split costs a pass over both operands and three launches, and a 128 x 48
 // tile with nine digit planes per operand needs every dimension of a few
-// hundred to pay (measured: 5.8x DFMA at 4096^3, 3.1x at 1024^3, slower on the
-// rank-32 reflector products 2048 x 32 x 4096 and 4096 x 2048 x 32).
+// hundred to pay (measured: 14.9x DFMA at 4096^3 and 12.7x at 2048^3; in its
+// first form 3.1x at 1024^3, and slower on the rank-32 reflector products
+// 2048 x 32 x 4096 and 4096 x 2048 x 32).
 static bool tcx_worth(int m, int n, int k) {
   return m >= 128 && n >= 128 && k >= 128 && (double)m * n * k >= 33554432.0;
 }

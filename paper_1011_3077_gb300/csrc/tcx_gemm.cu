@@ -17,8 +17,9 @@
 //     accumulator) in its own TMEM columns.  Every partial sum is an integer
 //     below 9 * 1792 * 32^2 < 2^24 as long as a chunk spans at most 1792 of K,
 //     so the FP32 accumulation is exact; after each chunk four drain warps
-//     read the ten accumulators (tcgen05.ld) and add them, scaled by
-//     2^(-6 l), to FP64 registers.  (The balanced digits halve the digit
+//     read the ten accumulators (tcgen05.ld), combine levels 0..4 and 5..9
+//     exactly in int64 and add each group, scaled by its power of two, to
+//     FP64 registers.  (The balanced digits halve the digit
 //     bound, so a chunk is four times longer than with digits in [0, 64]:
 //     the drain's FP64 work, on a pipe about 1/1800 of the tensor rate,
 //     shrinks fourfold.)
@@ -251,7 +252,6 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   } else if (warp == 1) {
     if (lane == 0) {
       // ---- MMA issuer: level l = i + j into TMEM columns l * TX_BN
-      constexpr uint32_t idesc = idesc_bf16_f32(TX_BM, TX_BN);
       uint32_t u = 0;
       bool ok = true;
       for (int kt = 0; kt < nk && ok; ++kt) {
@@ -284,18 +284,31 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             break;
           }
           tc_fence_after();
+          // A digit i against B digits j = j0..j1 in one MMA: the B planes
+          // lie back to back in shared memory (48 rows each, 1024-byte
+          // aligned), so rows 48 (j - j0) .. of an N = 48 (j1 - j0 + 1) operand
+          // are digit j, and with the accumulator at TMEM column 48 (i + j0)
+          // each digit's product lands in its level's columns 48 (i + j).
+          // Runs are cut where the first-write flag changes (the first write
+          // of level l in a chunk is the pair i = max(0, l - (DIG - 1))) and
+          // at 5 digits (N <= 256).
           const int jmax = std::min(TX_DIGITS - 1, TX_LEVELS - 1 - i);
-          for (int j = 0; j <= jmax; ++j) {
-            const int l = i + j;
-            // the first write of level l in a chunk: i = max(0, l - 8), kk = 0
-            const int ifirst = l > TX_DIGITS - 1 ? l - (TX_DIGITS - 1) : 0;
+          for (int j0 = 0; j0 <= jmax;) {
+            const bool f0 = (i == 0) || (j0 == TX_DIGITS - 1);
+            int j1 = j0;
+            while (j1 + 1 <= jmax && j1 + 1 - j0 < 5 &&
+                   ((i == 0) || (j1 + 1 == TX_DIGITS - 1)) == f0)
+              ++j1;
+            const int cnt = j1 - j0 + 1;
+            const uint32_t idesc = idesc_bf16_f32(TX_BM, TX_BN * cnt);
 #pragma unroll
             for (int kk = 0; kk < TX_BK / 16; ++kk) {
               const uint64_t ad = sw128_desc(smem_u32(S.a[sa]) + kk * 32);
-              const uint64_t bd = sw128_desc(smem_u32(S.b[sb][j]) + kk * 32);
-              const uint32_t acc = (kt == first && i == ifirst && kk == 0) ? 0u : 1u;
-              mma_bf16(tmem + (uint32_t)(l * TX_BN), ad, bd, idesc, acc);
+              const uint64_t bd = sw128_desc(smem_u32(S.b[sb][j0]) + kk * 32);
+              const uint32_t acc = (f0 && kt == first && kk == 0) ? 0u : 1u;
+              mma_bf16(tmem + (uint32_t)((i + j0) * TX_BN), ad, bd, idesc, acc);
             }
+            j0 = j1 + 1;
           }
           mma_commit(&S.aempty[sa]);
         }
@@ -320,18 +333,32 @@ tcx_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         break;
       }
       tc_fence_after();
-      double w = 1.0;   // 2^(-6 l)
+      // Each level's chunk sum is an integer below 2^24 in magnitude.  Levels
+      // g0..g1-1 (at most five) are combined exactly in int64 as
+      // sum_l L_l 2^(6 (g1 - 1 - l)) (< 2^49), so a group costs one
+      // int64 -> FP64 conversion and one FMA per element on the FP64 pipe
+      // instead of two per level.
+#pragma unroll
+      for (int t = 0; t < TX_BN / 16; ++t) {
+#pragma unroll
+        for (int g0 = 0; g0 < TX_LEVELS; g0 += 5) {
+          const int g1 = g0 + 5 < TX_LEVELS ? g0 + 5 : TX_LEVELS;
+          long long sum[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sum[j] = 0;
 #pragma unroll 1
-      for (int l = 0; l < TX_LEVELS; ++l) {
-        // 16-column loads: every start column (l * 48 + 16 t) is 16-aligned
+          for (int l = g0; l < g1; ++l) {
+            // 16-column loads: every start column (l * 48 + 16 t) is 16-aligned
+            float v[16];
+            tmem_ld16(tl + (uint32_t)(l * TX_BN + 16 * t), v);
+            const long long wgt = 1LL << (6 * (g1 - 1 - l));
 #pragma unroll
-        for (int t = 0; t < TX_BN / 16; ++t) {
-          float v[16];
-          tmem_ld16(tl + (uint32_t)(l * TX_BN + 16 * t), v);
+            for (int j = 0; j < 16; ++j) sum[j] += (long long)__float2int_rn(v[j]) * wgt;
+          }
+          const double sc = ldexp(1.0, -6 * (g1 - 1));   // 2^(-6 (g1 - 1)), exact
 #pragma unroll
-          for (int j = 0; j < 16; ++j) acc[16 * t + j] = fma((double)v[j], w, acc[16 * t + j]);
+          for (int j = 0; j < 16; ++j) acc[16 * t + j] = fma((double)sum[j], sc, acc[16 * t + j]);
         }
-        w *= 0x1p-6;
       }
       tc_fence_before();
       __syncwarp();
