@@ -9,10 +9,11 @@ generalized Schur forms of regular pencils (B = I + 0.1 G / sqrt(n), A =
 (Q T Q^T) B) -- with n log-uniform in [64, 4096], served by the library's
 request server under a 120 GB HBM budget.  One step = one completed request
 (every row of the path inside: region map, IRS squarings, GRURV splitter,
-similarity, split test, recursion, leaves, assembly).  Symmetric requests run
-in the unbiased FP32-level split form with FP64 refinement, the others in the
-FP64-accurate tensor-core form; `plain_fp64` serves the same trace with every
-contraction on the FP64 pipe.  Other workloads (--workload): schur, sym,
+similarity, split test, recursion, leaves, assembly).  Symmetric requests up
+to n = 1024 run in the split-precision form (each node at the error-free
+split tier its eigenvalue interval can resolve, FP64 refinement after an
+FP32-level split), the others in the FP64-accurate tensor-core form;
+`plain_fp64` serves the same trace with every contraction on the FP64 pipe.  Other workloads (--workload): schur, sym,
 batched (one persistent fused launch per batch), svd, cplane, step (one
 divide step at the root of the symmetric semicircle matrix), gemm (isolated
 products of each contraction form).
