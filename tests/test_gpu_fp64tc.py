@@ -184,3 +184,28 @@ def test_fp64tc_two_level_irs_iterates_match_oracle(E, n, sq):
     dR = torch.zeros((n, n), dtype=torch.float64, device="cuda")
     eigdc.eig_last_R(h, n, dR, n)
     assert np.max(np.abs(eigdc.to_host(dR) - res.Rs[-1])) <= 1e-11 * scale
+
+
+def test_irs_floor_stop_in_fp64tc(E):
+    """R-test with tau far below the rounding floor of the ratio (1e-18):
+    plain FP64 keeps the oracle's test and runs into maxit (j = 0..maxit), the
+    FP64-accurate tensor-core form also stops once the ratio is <= 1e-10 and
+    falls less than 4x over a squaring (the floor), well before maxit."""
+    eigdc, h, torch = E
+    n = 300
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((n, n))
+    B = rng.standard_normal((n, n)) + 2 * np.eye(n)
+    reg = eigdc.Region(0, 0.0, 1.0)
+    out = {}
+    for prec in (eigdc.EIG_FP64, eigdc.EIG_FP64_TC):
+        dA, dB = eigdc.to_device(A), eigdc.to_device(B)
+        p = eigdc.default_params(tau=1e-18, maxit=40, prec=prec)
+        rc, info = eigdc.eig_divide_step(h, n, dA, n, dB, n, reg, p)
+        out[prec] = (rc, info, eigdc.to_host(dA))
+    rc0, i0, A0 = out[eigdc.EIG_FP64]
+    rc1, i1, A1 = out[eigdc.EIG_FP64_TC]
+    assert rc0 == eigdc.EIG_NO_CONVERGENCE and i0.iters == 41 and i0.converged == 0
+    assert rc1 == eigdc.EIG_OK and i1.converged == 1 and i1.iters < 41
+    assert 0.0 <= i1.last_ratio <= 1e-10
+    assert np.all(np.isfinite(A1))
