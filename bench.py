@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--prec-sym", type=int, default=3, choices=[0, 1, 2, 3],
                     help="serve: precision of the symmetric requests (3: unbiased FP32-level "
                          "split with FP64 refinement)")
+    ap.add_argument("--rate", type=float, default=200.0,
+                    help="serve: mean arrival rate of the Poisson trace (requests/s); the "
+                         "configuration's 200/s saturates one GPU")
     ap.add_argument("--fused-tail", type=int, default=0,
                     help="symmetric solves (sym, serve): nodes of at most this many rows finish "
                          "in one launch of the fused batched solver (0: off)")
@@ -194,7 +197,7 @@ def reference_arm_serve(args):
     the oracle's sample solves of the three request kinds, and the trace's
     time is their n^3-scaled sum (the oracle serves one request at a time)."""
     from paper_1011_3077_gb300 import serving
-    arr, kinds, sizes = serving.trace(args.steps, SERVE_RATE, 64, 4096, (0.5, 0.3, 0.2), 5)
+    arr, kinds, sizes = serving.trace(args.steps, args.rate, 64, 4096, (0.5, 0.3, 0.2), 5)
     vals, samples, secs = [], [], []
     for i in range(args.warmup + args.steps):
         v, sample, t = serve_oracle_estimate(arr, kinds, sizes)
@@ -799,7 +802,7 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     seed = 5 + 101 * rank
-    kw = dict(rate=SERVE_RATE, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=args.workers,
+    kw = dict(rate=args.rate, nmin=64, nmax=4096, mix=(0.5, 0.3, 0.2), workers=args.workers,
               budget_gb=120.0, device=dev, fused_tail=args.fused_tail)
     prec, prec_sym = eigdc.EIG_FP64_TC, args.prec_sym
     if args.warmup > 0:
@@ -873,7 +876,7 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
                                                              "work": fam[f][2]} for f in fam}})
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        arr, kinds, sizes = serving.trace(args.steps, SERVE_RATE, 64, 4096, (0.5, 0.3, 0.2), seed)
+        arr, kinds, sizes = serving.trace(args.steps, args.rate, 64, 4096, (0.5, 0.3, 0.2), seed)
         v, sample, _ = serve_oracle_estimate(arr, kinds, sizes)
         cpu = {"kind": "oracle", "value": v, "unit": "solves/s", "cores": os.cpu_count(),
                "sample": sample}
@@ -887,7 +890,7 @@ def serve_arm(args, torch, eigdc, h, dev, stream, world):
                                        "20% generalized Schur of regular pencils, n log-uniform in "
                                        "[64, 4096], 120 GB HBM admission budget, continuous "
                                        "batching; one step = one completed request",
-                           "requests": args.steps, "rate_per_s": SERVE_RATE,
+                           "requests": args.steps, "rate_per_s": args.rate,
                            "nonsym_coupling": "strict upper N(0, (0.1/sqrt(n))^2): the "
                                               "reduced-coupling reading of the nonsymmetric "
                                               "construction (at 1/sqrt(n) the pseudospectra "
