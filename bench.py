@@ -469,7 +469,9 @@ def cplane_arm(args, torch, eigdc, h, dev, stream, world):
     dT = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     dU = torch.zeros((n, n), dtype=torch.complex128, device=dev)
     dw = torch.zeros(n, dtype=torch.complex128, device=dev)
-    params = eigdc.default_params(seed=0, leaf_size=64)
+    # the complex path has the FP64 and the FP64-accurate tensor-core forms
+    prec = args.prec if args.prec in (0, 2) else 2
+    params = eigdc.default_params(seed=0, leaf_size=64, prec=prec)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -521,7 +523,8 @@ def cplane_arm(args, torch, eigdc, h, dev, stream, world):
             "config": {"workload": "complex Schur form by lines at random angles (Sec. 3.3), "
                                    "real normal matrix with pairs a +- ib, a, b ~ U[-1.5, 1.5], "
                                    "n=%d, 64x64 complex leaves" % n,
-                       "n": n, "l2": "flushed between timed steps (512 MiB write)"},
+                       "n": n, "precision": PREC_NAMES[prec],
+                       "l2": "flushed between timed steps (512 MiB write)"},
             "splits": info.splits, "nodes": info.nodes, "squarings": info.total_iters,
             "backward_error": bwd, "orthogonality_frobenius": orth,
             "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": None,
